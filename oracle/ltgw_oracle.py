@@ -1,0 +1,310 @@
+"""CPU FP64 oracle for the LT-GW G0W0 hot path (Toelle, Niemeyer, Neugebauer,
+"Accelerating Analytic-Continuation GW Calculations with a Laplace
+Transformation and Natural Auxiliary Functions", arXiv:2307.04508).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain reference that the
+CUDA path is checked against.  Only the tests, the smoke check and the CPU
+baseline leg of the benchmark may import it; the product never does.  It
+shares no code with the CUDA path.
+
+Everything is float64 and follows the paper's statement of the problem in the
+paper's order:
+
+  frozen-core slice (Sec. 3)  ->  NAF metric K (Eq. nafeq, ov block only)
+  ->  eigenvectors of K above the threshold (NAF eigen-equation)
+  ->  R~ = R U (Eq. naftrafo)
+  ->  Pi(i w) directly (Eq. Pi) or through the Laplace moments M^m (Eq. LT and
+      the M^m factorisation that follows it)
+  ->  W^c_nm(i w) = sum_PQ R^P_nm {[1 - Pi]^-1 - 1}_PQ R^Q_nm
+      (Eq. ScreenedCoulombOrbital)
+  ->  Sigma^c_n(i w) by the modified Gauss-Legendre quadrature of
+      Eq. CorrelationSelfEnergy
+  ->  N-point Pade continued fraction (Vidberg & Serene, J. Low Temp. Phys. 29,
+      179 (1977), appendix)  ->  quasi-particle equation solved by Newton.
+
+Readings of points the paper leaves open (each one fixed once):
+  * spin: closed-shell spatial orbitals, Pi = -2 s sum_ia ..., s = 2 by
+    default (s = 1 is the literal spin-orbital form of Eq. Pi);
+  * the NAF metric sums occupied-virtual pairs of active occupied orbitals
+    only, without the closed-shell factor 2, and keeps eigenvalues strictly
+    greater than the threshold; a negative threshold switches NAF off;
+  * frozen-core orbitals leave Pi, K and the m-sum of Sigma, and cannot be
+    targets;
+  * eps_F = (eps_HOMO + eps_LUMO) / 2;
+  * Sigma is evaluated on all N_omega Gauss-Legendre nodes; the Pade fraction
+    passes through every second node (indices 0, 2, 4, ...; ceil(N_omega/2)
+    points) in ascending order.  The paper, too, continues from a smaller
+    frequency set (70 points) than it integrates on (128); through all nodes
+    the fraction amplifies 1e-15 relative noise in Sigma to ~1e-8 Ha in the
+    quasi-particle energy, through every second node to ~1e-13 Ha;
+  * eta = 0 (the real quasi-particle equation);
+  * Newton from eps_n, stop when |dE| < 1e-12 Ha, at most 100 steps.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "gl_grid", "fermi_level", "active_ov", "naf_metric", "naf_basis", "naf_project",
+    "pair_gaps", "polarizability_direct", "laplace_moments", "polarizability_lt",
+    "screened_interaction", "w_nm", "sigma_iw", "pade_coefficients", "pade_eval",
+    "qp_newton", "solve", "sinc_laplace_grid", "pade_nodes",
+]
+
+
+# ----------------------------------------------------------------------------
+# Grids
+# ----------------------------------------------------------------------------
+def gl_grid(n_omega: int, omega0: float = 0.5):
+    """Modified Gauss-Legendre rule on [0, inf) (Sec. 2, after Eq.
+    CorrelationSelfEnergy): Legendre nodes x in (-1, 1) mapped by
+    omega = omega0 (1 + x) / (1 - x), weight w * 2 omega0 / (1 - x)^2.
+    Nodes are returned in ascending omega."""
+    x, w = np.polynomial.legendre.leggauss(n_omega)
+    omega = omega0 * (1.0 + x) / (1.0 - x)
+    weight = w * 2.0 * omega0 / (1.0 - x) ** 2
+    order = np.argsort(omega)
+    return omega[order], weight[order]
+
+
+def sinc_laplace_grid(n_tau: int, t_lo: float, t_hi: float):
+    """A Laplace quadrature for 1/X = int_0^inf exp(-X tau) d tau (Eq. LT):
+    substitute tau = e^t and apply the trapezoid rule with n_tau equidistant
+    nodes on [t_lo, t_hi].  Returns (x_m, w_m) with 1/X ~ sum w_m exp(-X x_m).
+    Not minimax; any rule of this form is a valid Laplace grid for the
+    LT-mode checks, which feed the same grid to both sides."""
+    t = np.linspace(t_lo, t_hi, n_tau)
+    h = t[1] - t[0] if n_tau > 1 else 1.0
+    x = np.exp(t)
+    w = h * np.exp(t)
+    return x, w
+
+
+# ----------------------------------------------------------------------------
+# Frozen core and pair data
+# ----------------------------------------------------------------------------
+def fermi_level(eps: np.ndarray, n_occ: int) -> float:
+    """eps_F, read as the midpoint of the HOMO-LUMO gap."""
+    return 0.5 * (eps[n_occ - 1] + eps[n_occ])
+
+
+def active_ov(B_ov: np.ndarray, n_occ: int, n_virt: int, n_frozen: int) -> np.ndarray:
+    """Frozen-core slice (Sec. 3): drop the pairs i*n_virt+a with i < n_frozen."""
+    assert B_ov.shape[1] == n_occ * n_virt
+    return B_ov[:, n_frozen * n_virt:]
+
+
+def pair_gaps(eps: np.ndarray, n_occ: int, n_virt: int, n_frozen: int) -> np.ndarray:
+    """Delta_ia = eps_a - eps_i for active i (outer) and all a (inner)."""
+    occ = eps[n_frozen:n_occ]
+    virt = eps[n_occ:n_occ + n_virt]
+    return (virt[None, :] - occ[:, None]).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Natural auxiliary functions (Sec. 2, Eqs. nafeq and naftrafo)
+# ----------------------------------------------------------------------------
+def naf_metric(B_act: np.ndarray) -> np.ndarray:
+    """K_PQ = sum_{ia} R^P_ia R^Q_ia over active occupied-virtual pairs."""
+    return B_act @ B_act.T
+
+
+def naf_basis(K: np.ndarray, thresh: float):
+    """Diagonalise K and keep the eigenvectors whose eigenvalue exceeds the
+    threshold; they form the columns of U.  Returns (U, kept eigenvalues,
+    all eigenvalues ascending)."""
+    lam, V = np.linalg.eigh(K)
+    keep = lam > thresh
+    return V[:, keep], lam[keep], lam
+
+
+def naf_project(B: np.ndarray, U: np.ndarray) -> np.ndarray:
+    """R^{P~}_nm = sum_P R^P_nm U_{P P~}: here B is [P][nm], output [P~][nm]."""
+    return U.T @ B
+
+
+# ----------------------------------------------------------------------------
+# Polarisability (Eq. Pi and its Laplace form)
+# ----------------------------------------------------------------------------
+def polarizability_direct(Bt: np.ndarray, delta: np.ndarray, omegas: np.ndarray, spin: int = 2) -> np.ndarray:
+    """Pi_PQ(i w) = -2 s sum_ia R^P_ia Delta / (w^2 + Delta^2) R^Q_ia for every w."""
+    out = np.empty((len(omegas), Bt.shape[0], Bt.shape[0]))
+    for j, w in enumerate(omegas):
+        d = delta / (w * w + delta * delta)
+        out[j] = -2.0 * spin * ((Bt * d[None, :]) @ Bt.T)
+    return out
+
+
+def laplace_moments(Bt: np.ndarray, delta: np.ndarray, x: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """M^m_PQ = sum_ia R^P_ia w_m Delta_ia exp(-Delta_ia^2 x_m) R^Q_ia."""
+    out = np.empty((len(x), Bt.shape[0], Bt.shape[0]))
+    for m in range(len(x)):
+        c = w[m] * delta * np.exp(-delta * delta * x[m])
+        out[m] = (Bt * c[None, :]) @ Bt.T
+    return out
+
+
+def polarizability_lt(M: np.ndarray, omegas: np.ndarray, x: np.ndarray, spin: int = 2) -> np.ndarray:
+    """Pi_PQ(i w) ~ -2 s sum_m M^m_PQ exp(-w^2 x_m)."""
+    out = np.empty((len(omegas),) + M.shape[1:])
+    for j, om in enumerate(omegas):
+        e = np.exp(-om * om * x)
+        out[j] = -2.0 * spin * np.tensordot(e, M, axes=(0, 0))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Screened interaction (Eq. ScreenedCoulombOrbital)
+# ----------------------------------------------------------------------------
+def screened_interaction(Pi: np.ndarray) -> np.ndarray:
+    """C(i w) = [1 - Pi(i w)]^-1 - 1 through a Cholesky factorisation of the
+    symmetric positive definite 1 - Pi (Pi is negative semidefinite)."""
+    n = Pi.shape[-1]
+    eye = np.eye(n)
+    out = np.empty_like(Pi)
+    for j in range(Pi.shape[0]):
+        A = eye - Pi[j]
+        L = np.linalg.cholesky(A)
+        Linv = np.linalg.solve(L, eye)
+        out[j] = Linv.T @ Linv - eye
+    return out
+
+
+def w_nm(C: np.ndarray, Bt_tgt: np.ndarray) -> np.ndarray:
+    """W^c_nm(i w_j) = sum_PQ R^P_nm C_j,PQ R^Q_nm for each target n (first
+    index of Bt_tgt [T][P][m]) and every orbital m; returns [T][m][j]."""
+    T, N, M = Bt_tgt.shape
+    out = np.empty((T, M, C.shape[0]))
+    for t in range(T):
+        b = Bt_tgt[t]
+        for j in range(C.shape[0]):
+            out[t, :, j] = np.einsum("pm,pm->m", b, C[j] @ b)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Self-energy on the imaginary axis (Eq. CorrelationSelfEnergy)
+# ----------------------------------------------------------------------------
+def sigma_iw(W: np.ndarray, eps_m: np.ndarray, eps_F: float, omegas: np.ndarray,
+             weights: np.ndarray, eval_at=None) -> np.ndarray:
+    """Sigma^c_n(i w_l) = -(1/pi) sum_m sum_j g_j z/(z^2 + w_j^2) W_nm(i w_j),
+    z = i w_l + eps_F - eps_m, with the modified Gauss-Legendre nodes w_j and
+    weights g_j.  W is [T][m][j]; the evaluation frequencies w_l default to the
+    nodes themselves.  Returns complex [T][l]."""
+    T = W.shape[0]
+    eval_at = omegas if eval_at is None else np.asarray(eval_at, dtype=np.float64)
+    out = np.empty((T, len(eval_at)), dtype=np.complex128)
+    for l, wl in enumerate(eval_at):
+        z = 1j * wl + eps_F - eps_m                                # [m]
+        kern = z[:, None] / (z[:, None] ** 2 + omegas[None, :] ** 2)  # [m][j]
+        kern = kern * weights[None, :]
+        out[:, l] = -np.einsum("tmj,mj->t", W, kern) / np.pi
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Analytic continuation: N-point Pade (Vidberg & Serene, appendix)
+# ----------------------------------------------------------------------------
+def pade_coefficients(z: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Continued-fraction coefficients a_p = g_p(z_p) with g_1(z_i) = u_i and
+    g_p(z) = [g_{p-1}(z_{p-1}) - g_{p-1}(z)] / [(z - z_{p-1}) g_{p-1}(z)]."""
+    n = len(z)
+    g = np.array(u, dtype=np.complex128)   # g_{p}(z_i) for i >= p, updated in place
+    a = np.empty(n, dtype=np.complex128)
+    a[0] = g[0]
+    for p in range(1, n):
+        g[p:] = (g[p - 1] - g[p:]) / ((z[p:] - z[p - 1]) * g[p:])
+        a[p] = g[p]
+    return a
+
+
+def pade_eval(z_nodes: np.ndarray, a: np.ndarray, z: complex):
+    """C_N(z) = a_1 / (1 + a_2 (z - z_1) / (1 + a_3 (z - z_2) / (1 + ...))),
+    evaluated from the innermost level outwards, with its derivative dC/dz."""
+    n = len(a)
+    t = 1.0 + 0j          # innermost denominator level
+    dt = 0.0 + 0j
+    for p in range(n - 1, 0, -1):
+        num = a[p] * (z - z_nodes[p - 1])
+        dnum = a[p]
+        new_t = 1.0 + num / t
+        new_dt = dnum / t - num * dt / (t * t)
+        t, dt = new_t, new_dt
+    val = a[0] / t
+    dval = -a[0] * dt / (t * t)
+    return val, dval
+
+
+def qp_newton(eps_n: float, shift: float, eps_F: float, z_nodes: np.ndarray, a: np.ndarray,
+              eta: float = 0.0, tol: float = 1e-12, max_iter: int = 100):
+    """Solve E = eps_n + Re Sigma^c_n(E) + shift with Sigma^c_n(E) = C_N(E - eps_F + i eta)
+    by Newton from E = eps_n.  Returns (E, status): status 0 converged, 1 not."""
+    E = eps_n
+    for _ in range(max_iter):
+        s, ds = pade_eval(z_nodes, a, complex(E - eps_F, eta))
+        f = E - eps_n - s.real - shift
+        fp = 1.0 - ds.real
+        dE = -f / fp
+        E = E + dE
+        if abs(dE) < tol:
+            return E, 0
+    return E, 1
+
+
+# ----------------------------------------------------------------------------
+# Whole path
+# ----------------------------------------------------------------------------
+def pade_nodes(n_omega: int) -> np.ndarray:
+    """Indices of the Gauss-Legendre nodes the continuation passes through."""
+    return np.arange(0, n_omega, 2)
+
+
+def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=24,
+          omega0=0.5, naf_thresh=-1.0, spin=2, tau_x=None, tau_w=None, return_all=False):
+    """One G0W0 solve.  Direct Pi (Eq. Pi) unless a Laplace grid (tau_x, tau_w)
+    is given, in which case Pi is built from the moments M^m.
+    B_ov [P][i*n_virt+a] (all occupied i), B_tgt [T][P][m] (all orbitals m).
+    Returns (sigma [T][n_omega] complex, e_qp [T], status [T]) and, with
+    return_all, a dict of intermediates."""
+    eps = np.asarray(eps, dtype=np.float64)
+    targets = np.asarray(targets)
+    if np.any(targets < n_frozen):
+        raise ValueError("frozen-core orbitals cannot be targets")
+    omegas, weights = gl_grid(n_omega, omega0)
+    eF = fermi_level(eps, n_occ)
+    B_act = active_ov(B_ov, n_occ, n_virt, n_frozen)
+    delta = pair_gaps(eps, n_occ, n_virt, n_frozen)
+    inter = {"omegas": omegas, "weights": weights, "eps_F": eF}
+    if naf_thresh >= 0.0:
+        K = naf_metric(B_act)
+        U, lam_kept, lam_all = naf_basis(K, naf_thresh)
+        Bt = naf_project(B_act, U)
+        Bt_tgt = np.stack([naf_project(B_tgt[t][:, n_frozen:], U) for t in range(len(targets))])
+        inter.update(K=K, U=U, lam=lam_all, n_naf=U.shape[1])
+    else:
+        Bt = B_act
+        Bt_tgt = np.ascontiguousarray(B_tgt[:, :, n_frozen:])
+        inter.update(U=None, n_naf=Bt.shape[0])
+    if tau_x is None:
+        Pi = polarizability_direct(Bt, delta, omegas, spin)
+    else:
+        M = laplace_moments(Bt, delta, np.asarray(tau_x), np.asarray(tau_w))
+        Pi = polarizability_lt(M, omegas, np.asarray(tau_x), spin)
+        inter["M"] = M
+    C = screened_interaction(Pi)
+    W = w_nm(C, Bt_tgt)
+    eps_m = eps[n_frozen:]
+    sig = sigma_iw(W, eps_m, eF, omegas, weights)
+    sel = pade_nodes(n_omega)
+    z_nodes = 1j * omegas[sel]
+    e_qp = np.empty(len(targets))
+    status = np.empty(len(targets), dtype=np.int32)
+    coefs = []
+    for t, n in enumerate(targets):
+        a = pade_coefficients(z_nodes, sig[t][sel])
+        coefs.append(a)
+        e_qp[t], status[t] = qp_newton(eps[n], shift[t], eF, z_nodes, a)
+    if return_all:
+        inter.update(Bt=Bt, Bt_tgt=Bt_tgt, Pi=Pi, C=C, W=W, pade=np.array(coefs), delta=delta)
+        return sig, e_qp, status, inter
+    return sig, e_qp, status

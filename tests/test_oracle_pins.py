@@ -1,0 +1,277 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself (a closed form, an identity of the mathematics, a library routine, an
+independent analytic route), chosen so that a dropped term, a wrong sign, a
+wrong index or a transposed operand in the oracle fails at least one test."""
+import numpy as np
+import pytest
+
+from oracle import casida as CAS
+from oracle import ltgw_oracle as O
+from paper_2307_04508_gb300 import synthetic as S
+
+HA2MEV = 27211.386245988
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return S.make_workload(S.TINY)
+
+
+# ---------------------------------------------------------------- GL grid
+@pytest.mark.parametrize("a", [0.05, 0.3, 1.0, 4.0])
+def test_gl_grid_lorentzian_closed_form(a):
+    # int_0^inf dw / (a^2 + w^2) = pi / (2 a)
+    w, g = O.gl_grid(128, 0.5)
+    got = np.sum(g / (a * a + w * w))
+    assert abs(got - np.pi / (2 * a)) < 1e-6 * np.pi / (2 * a) + 1e-9
+
+
+def test_gl_grid_second_closed_form():
+    # int_0^inf w^2 / (a^2 + w^2)^2 dw = pi / (4 a)
+    a = 0.7
+    w, g = O.gl_grid(96, 0.5)
+    got = np.sum(g * w * w / (a * a + w * w) ** 2)
+    assert abs(got - np.pi / (4 * a)) < 1e-10
+
+
+def test_gl_grid_ascending_positive():
+    w, g = O.gl_grid(24, 0.5)
+    assert np.all(np.diff(w) > 0) and np.all(w > 0) and np.all(g > 0)
+    # midpoint of the map: x = 0 -> omega0 (odd n has a node there)
+    w5, _ = O.gl_grid(5, 0.5)
+    assert abs(w5[2] - 0.5) < 1e-15
+
+
+# ---------------------------------------------------------------- Pi
+@pytest.mark.parametrize("spin", [1, 2])
+def test_pi_single_pair_closed_form(spin):
+    R, d = 0.37, 0.81
+    B = np.array([[R]])
+    om = np.array([0.0, 0.2, 3.0])
+    Pi = O.polarizability_direct(B, np.array([d]), om, spin)
+    for j, w in enumerate(om):
+        assert abs(Pi[j, 0, 0] - (-2 * spin * R * R * d / (w * w + d * d))) < 4e-16
+
+
+def test_pi_symmetric_negative_semidefinite(tiny):
+    sig, e, st, it = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift,
+                             4, 16, 0, n_omega=24, return_all=True)
+    for P in it["Pi"]:
+        assert np.abs(P - P.T).max() < 1e-15 * np.abs(P).max()
+        assert np.linalg.eigvalsh(P).max() < 1e-14
+    # magnitude falls with frequency
+    norms = [np.linalg.norm(P) for P in it["Pi"]]
+    assert np.all(np.diff(norms) < 0)
+
+
+def test_pi_pair_sum_is_brute_force(tiny):
+    # element-by-element double loop over P, Q and the pair sum (tiny sizes)
+    d = O.pair_gaps(tiny.eps, 4, 16, 0)
+    B = tiny.B_ov[:6, :]
+    w = 0.37
+    Pi = O.polarizability_direct(B, d, np.array([w]), 2)[0]
+    for P in range(6):
+        for Q in range(6):
+            acc = 0.0
+            for i in range(4):
+                for a in range(16):
+                    dia = tiny.eps[4 + a] - tiny.eps[i]
+                    acc += B[P, i * 16 + a] * dia / (w * w + dia * dia) * B[Q, i * 16 + a]
+            assert abs(Pi[P, Q] - (-4.0 * acc)) < 1e-15
+
+
+def test_laplace_mode_within_quadrature_bound(tiny):
+    # Any Laplace rule with scalar error eq = max_X |X sum_m w_m e^{-X x_m} - 1|
+    # over the X range in use bounds the matrix error: -eq Pi <= Pi_LT - Pi <= eq Pi.
+    delta = O.pair_gaps(tiny.eps, 4, 16, 0)
+    om, _ = O.gl_grid(24, 0.5)
+    x, wt = O.sinc_laplace_grid(90, -30.0, 4.5)
+    X = np.concatenate([(om[:, None] ** 2 + delta[None, :] ** 2).ravel()])
+    eq = np.max(np.abs(X * (np.exp(-np.outer(X, x)) @ wt) - 1.0))
+    assert eq < 1e-6
+    Pd = O.polarizability_direct(tiny.B_ov, delta, om, 2)
+    M = O.laplace_moments(tiny.B_ov, delta, x, wt)
+    Pl = O.polarizability_lt(M, om, x, 2)
+    for j in range(len(om)):
+        D = Pl[j] - Pd[j]
+        # -Pd is PSD; check |v^T D v| <= eq * v^T (-Pd) v on its eigenbasis
+        lam, V = np.linalg.eigh(-Pd[j])
+        Dv = V.T @ D @ V
+        assert np.all(np.abs(np.diag(Dv)) <= eq * lam + 1e-15)
+        assert np.linalg.norm(D) <= eq * np.linalg.norm(Pd[j]) * np.sqrt(Pd.shape[1]) + 1e-15
+
+
+def test_laplace_moment_sign_and_weight(tiny):
+    # single Laplace point: M = B diag(w Delta e^{-Delta^2 x}) B^T; with x -> 0, w = 1
+    # the moment is B diag(Delta) B^T (the e^{-Delta^2 x} factor must be present)
+    delta = O.pair_gaps(tiny.eps, 4, 16, 0)
+    M0 = O.laplace_moments(tiny.B_ov, delta, np.array([0.0]), np.array([1.0]))[0]
+    assert np.allclose(M0, (tiny.B_ov * delta) @ tiny.B_ov.T, rtol=0, atol=1e-15)
+    M1 = O.laplace_moments(tiny.B_ov, delta, np.array([0.5]), np.array([2.0]))[0]
+    assert np.allclose(M1, (tiny.B_ov * (2.0 * delta * np.exp(-0.5 * delta ** 2))) @ tiny.B_ov.T,
+                       rtol=0, atol=1e-15)
+    # recombination: Pi = -2 s sum_m e^{-w^2 x_m} M^m
+    P = O.polarizability_lt(np.stack([M0, M1]), np.array([0.3]), np.array([0.0, 0.5]), 2)[0]
+    assert np.allclose(P, -4.0 * (M0 + np.exp(-0.09 * 0.5) * M1), rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- screening
+def test_screening_matches_woodbury_form(tiny):
+    # C = (1 - Pi)^-1 - 1 with Pi = -R D R^T equals -R (D^-1 + R^T R)^-1 R^T
+    delta = O.pair_gaps(tiny.eps, 4, 16, 0)
+    B = tiny.B_ov
+    for w in (0.0, 0.4, 5.0):
+        Pi = O.polarizability_direct(B, delta, np.array([w]), 2)
+        C = O.screened_interaction(Pi)[0]
+        Dinv = np.diag((w * w + delta * delta) / (4.0 * delta))
+        Cw = -B @ np.linalg.solve(Dinv + B.T @ B, B.T)
+        assert np.abs(C - Cw).max() < 1e-13
+
+
+def test_w_nonpositive_and_decaying(tiny):
+    sig, e, st, it = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift,
+                             4, 16, 0, n_omega=24, return_all=True)
+    W = it["W"]
+    assert W.max() <= 1e-15
+    assert np.all(np.diff(-W, axis=2) <= 1e-15)
+    for C in it["C"]:
+        assert np.linalg.eigvalsh(C).max() <= 1e-14
+
+
+# ---------------------------------------------------------------- sigma and QP
+def test_sigma_conjugate_symmetry(tiny):
+    sig, e, st, it = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift,
+                             4, 16, 0, n_omega=24, return_all=True)
+    om = np.array([0.1, 0.9, 3.3])
+    sp = O.sigma_iw(it["W"], tiny.eps, it["eps_F"], it["omegas"], it["weights"], om)
+    sm = O.sigma_iw(it["W"], tiny.eps, it["eps_F"], it["omegas"], it["weights"], -om)
+    assert np.abs(sm - np.conj(sp)).max() < 1e-16
+
+
+def test_sigma_converges_to_casida(tiny):
+    errs = []
+    for nw in (24, 96):
+        sig, e, st, it = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift,
+                                 4, 16, 0, n_omega=nw, return_all=True)
+        _, _, fns, _ = CAS.g0w0_analytic(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16)
+        probe = np.array([0.05, 0.3, 1.0])
+        sp = O.sigma_iw(it["W"], tiny.eps, it["eps_F"], it["omegas"], it["weights"], probe)
+        ref = np.array([[fns[t](1j * w + it["eps_F"]) for w in probe] for t in range(2)])
+        errs.append(np.abs(sp - ref).max())
+    assert errs[1] < errs[0] and errs[1] < 2e-5
+
+
+def test_qp_matches_fully_analytic_g0w0(tiny):
+    # The paper's AC agrees with the analytic reference to its printed 0.1 meV.
+    ea, sa, _, _ = CAS.g0w0_analytic(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16)
+    assert np.all(sa == 0)
+    _, e24, s24 = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16, 0, n_omega=24)
+    _, e128, s128 = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16, 0, n_omega=128)
+    assert np.all(s24 == 0) and np.all(s128 == 0)
+    assert np.abs(e24 - ea).max() * HA2MEV < 0.1
+    assert np.abs(e128 - ea).max() * HA2MEV < 0.01
+    # a genuine correction: QP energies move away from the orbital energies
+    assert np.abs(ea - tiny.eps[tiny.targets] - tiny.shift).min() > 1e-4
+
+
+def test_qp_matches_analytic_with_frozen_core_and_spin1():
+    p = S.make_problem(6, 14, 40, n_frozen=2, seed=77, n_targets=4)
+    for spin in (1, 2):
+        ea, sa, _, _ = CAS.g0w0_analytic(p.eps, p.B_ov, p.B_tgt, p.targets, p.shift, 6, 14, 2, spin=spin)
+        _, e, s = O.solve(p.eps, p.B_ov, p.B_tgt, p.targets, p.shift, 6, 14, 2, n_omega=64, spin=spin)
+        assert np.all(s == 0) and np.abs(e - ea).max() * HA2MEV < 0.01
+
+
+def test_pade_exact_on_rational():
+    rng = np.random.default_rng(5)
+    poles = np.array([0.7, -1.3, 2.2])
+    res = rng.uniform(0.1, 1.0, 3)
+    f = lambda z: np.sum(res / (z - poles))
+    zn = 1j * np.linspace(0.1, 4.0, 6)      # [2/3] rational: 6 points fix it
+    a = O.pade_coefficients(zn, np.array([f(z) for z in zn]))
+    for z in (0.3 + 0.0j, -0.5 + 0.2j, 1.9 + 0.01j, 5j):
+        v, dv = O.pade_eval(zn, a, z)
+        assert abs(v - f(z)) < 1e-10 * max(1, abs(f(z)))
+        df = -np.sum(res / (z - poles) ** 2)
+        assert abs(dv - df) < 1e-8 * max(1, abs(df))
+
+
+def test_pade_interpolates_nodes():
+    zn = 1j * np.linspace(0.05, 3.0, 12)
+    u = np.exp(-zn) / (1.0 + zn * zn)
+    a = O.pade_coefficients(zn, u)
+    for z, uu in zip(zn, u):
+        assert abs(O.pade_eval(zn, a, z)[0] - uu) < 1e-12
+
+
+def test_newton_single_pole_quadratic():
+    # Sigma(E) = A / (E - eF - p): QP equation becomes a quadratic in E
+    A, p, eF, e0, sh = 0.02, 0.9, -0.1, -0.4, 0.01
+    zn = 1j * np.linspace(0.1, 3.0, 8)
+    a = O.pade_coefficients(zn, A / (zn - p))
+    E, st = O.qp_newton(e0, sh, eF, zn, a)
+    b = e0 + sh + eF + p
+    c = (e0 + sh) * (eF + p) - A
+    roots = np.roots([1.0, -b, c]).real
+    assert st == 0
+    assert np.min(np.abs(roots - E)) < 1e-12
+    assert abs(E - roots[np.argmin(np.abs(roots - e0))]) < 1e-12
+
+
+# ---------------------------------------------------------------- NAF and frozen core
+def test_naf_threshold_zero_is_orthogonal_transform(tiny):
+    ref = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16, 0, n_omega=24,
+                  return_all=True)
+    naf = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16, 0, n_omega=24,
+                  naf_thresh=0.0, return_all=True)
+    assert naf[3]["n_naf"] == 48
+    U = naf[3]["U"]
+    assert np.abs(U.T @ U - np.eye(48)).max() < 1e-13
+    assert np.abs(naf[3]["W"] - ref[3]["W"]).max() < 1e-13
+    assert np.abs(naf[0] - ref[0]).max() < 1e-13
+    assert np.abs(naf[1] - ref[1]).max() < 1e-11
+    # basis-invariant Pi: U Pi_naf U^T equals Pi
+    assert np.abs(U @ naf[3]["Pi"][3] @ U.T - ref[3]["Pi"][3]).max() < 1e-13
+
+
+def test_naf_truncation_keeps_top_eigenspace(tiny):
+    sig, e, st, it = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16, 0,
+                             n_omega=24, naf_thresh=1e-3, return_all=True)
+    K, U, lam = it["K"], it["U"], it["lam"]
+    k = int(np.sum(lam > 1e-3))
+    assert 0 < k < 48 and U.shape[1] == k
+    assert np.abs(K @ U - U @ np.diag(lam[lam > 1e-3])).max() < 1e-13
+    # K eigenvalues are those of the ov Gram matrix (library routine)
+    sv = np.linalg.svd(tiny.B_ov, compute_uv=False) ** 2
+    assert np.allclose(np.sort(sv), lam, rtol=0, atol=1e-14)
+    # the truncated answer stays close to the full one (paper: a few meV at 1e-2)
+    _, e_full, _ = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift, 4, 16, 0, n_omega=24)
+    assert np.abs(e - e_full).max() * HA2MEV < 20.0
+
+
+def test_frozen_core_equals_removed_orbital():
+    # Freezing orbital 0 must equal deleting it from the problem altogether.
+    p = S.make_problem(5, 12, 30, n_frozen=1, seed=91, n_targets=2)
+    _, e1, s1 = O.solve(p.eps, p.B_ov, p.B_tgt, p.targets, p.shift, 5, 12, 1, n_omega=32)
+    eps2 = p.eps[1:]
+    Bov2 = p.B_ov[:, 12:]
+    Btg2 = p.B_tgt[:, :, 1:]
+    _, e2, s2 = O.solve(eps2, Bov2, Btg2, p.targets - 1, p.shift, 4, 12, 0, n_omega=32)
+    assert np.abs(e1 - e2).max() < 1e-13
+
+
+def test_pade_node_choice_is_well_conditioned(tiny):
+    # Through every second node, 1e-15 relative noise in Sigma(i w) moves the
+    # quasi-particle energy by far less than the 1e-8 Ha parity bar.
+    sig, e, st, it = O.solve(tiny.eps, tiny.B_ov, tiny.B_tgt, tiny.targets, tiny.shift,
+                             4, 16, 0, n_omega=24, return_all=True)
+    sel = O.pade_nodes(24)
+    assert list(sel) == list(range(0, 24, 2))
+    zn = 1j * it["omegas"][sel]
+    rng = np.random.default_rng(3)
+    for t, n in enumerate(tiny.targets):
+        for _ in range(4):
+            noise = 1e-15 * (rng.standard_normal(len(sel)) + 1j * rng.standard_normal(len(sel)))
+            a = O.pade_coefficients(zn, sig[t][sel] * (1 + noise))
+            E, s = O.qp_newton(tiny.eps[n], tiny.shift[t], it["eps_F"], zn, a)
+            assert s == 0 and abs(E - e[t]) < 1e-10
