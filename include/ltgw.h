@@ -1,0 +1,171 @@
+/*
+ * ltgw.h - C ABI of the GB300 (sm_103a) LT-GW G0W0 library.
+ *
+ * The library computes the imaginary-frequency G0W0 self-energy of the
+ * analytic-continuation GW method accelerated by a Laplace transformation
+ * (LT), natural auxiliary functions (NAF) and the frozen-core approximation,
+ * as stated in Toelle, Niemeyer, Neugebauer, arXiv:2307.04508, Sec. 2:
+ *
+ *   W^c_nm(iw) = sum_PQ R^P_nm {[1 - Pi(iw)]^-1 - 1}_PQ R^Q_nm      (Eq. ScreenedCoulombOrbital)
+ *   Pi_PQ(iw)  = -2 s sum_ia R^P_ia D_ia / (w^2 + D_ia^2) R^Q_ia      (Eq. Pi; D_ia = e_a - e_i)
+ *   Pi_PQ(iw) ~= -2 s sum_m M^m_PQ exp(-w^2 x_m),
+ *   M^m_PQ     = sum_ia R^P_ia w_m D_ia exp(-D_ia^2 x_m) R^Q_ia        (Eq. LT and the M^m form)
+ *   Sigma^c_n(iw) = -(1/pi) sum_m int_0^inf dw' z/(z^2 + w'^2) W_nm(iw'),
+ *                   z = iw + e_F - e_m                                 (Eq. CorrelationSelfEnergy)
+ *   K_PQ = sum_ia R^P_ia R^Q_ia, U = eigenvectors of K above a threshold,
+ *   R~ = R U                                                            (Eqs. nafeq, naftrafo)
+ *
+ * followed by an N-point Pade continuation (Vidberg & Serene 1977) and the
+ * quasi-particle equation E = e_n + Re Sigma^c_n(E) + (Sigma_x - V_xc)_n.
+ *
+ * Conventions shared by every entry point:
+ *  - All matrices are row-major float64.  The caller owns every buffer; the
+ *    library never frees or keeps a caller pointer beyond the call.
+ *  - "any" pointer: host (pageable or pinned) or device memory; the library
+ *    detects which and stages host data itself.  "device" pointer: device
+ *    memory on the context's device.
+ *  - Work is issued on the given CUDA stream (cudaStream_t passed as void*;
+ *    NULL = the legacy default stream).  Calls that return host-visible
+ *    results synchronise that stream before returning.
+ *  - Every call returns an ltgw_status; no exception or abort crosses the ABI.
+ *    ltgw_last_error() gives a one-line description of the last failure.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *
+ * Readings of points the paper leaves open (fixed once, shared with the tests):
+ *  - closed-shell spatial orbitals: spin factor s (default 2) multiplies the
+ *    -2 of Eq. Pi; the NAF metric sums active occupied-virtual pairs without a
+ *    factor 2 and keeps eigenvalues strictly above the threshold;
+ *  - frozen-core orbitals leave Pi, K and the m-sum of Sigma and cannot be targets;
+ *  - e_F = (e_HOMO + e_LUMO)/2; eta = 0;
+ *  - the Pade fraction passes through every second Gauss-Legendre node
+ *    (indices 0, 2, 4, ...) in ascending order;
+ *  - Newton from e_n, |dE| < 1e-12 Ha, at most 100 steps.
+ */
+#ifndef LTGW_H
+#define LTGW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LTGW_OK = 0,
+  LTGW_ERR_BAD_ARG = 1,     /* an argument is out of range or inconsistent          */
+  LTGW_ERR_NOMEM = 2,       /* device or pinned-host allocation failed             */
+  LTGW_ERR_NOT_SPD = 3,     /* a pivot of 1 - Pi(iw) was not positive              */
+  LTGW_ERR_NO_CONVERGE = 4, /* a quasi-particle Newton solve did not converge      */
+  LTGW_ERR_DEVICE = 5,      /* a CUDA call failed                                  */
+  LTGW_ERR_EIG = 6,         /* the NAF eigensolver failed (non-finite or no vector) */
+  LTGW_ERR_NO_NAF = 7       /* the NAF threshold kept no auxiliary function        */
+} ltgw_status;
+
+enum { LTGW_FP64 = 0, LTGW_BF16X3 = 1, LTGW_FP8 = 2 };
+
+typedef struct {
+  int n_occ;          /* occupied orbitals, frozen core included                  */
+  int n_virt;         /* virtual orbitals                                         */
+  int n_frozen;       /* lowest occupied orbitals frozen (0 <= n_frozen < n_occ)  */
+  int n_aux;          /* auxiliary functions                                      */
+  int n_omega;        /* modified Gauss-Legendre points (2..256)                  */
+  int n_tau;          /* Laplace points when use_laplace != 0 (1..64)             */
+  double omega0;      /* GL map w = omega0 (1+x)/(1-x), Ha (> 0)                  */
+  double naf_thresh;  /* < 0: no NAF; >= 0: keep eigenvalues of K above it        */
+  int spin;           /* 1 (spin orbitals) or 2 (closed shell)                    */
+  int use_laplace;    /* 0: Pi from Eq. Pi; 1: Pi from the Laplace moments M^m     */
+  int precision;      /* LTGW_FP64 (the only value accepted by this version)      */
+  int reserved;       /* must be 0                                                */
+} ltgw_params;
+
+typedef struct {
+  int n_naf;                 /* auxiliary functions kept (n_aux without NAF)          */
+  int n_pade;                /* points the Pade fraction passes through               */
+  int n_tau;                 /* Laplace points used (0 in direct mode)                */
+  int naf_near_threshold;    /* eigenvalues within 1e-12*lambda_max of the threshold  */
+  double lt_max_rel_err;     /* max |X sum w e^{-X x} - 1| over the library grid's
+                                interval (NaN when the caller supplied the grid)      */
+  double ms_naf, ms_pi, ms_screen, ms_wnm, ms_sigma_qp, ms_total; /* last solve, device time */
+  double ms_pi_kernel;       /* summed device time of the Pi-build kernel launches    */
+  int pi_kernel_launches;    /* Pi-build kernel launches in the last solve            */
+  int kernel_launches;       /* all kernel launches in the last solve                 */
+} ltgw_stats;
+
+typedef struct ltgw_ctx ltgw_ctx;
+
+/* Create a context on CUDA device `device` (it becomes current on this thread).
+ * The context owns a device workspace that grows to the largest solve seen. */
+ltgw_status ltgw_create(ltgw_ctx **out, int device);
+void ltgw_destroy(ltgw_ctx *ctx);
+const char *ltgw_status_string(ltgw_status s);
+const char *ltgw_last_error(const ltgw_ctx *ctx);
+
+/* Turn per-stage CUDA-event timing on (1) or off (0); off by default. */
+ltgw_status ltgw_set_timing(ltgw_ctx *ctx, int on);
+ltgw_status ltgw_get_stats(const ltgw_ctx *ctx, ltgw_stats *out);
+
+/*
+ * One G0W0 solve: the whole path of Sec. 2 from orbital energies and RI
+ * tensor blocks to Sigma^c_n(iw) and quasi-particle energies.
+ *   eps      any [n_occ+n_virt]            orbital energies, ascending, Ha
+ *   B_ov     any [n_aux][n_occ*n_virt]     R^P_ia, pair index i*n_virt+a, all occupied i
+ *   B_tgt    any [n_tgt][n_aux][n_occ+n_virt]  R^P_nm for n = targets[t], all m
+ *   targets  any [n_tgt]                   orbital indices, n_frozen <= n < n_occ+n_virt
+ *   shift    any [n_tgt]                   (Sigma_x - V_xc)_n, Ha
+ *   tau_x, tau_w  any [n_tau] or NULL      Laplace grid; NULL: the library fits a
+ *                                          minimax grid on the paper's interval
+ *   sigma_iw any [n_tgt][n_omega][2]       out: Sigma^c_n(i w_l) (re, im) at the GL nodes
+ *   e_qp     any [n_tgt]                   out: quasi-particle energies, Ha
+ *   qp_status any [n_tgt]                  out: 0 converged, 1 not
+ * Returns LTGW_ERR_NO_CONVERGE (after writing every output) when a state did
+ * not converge.  Synchronises `stream`.
+ */
+ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps,
+                       const double *B_ov, const double *B_tgt, const int *targets,
+                       int n_tgt, const double *shift, const double *tau_x,
+                       const double *tau_w, double *sigma_iw, double *e_qp,
+                       int *qp_status, void *stream);
+
+/* ---- grids (host only, no context) ------------------------------------- */
+
+/* Modified Gauss-Legendre rule on [0, inf) (Sec. 2 after Eq.
+ * CorrelationSelfEnergy): Legendre nodes mapped by w = omega0 (1+x)/(1-x),
+ * weights g = w_GL * 2 omega0 / (1-x)^2, ascending.  omega, weight: host [n]. */
+ltgw_status ltgw_gl_grid(int n, double omega0, double *omega, double *weight);
+
+/* Minimax Laplace grid (Sec. 3: bounds and epsilon_LT): x_m, w_m (host [n_tau])
+ * with 1/X ~ sum_m w_m exp(-X x_m) on [a, b], fitted by a Remez exchange
+ * on the relative error.  *max_rel_err receives max |X sum w e^{-X x} - 1|. */
+ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *x, double *w,
+                              double *max_rel_err);
+
+/* ---- single steps on device buffers (for checking and composition) ------ */
+
+/* NAF basis (Eqs. nafeq and NAF eigen-equation): K = B B^T over the n_pairs
+ * columns of B (device [n_aux][ld], ld >= n_pairs), eigenpairs of K, and the
+ * eigenvectors with eigenvalue > thresh written as the rows of Ut (device
+ * [n_aux][n_aux] capacity; rows 0..n_naf-1 used, descending eigenvalue).
+ * lambda: device [n_aux] capacity, kept eigenvalues, descending.  Synchronises. */
+ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B,
+                           int64_t ld, double thresh, double *Ut, double *lambda,
+                           int *n_naf, void *stream);
+
+/* Polarisability at the GL frequencies `omegas` (host [n_omega]) from the
+ * pair block Bt (device [N][n_pairs]) and gaps delta (device [n_pairs]):
+ * n_tau == 0 evaluates Eq. Pi directly, n_tau > 0 the Laplace form with the
+ * host grid (x, w).  Pi: device [n_omega][N][N], full symmetric.  Stream-ordered. */
+ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                const double *delta, int n_omega, const double *omegas,
+                                int n_tau, const double *x, const double *w, int spin,
+                                double *Pi, void *stream);
+
+/* Screening (Eq. ScreenedCoulombOrbital): C_j = [1 - Pi_j]^-1 - 1 for each of
+ * n_omega matrices (device [n_omega][N][N] in and out, may not alias).
+ * Synchronises; LTGW_ERR_NOT_SPD if a pivot was not positive. */
+ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C,
+                        void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTGW_H */

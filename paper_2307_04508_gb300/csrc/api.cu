@@ -1,0 +1,607 @@
+// C ABI of the LT-GW library: argument checking, workspace, host/device
+// staging and the order of the steps of Sec. 2 (frozen-core slice -> NAF ->
+// Pi -> screening -> W_nm -> Sigma(i w) -> Pade -> Newton).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ltgw {
+int g_launch_count = 0;
+}
+
+using namespace ltgw;
+
+namespace {
+
+// Device bump allocator; grows (free + malloc) only between calls.
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, off = 0;
+  bool sizing = false;
+  size_t need = 0;
+  void begin_sizing() { sizing = true; need = 0; off = 0; }
+  template <class T>
+  T *take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = sizing ? nullptr : reinterpret_cast<T *>(base + off);
+    off += std::max<size_t>(n, 1) * sizeof(T);
+    if (sizing) need = off;
+    return p;
+  }
+  cudaError_t commit() {
+    sizing = false;
+    size_t want = need;
+    off = 0;
+    if (want <= cap) return cudaSuccess;
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&base, want);
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+  }
+};
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+enum Stage { EV_START = 0, EV_NAF, EV_PI0, EV_PI1, EV_PI, EV_SCREEN, EV_WNM, EV_SIGQP, EV_END, EV_COUNT };
+
+}  // namespace
+
+struct ltgw_ctx {
+  int device = 0;
+  ltgw_status st = LTGW_OK;
+  std::string err;
+  Arena a1, a2, a3;  // a1: inputs; a2: after the NAF count is known; a3: NAF scratch
+  int *flags = nullptr;
+  bool timing = false;
+  cudaEvent_t ev[EV_COUNT] = {};
+  ltgw_stats stats{};
+  int launches = 0;
+
+  void fail(ltgw_status c, const std::string &m) {
+    if (st == LTGW_OK) { st = c; err = m; }
+  }
+  ltgw_status status() const { return st; }
+  void reset() { st = LTGW_OK; err.clear(); launches = 0; }
+  void mark(Stage s, cudaStream_t stream) {
+    if (timing) cudaEventRecord(ev[s], stream);
+  }
+  double ms(Stage a, Stage b) {
+    float t = 0.f;
+    if (!timing) return 0.0;
+    if (cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) { cudaGetLastError(); return 0.0; }
+    return (double)t;
+  }
+};
+
+#define CHECK_LAUNCH(ctx, expr, nk)                                                              \
+  do {                                                                                           \
+    cudaError_t _e = (expr);                                                                     \
+    (ctx)->launches += (nk);                                                                     \
+    if (_e != cudaSuccess) {                                                                     \
+      (ctx)->fail(LTGW_ERR_DEVICE, std::string(#expr) + ": " + cudaGetErrorString(_e));          \
+      return (ctx)->status();                                                                    \
+    }                                                                                            \
+  } while (0)
+
+#define REQUIRE(ctx, cond, msg)                                                                  \
+  do {                                                                                           \
+    if (!(cond)) {                                                                               \
+      (ctx)->fail(LTGW_ERR_BAD_ARG, msg);                                                        \
+      return (ctx)->status();                                                                    \
+    }                                                                                            \
+  } while (0)
+
+namespace {
+
+ltgw_status copy_in(ltgw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return LTGW_OK;
+  LTGW_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  return LTGW_OK;
+}
+
+ltgw_status read_small(ltgw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return LTGW_OK;
+  LTGW_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  return LTGW_OK;
+}
+
+ltgw_status check_flags(ltgw_ctx *ctx, cudaStream_t s) {
+  int h[FLAG_COUNT];
+  if (read_small(ctx, h, ctx->flags, sizeof(h), s) != LTGW_OK) return ctx->status();
+  if (h[FLAG_EIG]) ctx->fail(LTGW_ERR_EIG, "NAF eigensolver: inverse iteration produced a non-finite vector");
+  if (h[FLAG_NOT_SPD]) ctx->fail(LTGW_ERR_NOT_SPD, "screening: a pivot of 1 - Pi(iw) was not positive");
+  return ctx->status();
+}
+
+// NAF basis on device data: K = B B^T, eigenvectors with eigenvalue > thresh
+// as rows of Ut (descending eigenvalue), their eigenvalues in lam.
+ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, const double *B,
+                          int64_t ld, double thresh, double *Ut, double *lam_out, int *k_out,
+                          int *near_out, cudaStream_t s) {
+  EigWork w;
+  auto layout = [&](Arena &A) {
+    w.A = A.take<double>((size_t)n * n);
+    w.V = A.take<double>((size_t)n * n);
+    w.d = A.take<double>(n);
+    w.e = A.take<double>(n);
+    w.tau = A.take<double>(n);
+    w.p = A.take<double>(n);
+    w.w = A.take<double>(n);
+    w.scal = A.take<double>(8);
+    w.lam = A.take<double>(n);
+    w.X = A.take<double>((size_t)n * n);
+    w.lu = A.take<double>((size_t)5 * n * n);
+    w.count = A.take<int>(2);
+  };
+  ar.begin_sizing();
+  layout(ar);
+  if (ar.commit() != cudaSuccess) {
+    ctx->fail(LTGW_ERR_NOMEM, "NAF workspace allocation failed");
+    return ctx->status();
+  }
+  layout(ar);
+  GemmF64Args g;
+  g.M = n; g.N = n; g.K = n_pairs;
+  g.A = B; g.lda = ld; g.B = B; g.ldb = ld;
+  g.C = w.A; g.ldc = n;
+  g.syrk = 1;
+  CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
+  int nl = 0;
+  cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl);
+  ctx->launches += nl;
+  if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("eig_tridiag: ") + cudaGetErrorString(e)); return ctx->status(); }
+  int cnt[2] = {0, 0};
+  if (read_small(ctx, cnt, w.count, sizeof(cnt), s) != LTGW_OK) return ctx->status();
+  const int k = cnt[0];
+  *k_out = k;
+  if (near_out) *near_out = cnt[1];
+  if (k <= 0) { ctx->fail(LTGW_ERR_NO_NAF, "NAF threshold kept no auxiliary function"); return ctx->status(); }
+  nl = 0;
+  e = launch_eig_vectors(w, n, k, Ut, ctx->flags, s, &nl);
+  ctx->launches += nl;
+  if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("eig_vectors: ") + cudaGetErrorString(e)); return ctx->status(); }
+  if (lam_out) LTGW_CUDA(ctx, cudaMemcpyAsync(lam_out, w.lam, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return LTGW_OK;
+}
+
+// Pi at the GL frequencies, direct (n_tau == 0) or through Laplace moments.
+ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, int64_t ldb,
+                               const double *delta, int n_omega, const double *d_omega,
+                               int n_tau, const double *d_x, const double *d_w, const double *d_E,
+                               double *M, int spin, double *Pi, cudaStream_t s) {
+  GemmF64Args g;
+  g.M = N; g.N = N; g.K = n_pairs;
+  g.A = Bt; g.lda = ldb; g.B = Bt; g.ldb = ldb;
+  g.ldc = N; g.strideC = (int64_t)N * N;
+  g.syrk = 1;
+  g.delta = delta;
+  ctx->mark(EV_PI0, s);
+  if (n_tau == 0) {
+    g.C = Pi;
+    g.alpha = -2.0 * spin;
+    g.scale_mode = SCALE_DIRECT;
+    g.batch_p0 = d_omega;
+    CHECK_LAUNCH(ctx, launch_gemm_f64(g, n_omega, true, true, s), 1);
+    ctx->mark(EV_PI1, s);
+  } else {
+    g.C = M;
+    g.alpha = 1.0;
+    g.scale_mode = SCALE_LAPLACE;
+    g.batch_p0 = d_x;
+    g.batch_p1 = d_w;
+    CHECK_LAUNCH(ctx, launch_gemm_f64(g, n_tau, true, true, s), 1);
+    ctx->mark(EV_PI1, s);
+    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
+  }
+  return LTGW_OK;
+}
+
+ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
+  REQUIRE(ctx, p != nullptr, "params is NULL");
+  REQUIRE(ctx, p->n_occ >= 1 && p->n_virt >= 1 && p->n_aux >= 1, "n_occ, n_virt, n_aux must be >= 1");
+  REQUIRE(ctx, p->n_frozen >= 0 && p->n_frozen < p->n_occ, "need 0 <= n_frozen < n_occ");
+  REQUIRE(ctx, p->n_omega >= 1 && p->n_omega <= 256, "n_omega must be in [1, 256]");
+  REQUIRE(ctx, p->omega0 > 0.0 && isfinite(p->omega0), "omega0 must be positive");
+  REQUIRE(ctx, p->spin == 1 || p->spin == 2, "spin must be 1 or 2");
+  REQUIRE(ctx, p->use_laplace == 0 || p->use_laplace == 1, "use_laplace must be 0 or 1");
+  REQUIRE(ctx, !p->use_laplace || (p->n_tau >= 1 && p->n_tau <= 32), "n_tau must be in [1, 32]");
+  REQUIRE(ctx, p->precision == LTGW_FP64, "only LTGW_FP64 is accepted by this version");
+  REQUIRE(ctx, p->reserved == 0, "reserved must be 0");
+  REQUIRE(ctx, isfinite(p->naf_thresh), "naf_thresh must be finite");
+  return LTGW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ltgw_status_string(ltgw_status s) {
+  switch (s) {
+    case LTGW_OK: return "ok";
+    case LTGW_ERR_BAD_ARG: return "bad argument";
+    case LTGW_ERR_NOMEM: return "out of memory";
+    case LTGW_ERR_NOT_SPD: return "1 - Pi not positive definite";
+    case LTGW_ERR_NO_CONVERGE: return "quasi-particle solve did not converge";
+    case LTGW_ERR_DEVICE: return "CUDA error";
+    case LTGW_ERR_EIG: return "eigensolver failure";
+    case LTGW_ERR_NO_NAF: return "no natural auxiliary function kept";
+  }
+  return "unknown status";
+}
+
+ltgw_status ltgw_create(ltgw_ctx **out, int device) {
+  if (!out) return LTGW_ERR_BAD_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return LTGW_ERR_DEVICE;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return LTGW_ERR_DEVICE;
+  ltgw_ctx *c = new ltgw_ctx();
+  c->device = device;
+  if (cudaMalloc(&c->flags, FLAG_COUNT * sizeof(int)) != cudaSuccess) {
+    delete c;
+    return LTGW_ERR_NOMEM;
+  }
+  for (auto &e : c->ev) cudaEventCreate(&e);
+  *out = c;
+  return LTGW_OK;
+}
+
+void ltgw_destroy(ltgw_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  ctx->a1.release();
+  ctx->a2.release();
+  ctx->a3.release();
+  if (ctx->flags) cudaFree(ctx->flags);
+  for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char *ltgw_last_error(const ltgw_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+ltgw_status ltgw_set_timing(ltgw_ctx *ctx, int on) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->timing = (on != 0);
+  return LTGW_OK;
+}
+
+ltgw_status ltgw_get_stats(const ltgw_ctx *ctx, ltgw_stats *out) {
+  if (!ctx || !out) return LTGW_ERR_BAD_ARG;
+  *out = ctx->stats;
+  return LTGW_OK;
+}
+
+ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, const double *B_ov,
+                       const double *B_tgt, const int *targets, int n_tgt, const double *shift,
+                       const double *tau_x, const double *tau_w, double *sigma_iw, double *e_qp,
+                       int *qp_status, void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  if (validate(ctx, p) != LTGW_OK) return ctx->status();
+  REQUIRE(ctx, eps && B_ov && B_tgt && targets && shift && sigma_iw && e_qp && qp_status,
+          "a required pointer is NULL");
+  REQUIRE(ctx, n_tgt >= 1, "n_tgt must be >= 1");
+  REQUIRE(ctx, (tau_x == nullptr) == (tau_w == nullptr), "tau_x and tau_w must both be given or both NULL");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n_occ = p->n_occ, n_virt = p->n_virt, n_fc = p->n_frozen, n_aux = p->n_aux;
+  const int n_orb = n_occ + n_virt, n_act = n_occ - n_fc, n_orb_act = n_orb - n_fc;
+  const int64_t n_ov_all = (int64_t)n_occ * n_virt, n_ov = (int64_t)n_act * n_virt;
+  const int n_omega = p->n_omega, T = n_tgt;
+  const int n_tau = p->use_laplace ? p->n_tau : 0;
+  const bool naf = p->naf_thresh >= 0.0;
+  ctx->stats = ltgw_stats{};
+  ctx->mark(EV_START, s);
+
+  // small inputs on the host
+  std::vector<double> h_eps(n_orb), h_shift(T);
+  std::vector<int> h_tg(T);
+  if (read_small(ctx, h_eps.data(), eps, n_orb * sizeof(double), s) != LTGW_OK) return ctx->status();
+  if (read_small(ctx, h_tg.data(), targets, T * sizeof(int), s) != LTGW_OK) return ctx->status();
+  if (read_small(ctx, h_shift.data(), shift, T * sizeof(double), s) != LTGW_OK) return ctx->status();
+  for (int i = 0; i < n_orb; ++i) REQUIRE(ctx, isfinite(h_eps[i]), "eps has a non-finite entry");
+  for (int i = 1; i < n_orb; ++i) REQUIRE(ctx, h_eps[i] >= h_eps[i - 1], "eps must be ascending");
+  REQUIRE(ctx, h_eps[n_occ] > h_eps[n_occ - 1], "need eps_LUMO > eps_HOMO");
+  for (int t = 0; t < T; ++t)
+    REQUIRE(ctx, h_tg[t] >= n_fc && h_tg[t] < n_orb, "target outside the active orbitals");
+  const double eF = 0.5 * (h_eps[n_occ - 1] + h_eps[n_occ]);
+  std::vector<double> h_om(n_omega), h_wt(n_omega);
+  if (ltgw_gl_grid(n_omega, p->omega0, h_om.data(), h_wt.data()) != LTGW_OK) {
+    ctx->fail(LTGW_ERR_BAD_ARG, "GL grid");
+    return ctx->status();
+  }
+  std::vector<double> h_x(n_tau), h_w(n_tau), h_E((size_t)n_omega * std::max(n_tau, 1));
+  ctx->stats.lt_max_rel_err = NAN;
+  if (n_tau) {
+    if (tau_x) {
+      if (read_small(ctx, h_x.data(), tau_x, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
+      if (read_small(ctx, h_w.data(), tau_w, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
+    } else {
+      double gap = h_eps[n_occ] - h_eps[n_occ - 1];
+      double lo = gap * gap + h_om[0] * h_om[0];
+      double span = h_eps[n_orb - 1] - h_eps[n_fc];
+      double hi = std::max(span * span, 1e4);
+      double err = 0.0;
+      if (ltgw_laplace_grid(n_tau, lo, hi, h_x.data(), h_w.data(), &err) != LTGW_OK) {
+        ctx->fail(LTGW_ERR_BAD_ARG, "Laplace grid fit");
+        return ctx->status();
+      }
+      ctx->stats.lt_max_rel_err = err;
+    }
+    for (int j = 0; j < n_omega; ++j)
+      for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * h_x[k]);
+  }
+  std::vector<double> h_epsn(T);
+  for (int t = 0; t < T; ++t) h_epsn[t] = h_eps[h_tg[t]];
+
+  const bool bov_dev = is_device_ptr(B_ov), btg_dev = is_device_ptr(B_tgt);
+  // ---- phase-1 workspace: inputs, grids, NAF
+  double *d_eps, *d_delta, *d_om, *d_wt, *d_x, *d_w, *d_E, *d_epsn, *d_shift, *d_Bov, *d_Btg, *d_Ut, *d_lam;
+  auto layout1 = [&](Arena &A) {
+    d_eps = A.take<double>(n_orb);
+    d_delta = A.take<double>(n_ov);
+    d_om = A.take<double>(n_omega);
+    d_wt = A.take<double>(n_omega);
+    d_x = A.take<double>(std::max(n_tau, 1));
+    d_w = A.take<double>(std::max(n_tau, 1));
+    d_E = A.take<double>(h_E.size());
+    d_epsn = A.take<double>(T);
+    d_shift = A.take<double>(T);
+    d_Bov = bov_dev ? const_cast<double *>(B_ov) : A.take<double>((size_t)n_aux * n_ov_all);
+    d_Btg = btg_dev ? const_cast<double *>(B_tgt) : A.take<double>((size_t)T * n_aux * n_orb);
+    d_Ut = naf ? A.take<double>((size_t)n_aux * n_aux) : nullptr;
+    d_lam = naf ? A.take<double>(n_aux) : nullptr;
+  };
+  ctx->a1.begin_sizing();
+  layout1(ctx->a1);
+  if (ctx->a1.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "input workspace allocation failed"); return ctx->status(); }
+  layout1(ctx->a1);
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  copy_in(ctx, d_eps, h_eps.data(), n_orb * sizeof(double), s);
+  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
+  copy_in(ctx, d_wt, h_wt.data(), n_omega * sizeof(double), s);
+  if (n_tau) {
+    copy_in(ctx, d_x, h_x.data(), n_tau * sizeof(double), s);
+    copy_in(ctx, d_w, h_w.data(), n_tau * sizeof(double), s);
+    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+  }
+  copy_in(ctx, d_epsn, h_epsn.data(), T * sizeof(double), s);
+  copy_in(ctx, d_shift, h_shift.data(), T * sizeof(double), s);
+  if (!bov_dev) copy_in(ctx, d_Bov, B_ov, (size_t)n_aux * n_ov_all * sizeof(double), s);
+  if (!btg_dev) copy_in(ctx, d_Btg, B_tgt, (size_t)T * n_aux * n_orb * sizeof(double), s);
+  if (ctx->status() != LTGW_OK) return ctx->status();
+  CHECK_LAUNCH(ctx, launch_pair_gaps(d_eps, n_occ, n_virt, n_fc, d_delta, s), 1);
+
+  // ---- frozen-core slice: the active pairs are the trailing columns
+  const double *B_act = d_Bov + (int64_t)n_fc * n_virt;
+  const int64_t ld_act = n_ov_all;
+
+  // ---- NAF (Eqs. nafeq, naftrafo) on a separate arena for its scratch
+  int N = n_aux, near = 0;
+  if (naf) {
+    if (naf_basis_dev(ctx, ctx->a3, n_aux, n_ov, B_act, ld_act, p->naf_thresh, d_Ut, d_lam, &N, &near, s) != LTGW_OK)
+      return ctx->status();
+  }
+  ctx->stats.n_naf = N;
+  ctx->stats.naf_near_threshold = near;
+
+  // ---- phase-2 workspace
+  double *d_Bt = nullptr, *d_Btt = nullptr, *d_M = nullptr, *d_Pi, *d_X0, *d_X1, *d_C, *d_W, *d_sig, *d_eqp;
+  int *d_st;
+  auto layout2 = [&](Arena &A) {
+    d_Bt = naf ? A.take<double>((size_t)N * n_ov) : nullptr;
+    d_Btt = naf ? A.take<double>((size_t)T * N * n_orb_act) : nullptr;
+    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
+    d_Pi = A.take<double>((size_t)n_omega * N * N);
+    d_X0 = A.take<double>((size_t)n_omega * N * N);
+    d_X1 = A.take<double>((size_t)n_omega * N * N);
+    d_C = A.take<double>((size_t)n_omega * N * N);
+    d_W = A.take<double>((size_t)n_omega * T * n_orb_act);
+    d_sig = A.take<double>((size_t)T * n_omega * 2);
+    d_eqp = A.take<double>(T);
+    d_st = A.take<int>(T);
+  };
+  ctx->a2.begin_sizing();
+  layout2(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "solve workspace allocation failed"); return ctx->status(); }
+  layout2(ctx->a2);
+
+  const double *Bt = B_act;
+  int64_t ld_bt = ld_act;
+  const double *Btt = d_Btg + n_fc;
+  int64_t ld_btt = n_orb, stride_btt = (int64_t)n_aux * n_orb;
+  if (naf) {
+    GemmF64Args g;  // R~_ov = U^T R_ov
+    g.M = N; g.N = (int)std::min<int64_t>(n_ov, INT32_MAX); g.K = n_aux;
+    g.A = d_Ut; g.lda = n_aux;
+    g.B = B_act; g.ldb = ld_act;
+    g.C = d_Bt; g.ldc = n_ov;
+    CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+    GemmF64Args h;  // R~_tgt[t] = U^T R_tgt[t][:, active]
+    h.M = N; h.N = n_orb_act; h.K = n_aux;
+    h.A = d_Ut; h.lda = n_aux; h.strideA = 0;
+    h.B = d_Btg + n_fc; h.ldb = n_orb; h.strideB = (int64_t)n_aux * n_orb;
+    h.C = d_Btt; h.ldc = n_orb_act; h.strideC = (int64_t)N * n_orb_act;
+    CHECK_LAUNCH(ctx, launch_gemm_f64(h, T, true, false, s), 1);
+    Bt = d_Bt; ld_bt = n_ov;
+    Btt = d_Btt; ld_btt = n_orb_act; stride_btt = (int64_t)N * n_orb_act;
+  }
+  ctx->mark(EV_NAF, s);
+
+  // ---- Pi (Eq. Pi or the Laplace form)
+  if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                         p->spin, d_Pi, s) != LTGW_OK)
+    return ctx->status();
+  ctx->mark(EV_PI, s);
+
+  // ---- screening
+  int nl = 0;
+  cudaError_t e = launch_screen(d_Pi, N, n_omega, d_X0, d_X1, d_C, ctx->flags, s, &nl);
+  ctx->launches += nl;
+  if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
+  ctx->mark(EV_SCREEN, s);
+
+  // ---- W_nm(i w_j)
+  ColDotArgs cd;
+  cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;
+  cd.C = d_C; cd.ldc = N; cd.strideC = (int64_t)N * N;
+  cd.Bt = Btt; cd.ldb = ld_btt; cd.strideBt = stride_btt;
+  cd.W = d_W; cd.ldw = n_orb_act;
+  CHECK_LAUNCH(ctx, launch_gemm_coldot(cd, n_omega, s), 1);
+  ctx->mark(EV_WNM, s);
+
+  // ---- Sigma(i w), Pade, Newton
+  SigmaArgs sa;
+  sa.n_tgt = T; sa.n_omega = n_omega; sa.n_orb = n_orb_act;
+  sa.W = d_W; sa.eps_m = d_eps + n_fc; sa.omega = d_om; sa.weight = d_wt;
+  sa.eps_F = eF; sa.sigma = d_sig;
+  CHECK_LAUNCH(ctx, launch_sigma(sa, s), 1);
+  QpArgs q;
+  q.n_tgt = T; q.n_omega = n_omega; q.pade_stride = 2;
+  q.sigma = d_sig; q.omega = d_om; q.eps_n = d_epsn; q.shift = d_shift;
+  q.eps_F = eF; q.eta = 0.0; q.tol = 1e-12; q.max_iter = 100;
+  q.e_qp = d_eqp; q.status = d_st;
+  CHECK_LAUNCH(ctx, launch_qp(q, s), 1);
+  ctx->mark(EV_SIGQP, s);
+
+  // ---- outputs
+  LTGW_CUDA(ctx, cudaMemcpyAsync(sigma_iw, d_sig, (size_t)T * n_omega * 2 * sizeof(double), cudaMemcpyDefault, s));
+  LTGW_CUDA(ctx, cudaMemcpyAsync(e_qp, d_eqp, (size_t)T * sizeof(double), cudaMemcpyDefault, s));
+  LTGW_CUDA(ctx, cudaMemcpyAsync(qp_status, d_st, (size_t)T * sizeof(int), cudaMemcpyDefault, s));
+  ctx->mark(EV_END, s);
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  if (check_flags(ctx, s) != LTGW_OK) return ctx->status();
+
+  ltgw_stats &st = ctx->stats;
+  st.n_pade = (n_omega + 1) / 2;
+  st.n_tau = n_tau;
+  st.kernel_launches = ctx->launches;
+  st.pi_kernel_launches = 1;
+  st.ms_naf = ctx->ms(EV_START, EV_NAF);
+  st.ms_pi = ctx->ms(EV_NAF, EV_PI);
+  st.ms_pi_kernel = ctx->ms(EV_PI0, EV_PI1);
+  st.ms_screen = ctx->ms(EV_PI, EV_SCREEN);
+  st.ms_wnm = ctx->ms(EV_SCREEN, EV_WNM);
+  st.ms_sigma_qp = ctx->ms(EV_WNM, EV_SIGQP);
+  st.ms_total = ctx->ms(EV_START, EV_END);
+
+  std::vector<int> hs(T);
+  if (read_small(ctx, hs.data(), qp_status, T * sizeof(int), s) != LTGW_OK) return ctx->status();
+  for (int t = 0; t < T; ++t)
+    if (hs[t] != 0) ctx->fail(LTGW_ERR_NO_CONVERGE, "a quasi-particle Newton solve did not converge");
+  return ctx->status();
+}
+
+ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B, int64_t ld,
+                           double thresh, double *Ut, double *lambda, int *n_naf, void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, n_aux >= 1 && n_pairs >= 1 && ld >= n_pairs, "bad sizes");
+  REQUIRE(ctx, B && Ut && lambda && n_naf, "a required pointer is NULL");
+  REQUIRE(ctx, is_device_ptr(B) && is_device_ptr(Ut) && is_device_ptr(lambda), "B, Ut, lambda must be device pointers");
+  REQUIRE(ctx, isfinite(thresh), "thresh must be finite");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  int k = 0, near = 0;
+  if (naf_basis_dev(ctx, ctx->a3, n_aux, n_pairs, B, ld, thresh, Ut, lambda, &k, &near, s) != LTGW_OK)
+    return ctx->status();
+  *n_naf = k;
+  ctx->stats.n_naf = k;
+  ctx->stats.naf_near_threshold = near;
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  return check_flags(ctx, s);
+}
+
+ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                const double *delta, int n_omega, const double *omegas, int n_tau,
+                                const double *x, const double *w, int spin, double *Pi, void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
+  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
+  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
+  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
+  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
+  for (int j = 0; j < n_omega; ++j)
+    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
+  double *d_om, *d_x, *d_w, *d_E, *d_M;
+  auto layout = [&](Arena &A) {
+    d_om = A.take<double>(n_omega);
+    d_x = A.take<double>(std::max(n_tau, 1));
+    d_w = A.take<double>(std::max(n_tau, 1));
+    d_E = A.take<double>(h_E.size());
+    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
+  };
+  ctx->a2.begin_sizing();
+  layout(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
+  layout(ctx->a2);
+  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
+  if (n_tau) {
+    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
+    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
+    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+  }
+  if (ctx->status() != LTGW_OK) return ctx->status();
+  if (polarizability_dev(ctx, N, n_pairs, Bt, n_pairs, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                         spin, Pi, s) != LTGW_OK)
+    return ctx->status();
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));  // the staged grid lives in the workspace
+  return LTGW_OK;
+}
+
+ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C, void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, N >= 1 && n_omega >= 1, "bad sizes");
+  REQUIRE(ctx, Pi && C && Pi != C, "Pi and C must be distinct non-NULL pointers");
+  REQUIRE(ctx, is_device_ptr(Pi) && is_device_ptr(C), "Pi and C must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  double *X0, *X1;
+  auto layout = [&](Arena &A) {
+    X0 = A.take<double>((size_t)n_omega * N * N);
+    X1 = A.take<double>((size_t)n_omega * N * N);
+  };
+  ctx->a2.begin_sizing();
+  layout(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
+  layout(ctx->a2);
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  int nl = 0;
+  cudaError_t e = launch_screen(Pi, N, n_omega, X0, X1, C, ctx->flags, s, &nl);
+  if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  return check_flags(ctx, s);
+}
+
+}  // extern "C"

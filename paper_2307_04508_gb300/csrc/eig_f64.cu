@@ -1,0 +1,424 @@
+// FP64 symmetric eigensolver for the natural auxiliary functions (Sec. 2:
+// diagonalise K, keep the eigenvectors whose eigenvalue exceeds eps_NAF).
+//
+//  1. Householder reduction K = Q T Q^T to tridiagonal T (one reflector per
+//     step: reflector, symmetric mat-vec, rank-2 update of the trailing block);
+//  2. Sturm-sequence count of the eigenvalues of T above the threshold;
+//  3. bisection for the kept eigenvalues, one thread each, with T in shared memory;
+//  4. inverse iteration for their eigenvectors (tridiagonal LU with row
+//     interchanges), with modified Gram-Schmidt inside groups of nearly equal
+//     eigenvalues;
+//  5. symmetric re-orthonormalisation X <- X (3 - X^T X)/2 twice, which removes
+//     the small non-orthogonality inverse iteration leaves between close
+//     eigenvalues without leaving the span of X;
+//  6. back-transformation U = Q X, written transposed as the rows of Ut.
+//
+// Only the kept eigenvectors are formed.  Householder convention: H = 1 - tau v v^T,
+// v_0 = 1, H x = beta e_1.
+#include <float.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ltgw {
+namespace {
+
+constexpr int RB = 1024;  // threads of the single-block kernels
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (lane == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Reflector for column k: x = A[k+1:n, k].
+__global__ void __launch_bounds__(RB) hh_reflector_kernel(const double *A, double *V, double *d,
+                                                          double *e, double *tau, double *scal,
+                                                          int n, int k) {
+  __shared__ double sh[32];
+  const int L = n - k - 1;
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) {
+    double x = A[(int64_t)(k + 1 + i) * n + k];
+    s = fma(x, x, s);
+  }
+  const double sigma = block_sum(s, sh);
+  const double alpha = A[(int64_t)(k + 1) * n + k];
+  double t, beta, sc;
+  if (sigma == 0.0) {
+    t = 0.0; beta = alpha; sc = 0.0;
+  } else {
+    double nrm = sqrt(alpha * alpha + sigma);
+    beta = (alpha >= 0.0) ? -nrm : nrm;
+    t = (beta - alpha) / beta;
+    sc = 1.0 / (alpha - beta);
+  }
+  double *v = V + (int64_t)k * n + (k + 1);
+  for (int i = threadIdx.x; i < L; i += blockDim.x)
+    v[i] = (i == 0) ? 1.0 : A[(int64_t)(k + 1 + i) * n + k] * sc;
+  if (threadIdx.x == 0) {
+    d[k] = A[(int64_t)k * n + k];
+    e[k] = beta;
+    tau[k] = t;
+    scal[0] = t;
+  }
+}
+
+// p = tau * A22 v, one warp per row of the trailing block.
+__global__ void hh_symv_kernel(const double *__restrict__ A, const double *__restrict__ V,
+                               double *__restrict__ p, const double *__restrict__ scal, int n,
+                               int k) {
+  const int L = n - k - 1;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= L) return;
+  const double *row = A + (int64_t)(k + 1 + warp) * n + (k + 1);
+  const double *v = V + (int64_t)k * n + (k + 1);
+  double s = 0.0;
+  for (int j = lane; j < L; j += 32) s = fma(row[j], v[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) p[warp] = scal[0] * s;
+}
+
+// w = p - (tau/2)(p.v) v
+__global__ void __launch_bounds__(RB) hh_w_kernel(const double *V, const double *p, double *w,
+                                                  const double *scal, int n, int k) {
+  __shared__ double sh[32];
+  const int L = n - k - 1;
+  const double *v = V + (int64_t)k * n + (k + 1);
+  double s = 0.0;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) s = fma(p[i], v[i], s);
+  const double gamma = 0.5 * scal[0] * block_sum(s, sh);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) w[i] = p[i] - gamma * v[i];
+}
+
+// A22 -= v w^T + w v^T
+__global__ void hh_update_kernel(double *__restrict__ A, const double *__restrict__ V,
+                                 const double *__restrict__ w, int n, int k) {
+  const int L = n - k - 1;
+  const double *v = V + (int64_t)k * n + (k + 1);
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < LL;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / L), j = (int)(e - (int64_t)i * L);
+    double *a = A + (int64_t)(k + 1 + i) * n + (k + 1 + j);
+    *a -= v[i] * w[j] + w[i] * v[j];
+  }
+}
+
+// Last diagonal / off-diagonal entries once every reflector is applied.
+__global__ void hh_finalize_kernel(const double *A, double *d, double *e, int n) {
+  if (threadIdx.x != 0) return;
+  if (n >= 2) {
+    d[n - 2] = A[(int64_t)(n - 2) * n + (n - 2)];
+    e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+  }
+  d[n - 1] = A[(int64_t)(n - 1) * n + (n - 1)];
+  e[n - 1] = 0.0;
+}
+
+// Number of eigenvalues of T below x (signs of the LDL^T pivots of T - x).
+__device__ int sturm_count(const double *d, const double *e2, int n, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++c;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+// scal[1..3] = lower / upper Gershgorin bound, pivmin; count[0] = #eig > thresh.
+__global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *d, const double *e,
+                                                            int n, double thresh, double *scal,
+                                                            double *e2, int *count) {
+  __shared__ double s_lo[RB], s_hi[RB], s_e[RB];
+  double lo = DBL_MAX, hi = -DBL_MAX, em = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < n - 1) {
+      e2[i] = e[i] * e[i];
+      em = fmax(em, e2[i]);
+    }
+  }
+  s_lo[threadIdx.x] = lo; s_hi[threadIdx.x] = hi; s_e[threadIdx.x] = em;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + s]);
+      s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + s]);
+      s_e[threadIdx.x] = fmax(s_e[threadIdx.x], s_e[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double pivmin = DBL_MIN * fmax(1.0, s_e[0]);
+    scal[1] = s_lo[0] - 2.0 * DBL_EPSILON * fabs(s_lo[0]) - 4.0 * pivmin - 1e-300;
+    scal[2] = s_hi[0] + 2.0 * DBL_EPSILON * fabs(s_hi[0]) + 4.0 * pivmin + 1e-300;
+    scal[3] = pivmin;
+    scal[4] = fmax(fabs(s_lo[0]), fabs(s_hi[0]));  // ||T|| bound
+    int below = sturm_count(d, e2, n, thresh, pivmin);
+    count[0] = n - below;
+    // eigenvalues within 1e-12 * ||T|| of the threshold (tie diagnostics)
+    double tol = 1e-12 * scal[4];
+    count[1] = sturm_count(d, e2, n, thresh + tol, pivmin) - sturm_count(d, e2, n, thresh - tol, pivmin);
+  }
+}
+
+// lam[r] = (n-1-r)-th smallest eigenvalue (r-th largest), r < k.  d and e^2 in smem.
+__global__ void bisect_kernel(const double *d, const double *e2g, const double *scal, int n,
+                              int k, double *lam) {
+  extern __shared__ double sm[];
+  double *sd = sm, *se2 = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = d[i];
+    se2[i] = (i < n - 1) ? e2g[i] : 0.0;
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  const int idx = n - 1 - r;  // ascending index of the wanted eigenvalue
+  double lo = scal[1], hi = scal[2];
+  const double pivmin = scal[3];
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi)
+      break;
+    if (sturm_count(sd, se2, n, mid, pivmin) > idx) hi = mid;
+    else lo = mid;
+  }
+  lam[r] = 0.5 * (lo + hi);
+}
+
+// Inverse iteration for the eigenvectors of T, one thread per group of
+// consecutive eigenvalues closer than gtol (groups are orthogonalised
+// internally).  X[i*k + r] receives the vector of lam[r].
+__global__ void inverse_iteration_kernel(const double *d, const double *e, const double *lam,
+                                         const double *scal, int n, int k, double *X,
+                                         double *lu, int *flags) {
+  const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r0 >= k) return;
+  const double tnorm = scal[4];
+  const double gtol = 1e-7 * tnorm;
+  if (r0 > 0 && lam[r0 - 1] - lam[r0] <= gtol) return;  // not the first of its group
+  int r1 = r0 + 1;
+  while (r1 < k && lam[r1 - 1] - lam[r1] <= gtol) ++r1;
+  // scratch for this thread: dl, dd, du, du2, piv (strided by k for coalescing)
+  double *dl = lu, *dd = lu + (int64_t)n * k, *du = lu + 2 * (int64_t)n * k;
+  double *du2 = lu + 3 * (int64_t)n * k, *pv = lu + 4 * (int64_t)n * k;
+  const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+  double prev = 0.0;
+  for (int r = r0; r < r1; ++r) {
+    double lm = lam[r];
+    if (r > r0) {
+      double pert = 10.0 * DBL_EPSILON * fmax(fabs(lm), tnorm * 1e-3);
+      if (prev - lm < pert) lm = prev - pert;
+    }
+    prev = lm;
+#define S(a, i) a[(int64_t)(i) * k + r]
+    // LU of T - lm with row interchanges
+    for (int i = 0; i < n; ++i) {
+      S(dd, i) = d[i] - lm;
+      if (i < n - 1) { S(dl, i) = e[i]; S(du, i) = e[i]; }
+      S(du2, i) = 0.0;
+    }
+    for (int i = 0; i < n - 1; ++i) {
+      double di = S(dd, i), li = S(dl, i);
+      if (fabs(di) >= fabs(li)) {
+        S(pv, i) = 0.0;
+        if (di == 0.0) { di = tiny; S(dd, i) = di; }
+        double f = li / di;
+        S(dl, i) = f;
+        S(dd, i + 1) -= f * S(du, i);
+      } else {
+        S(pv, i) = 1.0;
+        double f = di / li;
+        S(dd, i) = li;
+        S(dl, i) = f;
+        double tmp = S(du, i);
+        S(du, i) = S(dd, i + 1);
+        S(dd, i + 1) = tmp - f * S(dd, i + 1);
+        if (i < n - 2) {
+          S(du2, i) = S(du, i + 1);
+          S(du, i + 1) = -f * S(du, i + 1);
+        }
+      }
+    }
+    if (S(dd, n - 1) == 0.0) S(dd, n - 1) = tiny;
+    for (int i = 0; i < n; ++i)
+      if (fabs(S(dd, i)) < tiny) S(dd, i) = copysign(tiny, S(dd, i));
+    // start vector: deterministic, no special structure
+    for (int i = 0; i < n; ++i) S(X, i) = 1.0 + 0.5 * sin(0.7548776662 * (i + 1) + 0.5698402910 * (r + 1));
+    for (int iter = 0; iter < 4; ++iter) {
+      // forward: apply L^-1 with the interchanges
+      for (int i = 0; i < n - 1; ++i) {
+        if (S(pv, i) == 0.0) {
+          S(X, i + 1) -= S(dl, i) * S(X, i);
+        } else {
+          double t = S(X, i);
+          S(X, i) = S(X, i + 1);
+          S(X, i + 1) = t - S(dl, i) * S(X, i);
+        }
+      }
+      // backward: U^-1
+      for (int i = n - 1; i >= 0; --i) {
+        double s = S(X, i);
+        if (i + 1 < n) s -= S(du, i) * S(X, i + 1);
+        if (i + 2 < n) s -= S(du2, i) * S(X, i + 2);
+        S(X, i) = s / S(dd, i);
+      }
+      // orthogonalise against the earlier vectors of this group
+      for (int q = r0; q < r; ++q) {
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot += X[(int64_t)i * k + q] * S(X, i);
+        for (int i = 0; i < n; ++i) S(X, i) -= dot * X[(int64_t)i * k + q];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) nrm += S(X, i) * S(X, i);
+      nrm = sqrt(nrm);
+      if (!(nrm > 0.0) || !isfinite(nrm)) { atomicExch(&flags[FLAG_EIG], 1); break; }
+      double inv = 1.0 / nrm;
+      for (int i = 0; i < n; ++i) S(X, i) *= inv;
+    }
+#undef S
+  }
+}
+
+// F = (3 I - G) / 2 for a k x k Gram matrix G (in place).
+__global__ void lowdin_factor_kernel(double *G, int k) {
+  int64_t kk = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kk;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), j = (int)(e - (int64_t)i * k);
+    G[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * G[e];
+  }
+}
+
+// Y = H_0 H_1 ... H_{n-3} X for a slab of 16 columns per block, then Ut = Y^T.
+constexpr int BT_COLS = 16;
+__global__ void __launch_bounds__(256) back_transform_kernel(const double *__restrict__ V,
+                                                             const double *__restrict__ tau,
+                                                             double *__restrict__ X, int n,
+                                                             int k, double *__restrict__ Ut) {
+  __shared__ double red[16][BT_COLS];
+  __shared__ double g[BT_COLS];
+  const int c = threadIdx.x % BT_COLS, rg = threadIdx.x / BT_COLS;  // 16 row groups
+  const int col = blockIdx.x * BT_COLS + c;
+  const bool ok = col < k;
+  for (int kk = n - 3; kk >= 0; --kk) {
+    const double t = tau[kk];
+    if (t == 0.0) continue;  // uniform across the block
+    const double *v = V + (int64_t)kk * n;
+    double s = 0.0;
+    if (ok)
+      for (int r = kk + 1 + rg; r < n; r += 16) s = fma(v[r], X[(int64_t)r * k + col], s);
+    red[rg][c] = s;
+    __syncthreads();
+    if (rg == 0) {
+      double a = 0.0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) a += red[q][c];
+      g[c] = t * a;
+    }
+    __syncthreads();
+    if (ok) {
+      const double gc = g[c];
+      for (int r = kk + 1 + rg; r < n; r += 16) X[(int64_t)r * k + col] -= v[r] * gc;
+    }
+    __syncthreads();
+  }
+  // transpose out: Ut[col][r]
+  for (int q = 0; q < BT_COLS; ++q) {
+    int cc = blockIdx.x * BT_COLS + q;
+    if (cc >= k) break;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) Ut[(int64_t)cc * n + r] = X[(int64_t)r * k + cc];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches) {
+  for (int k = 0; k + 2 < n; ++k) {
+    const int L = n - k - 1;
+    hh_reflector_kernel<<<1, RB, 0, s>>>(w.A, w.V, w.d, w.e, w.tau, w.scal, n, k);
+    int symv_blocks = (L * 32 + 255) / 256;
+    hh_symv_kernel<<<symv_blocks, 256, 0, s>>>(w.A, w.V, w.p, w.scal, n, k);
+    hh_w_kernel<<<1, RB, 0, s>>>(w.V, w.p, w.w, w.scal, n, k);
+    int64_t LL = (int64_t)L * L;
+    int ub = (int)((LL + 255) / 256);
+    if (ub > 152 * 8) ub = 152 * 8;
+    hh_update_kernel<<<ub, 256, 0, s>>>(w.A, w.V, w.w, n, k);
+    *launches += 4;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  hh_finalize_kernel<<<1, 32, 0, s>>>(w.A, w.d, w.e, n);
+  // e2 reuses w.p (length n)
+  tridiag_bounds_kernel<<<1, RB, 0, s>>>(w.d, w.e, n, thresh, w.scal, w.p, w.count);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags, cudaStream_t s,
+                               int *launches) {
+  if (k <= 0) return cudaSuccess;
+  size_t smem = 2 * (size_t)n * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  bisect_kernel<<<(k + 127) / 128, 128, smem, s>>>(w.d, w.p, w.scal, n, k, w.lam);
+  inverse_iteration_kernel<<<(k + 63) / 64, 64, 0, s>>>(w.d, w.e, w.lam, w.scal, n, k, w.X, w.lu,
+                                                        flags);
+  *launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // re-orthonormalise twice: G = X^T X, F = (3 - G)/2, X <- X F
+  double *G = w.lu;                       // k*k scratch (inverse-iteration scratch is free now)
+  double *Xn = w.lu + (int64_t)k * k;     // n*k scratch
+  for (int pass = 0; pass < 2; ++pass) {
+    GemmF64Args g;
+    g.M = k; g.N = k; g.K = n;
+    g.A = w.X; g.lda = k;   // A[kidx][m] = X[i][m]  (M-major)
+    g.B = w.X; g.ldb = k;   // B[kidx][n] = X[i][n]  (N-major)
+    g.C = G; g.ldc = k;
+    g.syrk = 1;
+    e = launch_gemm_f64(g, 1, false, false, s);
+    if (e != cudaSuccess) return e;
+    lowdin_factor_kernel<<<152, 256, 0, s>>>(G, k);
+    GemmF64Args h;
+    h.M = n; h.N = k; h.K = k;
+    h.A = w.X; h.lda = k;   // K-major rows of X
+    h.B = G; h.ldb = k;     // N-major
+    h.C = Xn; h.ldc = k;
+    e = launch_gemm_f64(h, 1, true, false, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(w.X, Xn, (size_t)n * k * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    *launches += 3;
+  }
+  back_transform_kernel<<<(k + BT_COLS - 1) / BT_COLS, 256, 0, s>>>(w.V, w.tau, w.X, n, k, Ut);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace ltgw

@@ -1,0 +1,95 @@
+// Bandwidth-bound helpers of the LT-GW path: pair gaps, the Laplace
+// recombination of the moments onto the frequency grid, strided copies.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ltgw {
+namespace {
+
+__global__ void pair_gaps_kernel(const double *eps, int n_occ, int n_virt, int n_frozen,
+                                 double *delta) {
+  int64_t n_act = n_occ - n_frozen;
+  int64_t total = n_act * n_virt;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = p / n_virt, a = p - i * n_virt;
+    delta[p] = eps[n_occ + a] - eps[n_frozen + i];
+  }
+}
+
+// Pi(i w_j) = alpha * sum_k exp(-w_j^2 x_k) M^k (the frequency recombination
+// of the Laplace moments).  E[j][k] = exp(-w_j^2 x_k) is precomputed on the
+// host.  Each thread owns one matrix element and streams the N_tau moments
+// once, writing all N_omega outputs: N_tau reads + N_omega writes per element.
+template <int MAXT>
+__global__ void recombine_kernel(const double *__restrict__ M, int n_tau,
+                                 const double *__restrict__ E, int n_omega, int64_t n_elem,
+                                 double alpha, double *__restrict__ Pi) {
+  __shared__ double sE[64 * MAXT];
+  for (int i = threadIdx.x; i < n_omega * n_tau; i += blockDim.x) sE[i] = E[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double m[MAXT];
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) m[k] = (k < n_tau) ? M[(int64_t)k * n_elem + e] : 0.0;
+    for (int j = 0; j < n_omega; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < MAXT; ++k)
+        if (k < n_tau) s = fma(sE[j * n_tau + k], m[k], s);
+      Pi[(int64_t)j * n_elem + e] = alpha * s;
+    }
+  }
+}
+
+__global__ void copy_cols_kernel(const double *src, int64_t lds, int64_t c0, double *dst,
+                                 int64_t ldd, int rows, int64_t cols, int64_t strideS,
+                                 int64_t strideD) {
+  int b = blockIdx.z;
+  int r = blockIdx.y;
+  const double *s = src + b * strideS + (int64_t)r * lds + c0;
+  double *d = dst + b * strideD + (int64_t)r * ldd;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cols;
+       c += (int64_t)gridDim.x * blockDim.x)
+    d[c] = s[c];
+}
+
+}  // namespace
+
+cudaError_t launch_pair_gaps(const double *eps, int n_occ, int n_virt, int n_frozen,
+                             double *delta, cudaStream_t s) {
+  int64_t total = (int64_t)(n_occ - n_frozen) * n_virt;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  pair_gaps_kernel<<<blocks, 256, 0, s>>>(eps, n_occ, n_virt, n_frozen, delta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recombine(const double *M, int n_tau, const double *E, int n_omega,
+                             int64_t n_elem, double alpha, double *Pi, cudaStream_t s) {
+  if (n_tau > 32 || n_omega > 64) return cudaErrorInvalidValue;
+  int blocks = (int)((n_elem + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (n_tau <= 8)
+    recombine_kernel<8><<<blocks, 256, 0, s>>>(M, n_tau, E, n_omega, n_elem, alpha, Pi);
+  else if (n_tau <= 16)
+    recombine_kernel<16><<<blocks, 256, 0, s>>>(M, n_tau, E, n_omega, n_elem, alpha, Pi);
+  else
+    recombine_kernel<32><<<blocks, 256, 0, s>>>(M, n_tau, E, n_omega, n_elem, alpha, Pi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_cols(const double *src, int64_t lds, int64_t c0, double *dst,
+                             int64_t ldd, int rows, int64_t cols, int batch,
+                             int64_t strideS, int64_t strideD, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return cudaSuccess;
+  int bx = (int)((cols + 255) / 256);
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, rows, batch);
+  copy_cols_kernel<<<grid, 256, 0, s>>>(src, lds, c0, dst, ldd, rows, cols, strideS, strideD);
+  return cudaGetLastError();
+}
+
+}  // namespace ltgw

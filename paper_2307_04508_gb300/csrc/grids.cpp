@@ -1,0 +1,335 @@
+// Host-side quadrature grids of the LT-GW path.
+//
+//  * modified Gauss-Legendre rule on [0, inf) for the frequency integral of
+//    Eq. CorrelationSelfEnergy: Legendre nodes by Newton's method on the
+//    three-term recurrence, mapped by w = w0 (1+x)/(1-x);
+//  * minimax Laplace grid for Eq. LT: 1/X ~ sum_m w_m exp(-X x_m) on [a, b]
+//    (Sec. 3: a = gap^2 + w_min^2, b = max(largest gap^2, 1e4)), minimising the
+//    error of 1/X scaled by a (the criterion the paper's epsilon_LT bounds).
+//    Start: the best trapezoid rule in t = log(tau) for 1/X = int exp(t - X e^t) dt
+//    over a search of its offset and step; then L_p fits for p = 2..128, which
+//    approach the minimax solution; then a Remez exchange on the 2k+1
+//    alternation points.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/ltgw.h"
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- Legendre
+void legendre_nodes(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 1; j < n; ++j) {
+        double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) {
+        // refresh the derivative at the converged node
+        p0 = 1.0; p1 = z;
+        for (int j = 1; j < n; ++j) {
+          double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+          p0 = p1;
+          p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[i] = -z;             // ascending
+    x[n - 1 - i] = z;
+    w[i] = wt;
+    w[n - 1 - i] = wt;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// ---------------------------------------------------------------- Laplace fit
+// Work on y = X / a in [1, R]; the grid for [a, b] is x_m = alpha_m / a,
+// w_m = omega_m / a.  Parameters are logs: alpha = e^p, omega = e^q.  The
+// error is absolute in 1/y, i.e. the error of 1/X scaled by a.
+struct ExpSum {
+  int k = 0;
+  std::vector<double> p, q;  // log alpha, log omega
+  double s(double y) const {
+    double t = 0.0;
+    for (int v = 0; v < k; ++v) t += exp(q[v] - exp(p[v]) * y);
+    return t;
+  }
+  double r(double y) const { return 1.0 / y - s(y); }
+};
+
+std::vector<double> log_grid(double R, int n) {
+  std::vector<double> y(n + 1);
+  double lr = log(R);
+  for (int i = 0; i <= n; ++i) y[i] = exp(lr * i / n);
+  return y;
+}
+
+double sup_err(const ExpSum &f, const std::vector<double> &y) {
+  double m = 0.0;
+  for (double v : y) m = std::max(m, fabs(f.r(v)));
+  return m;
+}
+
+ExpSum sinc_rule(int k, double t0, double h) {
+  ExpSum f;
+  f.k = k;
+  f.p.resize(k);
+  f.q.resize(k);
+  for (int v = 0; v < k; ++v) {
+    double t = t0 + h * v;
+    f.p[v] = t;              // alpha = e^t
+    f.q[v] = log(h) + t;     // omega = h e^t
+  }
+  return f;
+}
+
+// Solve the dense system M x = b by Gaussian elimination with partial
+// pivoting; returns false when singular.
+bool dense_solve(std::vector<double> &M, std::vector<double> &b, int n) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(M[r * n + c]) > fabs(M[piv * n + c])) piv = r;
+    if (!(fabs(M[piv * n + c]) > 1e-300)) return false;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) std::swap(M[c * n + j], M[piv * n + j]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = M[r * n + c] / M[c * n + c];
+      if (f == 0.0) continue;
+      for (int j = c; j < n; ++j) M[r * n + j] -= f * M[c * n + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double s = b[c];
+    for (int j = c + 1; j < n; ++j) s -= M[c * n + j] * b[j];
+    b[c] = s / M[c * n + c];
+  }
+  return true;
+}
+
+// Minimise sum_i |r(y_i)|^pw for pw = 2, 4, ..., 128 (Levenberg-Marquardt on
+// the residuals |r|^{pw/2} sign r): the L_p minimisers approach the minimax
+// solution and give Remez a start with the full alternation.
+void lp_continuation(ExpSum &f, const std::vector<double> &y) {
+  const int k = f.k, m = 2 * k, n = (int)y.size();
+  std::vector<double> J((size_t)n * m), fr(n), H(m * m), g(m);
+  for (double pw = 2.0; pw <= 128.0; pw *= 2.0) {
+    double lam = 1e-2;
+    for (int it = 0; it < 80; ++it) {
+      double sc = sup_err(f, y);
+      if (!(sc > 0.0)) return;
+      double obj = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double yi = y[i], s = 0.0;
+        double *Ji = &J[(size_t)i * m];
+        for (int v = 0; v < k; ++v) {
+          double al = exp(f.p[v]), t = exp(f.q[v] - al * yi);
+          s += t;
+          Ji[v] = yi * al * t;   // d r / d p_v
+          Ji[k + v] = -t;        // d r / d q_v
+        }
+        double rn = (1.0 / yi - s) / sc;
+        double a = fabs(rn);
+        double fi = pow(a, 0.5 * pw) * (rn >= 0 ? 1.0 : -1.0);
+        double dfac = 0.5 * pw * pow(a, 0.5 * pw - 1.0) / sc;
+        for (int c = 0; c < m; ++c) Ji[c] *= dfac;
+        fr[i] = fi;
+        obj += fi * fi;
+      }
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(g.begin(), g.end(), 0.0);
+      for (int i = 0; i < n; ++i) {
+        const double *Ji = &J[(size_t)i * m];
+        for (int a = 0; a < m; ++a) {
+          g[a] += Ji[a] * fr[i];
+          for (int b = 0; b <= a; ++b) H[a * m + b] += Ji[a] * Ji[b];
+        }
+      }
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < a; ++b) H[b * m + a] = H[a * m + b];
+      bool improved = false;
+      for (int tries = 0; tries < 30; ++tries) {
+        std::vector<double> M = H, d = g;
+        for (int a = 0; a < m; ++a) M[a * m + a] += lam * (H[a * m + a] + 1e-12);
+        if (!dense_solve(M, d, m)) { lam *= 5.0; continue; }
+        ExpSum t = f;
+        for (int v = 0; v < k; ++v) { t.p[v] -= d[v]; t.q[v] -= d[k + v]; }
+        double o2 = 0.0;
+        bool fin = true;
+        for (int i = 0; i < n && fin; ++i) {
+          double rr = fabs(t.r(y[i]) / sc);
+          double fi = pow(rr, 0.5 * pw);
+          o2 += fi * fi;
+          fin = isfinite(o2);
+        }
+        if (fin && o2 < obj) {
+          f = t;
+          lam = std::max(lam / 3.0, 1e-10);
+          improved = true;
+          break;
+        }
+        lam *= 5.0;
+      }
+      if (!improved) break;
+    }
+  }
+}
+
+// Alternating extrema of r on [1, R]: the largest |r| in each run of equal
+// sign, trimmed at the smaller end down to `want` points.
+bool find_extrema(const ExpSum &f, double R, int want, std::vector<double> &ys) {
+  std::vector<double> y = log_grid(R, 20000);
+  std::vector<double> ey, er;
+  int cur = 0;
+  double by = 1.0, br = 0.0;
+  for (double v : y) {
+    double r = f.r(v);
+    int sg = (r >= 0.0) ? 1 : -1;
+    if (cur == 0) { cur = sg; by = v; br = r; continue; }
+    if (sg != cur) {
+      ey.push_back(by); er.push_back(br);
+      cur = sg; by = v; br = r;
+    } else if (fabs(r) > fabs(br)) {
+      by = v; br = r;
+    }
+  }
+  ey.push_back(by); er.push_back(br);
+  while ((int)ey.size() > want) {
+    if (fabs(er.front()) < fabs(er.back())) { ey.erase(ey.begin()); er.erase(er.begin()); }
+    else { ey.pop_back(); er.pop_back(); }
+  }
+  if ((int)ey.size() != want) return false;
+  ys = ey;
+  return true;
+}
+
+// Newton on r(y_i) = (-1)^i E (i = 0..2k) in (p, q, E), damped.
+bool remez_step(ExpSum &f, const std::vector<double> &ys, double &E) {
+  const int k = f.k, n = 2 * k + 1;
+  double e0 = 0.0;
+  for (int i = 0; i < n; ++i) e0 += f.r(ys[i]) * ((i % 2) ? -1.0 : 1.0);
+  E = e0 / n;
+  auto resid = [&](const ExpSum &g, double Eg) {
+    double fn = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double Fi = g.r(ys[i]) - ((i % 2) ? -1.0 : 1.0) * Eg;
+      fn += Fi * Fi;
+    }
+    return sqrt(fn);
+  };
+  for (int it = 0; it < 50; ++it) {
+    std::vector<double> J(n * n), F(n);
+    for (int i = 0; i < n; ++i) {
+      double y = ys[i], sg = (i % 2) ? -1.0 : 1.0, s = 0.0;
+      for (int v = 0; v < k; ++v) {
+        double al = exp(f.p[v]), t = exp(f.q[v] - al * y);
+        s += t;
+        J[i * n + v] = y * al * t;
+        J[i * n + k + v] = -t;
+      }
+      J[i * n + 2 * k] = -sg;
+      F[i] = 1.0 / y - s - sg * E;
+    }
+    double fn = resid(f, E);
+    if (fn < 1e-15 * std::max(1e-300, fabs(E))) return true;
+    if (!dense_solve(J, F, n)) return false;
+    double step = 1.0;
+    bool ok = false;
+    for (int ls = 0; ls < 40; ++ls) {
+      ExpSum g = f;
+      for (int v = 0; v < k; ++v) { g.p[v] -= step * F[v]; g.q[v] -= step * F[k + v]; }
+      double Eg = E - step * F[2 * k];
+      if (resid(g, Eg) < fn) { f = g; E = Eg; ok = true; break; }
+      step *= 0.5;
+    }
+    if (!ok) return true;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" ltgw_status ltgw_gl_grid(int n, double omega0, double *omega, double *weight) {
+  if (n < 1 || n > 4096 || !(omega0 > 0.0) || !omega || !weight) return LTGW_ERR_BAD_ARG;
+  std::vector<double> x, w;
+  legendre_nodes(n, x, w);
+  for (int i = 0; i < n; ++i) {
+    omega[i] = omega0 * (1.0 + x[i]) / (1.0 - x[i]);
+    weight[i] = w[i] * 2.0 * omega0 / ((1.0 - x[i]) * (1.0 - x[i]));
+  }
+  return LTGW_OK;
+}
+
+extern "C" ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *x, double *w,
+                                         double *max_err) {
+  if (n_tau < 1 || n_tau > 64 || !(a > 0.0) || !(b > a) || !x || !w) return LTGW_ERR_BAD_ARG;
+  const double R = b / a;
+  const int k = n_tau;
+  const double lr = log(R);
+  // 1. best trapezoid rule in t = log(tau) over a coarse search of offset and step
+  std::vector<double> coarse = log_grid(R, 600);
+  ExpSum best;
+  double best_err = 1e300;
+  for (int ih = 0; ih < 40; ++ih) {
+    double h = 0.3 + 3.7 * ih / 39.0;
+    for (int it = 0; it < 60; ++it) {
+      double t0 = -lr - 6.0 + (lr + 8.0) * it / 59.0;
+      ExpSum f = sinc_rule(k, t0, h);
+      double e = sup_err(f, coarse);
+      if (e < best_err) { best_err = e; best = f; }
+    }
+  }
+  std::vector<double> fine = log_grid(R, 40000);
+  // 2. L_p continuation toward the minimax solution
+  ExpSum cur = best;
+  lp_continuation(cur, log_grid(R, 3000));
+  double e_cur = sup_err(cur, fine);
+  best_err = sup_err(best, fine);
+  if (e_cur < best_err) { best = cur; best_err = e_cur; }
+  // 3. Remez exchange polish; keep the best grid seen
+  for (int outer = 0; outer < 30; ++outer) {
+    std::vector<double> ys;
+    if (!find_extrema(cur, R, 2 * k + 1, ys)) break;
+    ExpSum trial = cur;
+    double E = 0.0;
+    if (!remez_step(trial, ys, E)) break;
+    bool finite = true;
+    for (int v = 0; v < k; ++v) finite = finite && isfinite(trial.p[v]) && isfinite(trial.q[v]);
+    if (!finite) break;
+    double e = sup_err(trial, fine);
+    if (!(e < 1.0)) break;
+    cur = trial;
+    if (e < best_err) { best_err = e; best = trial; }
+    if (fabs(e - fabs(E)) <= 1e-4 * fabs(E)) break;  // equioscillation reached
+  }
+  // 4. map back to [a, b]; ascending x
+  std::vector<std::pair<double, double>> g(k);
+  for (int v = 0; v < k; ++v) g[v] = {exp(best.p[v]) / a, exp(best.q[v]) / a};
+  std::sort(g.begin(), g.end());
+  for (int v = 0; v < k; ++v) { x[v] = g[v].first; w[v] = g[v].second; }
+  if (max_err) *max_err = best_err;
+  return LTGW_OK;
+}

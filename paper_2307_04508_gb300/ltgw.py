@@ -1,0 +1,216 @@
+"""Python binding of the LT-GW C ABI (include/ltgw.h): argument marshalling only.
+
+Every function here calls the CUDA library ``libltgw.so`` built in-tree by
+``paper_2307_04508_gb300.build``; nothing is computed in Python.  Arrays may be
+numpy arrays (host memory) or torch CUDA tensors (device memory); the library
+detects which.  Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libltgw.so")
+
+LTGW_OK, LTGW_ERR_BAD_ARG, LTGW_ERR_NOMEM, LTGW_ERR_NOT_SPD = 0, 1, 2, 3
+LTGW_ERR_NO_CONVERGE, LTGW_ERR_DEVICE, LTGW_ERR_EIG, LTGW_ERR_NO_NAF = 4, 5, 6, 7
+LTGW_FP64, LTGW_BF16X3, LTGW_FP8 = 0, 1, 2
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_occ", ctypes.c_int), ("n_virt", ctypes.c_int), ("n_frozen", ctypes.c_int),
+                ("n_aux", ctypes.c_int), ("n_omega", ctypes.c_int), ("n_tau", ctypes.c_int),
+                ("omega0", ctypes.c_double), ("naf_thresh", ctypes.c_double), ("spin", ctypes.c_int),
+                ("use_laplace", ctypes.c_int), ("precision", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_naf", ctypes.c_int), ("n_pade", ctypes.c_int), ("n_tau", ctypes.c_int),
+                ("naf_near_threshold", ctypes.c_int), ("lt_max_rel_err", ctypes.c_double),
+                ("ms_naf", ctypes.c_double), ("ms_pi", ctypes.c_double), ("ms_screen", ctypes.c_double),
+                ("ms_wnm", ctypes.c_double), ("ms_sigma_qp", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_pi_kernel", ctypes.c_double), ("pi_kernel_launches", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LtgwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ltgw status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# exported symbols and their ctypes signatures
+_P, _I, _D, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+SIGNATURES = {
+    "ltgw_create": (_I, [ctypes.POINTER(ctypes.c_void_p), _I]),
+    "ltgw_destroy": (None, [_P]),
+    "ltgw_status_string": (ctypes.c_char_p, [_I]),
+    "ltgw_last_error": (ctypes.c_char_p, [_P]),
+    "ltgw_set_timing": (_I, [_P, _I]),
+    "ltgw_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "ltgw_solve": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "ltgw_gl_grid": (_I, [_I, _D, _P, _P]),
+    "ltgw_laplace_grid": (_I, [_I, _D, _D, _P, _P, _P]),
+    "ltgw_naf_basis": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
+    "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
+}
+
+
+def load():
+    """Load libltgw.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"LT-GW CUDA library not built ({LIB_PATH} missing); "
+                               "run `python -m paper_2307_04508_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (contiguous), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def status_string(st: int) -> str:
+    return load().ltgw_status_string(st).decode()
+
+
+def gl_grid(n: int, omega0: float = 0.5):
+    om, wt = np.zeros(n), np.zeros(n)
+    st = load().ltgw_gl_grid(n, omega0, om.ctypes.data, wt.ctypes.data)
+    if st:
+        raise LtgwError(st, status_string(st))
+    return om, wt
+
+
+def laplace_grid(n_tau: int, a: float, b: float):
+    x, w, e = np.zeros(n_tau), np.zeros(n_tau), ctypes.c_double()
+    st = load().ltgw_laplace_grid(n_tau, a, b, x.ctypes.data, w.ctypes.data, ctypes.byref(e))
+    if st:
+        raise LtgwError(st, status_string(st))
+    return x, w, e.value
+
+
+class Context:
+    """One ltgw_ctx on a CUDA device (ltgw_create / ltgw_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        st = self._lib.ltgw_create(ctypes.byref(h), device)
+        if st:
+            raise LtgwError(st, f"ltgw_create failed: {status_string(st)}")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ltgw_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, allow=()):
+        if st and st not in allow:
+            raise LtgwError(st, self._lib.ltgw_last_error(self.handle).decode())
+        return st
+
+    def set_timing(self, on: bool):
+        self._check(self._lib.ltgw_set_timing(self.handle, int(bool(on))))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._lib.ltgw_get_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def solve(self, params: Params, eps, B_ov, B_tgt, targets, shift, sigma_out, e_qp_out,
+              status_out, tau_x=None, tau_w=None, stream=None, allow_no_converge=True) -> int:
+        """ltgw_solve on caller-provided buffers (numpy = host, torch CUDA = device)."""
+        n_tgt = int(targets.shape[0])
+        st = self._lib.ltgw_solve(self.handle, ctypes.byref(params), _ptr(eps), _ptr(B_ov), _ptr(B_tgt),
+                                  _ptr(targets), n_tgt, _ptr(shift), _ptr(tau_x), _ptr(tau_w),
+                                  _ptr(sigma_out), _ptr(e_qp_out), _ptr(status_out), _stream_ptr(stream))
+        return self._check(st, allow=(LTGW_ERR_NO_CONVERGE,) if allow_no_converge else ())
+
+    def naf_basis(self, B, n_pairs: int, ld: int, thresh: float, Ut, lam, stream=None) -> int:
+        k = ctypes.c_int()
+        st = self._lib.ltgw_naf_basis(self.handle, int(B.shape[0]), n_pairs, _ptr(B), ld, thresh, _ptr(Ut),
+                                      _ptr(lam), ctypes.byref(k), _stream_ptr(stream))
+        self._check(st)
+        return k.value
+
+    def polarizability(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None, stream=None):
+        N, n_pairs = int(Bt.shape[0]), int(Bt.shape[1])
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        n_tau = 0 if x is None else len(x)
+        xx = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        st = self._lib.ltgw_polarizability(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om), _ptr(om),
+                                           n_tau, _ptr(xx), _ptr(ww), spin, _ptr(Pi), _stream_ptr(stream))
+        self._check(st)
+
+    def screen(self, Pi, C, stream=None):
+        n_omega, N = int(Pi.shape[0]), int(Pi.shape[1])
+        self._check(self._lib.ltgw_screen(self.handle, N, n_omega, _ptr(Pi), _ptr(C), _stream_ptr(stream)))
+
+
+def make_params(n_occ, n_virt, n_aux, n_frozen=0, n_omega=32, n_tau=8, omega0=0.5, naf_thresh=-1.0,
+                spin=2, use_laplace=False, precision=LTGW_FP64) -> Params:
+    return Params(n_occ, n_virt, n_frozen, n_aux, n_omega, n_tau if use_laplace else 0, omega0,
+                  naf_thresh, spin, int(bool(use_laplace)), precision, 0)
+
+
+def solve_problem(ctx: Context, prob, n_omega=32, n_tau=8, naf_thresh=-1.0, use_laplace=False, spin=2,
+                  omega0=0.5, tau=None, device_arrays=None, stream=None):
+    """Solve a synthetic ``Problem`` (host numpy arrays) and return
+    (sigma [T][n_omega] complex, e_qp [T], status [T]).  ``device_arrays``,
+    if given, is a dict of torch CUDA tensors used instead of the host inputs."""
+    p = make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, n_omega, n_tau, omega0, naf_thresh,
+                    spin, use_laplace)
+    T = len(prob.targets)
+    sig = np.zeros((T, n_omega, 2))
+    e = np.zeros(T)
+    st = np.zeros(T, dtype=np.int32)
+    src = device_arrays or {}
+    tx, tw = (None, None) if tau is None else (np.ascontiguousarray(tau[0]), np.ascontiguousarray(tau[1]))
+    ctx.solve(p, src.get("eps", prob.eps), src.get("B_ov", prob.B_ov), src.get("B_tgt", prob.B_tgt),
+              src.get("targets", np.ascontiguousarray(prob.targets, dtype=np.int32)), src.get("shift", prob.shift),
+              sig, e, st, tau_x=tx, tau_w=tw, stream=stream)
+    return sig[..., 0] + 1j * sig[..., 1], e, st
