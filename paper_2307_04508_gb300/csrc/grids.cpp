@@ -7,13 +7,14 @@
 //    (Sec. 3: a = gap^2 + w_min^2, b = max(largest gap^2, 1e4)), minimising the
 //    error of 1/X scaled by a (the criterion the paper's epsilon_LT bounds).
 //    Start: the best trapezoid rule in t = log(tau) for 1/X = int exp(t - X e^t) dt
-//    over a search of its offset and step; then L_p fits for p = 2..128, which
+//    over a search of its offset and step; then L_p fits for p = 2..64, which
 //    approach the minimax solution; then a Remez exchange on the 2k+1
 //    alternation points.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "../../include/ltgw.h"
@@ -136,9 +137,9 @@ bool dense_solve(std::vector<double> &M, std::vector<double> &b, int n) {
 void lp_continuation(ExpSum &f, const std::vector<double> &y) {
   const int k = f.k, m = 2 * k, n = (int)y.size();
   std::vector<double> J((size_t)n * m), fr(n), H(m * m), g(m);
-  for (double pw = 2.0; pw <= 128.0; pw *= 2.0) {
+  for (double pw = 2.0; pw <= 64.0; pw *= 2.0) {
     double lam = 1e-2;
-    for (int it = 0; it < 80; ++it) {
+    for (int it = 0; it < 40; ++it) {
       double sc = sup_err(f, y);
       if (!(sc > 0.0)) return;
       double obj = 0.0;
@@ -201,7 +202,7 @@ void lp_continuation(ExpSum &f, const std::vector<double> &y) {
 // Alternating extrema of r on [1, R]: the largest |r| in each run of equal
 // sign, trimmed at the smaller end down to `want` points.
 bool find_extrema(const ExpSum &f, double R, int want, std::vector<double> &ys) {
-  std::vector<double> y = log_grid(R, 20000);
+  std::vector<double> y = log_grid(R, 8000);
   std::vector<double> ey, er;
   int cur = 0;
   double by = 1.0, br = 0.0;
@@ -283,33 +284,22 @@ extern "C" ltgw_status ltgw_gl_grid(int n, double omega0, double *omega, double 
   return LTGW_OK;
 }
 
-extern "C" ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *x, double *w,
-                                         double *max_err) {
-  if (n_tau < 1 || n_tau > 64 || !(a > 0.0) || !(b > a) || !x || !w) return LTGW_ERR_BAD_ARG;
-  const double R = b / a;
-  const int k = n_tau;
-  const double lr = log(R);
-  // 1. best trapezoid rule in t = log(tau) over a coarse search of offset and step
-  std::vector<double> coarse = log_grid(R, 600);
-  ExpSum best;
-  double best_err = 1e300;
-  for (int ih = 0; ih < 40; ++ih) {
-    double h = 0.3 + 3.7 * ih / 39.0;
-    for (int it = 0; it < 60; ++it) {
-      double t0 = -lr - 6.0 + (lr + 8.0) * it / 59.0;
-      ExpSum f = sinc_rule(k, t0, h);
-      double e = sup_err(f, coarse);
-      if (e < best_err) { best_err = e; best = f; }
-    }
-  }
-  std::vector<double> fine = log_grid(R, 40000);
-  // 2. L_p continuation toward the minimax solution
-  ExpSum cur = best;
-  lp_continuation(cur, log_grid(R, 3000));
-  double e_cur = sup_err(cur, fine);
-  best_err = sup_err(best, fine);
-  if (e_cur < best_err) { best = cur; best_err = e_cur; }
-  // 3. Remez exchange polish; keep the best grid seen
+namespace {
+
+// Fitted grids on [1, R] by (k, R), reused by later calls: an exact hit is
+// returned as is; a fit for the same k within a factor 8 in R seeds the Remez
+// exchange directly.  Process-wide, guarded by a mutex.
+struct CachedFit {
+  int k;
+  double R, err;
+  ExpSum f;
+};
+std::mutex g_fit_mutex;
+std::vector<CachedFit> g_fit_cache;
+
+// Remez exchange from `cur`; returns the best grid seen and its error.
+void remez_polish(ExpSum &best, double &best_err, ExpSum cur, double R, const std::vector<double> &fine) {
+  const int k = cur.k;
   for (int outer = 0; outer < 30; ++outer) {
     std::vector<double> ys;
     if (!find_extrema(cur, R, 2 * k + 1, ys)) break;
@@ -325,11 +315,75 @@ extern "C" ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *
     if (e < best_err) { best_err = e; best = trial; }
     if (fabs(e - fabs(E)) <= 1e-4 * fabs(E)) break;  // equioscillation reached
   }
-  // 4. map back to [a, b]; ascending x
+}
+
+ExpSum fit_unit_interval(int k, double R, double &err_out) {
+  const double lr = log(R);
+  std::vector<double> fine = log_grid(R, 12000);
+  {
+    std::lock_guard<std::mutex> lock(g_fit_mutex);
+    for (const CachedFit &c : g_fit_cache)
+      if (c.k == k && c.R == R) { err_out = c.err; return c.f; }
+  }
+  ExpSum best;
+  double best_err = 1e300;
+  // warm start from a cached fit for the same k at a nearby R
+  ExpSum seed;
+  bool have_seed = false;
+  {
+    std::lock_guard<std::mutex> lock(g_fit_mutex);
+    double bestd = log(8.0);
+    for (const CachedFit &c : g_fit_cache)
+      if (c.k == k && fabs(log(c.R / R)) < bestd) { bestd = fabs(log(c.R / R)); seed = c.f; have_seed = true; }
+  }
+  if (have_seed) {
+    best = seed;
+    best_err = sup_err(seed, fine);
+    remez_polish(best, best_err, seed, R, fine);
+  }
+  if (!have_seed || !(best_err < 1.0)) {
+    // 1. best trapezoid rule in t = log(tau) over a coarse search of offset and step
+    std::vector<double> coarse = log_grid(R, 300);
+    best_err = 1e300;
+    for (int ih = 0; ih < 30; ++ih) {
+      double h = 0.3 + 3.7 * ih / 29.0;
+      for (int it = 0; it < 40; ++it) {
+        double t0 = -lr - 6.0 + (lr + 8.0) * it / 39.0;
+        ExpSum f = sinc_rule(k, t0, h);
+        double e = sup_err(f, coarse);
+        if (e < best_err) { best_err = e; best = f; }
+      }
+    }
+    // 2. L_p continuation toward the minimax solution
+    ExpSum cur = best;
+    lp_continuation(cur, log_grid(R, 800));
+    double e_cur = sup_err(cur, fine);
+    best_err = sup_err(best, fine);
+    if (e_cur < best_err) { best = cur; best_err = e_cur; }
+    // 3. Remez exchange polish
+    remez_polish(best, best_err, cur, R, fine);
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_fit_mutex);
+    if (g_fit_cache.size() < 4096) g_fit_cache.push_back({k, R, best_err, best});
+  }
+  err_out = best_err;
+  return best;
+}
+
+}  // namespace
+
+extern "C" ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *x, double *w,
+                                         double *max_err) {
+  if (n_tau < 1 || n_tau > 64 || !(a > 0.0) || !(b > a) || !x || !w) return LTGW_ERR_BAD_ARG;
+  const int k = n_tau;
+  double err = 0.0;
+  ExpSum best = fit_unit_interval(k, b / a, err);
+  // map back to [a, b]; ascending x
   std::vector<std::pair<double, double>> g(k);
   for (int v = 0; v < k; ++v) g[v] = {exp(best.p[v]) / a, exp(best.q[v]) / a};
   std::sort(g.begin(), g.end());
   for (int v = 0; v < k; ++v) { x[v] = g[v].first; w[v] = g[v].second; }
-  if (max_err) *max_err = best_err;
+  if (max_err) *max_err = err;
   return LTGW_OK;
 }
