@@ -165,6 +165,31 @@ ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const dou
 ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C,
                         void *stream);
 
+/* ---- allocation-free screening ------------------------------------------ */
+
+/* Largest n_omega * N * N accepted by ltgw_screen_static. */
+#define LTGW_SCREEN_STATIC_MAX_ELEMS (1u << 19)
+
+/* The paper has no counterpart to this entry point.  It computes the same
+ * C_j = [1 - Pi_j]^-1 - 1 as ltgw_screen, for callers that cannot allocate
+ * device memory when they call: a process whose device memory is already
+ * claimed in full by another allocator (a framework's caching allocator or a
+ * pre-reserved pool), or a latency-sensitive caller that cannot afford
+ * cudaMalloc/cudaFree, which may block and synchronise the device.  It needs
+ * no context and calls no allocating routine: its scratch (two sweep buffers
+ * of LTGW_SCREEN_STATIC_MAX_ELEMS doubles, 4 MiB each, and an error flag) is a
+ * fixed device array that every GPU loading the library holds until the
+ * process exits.
+ *   N, n_omega  matrix size and count, n_omega * N * N <= LTGW_SCREEN_STATIC_MAX_ELEMS;
+ *               larger sizes return LTGW_ERR_BAD_ARG before any GPU work
+ *   Pi, C       device [n_omega][N][N] on the current device, distinct
+ * Runs on `stream` and synchronises it; LTGW_ERR_NOT_SPD if a pivot was not
+ * positive.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array per device, so calls that
+ * overlap on the GPU (other streams, other host threads) race. */
+ltgw_status ltgw_screen_static(int N, int n_omega, const double *Pi, double *C, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,7 +62,10 @@ SIGNATURES = {
     "ltgw_naf_basis": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
+    "ltgw_screen_static": (_I, [_I, _I, _P, _P, _P]),
 }
+
+SCREEN_STATIC_MAX_ELEMS = 1 << 19
 
 
 def load():
@@ -189,6 +192,13 @@ class Context:
     def screen(self, Pi, C, stream=None):
         n_omega, N = int(Pi.shape[0]), int(Pi.shape[1])
         self._check(self._lib.ltgw_screen(self.handle, N, n_omega, _ptr(Pi), _ptr(C), _stream_ptr(stream)))
+
+
+def screen_static(Pi, C, stream=None) -> int:
+    """ltgw_screen_static: the screening step with library-held scratch (no
+    allocation); returns the status code."""
+    n_omega, N = int(Pi.shape[0]), int(Pi.shape[1])
+    return load().ltgw_screen_static(N, n_omega, _ptr(Pi), _ptr(C), _stream_ptr(stream))
 
 
 def make_params(n_occ, n_virt, n_aux, n_frozen=0, n_omega=32, n_tau=8, omega0=0.5, naf_thresh=-1.0,
