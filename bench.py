@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="mid", choices=["tiny", "mid"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3"],
+                    help="fp64: every contraction in FP64; bf16x3: Pi on the tensor cores (split BF16)")
     return ap.parse_args()
 
 
@@ -155,8 +157,9 @@ def run_gpu(args):
     ctx = ltgw.Context(local)
     stream = torch.cuda.Stream()
     T = len(prob.targets)
+    mixed = args.precision == "bf16x3"
     p = ltgw.make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, cfg["n_omega"], cfg["n_tau"],
-                         0.5, cfg["naf_thresh"], 2, True)
+                         0.5, cfg["naf_thresh"], 2, True, ltgw.LTGW_BF16X3 if mixed else ltgw.LTGW_FP64)
     # device-resident inputs and outputs
     dev = {"eps": torch.from_numpy(prob.eps).cuda(), "B_ov": torch.from_numpy(prob.B_ov).cuda(),
            "B_tgt": torch.from_numpy(prob.B_tgt).cuda(),
@@ -207,6 +210,19 @@ def run_gpu(args):
     clocks = clk.summary()
     alu_peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
     achieved = pi_flops / (pi_avg_ms / 1e3) / 1e12
+    if mixed:
+        # three BF16 products (hi*hi, hi*lo, lo*hi) per useful product
+        tc_achieved = 3 * pi_flops / (pi_avg_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "tc_split_gemm_kernel (Pi(tau_k) split-BF16 SYRK, tcgen05)",
+                    "achieved": tc_achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": tc_achieved / pk["bf16_tflops"],
+                    "peak_source": f"bf16_tflops (burst) of {src} MEASURED_PEAKS.json",
+                    "flops_per_launch": 3 * pi_flops, "traffic": None}
+    else:
+        roofline = {"bound": "alu", "kernel": "gemm_f64_kernel (Pi(tau_k) scaled SYRK)",
+                    "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                    "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
+                    "flops_per_launch": pi_flops, "traffic": None}
     # end-to-end: host (pinned) inputs and outputs through the same C ABI call
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
            {"eps": prob.eps, "B_ov": prob.B_ov, "B_tgt": prob.B_tgt,
@@ -226,16 +242,14 @@ def run_gpu(args):
     e2e = world * e2e_steps / (time.perf_counter() - t0)
     line = {"metric": "G0W0 solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "l2": "256 MB buffer written between steps; inputs 553 MB > L2",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if mixed else "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": args.precision,
+                       "l2": "256 MB buffer written between steps; inputs 553 MB > L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "pi_build_tflops": achieved, "n_naf": N,
             "stage_ms": {k: st[k] for k in ("ms_naf", "ms_pi", "ms_screen", "ms_wnm", "ms_sigma_qp", "ms_total")},
-            "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel (Pi(tau_k) scaled SYRK)",
-                         "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                         "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
-                         "traffic": None, "algorithmic_bytes": pi_bytes_min},
+            "roofline": roofline, "pi_algorithmic_bytes": pi_bytes_min,
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "peaks_source": src}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -250,7 +264,8 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": n / dt, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{n} full direct-AC solve(s) of the same workload (numpy FP64)"}
         e_gpu = out_host[1].numpy()
-        line["lt_vs_direct_qp_max_mev"] = float(np.abs(e_gpu - e_o).max() * HA2MEV)
+        key = "qp_max_mev_vs_fp64_direct_oracle"
+        line[key] = float(np.abs(e_gpu - e_o).max() * HA2MEV)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -74,7 +74,8 @@ typedef struct {
   double naf_thresh;  /* < 0: no NAF; >= 0: keep eigenvalues of K above it        */
   int spin;           /* 1 (spin orbitals) or 2 (closed shell)                    */
   int use_laplace;    /* 0: Pi from Eq. Pi; 1: Pi from the Laplace moments M^m     */
-  int precision;      /* LTGW_FP64 (the only value accepted by this version)      */
+  int precision;      /* LTGW_FP64, or LTGW_BF16X3: Pi on the tensor cores with    */
+                      /* split-BF16 operands (see ltgw_polarizability_mixed)      */
   int reserved;       /* must be 0                                                */
 } ltgw_params;
 
@@ -158,6 +159,17 @@ ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const dou
                                 const double *delta, int n_omega, const double *omegas,
                                 int n_tau, const double *x, const double *w, int spin,
                                 double *Pi, void *stream);
+
+/* The same polarisability in the mixed-precision form: every product of the
+ * pair sum runs on the tensor cores with BF16 hi/lo split operands
+ * (x = bf16(x) + bf16(x - bf16(x)); hi*hi + hi*lo + lo*hi), the per-pair scale
+ * applied while the operands are loaded, FP32 accumulation drained to FP64
+ * every 16384 pairs.  Same arguments and layout as ltgw_polarizability;
+ * relative error about 1e-5.  Synchronises. */
+ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                      const double *delta, int n_omega, const double *omegas,
+                                      int n_tau, const double *x, const double *w, int spin,
+                                      double *Pi, void *stream);
 
 /* Screening (Eq. ScreenedCoulombOrbital): C_j = [1 - Pi_j]^-1 - 1 for each of
  * n_omega matrices (device [n_omega][N][N] in and out, may not alias).

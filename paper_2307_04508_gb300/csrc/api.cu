@@ -77,6 +77,10 @@ struct ltgw_ctx {
   cudaEvent_t ev[EV_COUNT] = {};
   ltgw_stats stats{};
   int launches = 0;
+  double pi_tc_flops = 0.0;
+  int n_sm = 148;
+  Arena a4;  // tensor-core scratch: tile lists and partial tiles
+  Arena a5;  // tensor-core operand copies consumed by the next contraction
 
   void fail(ltgw_status c, const std::string &m) {
     if (st == LTGW_OK) { st = c; err = m; }
@@ -132,14 +136,18 @@ ltgw_status check_flags(ltgw_ctx *ctx, cudaStream_t s) {
   if (read_small(ctx, h, ctx->flags, sizeof(h), s) != LTGW_OK) return ctx->status();
   if (h[FLAG_EIG]) ctx->fail(LTGW_ERR_EIG, "NAF eigensolver: inverse iteration produced a non-finite vector");
   if (h[FLAG_NOT_SPD]) ctx->fail(LTGW_ERR_NOT_SPD, "screening: a pivot of 1 - Pi(iw) was not positive");
+  if (h[FLAG_TC_TIMEOUT]) ctx->fail(LTGW_ERR_DEVICE, "tensor-core kernel: a pipeline wait timed out");
   return ctx->status();
 }
 
 // NAF basis on device data: K = B B^T, eigenvectors with eigenvalue > thresh
 // as rows of Ut (descending eigenvalue), their eigenvalues in lam.
+ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B, int64_t ld, double *K,
+                          cudaStream_t s);
+
 ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, const double *B,
                           int64_t ld, double thresh, double *Ut, double *lam_out, int *k_out,
-                          int *near_out, cudaStream_t s) {
+                          int *near_out, cudaStream_t s, bool mixed = false) {
   EigWork w;
   auto layout = [&](Arena &A) {
     w.A = A.take<double>((size_t)n * n);
@@ -154,6 +162,8 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     w.X = A.take<double>((size_t)n * n);
     w.lu = A.take<double>((size_t)5 * n * n);
     w.count = A.take<int>(2);
+    const int64_t nsplit = (n + 255) / 256;
+    w.wy = A.take<double>((size_t)(nsplit + 3) * 64 * (64 + (size_t)n));
   };
   ar.begin_sizing();
   layout(ar);
@@ -162,12 +172,17 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     return ctx->status();
   }
   layout(ar);
-  GemmF64Args g;
-  g.M = n; g.N = n; g.K = n_pairs;
-  g.A = B; g.lda = ld; g.B = B; g.ldb = ld;
-  g.C = w.A; g.ldc = n;
-  g.syrk = 1;
-  CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
+  if (mixed) {
+    if (naf_metric_tc(ctx, n, n_pairs, B, ld, w.A, s) != LTGW_OK) return ctx->status();
+  } else {
+    GemmF64Args g;
+    g.M = n; g.N = n; g.K = n_pairs;
+    g.A = B; g.lda = ld; g.B = B; g.ldb = ld;
+    g.C = w.A; g.ldc = n;
+    g.syrk = 1;
+    CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
+  }
+  LTGW_CUDA(ctx, cudaMemsetAsync(w.V, 0, (size_t)n * n * sizeof(double), s));
   int nl = 0;
   cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl);
   ctx->launches += nl;
@@ -218,6 +233,260 @@ ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const doub
   return LTGW_OK;
 }
 
+// Split-K plan: one CTA per SM, so choose the split count that fills whole
+// waves best while keeping at least 1024 pairs per CTA.
+int64_t tc_splits(const ltgw_ctx *ctx, int64_t units, int64_t Kp, int64_t *kps_out) {
+  const int64_t max_split = std::max<int64_t>(1, Kp / 1024);
+  int64_t splits = 1;
+  double best = -1.0;
+  for (int64_t sp = 1; sp <= std::min<int64_t>(max_split, 64); ++sp) {
+    const int64_t ctas = units * sp;
+    const int64_t waves = (ctas + ctx->n_sm - 1) / ctx->n_sm;
+    const double eff = (double)ctas / (double)(waves * ctx->n_sm);
+    const double score = eff - 0.002 * (double)sp;   // prefer fewer splits on ties
+    if (score > best) { best = score; splits = sp; }
+  }
+  int64_t kps = ((Kp + splits - 1) / splits + 63) / 64 * 64;
+  *kps_out = kps;
+  return (Kp + kps - 1) / kps;
+}
+
+std::vector<int> lower_tiles(int nI, std::vector<int> *tindex) {
+  std::vector<int> tiles;
+  if (tindex) tindex->assign((size_t)nI * nI, -1);
+  for (int I = 0; I < nI; ++I)
+    for (int J = 0; J <= I; ++J) {
+      if (tindex) (*tindex)[(size_t)I * nI + J] = (int)(tiles.size() / 2);
+      tiles.push_back(I);
+      tiles.push_back(J);
+    }
+  return tiles;
+}
+
+std::vector<int> full_tiles(int nI, int nJ) {
+  std::vector<int> tiles;
+  for (int I = 0; I < nI; ++I)
+    for (int J = 0; J < nJ; ++J) { tiles.push_back(I); tiles.push_back(J); }
+  return tiles;
+}
+
+// One split-BF16 contraction on the tensor cores.  Scratch (tile list,
+// partials) comes from `ar`; the caller reduces the partials (returned).
+struct TcRun {
+  double *partial = nullptr;
+  float *partial32 = nullptr;
+  float *cd_out = nullptr;
+  int splits = 1, groups = 1, n_tiles = 0;
+};
+ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int> &tiles, int coldot_rows,
+                   TcRun *run, cudaStream_t s) {
+  const int n_tiles = (int)(tiles.size() / 2);
+  const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
+  int64_t kps = 0;
+  int64_t splits = tc_splits(ctx, (int64_t)n_tiles * groups, g.Kp, &kps);
+  if (g.out_mode == TC_OUT_COLDOT) { kps = g.Kp; splits = 1; }
+  const bool f32 = g.out_mode != TC_OUT_COLDOT && kps <= g.drain_k;
+  if (g.out_mode != TC_OUT_COLDOT) g.out_mode = f32 ? TC_OUT_F32 : TC_OUT_F64;
+  int *d_tiles;
+  auto layout = [&](Arena &A) {
+    d_tiles = A.take<int>(tiles.size());
+    run->partial = (g.out_mode == TC_OUT_F64) ? A.take<double>((size_t)splits * groups * 4 * n_tiles * 128 * 128) : nullptr;
+    run->partial32 = (g.out_mode == TC_OUT_F32) ? A.take<float>((size_t)splits * groups * 4 * n_tiles * 128 * 128) : nullptr;
+    run->cd_out = (g.out_mode == TC_OUT_COLDOT) ? A.take<float>((size_t)splits * groups * coldot_rows * (size_t)g.cd_cols_p) : nullptr;
+  };
+  ar.begin_sizing();
+  layout(ar);
+  if (ar.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core workspace allocation failed"); return ctx->status(); }
+  layout(ar);
+  copy_in(ctx, d_tiles, tiles.data(), tiles.size() * sizeof(int), s);
+  g.tiles = d_tiles;
+  g.k_per_split = kps;
+  g.partial = run->partial;
+  g.partial32 = run->partial32;
+  g.cd_out = run->cd_out;
+  g.n_tile_rows = coldot_rows;
+  g.err = ctx->flags;
+  CHECK_LAUNCH(ctx, launch_tc_split_gemm(g, n_tiles, s), 1);
+  run->splits = (int)splits;
+  run->groups = groups;
+  run->n_tiles = n_tiles;
+  return LTGW_OK;
+}
+
+// Pi (direct) or the Laplace moments M^k in the split-BF16 form on the tensor
+// cores.  Operand: Af (FP32 [roundup(N,128)][roundup(n_pairs,64)]) when given,
+// else converted from the FP64 block Bt.  Scale table (the per-pair factor of
+// Eq. Pi or of the M^m form) is applied by the converter warps.
+ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, int64_t ldb,
+                              const float *Af_in, const double *delta, int n_omega, const double *d_omega,
+                              int n_tau, const double *d_x, const double *d_w, const double *d_E,
+                              double *M, int spin, double *Pi, cudaStream_t s) {
+  const int64_t Kp = (n_pairs + 63) / 64 * 64;
+  const int nI = (N + 127) / 128, Mp = nI * 128;
+  const int n_t = n_tau ? n_tau : n_omega;
+  std::vector<int> tindex;
+  std::vector<int> tiles = lower_tiles(nI, &tindex);
+  float *Af = nullptr, *scale;
+  int *d_tindex;
+  auto layout = [&](Arena &A) {
+    Af = Af_in ? nullptr : A.take<float>((size_t)Mp * Kp);
+    scale = A.take<float>((size_t)n_t * Kp);
+    d_tindex = A.take<int>(tindex.size());
+  };
+  ctx->a5.begin_sizing();
+  layout(ctx->a5);
+  if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core operand allocation failed"); return ctx->status(); }
+  layout(ctx->a5);
+  const float *A = Af_in ? Af_in : Af;
+  copy_in(ctx, d_tindex, tindex.data(), tindex.size() * sizeof(int), s);
+  if (!Af_in) CHECK_LAUNCH(ctx, launch_to_f32_padded(Bt, ldb, N, n_pairs, Af, Mp, Kp, s), 1);
+  CHECK_LAUNCH(ctx, launch_scale_table(delta, n_pairs, Kp, n_t, n_tau ? d_x : d_omega, n_tau ? d_w : nullptr,
+                                       n_tau ? SCALE_LAPLACE : SCALE_DIRECT, scale, s), 1);
+  TcGemmArgs g;
+  g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.n_t = n_t; g.nt_group = 4;
+  TcRun run;
+  ctx->mark(EV_PI0, s);
+  if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
+  ctx->mark(EV_PI1, s);
+  ctx->pi_tc_flops = 3.0 * 2.0 * (double)run.n_tiles * 128 * 128 * (double)Kp * n_t;
+  if (n_tau == 0) {
+    CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
+                                           nI, n_t, N, -2.0 * spin, Pi, s), 1);
+  } else {
+    CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
+                                           nI, n_t, N, 1.0, M, s), 1);
+    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
+  }
+  return LTGW_OK;
+}
+
+// NAF metric K = B B^T (Eq. nafeq) in the split-BF16 form; K: device [n][n] FP64.
+ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B, int64_t ld, double *K,
+                          cudaStream_t s) {
+  const int64_t Kp = (n_pairs + 63) / 64 * 64;
+  const int nI = (n + 127) / 128, Mp = nI * 128;
+  std::vector<int> tindex;
+  std::vector<int> tiles = lower_tiles(nI, &tindex);
+  float *Af, *ones;
+  int *d_tindex;
+  auto layout = [&](Arena &A) {
+    Af = A.take<float>((size_t)Mp * Kp);
+    ones = A.take<float>((size_t)Kp);
+    d_tindex = A.take<int>(tindex.size());
+  };
+  ctx->a5.begin_sizing();
+  layout(ctx->a5);
+  if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core operand allocation failed"); return ctx->status(); }
+  layout(ctx->a5);
+  copy_in(ctx, d_tindex, tindex.data(), tindex.size() * sizeof(int), s);
+  CHECK_LAUNCH(ctx, launch_to_f32_padded(B, ld, n, n_pairs, Af, Mp, Kp, s), 1);
+  CHECK_LAUNCH(ctx, launch_scale_table(nullptr, n_pairs, Kp, 1, nullptr, nullptr, SCALE_NONE, ones, s), 1);
+  TcGemmArgs g;
+  g.A = Af; g.B = Af; g.scale = ones; g.Kp = Kp; g.n_t = 1; g.nt_group = 1;
+  TcRun run;
+  if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
+  CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
+                                         nI, 1, n, 1.0, K, s), 1);
+  return LTGW_OK;
+}
+
+// Operands of the mixed form after the NAF step (Eq. naftrafo in split BF16):
+//   Bf       FP32 [roundup(N,128)][roundup(n_ov,64)]   R~_ov, the Pi operand
+//   BtT64    FP64 [T][n_orb_act][N]                      R~_tgt transposed (column dot)
+//   BtT32    FP32 [roundup(T n_orb_act,128)][roundup(N,64)]  the W_nm operand
+// With Ut == nullptr (no NAF) they are copies of the active blocks of B_ov, B_tgt.
+ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, const double *B_act, int64_t ld_act,
+                           int64_t n_ov, const double *B_tgt, int n_orb, int n_fc, int T, int n_orb_act, float *Bf,
+                           double *BtT64, float *BtT32, cudaStream_t s) {
+  const int64_t Kp_ov = (n_ov + 63) / 64 * 64;
+  const int MpN = (N + 127) / 128 * 128, KpN = (N + 63) / 64 * 64;
+  const int64_t rowsT = (int64_t)T * n_orb_act, rowsTp = (rowsT + 127) / 128 * 128;
+  if (!Ut) {
+    CHECK_LAUNCH(ctx, launch_to_f32_padded(B_act, ld_act, N, n_ov, Bf, MpN, Kp_ov, s), 1);
+    CHECK_LAUNCH(ctx, launch_transpose_f64(B_tgt, n_orb, n_fc, n_aux, n_orb_act, BtT64, N, T,
+                                           (int64_t)n_aux * n_orb, (int64_t)n_orb_act * N, s), 1);
+    CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_tgt, n_orb, n_fc, n_aux, n_orb_act, BtT32, KpN, n_orb_act, T,
+                                               (int64_t)n_aux * n_orb, (int64_t)n_orb_act * KpN, s), 1);
+    if (rowsTp > rowsT)
+      LTGW_CUDA(ctx, cudaMemsetAsync(BtT32 + rowsT * KpN, 0, (size_t)(rowsTp - rowsT) * KpN * sizeof(float), s));
+    return LTGW_OK;
+  }
+  const int Kpa = (n_aux + 63) / 64 * 64;
+  const int nI_ov = (int)((n_ov + 127) / 128);
+  const int MpT = (n_orb_act + 127) / 128 * 128;
+  float *UtF, *BactT, *BtgT, *ones;
+  auto layout = [&](Arena &A) {
+    UtF = A.take<float>((size_t)MpN * Kpa);
+    BactT = A.take<float>((size_t)nI_ov * 128 * Kpa);
+    BtgT = A.take<float>((size_t)T * MpT * Kpa);
+    ones = A.take<float>((size_t)std::max(T, 1) * Kpa);
+  };
+  ctx->a5.begin_sizing();
+  layout(ctx->a5);
+  if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core operand allocation failed"); return ctx->status(); }
+  layout(ctx->a5);
+  CHECK_LAUNCH(ctx, launch_to_f32_padded(Ut, n_aux, N, n_aux, UtF, MpN, Kpa, s), 1);
+  CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_act, ld_act, 0, n_aux, (int)n_ov, BactT, Kpa, nI_ov * 128, 1, 0, 0, s), 1);
+  CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_tgt, n_orb, n_fc, n_aux, n_orb_act, BtgT, Kpa, MpT, T,
+                                             (int64_t)n_aux * n_orb, (int64_t)MpT * Kpa, s), 1);
+  CHECK_LAUNCH(ctx, launch_scale_table(nullptr, n_aux, Kpa, std::max(T, 1), nullptr, nullptr, SCALE_NONE, ones, s), 1);
+  // R~_ov = U^T R_ov: rows N (A = U^T), columns n_ov (B rows = R_ov^T)
+  {
+    TcGemmArgs g;
+    g.A = UtF; g.B = BactT; g.scale = ones; g.Kp = Kpa; g.n_t = 1; g.nt_group = 1;
+    TcRun run;
+    const int nI = (N + 127) / 128;
+    if (tc_run(ctx, ctx->a4, g, full_tiles(nI, nI_ov), 0, &run, s) != LTGW_OK) return ctx->status();
+    CHECK_LAUNCH(ctx, launch_tc_reduce_full(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, nI_ov, N,
+                                            (int)n_ov, 1.0, nullptr, 0, 0, Bf, Kp_ov, MpN, 0, s), 1);
+  }
+  // R~_tgt[t]^T = R_tgt[t]^T U: per target t, rows n_orb_act (A), columns N (B rows = U^T)
+  {
+    TcGemmArgs g;
+    g.A = BtgT; g.a_group_stride = (int64_t)MpT * Kpa; g.B = UtF; g.scale = ones; g.Kp = Kpa;
+    g.n_t = T; g.nt_group = 1;
+    TcRun run;
+    const int nJ = (N + 127) / 128;
+    if (tc_run(ctx, ctx->a4, g, full_tiles(MpT / 128, nJ), 0, &run, s) != LTGW_OK) return ctx->status();
+    CHECK_LAUNCH(ctx, launch_tc_reduce_full(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, nJ,
+                                            n_orb_act, N, 1.0, BtT64, N, (int64_t)n_orb_act * N, BtT32, KpN,
+                                            n_orb_act, (int64_t)n_orb_act * KpN, s), 1);
+    if (rowsTp > rowsT)
+      LTGW_CUDA(ctx, cudaMemsetAsync(BtT32 + rowsT * KpN, 0, (size_t)(rowsTp - rowsT) * KpN * sizeof(float), s));
+  }
+  return LTGW_OK;
+}
+
+// W_nm(i w_j) (Eq. ScreenedCoulombOrbital) in the split-BF16 form: Y_j = C_j R~_tgt
+// on the tensor cores with the column dot against R~_tgt fused into the epilogue.
+ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, int n_orb_act, const double *BtT64,
+                   const float *BtT32, double *W, cudaStream_t s) {
+  const int KpN = (N + 63) / 64 * 64, MpN = (N + 127) / 128 * 128, nI = MpN / 128;
+  const int ncols = T * n_orb_act, nJ = (ncols + 127) / 128;
+  float *Cf, *ones;
+  auto layout = [&](Arena &A) {
+    Cf = A.take<float>((size_t)n_omega * MpN * KpN);
+    ones = A.take<float>((size_t)n_omega * KpN);
+  };
+  ctx->a5.begin_sizing();
+  layout(ctx->a5);
+  if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core operand allocation failed"); return ctx->status(); }
+  layout(ctx->a5);
+  // C_j is symmetric, so its transpose is its padded copy
+  CHECK_LAUNCH(ctx, launch_to_f32_transposed(C, N, 0, N, N, Cf, KpN, MpN, n_omega, (int64_t)N * N,
+                                             (int64_t)MpN * KpN, s), 1);
+  CHECK_LAUNCH(ctx, launch_scale_table(nullptr, N, KpN, n_omega, nullptr, nullptr, SCALE_NONE, ones, s), 1);
+  TcGemmArgs g;
+  g.A = Cf; g.a_group_stride = (int64_t)MpN * KpN; g.B = BtT32; g.scale = ones; g.Kp = KpN;
+  g.n_t = n_omega; g.nt_group = 1;
+  g.out_mode = TC_OUT_COLDOT;
+  g.cd_B = BtT64; g.cd_ld = N; g.cd_rows = N; g.cd_cols = ncols; g.cd_cols_p = nJ * 128;
+  TcRun run;
+  if (tc_run(ctx, ctx->a4, g, full_tiles(nI, nJ), nI, &run, s) != LTGW_OK) return ctx->status();
+  CHECK_LAUNCH(ctx, launch_tc_reduce_coldot(run.cd_out, run.splits, run.groups, nI, nJ * 128, ncols, W, ncols, s), 1);
+  return LTGW_OK;
+}
+
 ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
   REQUIRE(ctx, p != nullptr, "params is NULL");
   REQUIRE(ctx, p->n_occ >= 1 && p->n_virt >= 1 && p->n_aux >= 1, "n_occ, n_virt, n_aux must be >= 1");
@@ -227,7 +496,8 @@ ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
   REQUIRE(ctx, p->spin == 1 || p->spin == 2, "spin must be 1 or 2");
   REQUIRE(ctx, p->use_laplace == 0 || p->use_laplace == 1, "use_laplace must be 0 or 1");
   REQUIRE(ctx, !p->use_laplace || (p->n_tau >= 1 && p->n_tau <= 32), "n_tau must be in [1, 32]");
-  REQUIRE(ctx, p->precision == LTGW_FP64, "only LTGW_FP64 is accepted by this version");
+  REQUIRE(ctx, p->precision == LTGW_FP64 || p->precision == LTGW_BF16X3,
+          "precision must be LTGW_FP64 or LTGW_BF16X3");
   REQUIRE(ctx, p->reserved == 0, "reserved must be 0");
   REQUIRE(ctx, isfinite(p->naf_thresh), "naf_thresh must be finite");
   return LTGW_OK;
@@ -262,6 +532,10 @@ ltgw_status ltgw_create(ltgw_ctx **out, int device) {
   if (cudaSetDevice(device) != cudaSuccess) return LTGW_ERR_DEVICE;
   ltgw_ctx *c = new ltgw_ctx();
   c->device = device;
+  if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->n_sm < 1) {
+    cudaGetLastError();
+    c->n_sm = 148;
+  }
   if (cudaMalloc(&c->flags, FLAG_COUNT * sizeof(int)) != cudaSuccess) {
     delete c;
     return LTGW_ERR_NOMEM;
@@ -277,6 +551,8 @@ void ltgw_destroy(ltgw_ctx *ctx) {
   ctx->a1.release();
   ctx->a2.release();
   ctx->a3.release();
+  ctx->a4.release();
+  ctx->a5.release();
   if (ctx->flags) cudaFree(ctx->flags);
   for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
   delete ctx;
@@ -315,6 +591,7 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   const int n_omega = p->n_omega, T = n_tgt;
   const int n_tau = p->use_laplace ? p->n_tau : 0;
   const bool naf = p->naf_thresh >= 0.0;
+  const bool mixed = p->precision == LTGW_BF16X3;
   ctx->stats = ltgw_stats{};
   ctx->mark(EV_START, s);
 
@@ -404,7 +681,8 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   // ---- NAF (Eqs. nafeq, naftrafo) on a separate arena for its scratch
   int N = n_aux, near = 0;
   if (naf) {
-    if (naf_basis_dev(ctx, ctx->a3, n_aux, n_ov, B_act, ld_act, p->naf_thresh, d_Ut, d_lam, &N, &near, s) != LTGW_OK)
+    if (naf_basis_dev(ctx, ctx->a3, n_aux, n_ov, B_act, ld_act, p->naf_thresh, d_Ut, d_lam, &N, &near, s,
+                      mixed) != LTGW_OK)
       return ctx->status();
   }
   ctx->stats.n_naf = N;
@@ -413,9 +691,17 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   // ---- phase-2 workspace
   double *d_Bt = nullptr, *d_Btt = nullptr, *d_M = nullptr, *d_Pi, *d_X0, *d_X1, *d_C, *d_W, *d_sig, *d_eqp;
   int *d_st;
+  float *d_Bf = nullptr, *d_BtT32 = nullptr;
+  double *d_BtT64 = nullptr;
+  const int64_t Kp_ov = (n_ov + 63) / 64 * 64;
   auto layout2 = [&](Arena &A) {
-    d_Bt = naf ? A.take<double>((size_t)N * n_ov) : nullptr;
-    d_Btt = naf ? A.take<double>((size_t)T * N * n_orb_act) : nullptr;
+    d_Bt = (naf && !mixed) ? A.take<double>((size_t)N * n_ov) : nullptr;
+    d_Btt = (naf && !mixed) ? A.take<double>((size_t)T * N * n_orb_act) : nullptr;
+    if (mixed) {
+      d_Bf = A.take<float>((size_t)((N + 127) / 128 * 128) * Kp_ov);
+      d_BtT64 = A.take<double>((size_t)T * n_orb_act * N);
+      d_BtT32 = A.take<float>((size_t)(((int64_t)T * n_orb_act + 127) / 128 * 128) * ((N + 63) / 64 * 64));
+    }
     d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
     d_Pi = A.take<double>((size_t)n_omega * N * N);
     d_X0 = A.take<double>((size_t)n_omega * N * N);
@@ -435,7 +721,11 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   int64_t ld_bt = ld_act;
   const double *Btt = d_Btg + n_fc;
   int64_t ld_btt = n_orb, stride_btt = (int64_t)n_aux * n_orb;
-  if (naf) {
+  if (mixed) {
+    if (naf_project_tc(ctx, N, n_aux, naf ? d_Ut : nullptr, B_act, ld_act, n_ov, d_Btg, n_orb, n_fc, T, n_orb_act,
+                       d_Bf, d_BtT64, d_BtT32, s) != LTGW_OK)
+      return ctx->status();
+  } else if (naf) {
     GemmF64Args g;  // R~_ov = U^T R_ov
     g.M = N; g.N = (int)std::min<int64_t>(n_ov, INT32_MAX); g.K = n_aux;
     g.A = d_Ut; g.lda = n_aux;
@@ -454,9 +744,14 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   ctx->mark(EV_NAF, s);
 
   // ---- Pi (Eq. Pi or the Laplace form)
-  if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
-                         p->spin, d_Pi, s) != LTGW_OK)
+  if (mixed) {
+    if (polarizability_tc(ctx, N, n_ov, nullptr, 0, d_Bf, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E,
+                          d_M, p->spin, d_Pi, s) != LTGW_OK)
+      return ctx->status();
+  } else if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                                p->spin, d_Pi, s) != LTGW_OK) {
     return ctx->status();
+  }
   ctx->mark(EV_PI, s);
 
   // ---- screening
@@ -467,12 +762,16 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   ctx->mark(EV_SCREEN, s);
 
   // ---- W_nm(i w_j)
-  ColDotArgs cd;
-  cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;
-  cd.C = d_C; cd.ldc = N; cd.strideC = (int64_t)N * N;
-  cd.Bt = Btt; cd.ldb = ld_btt; cd.strideBt = stride_btt;
-  cd.W = d_W; cd.ldw = n_orb_act;
-  CHECK_LAUNCH(ctx, launch_gemm_coldot(cd, n_omega, s), 1);
+  if (mixed) {
+    if (wnm_tc(ctx, N, n_omega, d_C, T, n_orb_act, d_BtT64, d_BtT32, d_W, s) != LTGW_OK) return ctx->status();
+  } else {
+    ColDotArgs cd;
+    cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;
+    cd.C = d_C; cd.ldc = N; cd.strideC = (int64_t)N * N;
+    cd.Bt = Btt; cd.ldb = ld_btt; cd.strideBt = stride_btt;
+    cd.W = d_W; cd.ldw = n_orb_act;
+    CHECK_LAUNCH(ctx, launch_gemm_coldot(cd, n_omega, s), 1);
+  }
   ctx->mark(EV_WNM, s);
 
   // ---- Sigma(i w), Pade, Newton
@@ -577,6 +876,51 @@ ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const dou
     return ctx->status();
   LTGW_CUDA(ctx, cudaStreamSynchronize(s));  // the staged grid lives in the workspace
   return LTGW_OK;
+}
+
+ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                      const double *delta, int n_omega, const double *omegas, int n_tau,
+                                      const double *x, const double *w, int spin, double *Pi,
+                                      void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
+  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
+  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
+  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
+  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
+  for (int j = 0; j < n_omega; ++j)
+    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
+  double *d_om, *d_x, *d_w, *d_E, *d_M;
+  auto layout = [&](Arena &A) {
+    d_om = A.take<double>(n_omega);
+    d_x = A.take<double>(std::max(n_tau, 1));
+    d_w = A.take<double>(std::max(n_tau, 1));
+    d_E = A.take<double>(h_E.size());
+    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
+  };
+  ctx->a2.begin_sizing();
+  layout(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
+  layout(ctx->a2);
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
+  if (n_tau) {
+    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
+    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
+    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+  }
+  if (ctx->status() != LTGW_OK) return ctx->status();
+  if (polarizability_tc(ctx, N, n_pairs, Bt, n_pairs, nullptr, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                        spin, Pi, s) != LTGW_OK)
+    return ctx->status();
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->stats.ms_pi_kernel = ctx->ms(EV_PI0, EV_PI1);
+  ctx->stats.pi_kernel_launches = 1;
+  return check_flags(ctx, s);
 }
 
 ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C, void *stream) {

@@ -46,6 +46,6 @@ struct Status {
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Device-side error flags written by kernels (one int each, zeroed per solve).
-enum DeviceFlag { FLAG_NOT_SPD = 0, FLAG_EIG = 1, FLAG_NONFINITE = 2, FLAG_COUNT = 8 };
+enum DeviceFlag { FLAG_NOT_SPD = 0, FLAG_EIG = 1, FLAG_NONFINITE = 2, FLAG_TC_TIMEOUT = 3, FLAG_COUNT = 8 };
 
 }  // namespace ltgw

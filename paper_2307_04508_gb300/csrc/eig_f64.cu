@@ -4,18 +4,21 @@
 //  1. Householder reduction K = Q T Q^T to tridiagonal T (one reflector per
 //     step: reflector, symmetric mat-vec, rank-2 update of the trailing block);
 //  2. Sturm-sequence count of the eigenvalues of T above the threshold;
-//  3. bisection for the kept eigenvalues, one thread each, with T in shared memory;
+//  3. multisection for the kept eigenvalues, one warp each, with T in shared memory;
 //  4. inverse iteration for their eigenvectors (tridiagonal LU with row
 //     interchanges), with modified Gram-Schmidt inside groups of nearly equal
 //     eigenvalues;
 //  5. symmetric re-orthonormalisation X <- X (3 - X^T X)/2 twice, which removes
 //     the small non-orthogonality inverse iteration leaves between close
 //     eigenvalues without leaving the span of X;
-//  6. back-transformation U = Q X, written transposed as the rows of Ut.
+//  6. back-transformation U = Q X in compact-WY blocks of 64 reflectors
+//     (split-K FP64 GEMMs), written transposed as the rows of Ut.
 //
 // Only the kept eigenvectors are formed.  Householder convention: H = 1 - tau v v^T,
 // v_0 = 1, H x = beta e_1.
 #include <float.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "common.cuh"
@@ -183,7 +186,10 @@ __global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *d, con
   }
 }
 
-// lam[r] = (n-1-r)-th smallest eigenvalue (r-th largest), r < k.  d and e^2 in smem.
+// lam[r] = (n-1-r)-th smallest eigenvalue (r-th largest), r < k, by
+// multisection: one warp per eigenvalue, each lane counts the eigenvalues
+// below one of 32 interior points of the current interval, so an interval
+// shrinks 33-fold per step.  d and e^2 are staged in shared memory.
 __global__ void bisect_kernel(const double *d, const double *e2g, const double *scal, int n,
                               int k, double *lam) {
   extern __shared__ double sm[];
@@ -193,19 +199,25 @@ __global__ void bisect_kernel(const double *d, const double *e2g, const double *
     se2[i] = (i < n - 1) ? e2g[i] : 0.0;
   }
   __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= k) return;
   const int idx = n - 1 - r;  // ascending index of the wanted eigenvalue
   double lo = scal[1], hi = scal[2];
   const double pivmin = scal[3];
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi)
-      break;
-    if (sturm_count(sd, se2, n, mid, pivmin) > idx) hi = mid;
-    else lo = mid;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const bool above = sturm_count(sd, se2, n, x, pivmin) > idx;  // eigenvalue idx < x
+    const unsigned b = __ballot_sync(0xffffffffu, above);
+    const int j = b ? (__ffs(b) - 1) : 32;
+    const double nlo = (j == 0) ? lo : lo + (hi - lo) * (double)j / 33.0;
+    const double nhi = (j == 32) ? hi : lo + (hi - lo) * (double)(j + 1) / 33.0;
+    if (!(nlo > lo || nhi < hi)) break;  // no progress at this resolution
+    lo = nlo;
+    hi = nhi;
   }
-  lam[r] = 0.5 * (lo + hi);
+  if (lane == 0) lam[r] = 0.5 * (lo + hi);
 }
 
 // Inverse iteration for the eigenvectors of T, one thread per group of
@@ -312,44 +324,60 @@ __global__ void lowdin_factor_kernel(double *G, int k) {
   }
 }
 
-// Y = H_0 H_1 ... H_{n-3} X for a slab of 16 columns per block, then Ut = Y^T.
-constexpr int BT_COLS = 16;
-__global__ void __launch_bounds__(256) back_transform_kernel(const double *__restrict__ V,
-                                                             const double *__restrict__ tau,
-                                                             double *__restrict__ X, int n,
-                                                             int k, double *__restrict__ Ut) {
-  __shared__ double red[16][BT_COLS];
-  __shared__ double g[BT_COLS];
-  const int c = threadIdx.x % BT_COLS, rg = threadIdx.x / BT_COLS;  // 16 row groups
-  const int col = blockIdx.x * BT_COLS + c;
-  const bool ok = col < k;
-  for (int kk = n - 3; kk >= 0; --kk) {
-    const double t = tau[kk];
-    if (t == 0.0) continue;  // uniform across the block
-    const double *v = V + (int64_t)kk * n;
-    double s = 0.0;
-    if (ok)
-      for (int r = kk + 1 + rg; r < n; r += 16) s = fma(v[r], X[(int64_t)r * k + col], s);
-    red[rg][c] = s;
-    __syncthreads();
-    if (rg == 0) {
-      double a = 0.0;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) a += red[q][c];
-      g[c] = t * a;
+// ---- compact-WY back-transformation: U = H_0 H_1 ... H_{n-3} X ----
+// For a block of nb consecutive reflectors j0..j0+nb-1 (rows of V, zero
+// outside j+1..n-1), H_j0 ... H_{j0+nb-1} = 1 - V_b T V_b^T with T upper
+// triangular (T_ii = tau_i, T[0:l, l] = -tau_l T[0:l, 0:l] G[0:l, l],
+// G = V_b^T V_b).  Blocks are applied from the last to the first:
+// Y <- Y - V_b (T (V_b^T Y)).
+constexpr int WY_NB = 64;
+constexpr int64_t WY_KSPLIT = 256;
+
+// dst[i] = sum_s src[s * stride + i]
+__global__ void sum_partials_kernel(const double *__restrict__ src, int nsplit, int64_t stride,
+                                    int64_t n, double *__restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int q = 0; q < nsplit; ++q) a += src[q * stride + i];
+    dst[i] = a;
+  }
+}
+
+// T (nb x nb, row-major, upper) from G = V_b^T V_b and tau[j0..j0+nb).
+__global__ void wy_build_t_kernel(const double *__restrict__ G, const double *__restrict__ tau,
+                                  int j0, int nb, double *__restrict__ T) {
+  __shared__ double sT[WY_NB][WY_NB + 1];
+  const int i = threadIdx.x;
+  for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) sT[q / WY_NB][q % WY_NB] = 0.0;
+  __syncthreads();
+  if (i < nb) sT[i][i] = tau[j0 + i];
+  __syncthreads();
+  for (int l = 1; l < nb; ++l) {
+    double v = 0.0;
+    if (i < l) {
+      for (int m = i; m < l; ++m) v += sT[i][m] * G[m * nb + l];
+      v *= -tau[j0 + l];
     }
     __syncthreads();
-    if (ok) {
-      const double gc = g[c];
-      for (int r = kk + 1 + rg; r < n; r += 16) X[(int64_t)r * k + col] -= v[r] * gc;
-    }
+    if (i < l) sT[i][l] = v;
     __syncthreads();
   }
-  // transpose out: Ut[col][r]
-  for (int q = 0; q < BT_COLS; ++q) {
-    int cc = blockIdx.x * BT_COLS + q;
-    if (cc >= k) break;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) Ut[(int64_t)cc * n + r] = X[(int64_t)r * k + cc];
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) T[q] = sT[q / nb][q % nb];
+}
+
+// Ut[c][r] = X[r][c]
+__global__ void transpose_kernel(const double *__restrict__ X, int n, int k, double *__restrict__ Ut) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    int r = r0 + q, c = c0 + threadIdx.x;
+    if (r < n && c < k) tile[q][threadIdx.x] = X[(int64_t)r * k + c];
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    int c = c0 + q, r = r0 + threadIdx.x;
+    if (r < n && c < k) Ut[(int64_t)c * n + r] = tile[threadIdx.x][q];
   }
 }
 
@@ -386,7 +414,7 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  bisect_kernel<<<(k + 127) / 128, 128, smem, s>>>(w.d, w.p, w.scal, n, k, w.lam);
+  bisect_kernel<<<(k + 7) / 8, 256, smem, s>>>(w.d, w.p, w.scal, n, k, w.lam);
   inverse_iteration_kernel<<<(k + 63) / 64, 64, 0, s>>>(w.d, w.e, w.lam, w.scal, n, k, w.X, w.lu,
                                                         flags);
   *launches += 2;
@@ -416,7 +444,54 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
     if (e != cudaSuccess) return e;
     *launches += 3;
   }
-  back_transform_kernel<<<(k + BT_COLS - 1) / BT_COLS, 256, 0, s>>>(w.V, w.tau, w.X, n, k, Ut);
+  // compact-WY back-transformation, blocks of WY_NB reflectors from the last
+  const int nref = n - 2;  // reflectors 0 .. n-3
+  double *Gp = w.wy;                                           // [nsplit][nb][nb]
+  const int nsplit_max = (int)((n + WY_KSPLIT - 1) / WY_KSPLIT);
+  double *W1p = Gp + (int64_t)nsplit_max * WY_NB * WY_NB;      // [nsplit][nb][k]
+  double *Gs = W1p + (int64_t)nsplit_max * WY_NB * k;          // [nb][nb]
+  double *W1 = Gs + WY_NB * WY_NB;                             // [nb][k]
+  double *Tm = W1 + (int64_t)WY_NB * k;                        // [nb][nb]
+  double *W2 = Tm + WY_NB * WY_NB;                             // [nb][k]
+  for (int j0 = ((nref - 1) / WY_NB) * WY_NB; nref > 0 && j0 >= 0; j0 -= WY_NB) {
+    const int nb = std::min(WY_NB, nref - j0);
+    const int r0 = j0 + 1;              // first row where this block's V is non-zero
+    const int64_t len = n - r0;
+    const int nsplit = (int)((len + WY_KSPLIT - 1) / WY_KSPLIT);
+    GemmF64Args g;                      // G partials = V_b V_b^T over row chunks
+    g.M = nb; g.N = nb; g.K = len; g.ksplit = WY_KSPLIT;
+    g.A = w.V + (int64_t)j0 * n + r0; g.lda = n;
+    g.B = w.V + (int64_t)j0 * n + r0; g.ldb = n;
+    g.C = Gp; g.ldc = nb; g.strideC = (int64_t)nb * nb;
+    e = launch_gemm_f64(g, nsplit, true, true, s);
+    if (e != cudaSuccess) return e;
+    GemmF64Args h;                      // W1 partials = V_b^T Y over row chunks
+    h.M = nb; h.N = k; h.K = len; h.ksplit = WY_KSPLIT;
+    h.A = w.V + (int64_t)j0 * n + r0; h.lda = n;
+    h.B = w.X + (int64_t)r0 * k; h.ldb = k;
+    h.C = W1p; h.ldc = k; h.strideC = (int64_t)nb * k;
+    e = launch_gemm_f64(h, nsplit, true, false, s);
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<<<64, 256, 0, s>>>(Gp, nsplit, (int64_t)nb * nb, (int64_t)nb * nb, Gs);
+    sum_partials_kernel<<<152, 256, 0, s>>>(W1p, nsplit, (int64_t)nb * k, (int64_t)nb * k, W1);
+    wy_build_t_kernel<<<1, WY_NB, 0, s>>>(Gs, w.tau, j0, nb, Tm);
+    GemmF64Args t2;                     // W2 = T W1
+    t2.M = nb; t2.N = k; t2.K = nb;
+    t2.A = Tm; t2.lda = nb; t2.B = W1; t2.ldb = k; t2.C = W2; t2.ldc = k;
+    e = launch_gemm_f64(t2, 1, true, false, s);
+    if (e != cudaSuccess) return e;
+    GemmF64Args u;                      // Y[r0:, :] -= V_b^T W2
+    u.M = (int)len; u.N = k; u.K = nb;
+    u.A = w.V + (int64_t)j0 * n + r0; u.lda = n;   // A[kidx=i][m=r] = V[j0+i][r0+r]
+    u.B = W2; u.ldb = k;
+    u.C = w.X + (int64_t)r0 * k; u.ldc = k;
+    u.alpha = -1.0; u.beta = 1.0;
+    e = launch_gemm_f64(u, 1, false, false, s);
+    if (e != cudaSuccess) return e;
+    *launches += 7;
+  }
+  dim3 tb(32, 8), tg((k + 31) / 32, (n + 31) / 32);
+  transpose_kernel<<<tg, tb, 0, s>>>(w.X, n, k, Ut);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -111,14 +111,26 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
     m0 = blockIdx.y * BM;
     n0 = blockIdx.x * BN;
   }
-  const double *A = g.A + (int64_t)b * g.strideA;
-  const double *B = g.B + (int64_t)b * g.strideB;
+  const double *A, *B;
   double *C = g.C + (int64_t)b * g.strideC;
-  double p0 = g.batch_p0 ? g.batch_p0[b] : 0.0;
-  double p1 = g.batch_p1 ? g.batch_p1[b] : 0.0;
+  int64_t K = g.K;
+  const double *delta = g.delta;
+  double p0 = 0.0, p1 = 0.0;
+  if (g.ksplit > 0) {
+    const int64_t k0 = (int64_t)b * g.ksplit;
+    K = min(g.ksplit, g.K - k0);
+    A = g.A + (A_KMAJ ? k0 : k0 * g.lda);
+    B = g.B + (B_KMAJ ? k0 : k0 * g.ldb);
+    if (delta) delta += k0;
+  } else {
+    A = g.A + (int64_t)b * g.strideA;
+    B = g.B + (int64_t)b * g.strideB;
+    p0 = g.batch_p0 ? g.batch_p0[b] : 0.0;
+    p1 = g.batch_p1 ? g.batch_p1[b] : 0.0;
+  }
   double acc[4][4] = {};
-  tile_accumulate<A_KMAJ, B_KMAJ>(acc, sm, A, g.lda, B, g.ldb, m0, n0, g.M, g.N, g.K,
-                                  g.scale_mode, g.delta, p0, p1);
+  tile_accumulate<A_KMAJ, B_KMAJ>(acc, sm, A, g.lda, B, g.ldb, m0, n0, g.M, g.N, K,
+                                  g.scale_mode, delta, p0, p1);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -129,6 +141,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
       int gn = n0 + tx + 16 * j;
       if (gn >= g.N) continue;
       double v = g.alpha * acc[i][j];
+      if (g.beta != 0.0) v += g.beta * C[(int64_t)gm * g.ldc + gn];
       if (g.syrk) {
         if (gm >= gn) {
           C[(int64_t)gm * g.ldc + gn] = v;

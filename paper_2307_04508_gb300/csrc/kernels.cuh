@@ -24,6 +24,8 @@ struct GemmF64Args {
   const double *batch_p0 = nullptr;  // [batch] omega (direct) or x_m (Laplace), device
   const double *batch_p1 = nullptr;  // [batch] w_m (Laplace), device
   int syrk = 0;
+  double beta = 0.0;      // C = alpha * acc + beta * C
+  int64_t ksplit = 0;     // > 0: batch index b covers k in [b*ksplit, (b+1)*ksplit), C_b at b*strideC
 };
 cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b_kmaj,
                             cudaStream_t s);
@@ -66,12 +68,74 @@ struct EigWork {
   double *X = nullptr;                                // [n][kcap] tridiagonal eigenvectors
   double *lu = nullptr;                               // [5 n kcap] inverse-iteration scratch
   int *count = nullptr;                               // [2]
+  double *wy = nullptr;                               // [WY scratch] see eig_f64.cu
 };
 // Tridiagonalise A, count eigenvalues > thresh (returned through count[0]).
+// V must be zeroed by the caller before the call.
 cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches);
 // Eigenvalues (descending) and eigenvectors for the k largest, Ut = rows [k][n].
 cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
                                cudaStream_t s, int *launches);
+
+// ---- split-BF16 tensor-core contraction (tc_gemm.cu) ----
+// D_t = A diag(s_t) B^T for t < n_t; A [*][Kp], B [*][Kp], scale [n_t][Kp] FP32,
+// zero-padded (rows of A and B to 128, Kp to 64).  tiles: device list of
+// (tile row of A, tile row of B) pairs.  Output: FP64 partial tiles
+// partial[split][group][4][tile][128][128], group = t / 4.
+enum TcOut { TC_OUT_F64 = 0, TC_OUT_F32 = 1, TC_OUT_COLDOT = 2 };
+struct TcGemmArgs {
+  const float *A = nullptr, *B = nullptr, *scale = nullptr;
+  int64_t Kp = 0;
+  int n_t = 0;
+  int nt_group = 4;              // scales per CTA (1..4); group = blockIdx.y
+  int64_t a_group_stride = 0;    // A of group g starts at A + g * a_group_stride
+  const int *tiles = nullptr;
+  int64_t k_per_split = 0, drain_k = 16384;
+  int out_mode = TC_OUT_F64;     // F32 requires k_per_split <= drain_k
+  double *partial = nullptr;     // TC_OUT_F64
+  float *partial32 = nullptr;    // TC_OUT_F32
+  // TC_OUT_COLDOT (nt_group = 1): out[split][group][tile row][col] =
+  //   sum over the 128 tile rows r of D[r][col] * cd_B[col][r] (cd_B row-major, ld cd_ld)
+  const double *cd_B = nullptr;
+  int64_t cd_ld = 0;
+  int cd_rows = 0, cd_cols = 0;  // valid extent of cd_B's transpose (rows = D rows)
+  int n_tile_rows = 0, cd_cols_p = 0;
+  float *cd_out = nullptr;
+  int *err = nullptr;
+};
+cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s);
+size_t tc_gemm_smem_bytes();
+
+// ---- mixed-precision helpers (mixed.cu) ----
+// dst[c][r] = (float)src[r][c0 + c] for r < rows, c < cols; zero up to cols_p x rows_p
+// (batched over `batch` with strides in elements).
+cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0, int rows, int cols,
+                                     float *dst, int rows_p, int cols_p, int batch, int64_t strideS,
+                                     int64_t strideD, cudaStream_t s);
+// out[r][c] = alpha * sum over splits of full-grid partial tiles (tile = I * nJ + J) for
+// r < rows, c < cols; FP64 to out64 (ld ld64) and/or FP32 to out32 (ld ld32, zero padding
+// up to rows_p32 x ld32 is written too), per group g (strides in elements).
+cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32, int splits, int groups,
+                                  int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
+                                  int64_t ld64, int64_t stride64, float *out32, int64_t ld32,
+                                  int rows_p32, int64_t stride32, cudaStream_t s);
+// W[g][c] = sum over splits and tile rows of cd_out[split][g][I][c], c < cols.
+cudaError_t launch_tc_reduce_coldot(const float *cd_out, int splits, int groups, int n_tile_rows,
+                                    int cols_p, int cols, double *W, int64_t ldw, cudaStream_t s);
+// dst[r][c] = (float)src[r][c] for r < rows, c < cols; zero up to rows_p x cols_p.
+cudaError_t launch_to_f32_padded(const double *src, int64_t lds, int rows, int64_t cols, float *dst,
+                                 int rows_p, int64_t cols_p, cudaStream_t s);
+// scale[t][k] (FP32, zero for k >= K): direct w_t -> D/(w^2+D^2); Laplace (x_t, w_t) -> w D e^{-D^2 x}.
+cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n_t, const double *p0,
+                               const double *p1, int mode, float *scale, cudaStream_t s);
+// M_t = alpha * sum over splits of the partial tiles (FP64 or FP32), full symmetric
+// [n_t][N][N] FP64, for a lower tile list (tile_index [nI][nJ]).
+cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
+                                 int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
+                                 double *M, cudaStream_t s);
+// dst[c][r] = src[r][c0 + c] in FP64 (batched)
+cudaError_t launch_transpose_f64(const double *src, int64_t lds, int64_t c0, int rows, int cols, double *dst,
+                                 int64_t ldd, int batch, int64_t strideS, int64_t strideD, cudaStream_t s);
 
 // ---- self-energy, Pade and Newton (sigma_qp.cu) ----
 struct SigmaArgs {

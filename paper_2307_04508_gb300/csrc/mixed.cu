@@ -1,0 +1,228 @@
+// Bandwidth-bound helpers of the mixed-precision (split-BF16) path: FP32
+// padded operand copies, the per-pair scale table of the polarisability
+// (fused into the tensor-core operand load), and the FP64 reduction of the
+// split-K partial tiles into full symmetric matrices.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ltgw {
+namespace {
+
+__global__ void to_f32_padded_kernel(const double *__restrict__ src, int64_t lds, int rows, int64_t cols,
+                                     float *__restrict__ dst, int64_t cols_p) {
+  const int r = blockIdx.y;
+  const double *s = src + (int64_t)r * lds;
+  float *d = dst + (int64_t)r * cols_p;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cols_p;
+       c += (int64_t)gridDim.x * blockDim.x)
+    d[c] = (r < rows && c < cols) ? (float)s[c] : 0.0f;
+}
+
+__global__ void scale_table_kernel(const double *__restrict__ delta, int64_t K, int64_t Kp,
+                                   const double *__restrict__ p0, const double *__restrict__ p1,
+                                   int mode, float *__restrict__ scale) {
+  const int t = blockIdx.y;
+  const double a = p0 ? p0[t] : 0.0, b = p1 ? p1[t] : 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kp;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (k < K) {
+      const double d = delta ? delta[k] : 0.0;
+      v = (mode == SCALE_DIRECT) ? d / (a * a + d * d)
+          : (mode == SCALE_LAPLACE) ? b * d * exp(-d * d * a) : 1.0;
+    }
+    scale[(int64_t)t * Kp + k] = (float)v;
+  }
+}
+
+// One thread per lower-triangle element (i >= j) of one matrix t.  Partial
+// tiles are 128 x 128, four scales per group.
+__global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
+                                     int splits, int groups, int n_tiles, const int *__restrict__ tile_index,
+                                     int nJ, int N, double alpha, double *__restrict__ M) {
+  const int t = blockIdx.y;
+  const int grp = t / 4, slot = t % 4;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t ntri = (int64_t)N * (N + 1) / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ntri;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    // e -> (i, j), i >= j, row-major lower triangle
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while ((int64_t)i * (i + 1) / 2 > e) --i;
+    const int j = (int)(e - (int64_t)i * (i + 1) / 2);
+    const int tile = tile_index[(i / 128) * nJ + (j / 128)];
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      const int64_t off = ((((int64_t)s * groups + grp) * 4 + slot) * n_tiles + tile) * (128 * 128) +
+                          (i % 128) * 128 + (j % 128);
+      acc += partial32 ? (double)partial32[off] : partial[off];
+    }
+    acc *= alpha;
+    M[t * NN + (int64_t)i * N + j] = acc;
+    M[t * NN + (int64_t)j * N + i] = acc;
+  }
+}
+
+// dst[c][r] = src[r][c0 + c] (FP64 -> FP32), zero padding, 32 x 32 tiles through smem.
+__global__ void to_f32_transposed_kernel(const double *__restrict__ src, int64_t lds, int64_t c0, int rows,
+                                         int cols, float *__restrict__ dst, int rows_p, int cols_p,
+                                         int64_t strideS, int64_t strideD) {
+  __shared__ float tile[32][33];
+  const int b = blockIdx.z;
+  const double *S = src + b * strideS + c0;
+  float *D = dst + b * strideD;
+  const int r0 = blockIdx.y * 32, cb = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + q, c = cb + threadIdx.x;
+    tile[q][threadIdx.x] = (r < rows && c < cols) ? (float)S[(int64_t)r * lds + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int c = cb + q, r = r0 + threadIdx.x;
+    if (c < cols_p && r < rows_p) D[(int64_t)c * rows_p + r] = tile[threadIdx.x][q];
+  }
+}
+
+// dst[c][r] = src[r][c0 + c] in FP64, r < rows, c < cols (batched).
+__global__ void transpose_f64_kernel(const double *__restrict__ src, int64_t lds, int64_t c0, int rows, int cols,
+                                     double *__restrict__ dst, int64_t ldd, int64_t strideS, int64_t strideD) {
+  __shared__ double tile[32][33];
+  const int b = blockIdx.z;
+  const double *S = src + b * strideS + c0;
+  double *D = dst + b * strideD;
+  const int r0 = blockIdx.y * 32, cb = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + q, c = cb + threadIdx.x;
+    if (r < rows && c < cols) tile[q][threadIdx.x] = S[(int64_t)r * lds + c];
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int c = cb + q, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) D[(int64_t)c * ldd + r] = tile[threadIdx.x][q];
+  }
+}
+
+// Full-grid partial tiles -> FP64 and/or FP32 padded output, per group.
+__global__ void tc_reduce_full_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
+                                      int splits, int groups, int n_tiles, int nJ, int rows, int cols,
+                                      double alpha, double *__restrict__ out64, int64_t ld64, int64_t stride64,
+                                      float *__restrict__ out32, int64_t ld32, int rows_p32, int64_t stride32) {
+  const int g = blockIdx.z;
+  const int r = blockIdx.y;
+  const int grp = g, slot = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (out32 ? ld32 : cols);
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    if (r < rows && c < cols) {
+      const int tile = (r / 128) * nJ + (int)(c / 128);
+      const int64_t off = (int64_t)(r % 128) * 128 + (c % 128);
+      for (int s = 0; s < splits; ++s) {
+        const int64_t base = ((((int64_t)s * groups + grp) * 4 + slot) * n_tiles + tile) * (128 * 128);
+        acc += partial32 ? (double)partial32[base + off] : partial[base + off];
+      }
+      acc *= alpha;
+      if (out64) out64[g * stride64 + (int64_t)r * ld64 + c] = acc;
+    }
+    if (out32 && r < rows_p32) out32[g * stride32 + (int64_t)r * ld32 + c] = (float)acc;
+  }
+}
+
+__global__ void tc_reduce_coldot_kernel(const float *__restrict__ cd, int splits, int groups, int n_tile_rows,
+                                        int cols_p, int cols, double *__restrict__ W, int64_t ldw) {
+  const int g = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s)
+      for (int I = 0; I < n_tile_rows; ++I)
+        acc += (double)cd[(((int64_t)s * groups + g) * n_tile_rows + I) * cols_p + c];
+    W[(int64_t)g * ldw + c] = acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_to_f32_padded(const double *src, int64_t lds, int rows, int64_t cols, float *dst,
+                                 int rows_p, int64_t cols_p, cudaStream_t s) {
+  if (rows_p <= 0 || cols_p <= 0) return cudaSuccess;
+  int bx = (int)((cols_p + 255) / 256);
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, rows_p);
+  to_f32_padded_kernel<<<grid, 256, 0, s>>>(src, lds, rows, cols, dst, cols_p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n_t, const double *p0,
+                               const double *p1, int mode, float *scale, cudaStream_t s) {
+  if (n_t <= 0) return cudaSuccess;
+  int bx = (int)((Kp + 255) / 256);
+  if (bx > 152) bx = 152;
+  dim3 grid(bx, n_t);
+  scale_table_kernel<<<grid, 256, 0, s>>>(delta, K, Kp, p0, p1, mode, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
+                                 int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
+                                 double *M, cudaStream_t s) {
+  if (N <= 0 || n_t <= 0) return cudaSuccess;
+  int64_t ntri = (int64_t)N * (N + 1) / 2;
+  int bx = (int)((ntri + 255) / 256);
+  if (bx > 152 * 4) bx = 152 * 4;
+  dim3 grid(bx, n_t);
+  tc_reduce_sym_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, tile_index, nJ, N,
+                                            alpha, M);
+  return cudaGetLastError();
+}
+
+}  // namespace ltgw
+
+namespace ltgw {
+
+cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0, int rows, int cols,
+                                     float *dst, int rows_p, int cols_p, int batch, int64_t strideS,
+                                     int64_t strideD, cudaStream_t s) {
+  if (rows_p <= 0 || cols_p <= 0 || batch <= 0) return cudaSuccess;
+  dim3 block(32, 8), grid((cols_p + 31) / 32, (rows_p + 31) / 32, batch);
+  to_f32_transposed_kernel<<<grid, block, 0, s>>>(src, lds, c0, rows, cols, dst, rows_p, cols_p, strideS, strideD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32, int splits, int groups,
+                                  int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
+                                  int64_t ld64, int64_t stride64, float *out32, int64_t ld32,
+                                  int rows_p32, int64_t stride32, cudaStream_t s) {
+  const int nrows = out32 ? std::max(rows, rows_p32) : rows;
+  const int64_t ncols = out32 ? ld32 : cols;
+  if (nrows <= 0 || ncols <= 0 || groups <= 0) return cudaSuccess;
+  int bx = (int)((ncols + 255) / 256);
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, nrows, groups);
+  tc_reduce_full_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, nJ, rows, cols, alpha,
+                                             out64, ld64, stride64, out32, ld32, rows_p32, stride32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f64(const double *src, int64_t lds, int64_t c0, int rows, int cols, double *dst,
+                                 int64_t ldd, int batch, int64_t strideS, int64_t strideD, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return cudaSuccess;
+  dim3 block(32, 8), grid((cols + 31) / 32, (rows + 31) / 32, batch);
+  transpose_f64_kernel<<<grid, block, 0, s>>>(src, lds, c0, rows, cols, dst, ldd, strideS, strideD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_reduce_coldot(const float *cd_out, int splits, int groups, int n_tile_rows, int cols_p,
+                                    int cols, double *W, int64_t ldw, cudaStream_t s) {
+  if (cols <= 0 || groups <= 0) return cudaSuccess;
+  int bx = (cols + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, groups);
+  tc_reduce_coldot_kernel<<<grid, 256, 0, s>>>(cd_out, splits, groups, n_tile_rows, cols_p, cols, W, ldw);
+  return cudaGetLastError();
+}
+
+}  // namespace ltgw

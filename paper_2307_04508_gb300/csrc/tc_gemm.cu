@@ -1,0 +1,429 @@
+// Split-BF16 tensor-core contraction on sm_103a (tcgen05 + TMEM):
+//
+//   D_t[i][j] = sum_k A[i][k] s_t[k] B[j][k],   t = 0..n_t-1 (n_t <= 8)
+//
+// the scaled rank-k products of the LT-GW path (Pi(tau_k) moments, Eq. LT
+// and the M^m form; the NAF metric, Eq. nafeq; projections and the W_nm
+// contraction, Eqs. naftrafo and ScreenedCoulombOrbital) in the mixed
+// precision form: each operand value x is split into x_hi = bf16(x) and
+// x_lo = bf16(x - x_hi), and D accumulates hi*hi + hi*lo + lo*hi with FP32
+// accumulation in tensor memory, drained into FP64 every `drain_k` pairs.
+//
+// Operands are FP32, K-major, zero-padded to multiples of the tile (rows to
+// 128 / 64, K to 64) so the kernel needs no bounds checks.  The scale s_t is
+// applied to the A operand by the converter warps as they fill shared memory
+// (the per-pair scale is fused into the operand load); B is split once per
+// K-chunk and reused by all n_t products.
+//
+// CTA = one 128 x 128 output tile for up to 4 scales (4 x 128 TMEM columns),
+// one K-split range.  Operand tiles of 128 x 128 keep the tensor core's
+// shared-memory operand traffic within bandwidth.  Warp roles (21 warps):
+//   warp 0       TMEM allocation; lane 0 issues tcgen05.mma
+//   warps 1-16   converters: FP32 global -> scaled BF16 hi/lo in the 128B-swizzled
+//                K-major layout the tensor core reads
+//   warps 17-20  epilogue: tcgen05.ld of the accumulators, FP64 partial sums
+// Every mbarrier wait is bounded (about two seconds of wall time); on expiry
+// the CTA records an error flag and unwinds.
+#include <cuda_bf16.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ltgw {
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 64;    // tile rows (A), cols (B), K chunk
+constexpr int MAXT = 4;                       // scales per CTA (TMEM: 4 x 128 columns)
+constexpr int SA = 4, SB = 2;                 // A / B stage ring depths
+constexpr int CONV_WARPS = 16, EPI_WARPS = 4;
+constexpr int NTHREADS = 32 * (1 + CONV_WARPS + EPI_WARPS);
+constexpr uint32_t A_BYTES = TM * TK * 2;      // one bf16 tile, 16 KB
+constexpr uint32_t B_BYTES = TN * TK * 2;      // 16 KB
+constexpr uint32_t A_STAGE = 2 * A_BYTES;      // hi + lo
+constexpr uint32_t B_STAGE = 2 * B_BYTES;
+constexpr uint32_t SMEM_BYTES = SA * A_STAGE + SB * B_STAGE + 1024;  // + alignment slack
+
+struct Bars {
+  alignas(16) float scale[2][MAXT][TK];   // scale ring (converters only), read as float4
+  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full, acc_empty, fin;
+  uint64_t s_full[2], s_empty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+static_assert(offsetof(Bars, scale) % 16 == 0, "scale ring must be 16-byte aligned for float4 reads");
+static_assert((TK * sizeof(float)) % 16 == 0, "scale rows must keep 16-byte alignment");
+static_assert(offsetof(Bars, a_full) % 8 == 0, "mbarriers need 8-byte alignment");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on time-out (or, when
+// honor_abort, as soon as another role of the CTA has given up).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Bars *bars, int *err,
+                                          bool honor_abort = true) {
+  uint32_t done = 0;
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023) == 0) {
+      if (honor_abort && *(volatile int *)&bars->abort) return false;
+      uint64_t t = globaltimer();
+      if (it == 0) t0 = t;
+      else if (t - t0 > 2000000000ull) {
+        atomicExch(&err[FLAG_TC_TIMEOUT], 1);
+        *(volatile int *)&bars->abort = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused, swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// kind::f16, D = FP32, A = B = BF16, both K-major, M = 128, N = 64.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// Byte offset of the 16-byte chunk c (k = 8c..8c+7) of row r in a K-major,
+// 128B-swizzled tile: 8-row atoms of 1024 B, chunk index XOR (row mod 8).
+__device__ __forceinline__ uint32_t swz(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+// Split 8 floats into bf16 hi / lo and store both 16-byte chunks.
+__device__ __forceinline__ void split_store(const float v[8], uint8_t *hi, uint8_t *lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+    float2 hf = __bfloat1622float2(hb);
+    __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+    h[q] = *reinterpret_cast<uint32_t *>(&hb);
+    l[q] = *reinterpret_cast<uint32_t *>(&lb);
+  }
+  *reinterpret_cast<uint4 *>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4 *>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void load8(const float *p, float v[8]) {
+  float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+  float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = smem;                       // SA stages of [hi | lo]
+  uint8_t *sB = smem + SA * A_STAGE;        // SB stages of [hi | lo]
+  __shared__ __align__(16) Bars bars;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, grp = blockIdx.y, split = blockIdx.z;
+  const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
+  const int t0 = grp * g.nt_group;
+  const int nt = min(g.nt_group, g.n_t - t0);
+  const float *Ag = g.A + (int64_t)grp * g.a_group_stride;
+  const int64_t kb = (int64_t)split * g.k_per_split;
+  const int64_t ke = min(g.Kp, kb + g.k_per_split);
+  const int nchunks = (int)((ke - kb) / TK);
+  const int chunks_per_drain = (int)(g.drain_k / TK);
+  const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
+    for (int s = 0; s < SB; ++s) { mbar_init(&bars.b_full[s], CONV_WARPS); mbar_init(&bars.b_empty[s], 1); }
+    for (int s = 0; s < 2; ++s) { mbar_init(&bars.s_full[s], 8); mbar_init(&bars.s_empty[s], CONV_WARPS); }
+    mbar_init(&bars.acc_full, 1);
+    mbar_init(&bars.acc_empty, 32 * EPI_WARPS);
+    mbar_init(&bars.fin, 1);
+    bars.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        smem_u32(&bars.tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = bars.tmem_base;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int ia = 0, ib = 0;
+      uint32_t pa = 0, pb = 0;
+      bool ok = true;
+      for (int dr = 0; dr < ndrains && ok; ++dr) {
+        ok = mbar_wait(&bars.acc_empty, (dr & 1) ^ 1, &bars, g.err);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
+        for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
+          ok = mbar_wait(&bars.b_full[ib], pb, &bars, g.err);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t bhi = smem_u32(sB + ib * B_STAGE), blo = bhi + B_BYTES;
+          for (int t = 0; t < nt; ++t) {
+            ok = mbar_wait(&bars.a_full[ia], pa, &bars, g.err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ahi = smem_u32(sA + ia * A_STAGE), alo = ahi + A_BYTES;
+            const uint32_t d = tmem + (uint32_t)(t * TN);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk) {
+              const uint32_t off = kk * 32;
+              const uint32_t first = (c == dr * chunks_per_drain && kk == 0) ? 0u : 1u;
+              mma_bf16(d, make_desc(ahi + off), make_desc(bhi + off), first);
+              mma_bf16(d, make_desc(ahi + off), make_desc(blo + off), 1u);
+              mma_bf16(d, make_desc(alo + off), make_desc(bhi + off), 1u);
+            }
+            mma_commit(&bars.a_empty[ia]);
+            if (++ia == SA) { ia = 0; pa ^= 1; }
+          }
+          mma_commit(&bars.b_empty[ib]);
+          if (++ib == SB) { ib = 0; pb ^= 1; }
+        }
+        if (ok) mma_commit(&bars.acc_full);
+      }
+      // all issued MMAs complete before the CTA tears down
+      mma_commit(&bars.fin);
+      mbar_wait(&bars.fin, 0, &bars, g.err, false);
+    }
+    __syncwarp();
+  } else if (warp <= CONV_WARPS) {
+    // ---------------------------------------------------------------- converters
+    // Each thread converts rows r and r + 64 of both tiles at one 16-byte chunk
+    // (8 k values); one mbarrier arrival per warp after __syncwarp keeps the
+    // barrier traffic at 16 arrivals per stage.
+    const int ct = threadIdx.x - 32;           // 0 .. CONV_THREADS-1
+    const int cc = ct & 7;                     // 16-byte chunk (8 k values) within TK
+    const int r0 = ct >> 3, r1 = r0 + 64;      // 128 rows x 8 chunks = 1024 units, 2 per thread
+    const float *Ar0 = Ag + (int64_t)(ti * TM + r0) * g.Kp + cc * 8;
+    const float *Ar1 = Ag + (int64_t)(ti * TM + r1) * g.Kp + cc * 8;
+    const float *Br0 = g.B + (int64_t)(tj * TN + r0) * g.Kp + cc * 8;
+    const float *Br1 = g.B + (int64_t)(tj * TN + r1) * g.Kp + cc * 8;
+    // scales: threads 0..255 each fetch one value of the next chunk's 4 x 64
+    // table and publish it through a two-slot shared ring
+    const int st_t = ct >> 6, st_k = ct & 63;
+    const bool st_writer = ct < MAXT * TK;
+    const float *Sg = g.scale + (int64_t)(t0 + st_t) * g.Kp + st_k;
+    const bool st_live = st_writer && st_t < nt;
+    const uint32_t o0 = swz(r0, cc), o1 = swz(r1, cc);
+    int ia = 0, ib = 0;
+    uint32_t pa = 0, pb = 0;
+    float a0[8], a1[8], b0[8], b1[8], n0[8], n1[8], m0[8], m1[8];
+    float snext = st_live ? __ldg(Sg + kb) : 0.0f;
+    load8(Ar0 + kb, n0);
+    load8(Ar1 + kb, n1);
+    load8(Br0 + kb, m0);
+    load8(Br1 + kb, m1);
+    bool ok = true;
+    // publish chunk 0's scales
+    if (st_writer) {
+      bars.scale[0][st_t][st_k] = snext;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.s_full[0]);
+    }
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int64_t k0 = kb + (int64_t)c * TK;
+      const int sb = c & 1;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { a0[q] = n0[q]; a1[q] = n1[q]; b0[q] = m0[q]; b1[q] = m1[q]; }
+      if (c + 1 < nchunks) {  // prefetch the next chunk while this one converts
+        load8(Ar0 + k0 + TK, n0);
+        load8(Ar1 + k0 + TK, n1);
+        load8(Br0 + k0 + TK, m0);
+        load8(Br1 + k0 + TK, m1);
+        snext = st_live ? __ldg(Sg + k0 + TK) : 0.0f;
+      }
+      if (!mbar_wait(&bars.b_empty[ib], pb ^ 1, &bars, g.err)) break;
+      {
+        uint8_t *hi = sB + ib * B_STAGE;
+        split_store(b0, hi + o0, hi + B_BYTES + o0);
+        split_store(b1, hi + o1, hi + B_BYTES + o1);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.b_full[ib]);
+      if (++ib == SB) { ib = 0; pb ^= 1; }
+      if (!mbar_wait(&bars.s_full[sb], (c >> 1) & 1, &bars, g.err)) break;
+      for (int t = 0; t < nt; ++t) {
+        float sc[8], v0[8], v1[8];
+        {
+          const float4 *sp = reinterpret_cast<const float4 *>(&bars.scale[sb][t][cc * 8]);
+          float4 x = sp[0], y = sp[1];
+          sc[0] = x.x; sc[1] = x.y; sc[2] = x.z; sc[3] = x.w;
+          sc[4] = y.x; sc[5] = y.y; sc[6] = y.z; sc[7] = y.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { v0[q] = a0[q] * sc[q]; v1[q] = a1[q] * sc[q]; }
+        if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars, g.err)) { ok = false; break; }
+        uint8_t *hi = sA + ia * A_STAGE;
+        split_store(v0, hi + o0, hi + A_BYTES + o0);
+        split_store(v1, hi + o1, hi + A_BYTES + o1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.a_full[ia]);
+        if (++ia == SA) { ia = 0; pa ^= 1; }
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.s_empty[sb]);   // this warp is done with chunk c's scales
+      if (c + 1 < nchunks && st_writer) {              // publish chunk c+1's scales
+        const int nbuf = (c + 1) & 1;
+        if (!mbar_wait(&bars.s_empty[nbuf], (((c + 1) >> 1) & 1) ^ 1, &bars, g.err)) break;
+        bars.scale[nbuf][st_t][st_k] = snext;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.s_full[nbuf]);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int ew = warp & 3;                   // TMEM lane quarter this warp may read
+    const int row = ew * 32 + lane;
+    const int64_t tile_elems = (int64_t)TM * TN;
+    const int64_t base = (((int64_t)split * gridDim.y + grp) * MAXT * gridDim.x + tile) * tile_elems;
+    const int64_t tstride = (int64_t)gridDim.x * tile_elems;   // between scales
+    __shared__ float cd_red[EPI_WARPS][TN];
+    for (int dr = 0; dr < ndrains; ++dr) {
+      if (!mbar_wait(&bars.acc_full, dr & 1, &bars, g.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int t = 0; t < nt; ++t) {
+        for (int h = 0; h < TN / 32; ++h) {
+          uint32_t r[32];
+          const uint32_t a = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(t * TN + h * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(a));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (g.out_mode == TC_OUT_F64) {
+            double *oh = g.partial + base + t * tstride + (int64_t)row * TN + h * 32;
+            if (dr == 0) {
+#pragma unroll
+              for (int q = 0; q < 32; q += 2)
+                *reinterpret_cast<double2 *>(oh + q) =
+                    make_double2((double)__uint_as_float(r[q]), (double)__uint_as_float(r[q + 1]));
+            } else {
+#pragma unroll
+              for (int q = 0; q < 32; q += 2) {
+                double2 v = *reinterpret_cast<double2 *>(oh + q);
+                v.x += (double)__uint_as_float(r[q]);
+                v.y += (double)__uint_as_float(r[q + 1]);
+                *reinterpret_cast<double2 *>(oh + q) = v;
+              }
+            }
+          } else if (g.out_mode == TC_OUT_F32) {
+            float *oh = g.partial32 + base + t * tstride + (int64_t)row * TN + h * 32;
+#pragma unroll
+            for (int q = 0; q < 32; q += 4)
+              *reinterpret_cast<uint4 *>(oh + q) = make_uint4(r[q], r[q + 1], r[q + 2], r[q + 3]);
+          } else {
+            // column dot: D[row][col] * cd_B[col][row], summed over the 128 rows
+            const int grow = ti * TM + row;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int col = tj * TN + h * 32 + q;
+              float prod = 0.0f;
+              if (grow < g.cd_rows && col < g.cd_cols)
+                prod = __uint_as_float(r[q]) * (float)g.cd_B[(int64_t)col * g.cd_ld + grow];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) prod += __shfl_xor_sync(0xffffffffu, prod, o);
+              if (lane == 0) cd_red[ew][h * 32 + q] = prod;
+            }
+          }
+        }
+      }
+      if (g.out_mode == TC_OUT_COLDOT) {
+        asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI_WARPS) : "memory");   // epilogue warps only
+        if (row < TN) {
+          const float v = cd_red[0][row] + cd_red[1][row] + cd_red[2][row] + cd_red[3][row];
+          g.cd_out[(((int64_t)split * gridDim.y + grp) * g.n_tile_rows + ti) * g.cd_cols_p + tj * TN + row] = v;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(&bars.acc_empty);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+}  // namespace
+
+size_t tc_gemm_smem_bytes() { return SMEM_BYTES; }
+
+cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
+  if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
+  if (g.Kp % TK || g.k_per_split % TK || g.drain_k % TK || g.k_per_split <= 0 || g.drain_k <= 0)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(tc_split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  if (g.nt_group < 1 || g.nt_group > MAXT) return cudaErrorInvalidValue;
+  if (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) return cudaErrorInvalidValue;
+  if (g.out_mode == TC_OUT_COLDOT && (g.nt_group != 1 || g.k_per_split > g.drain_k)) return cudaErrorInvalidValue;
+  const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
+  const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
+  dim3 grid(n_tiles, groups, splits);
+  tc_split_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace ltgw

@@ -61,6 +61,7 @@ SIGNATURES = {
     "ltgw_laplace_grid": (_I, [_I, _D, _D, _P, _P, _P]),
     "ltgw_naf_basis": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "ltgw_polarizability_mixed": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
     "ltgw_screen_static": (_I, [_I, _I, _P, _P, _P]),
 }
@@ -187,6 +188,18 @@ class Context:
         ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
         st = self._lib.ltgw_polarizability(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om), _ptr(om),
                                            n_tau, _ptr(xx), _ptr(ww), spin, _ptr(Pi), _stream_ptr(stream))
+        self._check(st)
+
+    def polarizability_mixed(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None,
+                             stream=None):
+        N, n_pairs = int(Bt.shape[0]), int(Bt.shape[1])
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        n_tau = 0 if x is None else len(x)
+        xx = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        st = self._lib.ltgw_polarizability_mixed(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om),
+                                                 _ptr(om), n_tau, _ptr(xx), _ptr(ww), spin, _ptr(Pi),
+                                                 _stream_ptr(stream))
         self._check(st)
 
     def screen(self, Pi, C, stream=None):

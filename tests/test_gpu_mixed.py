@@ -1,0 +1,102 @@
+"""Mixed-precision (split-BF16 on tcgen05) polarisability against the FP64 oracle.
+
+The mixed form keeps about 16 bits per operand (x = bf16(x) + bf16(x - bf16(x)),
+three products) with FP32 accumulation drained to FP64 every 16384 pairs, so
+the bar here is a relative Frobenius error of 5e-5 on Pi and 1 meV on the
+quasi-particle energies (the mixed-precision target)."""
+import numpy as np
+import pytest
+
+from oracle import ltgw_oracle as O
+from paper_2307_04508_gb300 import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PI_TOL_MIXED = 5e-5
+QP_TOL_MIXED = 1e-3 / 27.211386245988  # 1 meV in Ha
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2307_04508_gb300 import ltgw
+    c = ltgw.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("N,P,n_om", [(1, 1, 3), (37, 301, 12), (130, 2000, 9), (200, 9000, 20)])
+def test_mixed_polarizability_direct_and_laplace(ctx, N, P, n_om):
+    rng = np.random.default_rng(N + P)
+    Bt = rng.standard_normal((N, P)) * 0.05
+    delta = rng.uniform(0.3, 4.0, P)
+    om, _ = O.gl_grid(n_om, 0.5)
+    Pi = torch.empty((n_om, N, N), dtype=torch.float64, device="cuda")
+    ctx.polarizability_mixed(_dev(Bt), _dev(delta), om, Pi, spin=2)
+    got = Pi.cpu().numpy()
+    ref = O.polarizability_direct(Bt, delta, om, 2)
+    err = _rel(got, ref)
+    print(f"direct N={N} P={P}: rel Frobenius error {err:.2e}")
+    assert err <= PI_TOL_MIXED
+    assert np.array_equal(got, np.swapaxes(got, 1, 2))
+    x, w = O.sinc_laplace_grid(7, -6.0, 2.0)
+    ctx.polarizability_mixed(_dev(Bt), _dev(delta), om, Pi, spin=2, x=x, w=w)
+    refl = O.polarizability_lt(O.laplace_moments(Bt, delta, x, w), om, x, 2)
+    errl = _rel(Pi.cpu().numpy(), refl)
+    print(f"laplace N={N} P={P}: rel Frobenius error {errl:.2e}")
+    assert errl <= PI_TOL_MIXED
+
+
+def test_mixed_solve_mid_workload(ctx):
+    """Mid workload (1800 auxiliary functions, NAF 1e-2) with Pi on the tensor
+    cores: QP energies within 1 meV of the FP64 oracle fed the same Laplace grid."""
+    from paper_2307_04508_gb300 import ltgw
+    prob = S.make_workload(S.MID)
+    tau = O.sinc_laplace_grid(8, -12.0, 3.0)
+    _, e_o, st_o = O.solve(prob.eps, prob.B_ov, prob.B_tgt, prob.targets, prob.shift, 60, 540, 10, n_omega=32,
+                           naf_thresh=1e-2, tau_x=tau[0], tau_w=tau[1])
+    p = ltgw.make_params(60, 540, 1800, 10, 32, 8, 0.5, 1e-2, 2, True, ltgw.LTGW_BF16X3)
+    T = len(prob.targets)
+    sig, e, st = np.zeros((T, 32, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
+    dev = [_dev(a) for a in (prob.eps, prob.B_ov, prob.B_tgt, prob.targets.astype(np.int32), prob.shift)]
+    ctx.solve(p, *dev, sig, e, st, tau_x=np.ascontiguousarray(tau[0]), tau_w=np.ascontiguousarray(tau[1]))
+    err = np.abs(e - e_o).max()
+    print(f"mixed solve: max QP error {err * 27211.386:.4f} meV")
+    assert np.all(st == 0) and err <= QP_TOL_MIXED
+
+
+@pytest.mark.parametrize("case", ["tiny_direct_nonaf", "ragged_naf_laplace", "ragged_frozen_direct_naf"])
+def test_mixed_solve_variants(ctx, case):
+    """Mixed form against the FP64 oracle in the same mode: every contraction
+    (NAF metric, projections, Pi, W_nm) on the tensor cores, the eigensolver,
+    screening, Pade and Newton in FP64."""
+    from paper_2307_04508_gb300 import ltgw
+    if case == "tiny_direct_nonaf":
+        prob, n_om, thr, tau = S.make_workload(S.TINY), 24, -1.0, None
+    elif case == "ragged_naf_laplace":
+        prob, n_om, thr = S.make_problem(9, 70, 150, n_frozen=1, seed=99, n_targets=3), 17, 5e-3
+        tau = O.sinc_laplace_grid(9, -11.0, 2.5)
+    else:
+        prob, n_om, thr, tau = S.make_problem(7, 45, 131, n_frozen=2, seed=4242, n_targets=4), 21, 1e-3, None
+    tx, tw = (None, None) if tau is None else tau
+    _, e_o, st_o = O.solve(prob.eps, prob.B_ov, prob.B_tgt, prob.targets, prob.shift, prob.n_occ, prob.n_virt,
+                           prob.n_frozen, n_omega=n_om, naf_thresh=thr, tau_x=tx, tau_w=tw)
+    p = ltgw.make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, n_om, 0 if tau is None else len(tx),
+                         0.5, thr, 2, tau is not None, ltgw.LTGW_BF16X3)
+    T = len(prob.targets)
+    sig, e, st = np.zeros((T, n_om, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
+    ctx.solve(p, prob.eps, prob.B_ov, prob.B_tgt, prob.targets.astype(np.int32), prob.shift, sig, e, st,
+              tau_x=None if tau is None else np.ascontiguousarray(tx),
+              tau_w=None if tau is None else np.ascontiguousarray(tw))
+    err = np.abs(e - e_o).max()
+    print(f"mixed solve {case}: max QP error {err * 27211.386:.4f} meV")
+    assert np.all(st == 0) and np.all(st_o == 0) and err <= QP_TOL_MIXED
