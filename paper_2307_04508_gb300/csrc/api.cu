@@ -162,8 +162,9 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     w.X = A.take<double>((size_t)n * n);
     w.lu = A.take<double>((size_t)5 * n * n);
     w.count = A.take<int>(2);
-    const int64_t nsplit = (n + 255) / 256;
+    const int64_t nsplit = (n + 63) / 64;
     w.wy = A.take<double>((size_t)(nsplit + 3) * 64 * (64 + (size_t)n));
+    w.grid_ws = A.take<double>((size_t)n + 2 * (size_t)ctx->n_sm + 8);
   };
   ar.begin_sizing();
   layout(ar);
@@ -172,6 +173,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     return ctx->status();
   }
   layout(ar);
+  w.flags = ctx->flags;
   if (mixed) {
     if (naf_metric_tc(ctx, n, n_pairs, B, ld, w.A, s) != LTGW_OK) return ctx->status();
   } else {
@@ -704,8 +706,8 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     }
     d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
     d_Pi = A.take<double>((size_t)n_omega * N * N);
-    d_X0 = A.take<double>((size_t)n_omega * N * N);
-    d_X1 = A.take<double>((size_t)n_omega * N * N);
+    d_X0 = A.take<double>(screen_blocked_scratch(N, n_omega));
+    d_X1 = nullptr;
     d_C = A.take<double>((size_t)n_omega * N * N);
     d_W = A.take<double>((size_t)n_omega * T * n_orb_act);
     d_sig = A.take<double>((size_t)T * n_omega * 2);
@@ -756,7 +758,7 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
 
   // ---- screening
   int nl = 0;
-  cudaError_t e = launch_screen(d_Pi, N, n_omega, d_X0, d_X1, d_C, ctx->flags, s, &nl);
+  cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl);
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
   ctx->mark(EV_SCREEN, s);
@@ -931,18 +933,15 @@ ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, dou
   REQUIRE(ctx, is_device_ptr(Pi) && is_device_ptr(C), "Pi and C must be device pointers");
   LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  double *X0, *X1;
-  auto layout = [&](Arena &A) {
-    X0 = A.take<double>((size_t)n_omega * N * N);
-    X1 = A.take<double>((size_t)n_omega * N * N);
-  };
+  double *X0;
+  auto layout = [&](Arena &A) { X0 = A.take<double>(screen_blocked_scratch(N, n_omega)); };
   ctx->a2.begin_sizing();
   layout(ctx->a2);
   if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
   layout(ctx->a2);
   LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
   int nl = 0;
-  cudaError_t e = launch_screen(Pi, N, n_omega, X0, X1, C, ctx->flags, s, &nl);
+  cudaError_t e = launch_screen_blocked(Pi, N, n_omega, X0, C, ctx->flags, s, &nl);
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
   LTGW_CUDA(ctx, cudaStreamSynchronize(s));
   return check_flags(ctx, s);

@@ -122,6 +122,174 @@ __global__ void hh_update_kernel(double *__restrict__ A, const double *__restric
   }
 }
 
+// ---- persistent Householder reduction (one cooperative launch) ----
+// All n-2 reflector steps in one kernel.  Row r of the working matrix belongs
+// to one warp for the whole reduction, so each
+// row is read and written by one SM only; data one block writes and another
+// reads (v, p, the column being reduced, the partial sums) go through L2
+// (ld.global.cg).  Rows are dealt round-robin over blocks, then warps.
+// Per step: [every block forms the reflector from the column in L2; p = tau
+// A22 v on its rows; partial p.v] barrier [rank-2 update + the next column's
+// partial norm] barrier.  Grid barriers use release/acquire atomics, are
+// bounded (about two seconds) and report through flags.
+struct GridBar {
+  unsigned count, gen;
+  int abort;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ bool grid_barrier(GridBar *gb, int *flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire(&gb->gen);
+    if (atom_add_acq_rel(&gb->count, 1u) == gridDim.x - 1) {
+      gb->count = 0;
+      atom_add_acq_rel(&gb->gen, 1u);   // release: the reset and every arrival happen-before
+    } else {
+      const uint64_t t0 = gtimer();
+      unsigned it = 0;
+      while (ld_acquire(&gb->gen) == g) {
+        if ((++it & 1023) == 0) {
+          if (*(volatile int *)&gb->abort) { ok = 0; break; }
+          if (gtimer() - t0 > 2000000000ull) {
+            atomicExch(&flags[FLAG_EIG], 1);
+            atomicExch(&gb->abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Fixed-order sum of the per-block partials (identical in every block).
+__device__ double sum_partials(const double *part, double *sh) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(part + b);
+  return block_sum(v, sh);
+}
+
+__global__ void __launch_bounds__(512) hh_persistent_kernel(double *A, double *V, double *d, double *e,
+                                                            double *tau, double *P, double *part1, double *part2,
+                                                            GridBar *gb, int n, int *flags) {
+  extern __shared__ double sm_vp[];   // v[n], p[n]
+  __shared__ double sh[32];
+  double *sv = sm_vp, *sp = sm_vp + n;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  // rows go round-robin over blocks first, so every SM gets rows
+  const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int nw = gridDim.x * wpb;
+  // partial norm of column 0 below the subdiagonal
+  {
+    double acc = 0.0;
+    for (int r = gw; r < n; r += nw)
+      if (r >= 2 && lane == 0) { double x = A[(int64_t)r * n]; acc += x * x; }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part1[blockIdx.x] = acc;
+  }
+  if (!grid_barrier(gb, flags)) return;
+  for (int k = 0; k + 2 < n; ++k) {
+    // ---- reflector for column k (x = A[k+1:n, k]), computed by every block
+    const double sigma = sum_partials(part1, sh);
+    const double alpha = __ldcg(A + (int64_t)(k + 1) * n + k);
+    double t, beta, sc;
+    if (sigma == 0.0) {
+      t = 0.0; beta = alpha; sc = 0.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sigma);
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      t = (beta - alpha) / beta;
+      sc = 1.0 / (alpha - beta);
+    }
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const double v = (j == k + 1) ? 1.0 : __ldcg(A + (int64_t)j * n + k) * sc;
+      sv[j] = v;
+      if (blockIdx.x == 0) V[(int64_t)k * n + j] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      d[k] = __ldcg(A + (int64_t)k * n + k);
+      e[k] = beta;
+      tau[k] = t;
+    }
+    __syncthreads();
+    // ---- p = tau A22 v (rows k+1..n-1), partial p.v
+    double pv = 0.0;
+    for (int r = gw; r < n; r += nw) {
+      if (r < k + 1) continue;
+      const double *row = A + (int64_t)r * n;
+      // 8 independent loads in flight per lane: the row streams from L2
+      double a8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int j = k + 1 + lane;
+      for (; j + 7 * 32 < n; j += 8 * 32) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = row[j + u * 32];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a8[u] = fma(x[u], sv[j + u * 32], a8[u]);
+      }
+      for (; j < n; j += 32) a8[0] = fma(row[j], sv[j], a8[0]);
+      double acc = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        const double pr = t * acc;
+        P[r] = pr;
+        pv += pr * sv[r];
+      }
+    }
+    pv = block_sum(pv, sh);
+    if (threadIdx.x == 0) part2[blockIdx.x] = pv;
+    if (!grid_barrier(gb, flags)) return;
+    // ---- A22 -= v w^T + w v^T with w = p - (tau/2)(p.v) v; next column's partial norm
+    const double gamma = 0.5 * t * sum_partials(part2, sh);
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) sp[j] = __ldcg(P + j) - gamma * sv[j];
+    __syncthreads();
+    double nx = 0.0;
+    for (int r = gw; r < n; r += nw) {
+      if (r < k + 1) continue;
+      double *row = A + (int64_t)r * n;
+      const double vr = sv[r], wr = sp[r];
+      int j = k + 1 + lane;
+      for (; j + 7 * 32 < n; j += 8 * 32) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = row[j + u * 32];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) row[j + u * 32] = x[u] - (vr * sp[j + u * 32] + wr * sv[j + u * 32]);
+      }
+      for (; j < n; j += 32) row[j] -= vr * sp[j] + wr * sv[j];
+      __syncwarp();
+      if (lane == 0 && r >= k + 3) { const double x = row[k + 1]; nx += x * x; }
+    }
+    nx = block_sum(nx, sh);
+    if (threadIdx.x == 0) part1[blockIdx.x] = nx;
+    if (!grid_barrier(gb, flags)) return;
+  }
+}
+
 // Last diagonal / off-diagonal entries once every reflector is applied.
 __global__ void hh_finalize_kernel(const double *A, double *d, double *e, int n) {
   if (threadIdx.x != 0) return;
@@ -133,6 +301,20 @@ __global__ void hh_finalize_kernel(const double *A, double *d, double *e, int n)
   e[n - 1] = 0.0;
 }
 
+// 1/q from the hardware reciprocal estimate refined by three Newton steps
+// y <- y (2 - q y) (each step squares the relative error), about 1 ulp: the
+// Sturm count below is exact for a matrix perturbed by a few ulps anyway, and
+// this avoids the IEEE division sequence, which is costly on this part's
+// FP64 pipe.  |q| >= pivmin > 0 keeps q away from zero and subnormals.
+__device__ __forceinline__ double recip_nr(double q) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
+  y = y * fma(-q, y, 2.0);
+  y = y * fma(-q, y, 2.0);
+  y = y * fma(-q, y, 2.0);
+  return y;
+}
+
 // Number of eigenvalues of T below x (signs of the LDL^T pivots of T - x).
 __device__ int sturm_count(const double *d, const double *e2, int n, double x, double pivmin) {
   int c = 0;
@@ -140,7 +322,7 @@ __device__ int sturm_count(const double *d, const double *e2, int n, double x, d
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0.0) ++c;
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    q = d[i] - x - e2[i - 1] * recip_nr(q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0.0) ++c;
   }
@@ -187,11 +369,14 @@ __global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *d, con
 }
 
 // lam[r] = (n-1-r)-th smallest eigenvalue (r-th largest), r < k, by
-// multisection: one warp per eigenvalue, each lane counts the eigenvalues
-// below one of 32 interior points of the current interval, so an interval
-// shrinks 33-fold per step.  d and e^2 are staged in shared memory.
+// multisection with BIS_L lanes per eigenvalue: each lane counts the
+// eigenvalues below one of BIS_L interior points, so an interval shrinks
+// (BIS_L + 1)-fold per step.  Few lanes per eigenvalue keep the total number
+// of FP64 divisions (the cost on this part) near that of plain bisection while
+// giving enough threads to hide their latency.  d and e^2 live in shared memory.
+constexpr int BIS_L = 4;
 __global__ void bisect_kernel(const double *d, const double *e2g, const double *scal, int n,
-                              int k, double *lam) {
+                              int k, int epw, double *lam) {
   extern __shared__ double sm[];
   double *sd = sm, *se2 = sm + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -200,32 +385,42 @@ __global__ void bisect_kernel(const double *d, const double *e2g, const double *
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= k) return;
-  const int idx = n - 1 - r;  // ascending index of the wanted eigenvalue
+  const int sub = lane % BIS_L, grp = lane / BIS_L;
+  const unsigned gmask = ((1u << BIS_L) - 1u) << (grp * BIS_L);
+  const int r = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * epw + grp;
+  const bool live = grp < epw && r < k;
+  const int idx = n - 1 - (live ? r : 0);  // ascending index of the wanted eigenvalue
   double lo = scal[1], hi = scal[2];
   const double pivmin = scal[3];
-  for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const bool above = sturm_count(sd, se2, n, x, pivmin) > idx;  // eigenvalue idx < x
-    const unsigned b = __ballot_sync(0xffffffffu, above);
-    const int j = b ? (__ffs(b) - 1) : 32;
-    const double nlo = (j == 0) ? lo : lo + (hi - lo) * (double)j / 33.0;
-    const double nhi = (j == 32) ? hi : lo + (hi - lo) * (double)(j + 1) / 33.0;
-    if (!(nlo > lo || nhi < hi)) break;  // no progress at this resolution
-    lo = nlo;
-    hi = nhi;
+  bool done = !live;
+  for (int it = 0; it < 200; ++it) {
+    if (!done && hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
+    if (__all_sync(0xffffffffu, done)) break;
+    const double x = lo + (hi - lo) * (double)(sub + 1) / (double)(BIS_L + 1);
+    const bool above = !done && sturm_count(sd, se2, n, x, pivmin) > idx;  // eigenvalue idx < x
+    const unsigned b = (__ballot_sync(0xffffffffu, above) & gmask) >> (grp * BIS_L);
+    if (!done) {
+      const int j = b ? (__ffs(b) - 1) : BIS_L;
+      const double nlo = (j == 0) ? lo : lo + (hi - lo) * (double)j / (double)(BIS_L + 1);
+      const double nhi = (j == BIS_L) ? hi : lo + (hi - lo) * (double)(j + 1) / (double)(BIS_L + 1);
+      if (!(nlo > lo || nhi < hi)) done = true;  // no progress at this resolution
+      lo = nlo;
+      hi = nhi;
+    }
   }
-  if (lane == 0) lam[r] = 0.5 * (lo + hi);
+  if (live && sub == 0) lam[r] = 0.5 * (lo + hi);
 }
 
 // Inverse iteration for the eigenvectors of T, one thread per group of
 // consecutive eigenvalues closer than gtol (groups are orthogonalised
 // internally).  X[i*k + r] receives the vector of lam[r].
-__global__ void inverse_iteration_kernel(const double *d, const double *e, const double *lam,
+__global__ void inverse_iteration_kernel(const double *dg, const double *eg, const double *lam,
                                          const double *scal, int n, int k, double *X,
                                          double *lu, int *flags) {
+  extern __shared__ double sde[];
+  double *d = sde, *e = sde + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { d[i] = dg[i]; e[i] = eg[i]; }
+  __syncthreads();
   const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (r0 >= k) return;
   const double tnorm = scal[4];
@@ -279,7 +474,7 @@ __global__ void inverse_iteration_kernel(const double *d, const double *e, const
       if (fabs(S(dd, i)) < tiny) S(dd, i) = copysign(tiny, S(dd, i));
     // start vector: deterministic, no special structure
     for (int i = 0; i < n; ++i) S(X, i) = 1.0 + 0.5 * sin(0.7548776662 * (i + 1) + 0.5698402910 * (r + 1));
-    for (int iter = 0; iter < 4; ++iter) {
+    for (int iter = 0; iter < 2; ++iter) {
       // forward: apply L^-1 with the interchanges
       for (int i = 0; i < n - 1; ++i) {
         if (S(pv, i) == 0.0) {
@@ -331,7 +526,7 @@ __global__ void lowdin_factor_kernel(double *G, int k) {
 // G = V_b^T V_b).  Blocks are applied from the last to the first:
 // Y <- Y - V_b (T (V_b^T Y)).
 constexpr int WY_NB = 64;
-constexpr int64_t WY_KSPLIT = 256;
+constexpr int64_t WY_KSPLIT = 64;
 
 // dst[i] = sum_s src[s * stride + i]
 __global__ void sum_partials_kernel(const double *__restrict__ src, int nsplit, int64_t stride,
@@ -384,6 +579,31 @@ __global__ void transpose_kernel(const double *__restrict__ X, int n, int k, dou
 }  // namespace
 
 cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches) {
+  // one cooperative launch when the grid fits on the device and v, p fit in shared memory
+  int dev = 0, nsm = 0, coop = 0, per_sm = 0;
+  const size_t smem = 2 * (size_t)n * sizeof(double);
+  bool persistent = n > 2 && smem <= 200 * 1024 && w.grid_ws != nullptr;
+  if (persistent) {
+    persistent = cudaGetDevice(&dev) == cudaSuccess &&
+                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                 cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+                 cudaFuncSetAttribute(hh_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem) == cudaSuccess &&
+                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_persistent_kernel, 512, smem) ==
+                     cudaSuccess &&
+                 per_sm >= 1;
+    cudaGetLastError();
+  }
+  if (persistent) {
+    double *P = w.grid_ws, *part1 = P + n, *part2 = part1 + nsm;
+    GridBar *gb = reinterpret_cast<GridBar *>(part2 + nsm);
+    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&w.A, &w.V, &w.d, &w.e, &w.tau, &P, &part1, &part2, &gb, (void *)&n, &w.flags};
+    e = cudaLaunchCooperativeKernel((const void *)hh_persistent_kernel, dim3(nsm), dim3(512), args, smem, s);
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+  } else {
   for (int k = 0; k + 2 < n; ++k) {
     const int L = n - k - 1;
     hh_reflector_kernel<<<1, RB, 0, s>>>(w.A, w.V, w.d, w.e, w.tau, w.scal, n, k);
@@ -397,6 +617,7 @@ cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s,
     *launches += 4;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
   }
   hh_finalize_kernel<<<1, 32, 0, s>>>(w.A, w.d, w.e, n);
   // e2 reuses w.p (length n)
@@ -414,9 +635,23 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  bisect_kernel<<<(k + 7) / 8, 256, smem, s>>>(w.d, w.p, w.scal, n, k, w.lam);
-  inverse_iteration_kernel<<<(k + 63) / 64, 64, 0, s>>>(w.d, w.e, w.lam, w.scal, n, k, w.X, w.lu,
-                                                        flags);
+  {
+    // one warp per block and at most 32 / BIS_L eigenvalues per warp, spread
+    // so that every SM gets work: the FP64 divisions of the Sturm counts are
+    // the cost on this part
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 148;
+    cudaGetLastError();
+    const int epw = std::max(1, std::min(32 / BIS_L, (k + nsm - 1) / nsm));
+    bisect_kernel<<<(k + epw - 1) / epw, 32, smem, s>>>(w.d, w.p, w.scal, n, k, epw, w.lam);
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e2 = cudaFuncSetAttribute(inverse_iteration_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (e2 != cudaSuccess) return e2;
+  }
+  inverse_iteration_kernel<<<(k + 31) / 32, 32, smem, s>>>(w.d, w.e, w.lam, w.scal, n, k, w.X, w.lu, flags);
   *launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

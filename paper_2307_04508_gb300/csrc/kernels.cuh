@@ -57,6 +57,11 @@ cudaError_t launch_copy_cols(const double *src, int64_t lds, int64_t c0, double 
 cudaError_t launch_screen(const double *Pi, int N, int n_omega, double *X0, double *X1,
                           double *C, int *flags, cudaStream_t s, int *launches);
 
+// Blocked form: work = screen_blocked_scratch(N, n_omega) doubles.
+size_t screen_blocked_scratch(int N, int n_omega);
+cudaError_t launch_screen_blocked(const double *Pi, int N, int n_omega, double *work, double *C, int *flags,
+                                  cudaStream_t s, int *launches);
+
 // ---- eigensolver (eig_f64.cu) ----
 struct EigWork {
   double *A = nullptr;      // [n][n] symmetric in, destroyed
@@ -69,6 +74,8 @@ struct EigWork {
   double *lu = nullptr;                               // [5 n kcap] inverse-iteration scratch
   int *count = nullptr;                               // [2]
   double *wy = nullptr;                               // [WY scratch] see eig_f64.cu
+  double *grid_ws = nullptr;                          // [n + 2 * n_sm + 2] persistent-reduction scratch
+  int *flags = nullptr;                               // device error flags
 };
 // Tridiagonalise A, count eigenvalues > thresh (returned through count[0]).
 // V must be zeroed by the caller before the call.
