@@ -6,7 +6,10 @@ frequency recombination, screening, W_nm, Sigma(i w), Pade and Newton.
 
 Workload (default): the mid-size synthetic system, 60 occupied orbitals (10
 frozen), 540 virtual, 1800 auxiliary functions, NAF at 1e-2, 32
-Gauss-Legendre frequencies, 8 Laplace points, 10 quasi-particle states, FP64.
+Gauss-Legendre frequencies, 8 Laplace points, 10 quasi-particle states.
+Default form: mixed precision (split-BF16 tensor-core contractions, FP64
+eigensolver / screening / Pade / Newton); the plain FP64 form is timed on the
+same inputs beside it and the QP deviation between the two is reported.
 
 Prints one JSON line.  --impl reference times the CPU oracle (direct AC-GW,
 FP64, numpy) on the same workload instead.
@@ -35,10 +38,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="mid", choices=["tiny", "mid"])
+    ap.add_argument("--workload", default="mid", choices=["tiny", "mid", "serving"])
+    ap.add_argument("--requests", type=int, default=512, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=3.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=4, help="serving: server worker slots")
+    ap.add_argument("--compare-prefix", type=int, default=32,
+                    help="serving: requests of the stream solved back to back in both forms for the ratio")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3"],
-                    help="fp64: every contraction in FP64; bf16x3: Pi on the tensor cores (split BF16)")
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"],
+                    help="bf16x3: every contraction on the tensor cores with split-BF16 operands (eigensolver, "
+                         "screening, Pade, Newton in FP64); fp64: every step in FP64")
     return ap.parse_args()
 
 
@@ -141,6 +150,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _solve_loop(ctx, p, dev, out_dev, stream, flush, steps, clk=None):
+    """Time `steps` device-resident solves with CUDA events (L2 flushed between)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stats = []
+    torch.cuda.synchronize()
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        ctx.solve(p, dev["eps"], dev["B_ov"], dev["B_tgt"], dev["targets"], dev["shift"], *out_dev, stream=stream)
+        ev[i][1].record(stream)
+        stats.append(ctx.stats())
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev]), stats
+
+
 def run_gpu(args):
     import torch
     from paper_2307_04508_gb300 import ltgw
@@ -158,9 +184,13 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     T = len(prob.targets)
     mixed = args.precision == "bf16x3"
-    p = ltgw.make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, cfg["n_omega"], cfg["n_tau"],
-                         0.5, cfg["naf_thresh"], 2, True, ltgw.LTGW_BF16X3 if mixed else ltgw.LTGW_FP64)
-    # device-resident inputs and outputs
+
+    def params(prec):
+        return ltgw.make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, cfg["n_omega"], cfg["n_tau"],
+                                0.5, cfg["naf_thresh"], 2, True, prec)
+
+    p = params(ltgw.LTGW_BF16X3 if mixed else ltgw.LTGW_FP64)
+    p64 = params(ltgw.LTGW_FP64)
     dev = {"eps": torch.from_numpy(prob.eps).cuda(), "B_ov": torch.from_numpy(prob.B_ov).cuda(),
            "B_tgt": torch.from_numpy(prob.B_tgt).cuda(),
            "targets": torch.from_numpy(prob.targets.astype(np.int32)).cuda(),
@@ -168,32 +198,16 @@ def run_gpu(args):
     out_dev = (torch.empty((T, cfg["n_omega"], 2), dtype=torch.float64, device="cuda"),
                torch.empty(T, dtype=torch.float64, device="cuda"), torch.empty(T, dtype=torch.int32, device="cuda"))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    def step_dev():
-        ctx.solve(p, dev["eps"], dev["B_ov"], dev["B_tgt"], dev["targets"], dev["shift"], *out_dev, stream=stream)
-
     ctx.set_timing(True)
+    # warm-up (also fits and caches the Laplace grid)
     for _ in range(max(args.warmup, 3)):
-        step_dev()
+        ctx.solve(p, dev["eps"], dev["B_ov"], dev["B_tgt"], dev["targets"], dev["shift"], *out_dev, stream=stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    pi_ms, launches, stage = [], 0, []
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            ev[i][0].record(stream)
-            step_dev()
-            ev[i][1].record(stream)
-            s = ctx.stats()
-            pi_ms.append(s["ms_pi_kernel"])
-            launches += s["kernel_launches"]
-            stage.append(s)
-        torch.cuda.synchronize()
-    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+        step_ms, stats = _solve_loop(ctx, p, dev, out_dev, stream, flush, args.steps)
+    e_main = out_dev[1].cpu().numpy().copy()
     if dist:
         t = torch.tensor([step_ms.sum()], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -201,28 +215,54 @@ def run_gpu(args):
     else:
         total_ms = float(step_ms.sum())
     value = world * args.steps / (total_ms / 1e3)
-    st = stage[-1]
+    st = stats[-1]
+    launches = int(sum(x["kernel_launches"] for x in stats))
     N, n_ov = st["n_naf"], (prob.n_occ - prob.n_frozen) * prob.n_virt
     pi_flops = cfg["n_tau"] * N * N * n_ov            # useful flops of one Pi build (N^2 K per SYRK)
-    pi_bytes_min = 8 * (N * n_ov + cfg["n_tau"] * N * N)
-    pi_avg_ms = float(np.mean(pi_ms))
+    pi_ms = float(np.mean([x["ms_pi_kernel"] for x in stats]))
+    tri_ms = float(np.mean([x["ms_tridiag"] for x in stats]))
     pk, src = peaks()
-    clocks = clk.summary()
     alu_peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-    achieved = pi_flops / (pi_avg_ms / 1e3) / 1e12
     if mixed:
         # three BF16 products (hi*hi, hi*lo, lo*hi) per useful product
-        tc_achieved = 3 * pi_flops / (pi_avg_ms / 1e3) / 1e12
-        roofline = {"bound": "tensor", "kernel": "tc_split_gemm_kernel (Pi(tau_k) split-BF16 SYRK, tcgen05)",
-                    "achieved": tc_achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                    "frac": tc_achieved / pk["bf16_tflops"],
-                    "peak_source": f"bf16_tflops (burst) of {src} MEASURED_PEAKS.json",
-                    "flops_per_launch": 3 * pi_flops, "traffic": None}
+        tc = 3 * pi_flops / (pi_ms / 1e3) / 1e12
+        roof_pi = {"bound": "tensor", "kernel": "tc_split_gemm_kernel (Pi(tau_k) moments, split-BF16 tcgen05)",
+                   "achieved": tc, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tc / pk["bf16_tflops"],
+                   "peak_source": f"bf16_tflops (burst, kernel of {pi_ms:.3f} ms) of {src} MEASURED_PEAKS.json",
+                   "flops_per_launch": 3 * pi_flops, "ms_per_launch": pi_ms, "traffic": None}
     else:
-        roofline = {"bound": "alu", "kernel": "gemm_f64_kernel (Pi(tau_k) scaled SYRK)",
-                    "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                    "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
-                    "flops_per_launch": pi_flops, "traffic": None}
+        a = pi_flops / (pi_ms / 1e3) / 1e12
+        roof_pi = {"bound": "alu", "kernel": "gemm_f64_kernel (Pi(tau_k) moments, FP64 SYRK)", "achieved": a,
+                   "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
+                   "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
+                   "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": None}
+    tri_flops = 4.0 / 3.0 * prob.n_aux ** 3
+    tri_ach = tri_flops / (tri_ms / 1e3) / 1e12
+    roof_tri = {"bound": "alu", "kernel": "hh_persistent_kernel (NAF Householder tridiagonalisation, FP64)",
+                "achieved": tri_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": tri_ach / alu_peak,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
+                "flops_per_launch": tri_flops, "ms_per_launch": tri_ms, "traffic": None}
+    roofline = roof_tri if tri_ms > pi_ms else roof_pi
+    clocks = clk.summary()
+    line = {"metric": "G0W0 solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if mixed else "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": args.precision,
+                       "l2": "256 MB buffer written between steps; inputs 553 MB > L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "pi_build_tflops": pi_flops / (pi_ms / 1e3) / 1e12, "n_naf": N,
+            "stage_ms": {k: st[k] for k in ("ms_naf", "ms_tridiag", "ms_pi", "ms_screen", "ms_wnm", "ms_sigma_qp",
+                                            "ms_total")},
+            "roofline": roofline, "roofline_pi_build": roof_pi, "gpu_launches": launches, "clocks": clocks,
+            "peaks_source": src}
+    if mixed:
+        # the plain FP64 form on the same workload, for the "vs plain FP64 form" part of the metric
+        ms64, _ = _solve_loop(ctx, p64, dev, out_dev, stream, flush, max(3, args.steps // 2))
+        e64 = out_dev[1].cpu().numpy()
+        line["fp64_form"] = {"solves_per_s": len(ms64) / (ms64.sum() / 1e3), "ms_per_solve": float(ms64.mean())}
+        line["speedup_vs_fp64_form"] = value / line["fp64_form"]["solves_per_s"]
+        line["qp_max_mev_vs_fp64_form"] = float(np.abs(e_main - e64).max() * HA2MEV)
     # end-to-end: host (pinned) inputs and outputs through the same C ABI call
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
            {"eps": prob.eps, "B_ov": prob.B_ov, "B_tgt": prob.B_tgt,
@@ -239,33 +279,20 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         ctx.solve(p, pin["eps"], pin["B_ov"], pin["B_tgt"], pin["targets"], pin["shift"], *out_host, stream=stream)
     torch.cuda.synchronize()
-    e2e = world * e2e_steps / (time.perf_counter() - t0)
-    line = {"metric": "G0W0 solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if mixed else "f64", "data": "synthetic",
-            "config": {"workload": desc, "precision": args.precision,
-                       "l2": "256 MB buffer written between steps; inputs 553 MB > L2",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "pi_build_tflops": achieved, "n_naf": N,
-            "stage_ms": {k: st[k] for k in ("ms_naf", "ms_pi", "ms_screen", "ms_wnm", "ms_sigma_qp", "ms_total")},
-            "roofline": roofline, "pi_algorithmic_bytes": pi_bytes_min,
-            "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clocks, "peaks_source": src}
+    line["e2e"] = {"value": world * e2e_steps / (time.perf_counter() - t0), "unit": "solves/s",
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # bounded oracle sample: full solves of the same workload on the host cores
         t0 = time.perf_counter()
         n = 0
-        sig_o = e_o = None
+        e_o = None
         while n < 2 and (time.perf_counter() - t0) < 25.0:
-            sig_o, e_o, st_o = oracle_solve(prob, cfg)
+            _, e_o, _ = oracle_solve(prob, cfg)
             n += 1
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": n / dt, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{n} full direct-AC solve(s) of the same workload (numpy FP64)"}
-        e_gpu = out_host[1].numpy()
-        key = "qp_max_mev_vs_fp64_direct_oracle"
-        line[key] = float(np.abs(e_gpu - e_o).max() * HA2MEV)
+        line["qp_max_mev_vs_fp64_direct_oracle"] = float(np.abs(e_main - e_o).max() * HA2MEV)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -273,10 +300,68 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """The serving stream: requests of mixed sizes (n_occ log-uniform in [8, 200],
+    N_aux = 3 (n_occ + n_virt)) arriving as a Poisson process, inputs generated on
+    the device at arrival, admitted onto the request server's slots."""
+    import torch
+    from paper_2307_04508_gb300 import ltgw, serving
+    from paper_2307_04508_gb300 import synthetic as S
+
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = S.serving_stream(args.requests, rate_hz=args.rate)
+    budget = int(0.6 * torch.cuda.get_device_properties(0).total_memory)
+    # same prefix of the stream, back to back, in both forms: the throughput ratio
+    pre = reqs[:min(args.compare_prefix, len(reqs))]
+    inputs = [serving.ingest(r, device=True) for r in pre]
+    cmp = {}
+    for name, prec in (("bf16x3", ltgw.LTGW_BF16X3), ("fp64", ltgw.LTGW_FP64)):
+        srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
+        try:
+            recs, wall, _ = serving.run_stream(srv, pre, prec, honor_arrivals=False, inputs=inputs)
+        finally:
+            srv.close()
+        cmp[name] = {"solves_per_s": len(recs) / wall, "e": {k: v["e_qp"].copy() for k, v in recs.items()},
+                     "ok": all(v["status"] in (0, 4) for v in recs.values())}
+    dev = max(np.abs(cmp["bf16x3"]["e"][k] - cmp["fp64"]["e"][k]).max() for k in cmp["fp64"]["e"]) * HA2MEV
+    del inputs
+    torch.cuda.empty_cache()
+    # the whole stream, open loop at the arrival rate, mixed form
+    srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
+    try:
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            recs, wall, ingest_s = serving.run_stream_pipelined(srv, reqs, ltgw.LTGW_BF16X3)
+    finally:
+        srv.close()
+    sm = serving.summarize(recs, wall, ingest_s)
+    line = {"metric": "G0W0 solves/s (serving stream)", "value": sm["solves_per_s"], "unit": "solves/s",
+            "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+            "data": "synthetic",
+            "config": {"workload": f"serving: {len(reqs)} requests, Poisson {args.rate}/s, n_occ log-uniform "
+                                   "[8,200], n_virt = u n_occ (u in [8,12]), N_aux = 3(n_occ+n_virt), NAF 1e-2, "
+                                   "N_omega 32, N_tau 8, 4 states; inputs generated on the device at arrival",
+                       "slots": args.slots, "hbm_budget_bytes": budget},
+            "latency_ms": {"p50": sm["p50_ms"], "p99": sm["p99_ms"],
+                           "p50_from_arrival": sm.get("p50_from_arrival_ms"),
+                           "p99_from_arrival": sm.get("p99_from_arrival_ms")},
+            "completed": sm["completed"], "ingest_s": ingest_s,
+            "prefix_comparison": {"requests": len(pre), "bf16x3_solves_per_s": cmp["bf16x3"]["solves_per_s"],
+                                  "fp64_solves_per_s": cmp["fp64"]["solves_per_s"],
+                                  "speedup": cmp["bf16x3"]["solves_per_s"] / cmp["fp64"]["solves_per_s"],
+                                  "qp_max_mev_bf16x3_vs_fp64": dev},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

@@ -44,6 +44,7 @@
 #ifndef LTGW_H
 #define LTGW_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -58,7 +59,8 @@ typedef enum {
   LTGW_ERR_NO_CONVERGE = 4, /* a quasi-particle Newton solve did not converge      */
   LTGW_ERR_DEVICE = 5,      /* a CUDA call failed                                  */
   LTGW_ERR_EIG = 6,         /* the NAF eigensolver failed (non-finite or no vector) */
-  LTGW_ERR_NO_NAF = 7       /* the NAF threshold kept no auxiliary function        */
+  LTGW_ERR_NO_NAF = 7,      /* the NAF threshold kept no auxiliary function        */
+  LTGW_ERR_TIMEOUT = 8      /* a wait for completions ran out of time              */
 } ltgw_status;
 
 enum { LTGW_FP64 = 0, LTGW_BF16X3 = 1, LTGW_FP8 = 2 };
@@ -90,6 +92,7 @@ typedef struct {
   double ms_pi_kernel;       /* summed device time of the Pi-build kernel launches    */
   int pi_kernel_launches;    /* Pi-build kernel launches in the last solve            */
   int kernel_launches;       /* all kernel launches in the last solve                 */
+  double ms_tridiag;         /* device time of the NAF Householder tridiagonalisation */
 } ltgw_stats;
 
 typedef struct ltgw_ctx ltgw_ctx;
@@ -176,6 +179,51 @@ ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, con
  * Synchronises; LTGW_ERR_NOT_SPD if a pivot was not positive. */
 ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C,
                         void *stream);
+
+/* ---- request server (continuous admission of solves) -------------------- */
+
+/* One G0W0 request: the arguments of ltgw_solve.  Every pointer must stay valid
+ * (and outputs unread) until the request's completion has been polled. */
+typedef struct {
+  ltgw_params p;
+  const double *eps, *B_ov, *B_tgt;   /* any; layouts as for ltgw_solve        */
+  const int *targets;
+  int n_tgt;
+  const double *shift, *tau_x, *tau_w;
+  double *sigma_iw, *e_qp;            /* outputs, any                          */
+  int *qp_status;
+} ltgw_request;
+
+typedef struct {
+  uint64_t ticket;      /* from ltgw_server_submit                              */
+  ltgw_status status;   /* what ltgw_solve returned for the request             */
+  double queue_ms;      /* submit -> start of service                           */
+  double service_ms;    /* start of service -> results written                  */
+  double latency_ms;    /* submit -> results written                            */
+  double start_ms;      /* start of service, ms since the server was created    */
+  double end_ms;        /* results written, ms since the server was created     */
+  char message[120];    /* ltgw_last_error of the solve ("" when status is OK)  */
+} ltgw_completion;
+
+typedef struct ltgw_server ltgw_server;
+
+/* A server with n_slots workers on `device`, each with its own context and
+ * non-blocking stream (requests in different slots overlap on the device).
+ * Requests are admitted in arrival order when a slot is free and the sum of
+ * the estimated footprints of the running requests stays within
+ * hbm_budget_bytes.  Each slot keeps its workspace between requests. */
+ltgw_status ltgw_server_create(ltgw_server **out, int device, int n_slots, size_t hbm_budget_bytes);
+/* Queue a request (never blocks on the GPU); LTGW_ERR_NOMEM if its estimated
+ * footprint alone exceeds the budget. */
+ltgw_status ltgw_server_submit(ltgw_server *srv, const ltgw_request *req, uint64_t *ticket);
+/* Move up to max_out completions (oldest first) into out; returns how many. */
+int ltgw_server_poll(ltgw_server *srv, ltgw_completion *out, int max_out);
+/* Wait until nothing is queued or running; LTGW_ERR_TIMEOUT after timeout_s. */
+ltgw_status ltgw_server_wait_all(ltgw_server *srv, double timeout_s);
+/* Finish the running requests, drop the queued ones, release everything. */
+void ltgw_server_destroy(ltgw_server *srv);
+/* Estimated device bytes of one solve (inputs staged + workspace). */
+size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt);
 
 /* ---- allocation-free screening ------------------------------------------ */
 

@@ -63,7 +63,7 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-enum Stage { EV_START = 0, EV_NAF, EV_PI0, EV_PI1, EV_PI, EV_SCREEN, EV_WNM, EV_SIGQP, EV_END, EV_COUNT };
+enum Stage { EV_START = 0, EV_NAF, EV_PI0, EV_PI1, EV_PI, EV_SCREEN, EV_WNM, EV_SIGQP, EV_END, EV_TRI0, EV_TRI1, EV_COUNT };
 
 }  // namespace
 
@@ -78,6 +78,7 @@ struct ltgw_ctx {
   ltgw_stats stats{};
   int launches = 0;
   double pi_tc_flops = 0.0;
+  int tri_n = 0;
   int n_sm = 148;
   Arena a4;  // tensor-core scratch: tile lists and partial tiles
   Arena a5;  // tensor-core operand copies consumed by the next contraction
@@ -186,7 +187,10 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   }
   LTGW_CUDA(ctx, cudaMemsetAsync(w.V, 0, (size_t)n * n * sizeof(double), s));
   int nl = 0;
+  ctx->mark(EV_TRI0, s);
   cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl);
+  ctx->mark(EV_TRI1, s);
+  ctx->tri_n = n;
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("eig_tridiag: ") + cudaGetErrorString(e)); return ctx->status(); }
   int cnt[2] = {0, 0};
@@ -519,6 +523,7 @@ const char *ltgw_status_string(ltgw_status s) {
     case LTGW_ERR_DEVICE: return "CUDA error";
     case LTGW_ERR_EIG: return "eigensolver failure";
     case LTGW_ERR_NO_NAF: return "no natural auxiliary function kept";
+    case LTGW_ERR_TIMEOUT: return "timed out";
   }
   return "unknown status";
 }
@@ -810,6 +815,7 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   st.ms_wnm = ctx->ms(EV_SCREEN, EV_WNM);
   st.ms_sigma_qp = ctx->ms(EV_WNM, EV_SIGQP);
   st.ms_total = ctx->ms(EV_START, EV_END);
+  st.ms_tridiag = naf ? ctx->ms(EV_TRI0, EV_TRI1) : 0.0;
 
   std::vector<int> hs(T);
   if (read_small(ctx, hs.data(), qp_status, T * sizeof(int), s) != LTGW_OK) return ctx->status();

@@ -19,6 +19,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <mutex>
 #include <math.h>
 
 #include "common.cuh"
@@ -576,6 +577,24 @@ __global__ void transpose_kernel(const double *__restrict__ X, int n, int k, dou
   }
 }
 
+// Raise a kernel's dynamic shared-memory limit once, to the most any call
+// may use; setting it per call races between host threads (one thread could
+// lower it between another thread's set and launch).
+cudaError_t allow_max_dynamic_smem(const void *kernel, std::once_flag &flag) {
+  cudaError_t result = cudaSuccess;
+  std::call_once(flag, [&] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if ((result = cudaGetDevice(&dev)) != cudaSuccess) return;
+    if ((result = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return;
+    if ((result = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return;
+    result = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes);
+  });
+  return result;
+}
+std::once_flag g_smem_hh, g_smem_bisect, g_smem_invit;
+
 }  // namespace
 
 cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches) {
@@ -587,8 +606,7 @@ cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s,
     persistent = cudaGetDevice(&dev) == cudaSuccess &&
                  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
                  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-                 cudaFuncSetAttribute(hh_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem) == cudaSuccess &&
+                 allow_max_dynamic_smem((const void *)hh_persistent_kernel, g_smem_hh) == cudaSuccess &&
                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_persistent_kernel, 512, smem) ==
                      cudaSuccess &&
                  per_sm >= 1;
@@ -630,9 +648,10 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
                                int *launches) {
   if (k <= 0) return cudaSuccess;
   size_t smem = 2 * (size_t)n * sizeof(double);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  {
+    cudaError_t e = allow_max_dynamic_smem((const void *)bisect_kernel, g_smem_bisect);
+    if (e != cudaSuccess) return e;
+    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel, g_smem_invit);
     if (e != cudaSuccess) return e;
   }
   {
@@ -645,11 +664,6 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
     cudaGetLastError();
     const int epw = std::max(1, std::min(32 / BIS_L, (k + nsm - 1) / nsm));
     bisect_kernel<<<(k + epw - 1) / epw, 32, smem, s>>>(w.d, w.p, w.scal, n, k, epw, w.lam);
-  }
-  if (smem > 48 * 1024) {
-    cudaError_t e2 = cudaFuncSetAttribute(inverse_iteration_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem);
-    if (e2 != cudaSuccess) return e2;
   }
   inverse_iteration_kernel<<<(k + 31) / 32, 32, smem, s>>>(w.d, w.e, w.lam, w.scal, n, k, w.X, w.lu, flags);
   *launches += 2;

@@ -1,0 +1,242 @@
+// Request server for G0W0 solves: continuous admission of requests of mixed
+// sizes onto a fixed set of worker slots.
+//
+// Each slot owns an ltgw context and a non-blocking CUDA stream, and runs one
+// solve at a time on a host thread of its own, so the kernels of different
+// requests overlap on the device.  A request is admitted, in arrival order,
+// as soon as a slot is free and its estimated device footprint fits in what
+// the budget leaves after the requests already running; completions record
+// the queueing, service and total latency of every request.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/ltgw.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Pending {
+  uint64_t ticket = 0;
+  ltgw_request req{};
+  size_t footprint = 0;
+  Clock::time_point t_submit;
+};
+
+struct Slot {
+  std::thread th;
+  bool has_job = false;
+  Pending job;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+struct ltgw_server {
+  int device = 0;
+  size_t budget = 0, in_flight = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Pending> queue;
+  std::vector<std::unique_ptr<Slot>> slots;
+  std::deque<ltgw_completion> done;
+  int running = 0;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  ltgw_status init_status = LTGW_OK;
+  int init_pending = 0;
+  Clock::time_point t_created = Clock::now();
+
+  // Admit queued requests in arrival order while a slot is free and the head
+  // fits in the remaining budget.  Caller holds mu.
+  void dispatch_locked() {
+    while (!queue.empty()) {
+      Pending &head = queue.front();
+      if (in_flight + head.footprint > budget && running > 0) return;
+      Slot *free_slot = nullptr;
+      for (auto &s : slots)
+        if (!s->has_job && !busy_slot(s.get())) { free_slot = s.get(); break; }
+      if (!free_slot) return;
+      free_slot->job = head;
+      free_slot->has_job = true;
+      in_flight += head.footprint;
+      ++running;
+      queue.pop_front();
+      cv_work.notify_all();
+    }
+  }
+  std::vector<Slot *> busy;
+  bool busy_slot(Slot *s) const { return std::find(busy.begin(), busy.end(), s) != busy.end(); }
+
+  void worker(Slot *slot) {
+    cudaSetDevice(device);
+    ltgw_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    ltgw_status st = ltgw_create(&ctx, device);
+    if (st == LTGW_OK && cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      st = LTGW_ERR_DEVICE;
+    }
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      if (st != LTGW_OK && init_status == LTGW_OK) init_status = st;
+      --init_pending;
+      cv_done.notify_all();
+    }
+    std::unique_lock<std::mutex> lock(mu);
+    while (true) {
+      cv_work.wait(lock, [&] { return stop || slot->has_job; });
+      if (!slot->has_job) break;
+      Pending job = slot->job;
+      slot->has_job = false;
+      busy.push_back(slot);
+      lock.unlock();
+      const Clock::time_point t_start = Clock::now();
+      ltgw_status rs = LTGW_ERR_DEVICE;
+      if (ctx) {
+        const ltgw_request &r = job.req;
+        rs = ltgw_solve(ctx, &r.p, r.eps, r.B_ov, r.B_tgt, r.targets, r.n_tgt, r.shift, r.tau_x, r.tau_w,
+                        r.sigma_iw, r.e_qp, r.qp_status, stream);
+      }
+      const Clock::time_point t_end = Clock::now();
+      lock.lock();
+      busy.erase(std::find(busy.begin(), busy.end(), slot));
+      in_flight -= job.footprint;
+      --running;
+      ltgw_completion c{};
+      c.ticket = job.ticket;
+      c.status = rs;
+      c.queue_ms = ms_between(job.t_submit, t_start);
+      c.service_ms = ms_between(t_start, t_end);
+      c.latency_ms = ms_between(job.t_submit, t_end);
+      c.start_ms = ms_between(t_created, t_start);
+      c.end_ms = ms_between(t_created, t_end);
+      if (rs != LTGW_OK && ctx) {
+        const char *m = ltgw_last_error(ctx);
+        size_t k = 0;
+        for (; m && m[k] && k + 1 < sizeof(c.message); ++k) c.message[k] = m[k];
+        c.message[k] = 0;
+      }
+      done.push_back(c);
+      dispatch_locked();
+      cv_done.notify_all();
+    }
+    lock.unlock();
+    if (stream) cudaStreamDestroy(stream);
+    if (ctx) ltgw_destroy(ctx);
+  }
+};
+
+extern "C" {
+
+size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt) {
+  if (!p || n_tgt < 1) return 0;
+  const size_t n_aux = (size_t)p->n_aux, n_occ = (size_t)p->n_occ, n_virt = (size_t)p->n_virt;
+  const size_t n_orb = n_occ + n_virt, n_act = n_occ - (size_t)p->n_frozen;
+  const size_t n_ov = n_act * n_virt, N = n_aux, T = (size_t)n_tgt, n_om = (size_t)p->n_omega;
+  const size_t n_tau = p->use_laplace ? (size_t)p->n_tau : 0;
+  size_t d = 0;  // doubles
+  d += n_aux * n_occ * n_virt + T * n_aux * n_orb;            // inputs staged on the device
+  if (p->naf_thresh >= 0.0) d += 10 * n_aux * n_aux;           // NAF metric, reflectors, vectors, scratch
+  d += n_tau * N * N + 2 * n_om * N * N;                       // Laplace moments, Pi, C
+  d += n_om * (N * N + 128 * N + 4096);                        // screening sweep scratch
+  d += T * N * n_orb + n_om * T * n_orb;                       // projected targets, W
+  if (p->precision == LTGW_BF16X3) d += (2 * n_aux * n_ov + N * n_ov) / 2 + n_om * N * N / 2;  // FP32 copies
+  else d += N * n_ov;                                          // projected ov block
+  return d * sizeof(double) + (64u << 20);                     // + fixed slack
+}
+
+ltgw_status ltgw_server_create(ltgw_server **out, int device, int n_slots, size_t hbm_budget_bytes) {
+  if (!out || n_slots < 1 || n_slots > 64 || hbm_budget_bytes == 0) return LTGW_ERR_BAD_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return LTGW_ERR_DEVICE;
+  }
+  ltgw_server *s = new ltgw_server();
+  s->device = device;
+  s->budget = hbm_budget_bytes;
+  s->init_pending = n_slots;
+  for (int i = 0; i < n_slots; ++i) s->slots.emplace_back(new Slot());
+  for (auto &slot : s->slots) {
+    Slot *sp = slot.get();
+    sp->th = std::thread([s, sp] { s->worker(sp); });
+  }
+  {
+    std::unique_lock<std::mutex> lock(s->mu);
+    s->cv_done.wait(lock, [&] { return s->init_pending == 0; });
+  }
+  if (s->init_status != LTGW_OK) {
+    ltgw_status st = s->init_status;
+    ltgw_server_destroy(s);
+    return st;
+  }
+  *out = s;
+  return LTGW_OK;
+}
+
+ltgw_status ltgw_server_submit(ltgw_server *s, const ltgw_request *req, uint64_t *ticket) {
+  if (!s || !req || !ticket) return LTGW_ERR_BAD_ARG;
+  if (!req->eps || !req->B_ov || !req->B_tgt || !req->targets || !req->shift || !req->sigma_iw || !req->e_qp ||
+      !req->qp_status || req->n_tgt < 1)
+    return LTGW_ERR_BAD_ARG;
+  const size_t fp = ltgw_request_footprint(&req->p, req->n_tgt);
+  if (fp > s->budget) return LTGW_ERR_NOMEM;
+  std::lock_guard<std::mutex> lock(s->mu);
+  Pending p;
+  p.ticket = s->next_ticket++;
+  p.req = *req;
+  p.footprint = fp;
+  p.t_submit = Clock::now();
+  s->queue.push_back(p);
+  *ticket = p.ticket;
+  s->dispatch_locked();
+  return LTGW_OK;
+}
+
+int ltgw_server_poll(ltgw_server *s, ltgw_completion *out, int max_out) {
+  if (!s || !out || max_out < 1) return 0;
+  std::lock_guard<std::mutex> lock(s->mu);
+  int n = 0;
+  while (n < max_out && !s->done.empty()) {
+    out[n++] = s->done.front();
+    s->done.pop_front();
+  }
+  return n;
+}
+
+ltgw_status ltgw_server_wait_all(ltgw_server *s, double timeout_s) {
+  if (!s) return LTGW_ERR_BAD_ARG;
+  std::unique_lock<std::mutex> lock(s->mu);
+  const bool ok = s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
+                                      [&] { return s->queue.empty() && s->running == 0; });
+  return ok ? LTGW_OK : LTGW_ERR_TIMEOUT;
+}
+
+void ltgw_server_destroy(ltgw_server *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+    s->queue.clear();
+  }
+  s->cv_work.notify_all();
+  for (auto &slot : s->slots)
+    if (slot->th.joinable()) slot->th.join();
+  delete s;
+}
+
+}  // extern "C"

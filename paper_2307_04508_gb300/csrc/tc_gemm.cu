@@ -26,6 +26,9 @@
 // the CTA records an error flag and unwinds.
 #include <cuda_bf16.h>
 #include <stddef.h>
+
+#include <mutex>
+
 #include <stdint.h>
 
 #include "common.cuh"
@@ -413,9 +416,13 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
   if (g.Kp % TK || g.k_per_split % TK || g.drain_k % TK || g.k_per_split <= 0 || g.drain_k <= 0)
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(tc_split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES);
-  if (e != cudaSuccess) return e;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   if (g.nt_group < 1 || g.nt_group > MAXT) return cudaErrorInvalidValue;
   if (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) return cudaErrorInvalidValue;
   if (g.out_mode == TC_OUT_COLDOT && (g.nt_group != 1 || g.k_per_split > g.drain_k)) return cudaErrorInvalidValue;

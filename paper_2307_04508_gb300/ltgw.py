@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libltgw.so")
 
 LTGW_OK, LTGW_ERR_BAD_ARG, LTGW_ERR_NOMEM, LTGW_ERR_NOT_SPD = 0, 1, 2, 3
 LTGW_ERR_NO_CONVERGE, LTGW_ERR_DEVICE, LTGW_ERR_EIG, LTGW_ERR_NO_NAF = 4, 5, 6, 7
+LTGW_ERR_TIMEOUT = 8
 LTGW_FP64, LTGW_BF16X3, LTGW_FP8 = 0, 1, 2
 
 
@@ -33,10 +34,23 @@ class Stats(ctypes.Structure):
                 ("ms_naf", ctypes.c_double), ("ms_pi", ctypes.c_double), ("ms_screen", ctypes.c_double),
                 ("ms_wnm", ctypes.c_double), ("ms_sigma_qp", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_pi_kernel", ctypes.c_double), ("pi_kernel_launches", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("ms_tridiag", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("p", Params), ("eps", ctypes.c_void_p), ("B_ov", ctypes.c_void_p), ("B_tgt", ctypes.c_void_p),
+                ("targets", ctypes.c_void_p), ("n_tgt", ctypes.c_int), ("shift", ctypes.c_void_p),
+                ("tau_x", ctypes.c_void_p), ("tau_w", ctypes.c_void_p), ("sigma_iw", ctypes.c_void_p),
+                ("e_qp", ctypes.c_void_p), ("qp_status", ctypes.c_void_p)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int), ("queue_ms", ctypes.c_double),
+                ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double), ("message", ctypes.c_char * 120)]
 
 
 class LtgwError(RuntimeError):
@@ -64,6 +78,12 @@ SIGNATURES = {
     "ltgw_polarizability_mixed": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
     "ltgw_screen_static": (_I, [_I, _I, _P, _P, _P]),
+    "ltgw_server_create": (_I, [ctypes.POINTER(ctypes.c_void_p), _I, _I, ctypes.c_size_t]),
+    "ltgw_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ltgw_server_poll": (_I, [_P, ctypes.POINTER(Completion), _I]),
+    "ltgw_server_wait_all": (_I, [_P, _D]),
+    "ltgw_server_destroy": (None, [_P]),
+    "ltgw_request_footprint": (ctypes.c_size_t, [ctypes.POINTER(Params), _I]),
 }
 
 SCREEN_STATIC_MAX_ELEMS = 1 << 19
@@ -205,6 +225,63 @@ class Context:
     def screen(self, Pi, C, stream=None):
         n_omega, N = int(Pi.shape[0]), int(Pi.shape[1])
         self._check(self._lib.ltgw_screen(self.handle, N, n_omega, _ptr(Pi), _ptr(C), _stream_ptr(stream)))
+
+
+class Server:
+    """ltgw_server: continuous admission of solves onto worker slots."""
+
+    def __init__(self, device: int = 0, n_slots: int = 4, hbm_budget_bytes: int = 64 << 30):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        st = self._lib.ltgw_server_create(ctypes.byref(h), device, n_slots, hbm_budget_bytes)
+        if st:
+            raise LtgwError(st, f"ltgw_server_create failed: {status_string(st)}")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, params: Params, eps, B_ov, B_tgt, targets, shift, sigma_out, e_qp_out, status_out,
+               tau_x=None, tau_w=None) -> int:
+        req = Request(params, _ptr(eps), _ptr(B_ov), _ptr(B_tgt), _ptr(targets), int(targets.shape[0]),
+                      _ptr(shift), _ptr(tau_x), _ptr(tau_w), _ptr(sigma_out), _ptr(e_qp_out), _ptr(status_out))
+        t = ctypes.c_uint64()
+        st = self._lib.ltgw_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if st:
+            raise LtgwError(st, status_string(st))
+        # the server reads the buffers later: keep them alive until polled
+        self._keep[t.value] = (eps, B_ov, B_tgt, targets, shift, tau_x, tau_w, sigma_out, e_qp_out, status_out)
+        return t.value
+
+    def poll(self, max_out: int = 256):
+        buf = (Completion * max_out)()
+        n = self._lib.ltgw_server_poll(self.handle, buf, max_out)
+        out = []
+        for i in range(n):
+            c = buf[i]
+            self._keep.pop(c.ticket, None)
+            out.append({"ticket": c.ticket, "status": c.status, "queue_ms": c.queue_ms,
+                        "service_ms": c.service_ms, "latency_ms": c.latency_ms, "start_ms": c.start_ms,
+                        "end_ms": c.end_ms, "message": c.message.decode()})
+        return out
+
+    def wait_all(self, timeout_s: float = 600.0):
+        st = self._lib.ltgw_server_wait_all(self.handle, timeout_s)
+        if st:
+            raise LtgwError(st, status_string(st))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ltgw_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def request_footprint(params: Params, n_tgt: int) -> int:
+    return int(load().ltgw_request_footprint(ctypes.byref(params), n_tgt))
 
 
 def screen_static(Pi, C, stream=None) -> int:

@@ -179,3 +179,28 @@ def make_workload(cfg: dict, **over) -> Problem:
     c = dict(cfg)
     c.update(over)
     return make_problem(c["n_occ"], c["n_virt"], c["n_aux"], c["n_frozen"], c["seed"], c["n_targets"])
+
+
+STREAM_SERVING = 4
+
+
+def serving_stream(n_requests: int = 512, rate_hz: float = 2.0, seed: int = 20230720, n_occ_min: int = 8,
+                   n_occ_max: int = 200):
+    """The serving workload: n_occ log-uniform in [n_occ_min, n_occ_max], frozen
+    core n_occ // 6, n_virt = round(u n_occ) with u uniform in [8, 12],
+    N_aux = 3 (n_occ + n_virt), 4 target states, request seed = seed + 1 + index,
+    Poisson arrivals at rate_hz (exponential gaps).  Draws come from Philox
+    stream 4 at counters (index, 0..2)."""
+    u0 = uniform(seed, STREAM_SERVING, n_requests, 0.0, 1.0, group=0)
+    u1 = uniform(seed, STREAM_SERVING, n_requests, 8.0, 12.0, group=1)
+    u2 = uniform(seed, STREAM_SERVING, n_requests, 0.0, 1.0, group=2)
+    lo, hi = np.log(n_occ_min), np.log(n_occ_max)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        n_occ = int(round(np.exp(lo + (hi - lo) * u0[i])))
+        n_virt = int(round(u1[i] * n_occ))
+        t += -np.log(1.0 - u2[i]) / rate_hz
+        out.append(dict(index=i, n_occ=n_occ, n_frozen=n_occ // 6, n_virt=n_virt, n_aux=3 * (n_occ + n_virt),
+                        n_targets=4, seed=seed + 1 + i, t_arrival=t))
+    return out
