@@ -93,6 +93,7 @@ typedef struct {
   int pi_kernel_launches;    /* Pi-build kernel launches in the last solve            */
   int kernel_launches;       /* all kernel launches in the last solve                 */
   double ms_tridiag;         /* device time of the NAF Householder tridiagonalisation */
+  double ms_generate;        /* host time spent in the block callback (streamed solve) */
 } ltgw_stats;
 
 typedef struct ltgw_ctx ltgw_ctx;
@@ -129,6 +130,26 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps,
                        int n_tgt, const double *shift, const double *tau_x,
                        const double *tau_w, double *sigma_iw, double *e_qp,
                        int *qp_status, void *stream);
+
+/*
+ * The same solve without the occupied-virtual block resident: the caller
+ * supplies the RI tensor one block of occupied orbitals at a time.
+ *   fill(user, i0, i1, dst, stream) writes R^P_ia for active occupied
+ *   orbitals i0 <= i < i1 (n_frozen <= i0 < i1 <= n_occ) into the device
+ *   buffer dst [n_aux][(i1-i0)*n_virt] (pair index (i-i0)*n_virt + a), with
+ *   its work complete (or ordered before later work on `stream`) when it
+ *   returns 0; any other return value aborts the solve (LTGW_ERR_BAD_ARG).
+ * Blocks hold occ_block orbitals (the last may hold fewer); each is requested
+ * twice: for the NAF metric K = sum over blocks of B B^T (Eq. nafeq), then for
+ * the projection R~ = U^T R (Eq. naftrafo).  Needs NAF (naf_thresh >= 0).
+ * Other arguments and outputs as for ltgw_solve.  Synchronises `stream`.
+ */
+typedef int (*ltgw_block_fn)(void *user, int i0, int i1, double *dst, void *stream);
+ltgw_status ltgw_solve_streamed(ltgw_ctx *ctx, const ltgw_params *p, const double *eps,
+                                ltgw_block_fn fill, void *user, int occ_block,
+                                const double *B_tgt, const int *targets, int n_tgt,
+                                const double *shift, const double *tau_x, const double *tau_w,
+                                double *sigma_iw, double *e_qp, int *qp_status, void *stream);
 
 /* ---- grids (host only, no context) ------------------------------------- */
 

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -79,6 +81,7 @@ struct ltgw_ctx {
   int launches = 0;
   double pi_tc_flops = 0.0;
   int tri_n = 0;
+  double gen_ms = 0.0;
   int n_sm = 148;
   Arena a4;  // tensor-core scratch: tile lists and partial tiles
   Arena a5;  // tensor-core operand copies consumed by the next contraction
@@ -144,11 +147,14 @@ ltgw_status check_flags(ltgw_ctx *ctx, cudaStream_t s) {
 // NAF basis on device data: K = B B^T, eigenvectors with eigenvalue > thresh
 // as rows of Ut (descending eigenvalue), their eigenvalues in lam.
 ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B, int64_t ld, double *K,
-                          cudaStream_t s);
+                          cudaStream_t s, double beta = 0.0);
+
+// K builder for the streamed solve: fills w.A (n x n) itself.
+using KBuilder = std::function<ltgw_status(double *K)>;
 
 ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, const double *B,
                           int64_t ld, double thresh, double *Ut, double *lam_out, int *k_out,
-                          int *near_out, cudaStream_t s, bool mixed = false) {
+                          int *near_out, cudaStream_t s, bool mixed = false, const KBuilder *build_K = nullptr) {
   EigWork w;
   auto layout = [&](Arena &A) {
     w.A = A.take<double>((size_t)n * n);
@@ -175,7 +181,9 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   }
   layout(ar);
   w.flags = ctx->flags;
-  if (mixed) {
+  if (build_K) {
+    if ((*build_K)(w.A) != LTGW_OK) return ctx->status();
+  } else if (mixed) {
     if (naf_metric_tc(ctx, n, n_pairs, B, ld, w.A, s) != LTGW_OK) return ctx->status();
   } else {
     GemmF64Args g;
@@ -368,7 +376,7 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
 
 // NAF metric K = B B^T (Eq. nafeq) in the split-BF16 form; K: device [n][n] FP64.
 ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B, int64_t ld, double *K,
-                          cudaStream_t s) {
+                          cudaStream_t s, double beta) {
   const int64_t Kp = (n_pairs + 63) / 64 * 64;
   const int nI = (n + 127) / 128, Mp = nI * 128;
   std::vector<int> tindex;
@@ -392,7 +400,7 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
   TcRun run;
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
   CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                         nI, 1, n, 1.0, K, s), 1);
+                                         nI, 1, n, 1.0, K, s, beta), 1);
   return LTGW_OK;
 }
 
@@ -401,9 +409,16 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
 //   BtT64    FP64 [T][n_orb_act][N]                      R~_tgt transposed (column dot)
 //   BtT32    FP32 [roundup(T n_orb_act,128)][roundup(N,64)]  the W_nm operand
 // With Ut == nullptr (no NAF) they are copies of the active blocks of B_ov, B_tgt.
+// With `window` set, only the ov part runs, for n_ov columns of B_act written
+// into columns [col0, col0 + n_ov) of Bf (row stride ld_bf); padding is left
+// to the caller.
+struct OvWindow {
+  int64_t col0 = 0, ld_bf = 0;
+};
+
 ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, const double *B_act, int64_t ld_act,
                            int64_t n_ov, const double *B_tgt, int n_orb, int n_fc, int T, int n_orb_act, float *Bf,
-                           double *BtT64, float *BtT32, cudaStream_t s) {
+                           double *BtT64, float *BtT32, cudaStream_t s, const OvWindow *window = nullptr) {
   const int64_t Kp_ov = (n_ov + 63) / 64 * 64;
   const int MpN = (N + 127) / 128 * 128, KpN = (N + 63) / 64 * 64;
   const int64_t rowsT = (int64_t)T * n_orb_act, rowsTp = (rowsT + 127) / 128 * 128;
@@ -424,7 +439,7 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   auto layout = [&](Arena &A) {
     UtF = A.take<float>((size_t)MpN * Kpa);
     BactT = A.take<float>((size_t)nI_ov * 128 * Kpa);
-    BtgT = A.take<float>((size_t)T * MpT * Kpa);
+    BtgT = window ? nullptr : A.take<float>((size_t)T * MpT * Kpa);
     ones = A.take<float>((size_t)std::max(T, 1) * Kpa);
   };
   ctx->a5.begin_sizing();
@@ -432,17 +447,26 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core operand allocation failed"); return ctx->status(); }
   layout(ctx->a5);
   CHECK_LAUNCH(ctx, launch_to_f32_padded(Ut, n_aux, N, n_aux, UtF, MpN, Kpa, s), 1);
-  CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_act, ld_act, 0, n_aux, (int)n_ov, BactT, Kpa, nI_ov * 128, 1, 0, 0, s), 1);
-  CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_tgt, n_orb, n_fc, n_aux, n_orb_act, BtgT, Kpa, MpT, T,
-                                             (int64_t)n_aux * n_orb, (int64_t)MpT * Kpa, s), 1);
+  if (B_act)
+    CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_act, ld_act, 0, n_aux, (int)n_ov, BactT, Kpa, nI_ov * 128, 1, 0, 0, s),
+                 1);
+  if (!window)
+    CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_tgt, n_orb, n_fc, n_aux, n_orb_act, BtgT, Kpa, MpT, T,
+                                               (int64_t)n_aux * n_orb, (int64_t)MpT * Kpa, s), 1);
   CHECK_LAUNCH(ctx, launch_scale_table(nullptr, n_aux, Kpa, std::max(T, 1), nullptr, nullptr, SCALE_NONE, ones, s), 1);
   // R~_ov = U^T R_ov: rows N (A = U^T), columns n_ov (B rows = R_ov^T)
-  {
+  if (B_act) {
     TcGemmArgs g;
     g.A = UtF; g.B = BactT; g.scale = ones; g.Kp = Kpa; g.n_t = 1; g.nt_group = 1;
     TcRun run;
     const int nI = (N + 127) / 128;
     if (tc_run(ctx, ctx->a4, g, full_tiles(nI, nI_ov), 0, &run, s) != LTGW_OK) return ctx->status();
+    if (window) {
+      CHECK_LAUNCH(ctx, launch_tc_reduce_full(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, nI_ov,
+                                              N, (int)n_ov, 1.0, nullptr, 0, 0, Bf + window->col0, window->ld_bf,
+                                              MpN, 0, s, n_ov), 1);
+      return LTGW_OK;
+    }
     CHECK_LAUNCH(ctx, launch_tc_reduce_full(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, nI_ov, N,
                                             (int)n_ov, 1.0, nullptr, 0, 0, Bf, Kp_ov, MpN, 0, s), 1);
   }
@@ -579,15 +603,24 @@ ltgw_status ltgw_get_stats(const ltgw_ctx *ctx, ltgw_stats *out) {
   return LTGW_OK;
 }
 
-ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, const double *B_ov,
-                       const double *B_tgt, const int *targets, int n_tgt, const double *shift,
-                       const double *tau_x, const double *tau_w, double *sigma_iw, double *e_qp,
-                       int *qp_status, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// One solve; with `fill` set, B_ov is not given and the occupied blocks are
+// requested from the caller twice (NAF metric, then projection).
+ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, const double *B_ov,
+                       ltgw_block_fn fill, void *user, int occ_block, const double *B_tgt, const int *targets,
+                       int n_tgt, const double *shift, const double *tau_x, const double *tau_w,
+                       double *sigma_iw, double *e_qp, int *qp_status, void *stream) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
   ctx->reset();
   if (validate(ctx, p) != LTGW_OK) return ctx->status();
-  REQUIRE(ctx, eps && B_ov && B_tgt && targets && shift && sigma_iw && e_qp && qp_status,
+  const bool streamed = fill != nullptr;
+  REQUIRE(ctx, eps && (B_ov || streamed) && B_tgt && targets && shift && sigma_iw && e_qp && qp_status,
           "a required pointer is NULL");
+  REQUIRE(ctx, !streamed || (p->naf_thresh >= 0.0 && occ_block >= 1),
+          "the streamed solve needs NAF (naf_thresh >= 0) and occ_block >= 1");
   REQUIRE(ctx, n_tgt >= 1, "n_tgt must be >= 1");
   REQUIRE(ctx, (tau_x == nullptr) == (tau_w == nullptr), "tau_x and tau_w must both be given or both NULL");
   LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -643,7 +676,10 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   std::vector<double> h_epsn(T);
   for (int t = 0; t < T; ++t) h_epsn[t] = h_eps[h_tg[t]];
 
-  const bool bov_dev = is_device_ptr(B_ov), btg_dev = is_device_ptr(B_tgt);
+  const bool bov_dev = streamed || is_device_ptr(B_ov), btg_dev = is_device_ptr(B_tgt);
+  const int blk = streamed ? std::min(occ_block, n_act) : 0;
+  double *d_blk = nullptr;
+  ctx->gen_ms = 0.0;
   // ---- phase-1 workspace: inputs, grids, NAF
   double *d_eps, *d_delta, *d_om, *d_wt, *d_x, *d_w, *d_E, *d_epsn, *d_shift, *d_Bov, *d_Btg, *d_Ut, *d_lam;
   auto layout1 = [&](Arena &A) {
@@ -657,6 +693,7 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     d_epsn = A.take<double>(T);
     d_shift = A.take<double>(T);
     d_Bov = bov_dev ? const_cast<double *>(B_ov) : A.take<double>((size_t)n_aux * n_ov_all);
+    d_blk = streamed ? A.take<double>((size_t)n_aux * blk * n_virt) : nullptr;
     d_Btg = btg_dev ? const_cast<double *>(B_tgt) : A.take<double>((size_t)T * n_aux * n_orb);
     d_Ut = naf ? A.take<double>((size_t)n_aux * n_aux) : nullptr;
     d_lam = naf ? A.take<double>(n_aux) : nullptr;
@@ -682,14 +719,41 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   CHECK_LAUNCH(ctx, launch_pair_gaps(d_eps, n_occ, n_virt, n_fc, d_delta, s), 1);
 
   // ---- frozen-core slice: the active pairs are the trailing columns
-  const double *B_act = d_Bov + (int64_t)n_fc * n_virt;
+  const double *B_act = streamed ? nullptr : d_Bov + (int64_t)n_fc * n_virt;
   const int64_t ld_act = n_ov_all;
+  // streamed: ask the caller for occupied block [i0, i1) into d_blk
+  auto get_block = [&](int i0, int i1) -> ltgw_status {
+    LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = fill(user, i0, i1, d_blk, (void *)s);
+    ctx->gen_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc != 0) { ctx->fail(LTGW_ERR_BAD_ARG, "the block callback reported an error"); return ctx->status(); }
+    return LTGW_OK;
+  };
+  KBuilder build_K = [&](double *K) -> ltgw_status {
+    LTGW_CUDA(ctx, cudaMemsetAsync(K, 0, (size_t)n_aux * n_aux * sizeof(double), s));
+    for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
+      const int i1 = std::min(n_occ, i0 + blk);
+      const int64_t cols = (int64_t)(i1 - i0) * n_virt;
+      if (get_block(i0, i1) != LTGW_OK) return ctx->status();
+      if (mixed) {
+        if (naf_metric_tc(ctx, n_aux, cols, d_blk, cols, K, s, 1.0) != LTGW_OK) return ctx->status();
+      } else {
+        GemmF64Args g;  // K += B_blk B_blk^T
+        g.M = n_aux; g.N = n_aux; g.K = cols;
+        g.A = d_blk; g.lda = cols; g.B = d_blk; g.ldb = cols;
+        g.C = K; g.ldc = n_aux; g.syrk = 1; g.beta = 1.0;
+        CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
+      }
+    }
+    return LTGW_OK;
+  };
 
   // ---- NAF (Eqs. nafeq, naftrafo) on a separate arena for its scratch
   int N = n_aux, near = 0;
   if (naf) {
     if (naf_basis_dev(ctx, ctx->a3, n_aux, n_ov, B_act, ld_act, p->naf_thresh, d_Ut, d_lam, &N, &near, s,
-                      mixed) != LTGW_OK)
+                      mixed, streamed ? &build_K : nullptr) != LTGW_OK)
       return ctx->status();
   }
   ctx->stats.n_naf = N;
@@ -728,17 +792,48 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   int64_t ld_bt = ld_act;
   const double *Btt = d_Btg + n_fc;
   int64_t ld_btt = n_orb, stride_btt = (int64_t)n_aux * n_orb;
-  if (mixed) {
+  if (mixed && streamed) {
+    const int64_t MpN = (N + 127) / 128 * 128;
+    LTGW_CUDA(ctx, cudaMemsetAsync(d_Bf, 0, (size_t)MpN * Kp_ov * sizeof(float), s));
+    for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
+      const int i1 = std::min(n_occ, i0 + blk);
+      const int64_t cols = (int64_t)(i1 - i0) * n_virt;
+      if (get_block(i0, i1) != LTGW_OK) return ctx->status();
+      OvWindow win;
+      win.col0 = (int64_t)(i0 - n_fc) * n_virt;
+      win.ld_bf = Kp_ov;
+      if (naf_project_tc(ctx, N, n_aux, d_Ut, d_blk, cols, cols, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64,
+                         d_BtT32, s, &win) != LTGW_OK)
+        return ctx->status();
+    }
+    if (naf_project_tc(ctx, N, n_aux, d_Ut, nullptr, 0, 0, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64, d_BtT32,
+                       s) != LTGW_OK)
+      return ctx->status();
+  } else if (mixed) {
     if (naf_project_tc(ctx, N, n_aux, naf ? d_Ut : nullptr, B_act, ld_act, n_ov, d_Btg, n_orb, n_fc, T, n_orb_act,
                        d_Bf, d_BtT64, d_BtT32, s) != LTGW_OK)
       return ctx->status();
   } else if (naf) {
-    GemmF64Args g;  // R~_ov = U^T R_ov
-    g.M = N; g.N = (int)std::min<int64_t>(n_ov, INT32_MAX); g.K = n_aux;
-    g.A = d_Ut; g.lda = n_aux;
-    g.B = B_act; g.ldb = ld_act;
-    g.C = d_Bt; g.ldc = n_ov;
-    CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+    if (streamed) {
+      for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
+        const int i1 = std::min(n_occ, i0 + blk);
+        const int64_t cols = (int64_t)(i1 - i0) * n_virt;
+        if (get_block(i0, i1) != LTGW_OK) return ctx->status();
+        GemmF64Args g;  // R~_ov[:, block] = U^T R_blk
+        g.M = N; g.N = (int)cols; g.K = n_aux;
+        g.A = d_Ut; g.lda = n_aux;
+        g.B = d_blk; g.ldb = cols;
+        g.C = d_Bt + (int64_t)(i0 - n_fc) * n_virt; g.ldc = n_ov;
+        CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+      }
+    } else {
+      GemmF64Args g;  // R~_ov = U^T R_ov
+      g.M = N; g.N = (int)std::min<int64_t>(n_ov, INT32_MAX); g.K = n_aux;
+      g.A = d_Ut; g.lda = n_aux;
+      g.B = B_act; g.ldb = ld_act;
+      g.C = d_Bt; g.ldc = n_ov;
+      CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+    }
     GemmF64Args h;  // R~_tgt[t] = U^T R_tgt[t][:, active]
     h.M = N; h.N = n_orb_act; h.K = n_aux;
     h.A = d_Ut; h.lda = n_aux; h.strideA = 0;
@@ -817,11 +912,38 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   st.ms_total = ctx->ms(EV_START, EV_END);
   st.ms_tridiag = naf ? ctx->ms(EV_TRI0, EV_TRI1) : 0.0;
 
+  st.ms_generate = ctx->gen_ms;
   std::vector<int> hs(T);
   if (read_small(ctx, hs.data(), qp_status, T * sizeof(int), s) != LTGW_OK) return ctx->status();
   for (int t = 0; t < T; ++t)
     if (hs[t] != 0) ctx->fail(LTGW_ERR_NO_CONVERGE, "a quasi-particle Newton solve did not converge");
   return ctx->status();
+}
+
+}  // namespace
+
+extern "C" {
+
+ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, const double *B_ov,
+                       const double *B_tgt, const int *targets, int n_tgt, const double *shift,
+                       const double *tau_x, const double *tau_w, double *sigma_iw, double *e_qp,
+                       int *qp_status, void *stream) {
+  return solve_impl(ctx, p, eps, B_ov, nullptr, nullptr, 0, B_tgt, targets, n_tgt, shift, tau_x, tau_w, sigma_iw,
+                    e_qp, qp_status, stream);
+}
+
+ltgw_status ltgw_solve_streamed(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, ltgw_block_fn fill,
+                                void *user, int occ_block, const double *B_tgt, const int *targets, int n_tgt,
+                                const double *shift, const double *tau_x, const double *tau_w, double *sigma_iw,
+                                double *e_qp, int *qp_status, void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  if (!fill) {
+    ctx->reset();
+    ctx->fail(LTGW_ERR_BAD_ARG, "fill callback is NULL");
+    return ctx->status();
+  }
+  return solve_impl(ctx, p, eps, nullptr, fill, user, occ_block, B_tgt, targets, n_tgt, shift, tau_x, tau_w,
+                    sigma_iw, e_qp, qp_status, stream);
 }
 
 ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B, int64_t ld,

@@ -120,12 +120,13 @@ cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0,
                                      float *dst, int rows_p, int cols_p, int batch, int64_t strideS,
                                      int64_t strideD, cudaStream_t s);
 // out[r][c] = alpha * sum over splits of full-grid partial tiles (tile = I * nJ + J) for
-// r < rows, c < cols; FP64 to out64 (ld ld64) and/or FP32 to out32 (ld ld32, zero padding
-// up to rows_p32 x ld32 is written too), per group g (strides in elements).
+// r < rows, c < cols; FP64 to out64 (ld ld64) and/or FP32 to out32 (ld ld32; columns
+// up to cols32 (default ld32) and rows up to rows_p32 are written, zero beyond the
+// data), per group g (strides in elements).
 cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32, int splits, int groups,
                                   int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
                                   int64_t ld64, int64_t stride64, float *out32, int64_t ld32,
-                                  int rows_p32, int64_t stride32, cudaStream_t s);
+                                  int rows_p32, int64_t stride32, cudaStream_t s, int64_t cols32 = -1);
 // W[g][c] = sum over splits and tile rows of cd_out[split][g][I][c], c < cols.
 cudaError_t launch_tc_reduce_coldot(const float *cd_out, int splits, int groups, int n_tile_rows,
                                     int cols_p, int cols, double *W, int64_t ldw, cudaStream_t s);
@@ -139,7 +140,7 @@ cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n
 // [n_t][N][N] FP64, for a lower tile list (tile_index [nI][nJ]).
 cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
                                  int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
-                                 double *M, cudaStream_t s);
+                                 double *M, cudaStream_t s, double beta = 0.0);
 // dst[c][r] = src[r][c0 + c] in FP64 (batched)
 cudaError_t launch_transpose_f64(const double *src, int64_t lds, int64_t c0, int rows, int cols, double *dst,
                                  int64_t ldd, int batch, int64_t strideS, int64_t strideD, cudaStream_t s);

@@ -43,7 +43,7 @@ __global__ void scale_table_kernel(const double *__restrict__ delta, int64_t K, 
 // tiles are 128 x 128, four scales per group.
 __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
                                      int splits, int groups, int n_tiles, const int *__restrict__ tile_index,
-                                     int nJ, int N, double alpha, double *__restrict__ M) {
+                                     int nJ, int N, double alpha, double beta, double *__restrict__ M) {
   const int t = blockIdx.y;
   const int grp = t / 4, slot = t % 4;
   const int64_t NN = (int64_t)N * N;
@@ -63,6 +63,7 @@ __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const f
       acc += partial32 ? (double)partial32[off] : partial[off];
     }
     acc *= alpha;
+    if (beta != 0.0) acc += beta * M[t * NN + (int64_t)i * N + j];
     M[t * NN + (int64_t)i * N + j] = acc;
     M[t * NN + (int64_t)j * N + i] = acc;
   }
@@ -111,11 +112,12 @@ __global__ void transpose_f64_kernel(const double *__restrict__ src, int64_t lds
 __global__ void tc_reduce_full_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
                                       int splits, int groups, int n_tiles, int nJ, int rows, int cols,
                                       double alpha, double *__restrict__ out64, int64_t ld64, int64_t stride64,
-                                      float *__restrict__ out32, int64_t ld32, int rows_p32, int64_t stride32) {
+                                      float *__restrict__ out32, int64_t ld32, int64_t cols32, int rows_p32,
+                                      int64_t stride32) {
   const int g = blockIdx.z;
   const int r = blockIdx.y;
   const int grp = g, slot = 0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (out32 ? ld32 : cols);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (out32 ? cols32 : cols);
        c += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
     if (r < rows && c < cols) {
@@ -168,14 +170,14 @@ cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n
 
 cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
                                  int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
-                                 double *M, cudaStream_t s) {
+                                 double *M, cudaStream_t s, double beta) {
   if (N <= 0 || n_t <= 0) return cudaSuccess;
   int64_t ntri = (int64_t)N * (N + 1) / 2;
   int bx = (int)((ntri + 255) / 256);
   if (bx > 152 * 4) bx = 152 * 4;
   dim3 grid(bx, n_t);
   tc_reduce_sym_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, tile_index, nJ, N,
-                                            alpha, M);
+                                            alpha, beta, M);
   return cudaGetLastError();
 }
 
@@ -195,15 +197,16 @@ cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0,
 cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32, int splits, int groups,
                                   int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
                                   int64_t ld64, int64_t stride64, float *out32, int64_t ld32,
-                                  int rows_p32, int64_t stride32, cudaStream_t s) {
+                                  int rows_p32, int64_t stride32, cudaStream_t s, int64_t cols32) {
+  if (cols32 < 0) cols32 = ld32;
   const int nrows = out32 ? std::max(rows, rows_p32) : rows;
-  const int64_t ncols = out32 ? ld32 : cols;
+  const int64_t ncols = out32 ? cols32 : cols;
   if (nrows <= 0 || ncols <= 0 || groups <= 0) return cudaSuccess;
   int bx = (int)((ncols + 255) / 256);
   if (bx > 64) bx = 64;
   dim3 grid(bx, nrows, groups);
   tc_reduce_full_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, nJ, rows, cols, alpha,
-                                             out64, ld64, stride64, out32, ld32, rows_p32, stride32);
+                                             out64, ld64, stride64, out32, ld32, cols32, rows_p32, stride32);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,8 @@ class Stats(ctypes.Structure):
                 ("ms_naf", ctypes.c_double), ("ms_pi", ctypes.c_double), ("ms_screen", ctypes.c_double),
                 ("ms_wnm", ctypes.c_double), ("ms_sigma_qp", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_pi_kernel", ctypes.c_double), ("pi_kernel_launches", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int), ("ms_tridiag", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_int), ("ms_tridiag", ctypes.c_double),
+                ("ms_generate", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,6 +62,9 @@ class LtgwError(RuntimeError):
 
 _lib = None
 
+BLOCK_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                            ctypes.c_void_p)
+
 # exported symbols and their ctypes signatures
 _P, _I, _D, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
 SIGNATURES = {
@@ -71,6 +75,8 @@ SIGNATURES = {
     "ltgw_set_timing": (_I, [_P, _I]),
     "ltgw_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "ltgw_solve": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "ltgw_solve_streamed": (_I, [_P, ctypes.POINTER(Params), _P, BLOCK_FN, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P,
+                                 _P, _P]),
     "ltgw_gl_grid": (_I, [_I, _D, _P, _P]),
     "ltgw_laplace_grid": (_I, [_I, _D, _D, _P, _P, _P]),
     "ltgw_naf_basis": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
@@ -126,6 +132,19 @@ def _stream_ptr(stream):
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+class _DeviceBuffer:
+    """Zero-copy torch view of library-owned device memory (for block callbacks)."""
+
+    def __init__(self, ptr: int, shape, typestr: str = "<f8"):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape), "typestr": typestr,
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, dtype: str = "<f8"):
+    import torch
+    return torch.as_tensor(_DeviceBuffer(ptr, shape, dtype), device="cuda")
 
 
 def status_string(st: int) -> str:
@@ -191,6 +210,28 @@ class Context:
         st = self._lib.ltgw_solve(self.handle, ctypes.byref(params), _ptr(eps), _ptr(B_ov), _ptr(B_tgt),
                                   _ptr(targets), n_tgt, _ptr(shift), _ptr(tau_x), _ptr(tau_w),
                                   _ptr(sigma_out), _ptr(e_qp_out), _ptr(status_out), _stream_ptr(stream))
+        return self._check(st, allow=(LTGW_ERR_NO_CONVERGE,) if allow_no_converge else ())
+
+    def solve_streamed(self, params: Params, eps, fill, occ_block: int, B_tgt, targets, shift, sigma_out,
+                       e_qp_out, status_out, tau_x=None, tau_w=None, stream=None, allow_no_converge=True) -> int:
+        """ltgw_solve_streamed; fill(i0, i1, dst_ptr, stream_ptr) writes the occupied block
+        [i0, i1) into the device buffer at dst_ptr and returns 0."""
+        errors = []
+
+        def _cb(user, i0, i1, dst, strm):
+            try:
+                return int(fill(i0, i1, dst, strm) or 0)
+            except Exception as ex:  # reported through the status, re-raised below
+                errors.append(ex)
+                return 1
+
+        cb = BLOCK_FN(_cb)
+        st = self._lib.ltgw_solve_streamed(self.handle, ctypes.byref(params), _ptr(eps), cb, None, occ_block,
+                                           _ptr(B_tgt), _ptr(targets), int(targets.shape[0]), _ptr(shift),
+                                           _ptr(tau_x), _ptr(tau_w), _ptr(sigma_out), _ptr(e_qp_out),
+                                           _ptr(status_out), _stream_ptr(stream))
+        if errors:
+            raise errors[0]
         return self._check(st, allow=(LTGW_ERR_NO_CONVERGE,) if allow_no_converge else ())
 
     def naf_basis(self, B, n_pairs: int, ld: int, thresh: float, Ut, lam, stream=None) -> int:

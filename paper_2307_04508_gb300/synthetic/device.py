@@ -150,3 +150,13 @@ class DeviceLaw:
         for t, p in enumerate(self.targets):
             out[t] = self._gemm(pair_normals_row(self.seed, self.n_aux, n_orb, int(p)))
         return out
+
+    def fill_block(self, i0: int, i1: int, dst_ptr: int) -> int:
+        """Block callback for ltgw_solve_streamed: B_ov columns of occupied
+        orbitals [i0, i1) into the library's device buffer at dst_ptr."""
+        import torch
+        from ..ltgw import device_view
+        dst = device_view(dst_ptr, (self.n_aux, (i1 - i0) * self.n_virt))
+        self.b_ov_block(i0, i1, out=dst)
+        torch.cuda.synchronize()
+        return 0

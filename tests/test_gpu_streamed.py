@@ -1,0 +1,72 @@
+"""The streamed solve (ltgw_solve_streamed): the RI tensor arrives one block of
+occupied orbitals at a time (NAF metric accumulated over blocks, then the
+projection block by block), with the same results as the resident solve."""
+import numpy as np
+import pytest
+
+from oracle import ltgw_oracle as O
+from paper_2307_04508_gb300 import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+QP_TOL = 1e-8
+QP_TOL_MIXED = 1e-3 / 27.211386245988
+
+
+@pytest.fixture(scope="module")
+def mid():
+    return S.make_workload(S.MID)
+
+
+@pytest.fixture(scope="module")
+def oracle_lt(mid):
+    tau = O.sinc_laplace_grid(8, -12.0, 3.0)
+    _, e, st = O.solve(mid.eps, mid.B_ov, mid.B_tgt, mid.targets, mid.shift, 60, 540, 10, n_omega=32,
+                       naf_thresh=1e-2, tau_x=tau[0], tau_w=tau[1])
+    return tau, e, st
+
+
+@pytest.mark.parametrize("mixed,occ_block", [(False, 7), (True, 7), (True, 50)])
+def test_streamed_matches_oracle(mid, oracle_lt, mixed, occ_block):
+    from paper_2307_04508_gb300 import ltgw
+    tau, e_o, st_o = oracle_lt
+    B_ov = torch.from_numpy(mid.B_ov).cuda()
+    calls = []
+
+    def fill(i0, i1, dst, strm):
+        calls.append((i0, i1))
+        view = ltgw.device_view(dst, (1800, (i1 - i0) * 540))
+        view.copy_(B_ov[:, i0 * 540:i1 * 540])
+        torch.cuda.synchronize()
+        return 0
+
+    ctx = ltgw.Context(0)
+    try:
+        p = ltgw.make_params(60, 540, 1800, 10, 32, 8, 0.5, 1e-2, 2, True,
+                             ltgw.LTGW_BF16X3 if mixed else ltgw.LTGW_FP64)
+        T = len(mid.targets)
+        sig, e, st = np.zeros((T, 32, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
+        ctx.solve_streamed(p, mid.eps, fill, occ_block, mid.B_tgt, mid.targets.astype(np.int32), mid.shift, sig, e,
+                           st, tau_x=np.ascontiguousarray(tau[0]), tau_w=np.ascontiguousarray(tau[1]))
+    finally:
+        ctx.close()
+    nblk = -(-50 // occ_block)
+    assert len(calls) == 2 * nblk and calls[0][0] == 10 and calls[nblk - 1][1] == 60
+    assert np.all(st == 0)
+    tol = QP_TOL_MIXED if mixed else QP_TOL
+    assert np.abs(e - e_o).max() <= tol, np.abs(e - e_o).max()
+
+
+def test_streamed_requires_naf(mid):
+    from paper_2307_04508_gb300 import ltgw
+    ctx = ltgw.Context(0)
+    try:
+        p = ltgw.make_params(60, 540, 1800, 10, 32, 8, 0.5, -1.0, 2, True)
+        T = len(mid.targets)
+        with pytest.raises(ltgw.LtgwError) as e:
+            ctx.solve_streamed(p, mid.eps, lambda *a: 0, 8, mid.B_tgt, mid.targets.astype(np.int32), mid.shift,
+                               np.zeros((T, 32, 2)), np.zeros(T), np.zeros(T, dtype=np.int32))
+        assert e.value.status == ltgw.LTGW_ERR_BAD_ARG
+    finally:
+        ctx.close()
