@@ -171,7 +171,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     w.count = A.take<int>(2);
     const int64_t nsplit = (n + 63) / 64;
     w.wy = A.take<double>((size_t)(nsplit + 3) * 64 * (64 + (size_t)n));
-    w.grid_ws = A.take<double>((size_t)n + 2 * (size_t)ctx->n_sm + 8);
+    w.grid_ws = A.take<double>((size_t)4 * n + 2 * (size_t)ctx->n_sm + 8);
   };
   ar.begin_sizing();
   layout(ar);
@@ -196,7 +196,8 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   LTGW_CUDA(ctx, cudaMemsetAsync(w.V, 0, (size_t)n * n * sizeof(double), s));
   int nl = 0;
   ctx->mark(EV_TRI0, s);
-  cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl);
+  bool f32 = mixed;
+  cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl, &f32);
   ctx->mark(EV_TRI1, s);
   ctx->tri_n = n;
   ctx->launches += nl;
@@ -208,7 +209,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   if (near_out) *near_out = cnt[1];
   if (k <= 0) { ctx->fail(LTGW_ERR_NO_NAF, "NAF threshold kept no auxiliary function"); return ctx->status(); }
   nl = 0;
-  e = launch_eig_vectors(w, n, k, Ut, ctx->flags, s, &nl);
+  e = launch_eig_vectors(w, n, k, Ut, ctx->flags, s, &nl, f32);
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("eig_vectors: ") + cudaGetErrorString(e)); return ctx->status(); }
   if (lam_out) LTGW_CUDA(ctx, cudaMemcpyAsync(lam_out, w.lam, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -946,8 +947,8 @@ ltgw_status ltgw_solve_streamed(ltgw_ctx *ctx, const ltgw_params *p, const doubl
                     sigma_iw, e_qp, qp_status, stream);
 }
 
-ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B, int64_t ld,
-                           double thresh, double *Ut, double *lambda, int *n_naf, void *stream) {
+static ltgw_status naf_basis_api(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B, int64_t ld,
+                                 double thresh, double *Ut, double *lambda, int *n_naf, void *stream, bool mixed) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
   ctx->reset();
   REQUIRE(ctx, n_aux >= 1 && n_pairs >= 1 && ld >= n_pairs, "bad sizes");
@@ -958,13 +959,23 @@ ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const doub
   cudaStream_t s = (cudaStream_t)stream;
   LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
   int k = 0, near = 0;
-  if (naf_basis_dev(ctx, ctx->a3, n_aux, n_pairs, B, ld, thresh, Ut, lambda, &k, &near, s) != LTGW_OK)
+  if (naf_basis_dev(ctx, ctx->a3, n_aux, n_pairs, B, ld, thresh, Ut, lambda, &k, &near, s, mixed) != LTGW_OK)
     return ctx->status();
   *n_naf = k;
   ctx->stats.n_naf = k;
   ctx->stats.naf_near_threshold = near;
   LTGW_CUDA(ctx, cudaStreamSynchronize(s));
   return check_flags(ctx, s);
+}
+
+ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B, int64_t ld,
+                           double thresh, double *Ut, double *lambda, int *n_naf, void *stream) {
+  return naf_basis_api(ctx, n_aux, n_pairs, B, ld, thresh, Ut, lambda, n_naf, stream, false);
+}
+
+ltgw_status ltgw_naf_basis_mixed(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B, int64_t ld,
+                                 double thresh, double *Ut, double *lambda, int *n_naf, void *stream) {
+  return naf_basis_api(ctx, n_aux, n_pairs, B, ld, thresh, Ut, lambda, n_naf, stream, true);
 }
 
 ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,

@@ -1,0 +1,1043 @@
+// Symmetric eigensolver for the natural auxiliary functions (Sec. 2:
+// diagonalise K, keep the eigenvectors whose eigenvalue exceeds eps_NAF).
+//
+//  1. Householder reduction K = Q T Q^T to tridiagonal T (one reflector per
+//     step: reflector, symmetric mat-vec, rank-2 update of the trailing block);
+//  2. Sturm-sequence count of the eigenvalues of T above the threshold;
+//  3. multisection for the kept eigenvalues, with T in shared memory;
+//  4. inverse iteration for their eigenvectors (tridiagonal LU with row
+//     interchanges), with modified Gram-Schmidt inside groups of nearly equal
+//     eigenvalues;
+//  5. symmetric re-orthonormalisation X <- X (3 - X^T X)/2 twice, which removes
+//     the small non-orthogonality inverse iteration leaves between close
+//     eigenvalues without leaving the span of X;
+//  6. back-transformation U = Q X in compact-WY blocks of 64 reflectors
+//     (split-K GEMMs), written transposed as the rows of Ut.
+//
+// Two arithmetic forms share this code: FP64 throughout (the plain form), and
+// FP32 for steps 1 and 3-6 (the mixed form, whose metric K already carries the
+// split-BF16 contraction's ~1e-6 relative error; FP32 runs at 64x the FP64
+// rate on this part).  Scalars of the reductions (norms, Householder
+// coefficients, partial sums) stay FP64 in both.  Only the kept eigenvectors
+// are formed.  Householder convention: H = 1 - tau v v^T, v_0 = 1, H x = beta e_1.
+#include <float.h>
+
+#include <algorithm>
+#include <mutex>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ltgw {
+namespace {
+
+constexpr int RB = 1024;        // threads of the single-block kernels
+constexpr int HH_MIN_ROWS = 4;  // fewest rows per block of the fused reduction
+
+template <typename T> struct Lim;
+template <> struct Lim<double> {
+  static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
+  static __device__ __forceinline__ double tiny() { return DBL_MIN; }
+  static constexpr double group_tol = 1e-7;   // inverse-iteration groups, relative to ||T||
+};
+template <> struct Lim<float> {
+  static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
+  static __device__ __forceinline__ float tiny() { return FLT_MIN; }
+  static constexpr double group_tol = 1e-5;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (lane == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ---- per-step kernels (FP64; used when a cooperative launch is not possible)
+// Reflector for column k: x = A[k+1:n, k].
+__global__ void __launch_bounds__(RB) hh_reflector_kernel(const double *A, double *V, double *d,
+                                                          double *e, double *tau, double *scal,
+                                                          int n, int k) {
+  __shared__ double sh[32];
+  const int L = n - k - 1;
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) {
+    double x = A[(int64_t)(k + 1 + i) * n + k];
+    s = fma(x, x, s);
+  }
+  const double sigma = block_sum(s, sh);
+  const double alpha = A[(int64_t)(k + 1) * n + k];
+  double t, beta, sc;
+  if (sigma == 0.0) {
+    t = 0.0; beta = alpha; sc = 0.0;
+  } else {
+    double nrm = sqrt(alpha * alpha + sigma);
+    beta = (alpha >= 0.0) ? -nrm : nrm;
+    t = (beta - alpha) / beta;
+    sc = 1.0 / (alpha - beta);
+  }
+  double *v = V + (int64_t)k * n + (k + 1);
+  for (int i = threadIdx.x; i < L; i += blockDim.x)
+    v[i] = (i == 0) ? 1.0 : A[(int64_t)(k + 1 + i) * n + k] * sc;
+  if (threadIdx.x == 0) {
+    d[k] = A[(int64_t)k * n + k];
+    e[k] = beta;
+    tau[k] = t;
+    scal[0] = t;
+  }
+}
+
+// p = tau * A22 v, one warp per row of the trailing block.
+__global__ void hh_symv_kernel(const double *__restrict__ A, const double *__restrict__ V,
+                               double *__restrict__ p, const double *__restrict__ scal, int n,
+                               int k) {
+  const int L = n - k - 1;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= L) return;
+  const double *row = A + (int64_t)(k + 1 + warp) * n + (k + 1);
+  const double *v = V + (int64_t)k * n + (k + 1);
+  double s = 0.0;
+  for (int j = lane; j < L; j += 32) s = fma(row[j], v[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) p[warp] = scal[0] * s;
+}
+
+// w = p - (tau/2)(p.v) v
+__global__ void __launch_bounds__(RB) hh_w_kernel(const double *V, const double *p, double *w,
+                                                  const double *scal, int n, int k) {
+  __shared__ double sh[32];
+  const int L = n - k - 1;
+  const double *v = V + (int64_t)k * n + (k + 1);
+  double s = 0.0;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) s = fma(p[i], v[i], s);
+  const double gamma = 0.5 * scal[0] * block_sum(s, sh);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) w[i] = p[i] - gamma * v[i];
+}
+
+// A22 -= v w^T + w v^T
+__global__ void hh_update_kernel(double *__restrict__ A, const double *__restrict__ V,
+                                 const double *__restrict__ w, int n, int k) {
+  const int L = n - k - 1;
+  const double *v = V + (int64_t)k * n + (k + 1);
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < LL;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / L), j = (int)(e - (int64_t)i * L);
+    double *a = A + (int64_t)(k + 1 + i) * n + (k + 1 + j);
+    *a -= v[i] * w[j] + w[i] * v[j];
+  }
+}
+
+// Last diagonal / off-diagonal entries once every reflector is applied.
+__global__ void hh_finalize_kernel(const double *A, double *d, double *e, int n) {
+  if (threadIdx.x != 0) return;
+  if (n >= 2) {
+    d[n - 2] = A[(int64_t)(n - 2) * n + (n - 2)];
+    e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+  }
+  d[n - 1] = A[(int64_t)(n - 1) * n + (n - 1)];
+  e[n - 1] = 0.0;
+}
+
+// ---- fused Householder reduction (one cooperative launch) ----
+// All n-2 reflector steps in one kernel with ONE grid barrier per step.
+// Writing A^(k) for the matrix after the first k rank-2 updates, reflector k
+// comes from row k of A^(k) (= column k by symmetry), p_k = tau_k A^(k)_22 v_k,
+// w_k = p_k - (tau_k/2)(p_k.v_k) v_k and A^(k+1)_22 = A^(k)_22 - v_k w_k^T - w_k v_k^T.
+// Row r belongs to block r mod G for the whole reduction (held in shared
+// memory when the block's rows fit there, else in place in global memory).
+// Step k:
+//  phase 1 (every block, identical arithmetic, so every block holds the same
+//    v_k): w_{k-1} from the full p_{k-1} and the per-block partials of
+//    p_{k-1}.v_{k-1}; row k of A^(k) from row k of A^(k-1), which its owner
+//    published during step k-1, minus update k-1; reflector k from it;
+//  phase 2 (own rows r > k): one pass that applies update k-1 and accumulates
+//    p_k[r] = tau_k sum_j A^(k)[r][j] v_k[j]; then the owner of row k+1
+//    copies that row to the published buffer;
+//  grid barrier.
+// p, the published row and the partials are double-buffered by step parity, so
+// a block still reading step k-1's copies never sees step k's writes.  Data
+// crossing blocks goes through L2 (ld.global.cg).  The barrier is bounded
+// (about two seconds) and reports through flags.
+struct GridBar {
+  unsigned count;   // arrivals so far; barrier j (0-based) is passed at count >= G (j + 1)
+  int abort;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier number j: one release-add per block, then an acquire poll of
+// the counter (bounded: about two seconds, then the abort flag and FLAG_EIG).
+__device__ bool grid_barrier(GridBar *gb, unsigned j, int *flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gridDim.x * (j + 1);
+    red_add_release(&gb->count, 1u);
+    if (ld_acquire(&gb->count) < target) {
+      const uint64_t t0 = gtimer();
+      unsigned it = 0;
+      while (ld_acquire(&gb->count) < target) {
+        if ((++it & 1023) == 0) {
+          if (*(volatile int *)&gb->abort) { ok = 0; break; }
+          if (gtimer() - t0 > 2000000000ull) {
+            atomicExch(&flags[FLAG_EIG], 1);
+            atomicExch(&gb->abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;   // in lane 0
+}
+
+// Fixed-order sum of the per-block partials (identical in every block).
+__device__ double sum_partials(const double *part, double *sh) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(part + b);
+  return block_sum(v, sh);
+}
+
+template <typename T>
+struct HhFusedArgs {
+  const double *A0;   // the input matrix (row 0 is read from here at step 0)
+  T *A;               // working rows, updated in place when they do not fit in shared memory
+  T *V;               // [n][n] reflectors, row k = v_k (columns k+1..n-1 written)
+  double *d, *e, *tau;
+  T *P;               // [2][n] p of the step, by parity
+  T *pub;             // [2][n] the next reflector's row, by parity
+  double *tail;       // [2] A^(n-3)[n-1][n-2 .. n-1], for the last 2 x 2 block
+  double *part;       // [2][G] per-block partials of p.v, by parity
+  GridBar *gb;
+  int *flags;
+  int n, R;           // R = rows per block
+};
+
+// One lane-strided pass over row[j0:j1): optional update a -= v_r w + w_r v
+// (UPD) and the dot with vc.  Eight loads are issued before their use so that
+// rows streamed from L2/HBM keep enough requests in flight.
+template <typename T, bool UPD>
+__device__ __forceinline__ T row_pass(T *row, int j0, int j1, const T *vp, const T *wv, const T *vc, T vr, T wr) {
+  const int lane = threadIdx.x & 31;
+  T acc0 = 0, acc1 = 0;
+  int j = j0 + lane;
+  for (; j + 7 * 32 < j1; j += 8 * 32) {
+    T x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = row[j + u * 32];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = j + u * 32;
+      T a = x[u];
+      if (UPD) {
+        a = fma(-vr, wv[q], fma(-wr, vp[q], a));
+        row[q] = a;
+      }
+      if (u & 1) acc1 = fma(a, vc[q], acc1); else acc0 = fma(a, vc[q], acc0);
+    }
+  }
+  for (; j < j1; j += 32) {
+    T a = row[j];
+    if (UPD) {
+      a = fma(-vr, wv[j], fma(-wr, vp[j], a));
+      row[j] = a;
+    }
+    acc0 = fma(a, vc[j], acc0);
+  }
+  return acc0 + acc1;
+}
+
+// FP64 instructions are scarce on this part (about 2 per clock per SM), so
+// the per-step bookkeeping keeps them off paths that every thread runs: in
+// the FP32 form the norm and p.v accumulate in FP32, reductions finish in
+// warp 0, and in the FP64 form phase 1 runs on HH_P1_FP64 threads only.
+constexpr int HH_P1_FP64 = 128;
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *smem = reinterpret_cast<T *>(smem_raw);
+  __shared__ double sh[32];
+  __shared__ T wbuf[16];          // per-warp partials
+  __shared__ T s_seg[16];
+  __shared__ double s_sc[3];      // x[k], x[k+1], gamma of the step
+  __shared__ double s_rf[3];      // tau, beta, 1 / (alpha - beta) of the reflector
+  const int n = g.n, G = gridDim.x, b = blockIdx.x, R = g.R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int p1 = (sizeof(T) == 8) ? min(HH_P1_FP64, (int)blockDim.x) : (int)blockDim.x;  // phase-1 team
+  const int p1w = p1 >> 5;
+  T *wv = smem + 2 * n;
+  T *rows = smem + 3 * n;   // SMEM: [R][n], local row lr is global row lr * G + b
+  const int n_own = (b < n) ? min(R, (n - 1 - b) / G + 1) : 0;
+  if (SMEM) {
+    for (int lr = 0; lr < n_own; ++lr) {
+      const double *src = g.A0 + (int64_t)(lr * G + b) * n;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) rows[(int64_t)lr * n + j] = (T)src[j];
+    }
+  }
+  T *vprev = smem + n, *vcur = smem;
+  double tau_prev = 0.0;
+  for (int k = 0; k + 2 < n; ++k) {
+    // ---- phase 1: row k of A^(k) into vcur, then reflector k in place.
+    // Team thread t owns x[j] for j = k + t + m * p1 (no barrier between
+    // writing x and its norm); the owners of j = k, k+1 stash them.
+    T *x = vcur;
+    T s2 = 0;
+    if (k == 0) {
+      if (threadIdx.x < p1)
+        for (int j = threadIdx.x; j < n; j += p1) {
+          const T xj = (T)__ldcg(g.A0 + j);
+          x[j] = xj;
+          if (j >= 2) s2 = fma(xj, xj, s2);
+          if (j < 2) s_sc[j] = (double)xj;
+        }
+    } else {
+      const T *Pk = g.P + (size_t)((k - 1) & 1) * n;
+      const T *pb = g.pub + (size_t)(k & 1) * n;
+      // one round trip: warp 0 sums the partials while the team loads p, row k
+      if (warp == 0) {
+        double a = 0.0;
+        for (int q = lane; q < G; q += 32) a += __ldcg(g.part + (size_t)((k - 1) & 1) * G + q);
+        a = warp_sum(a);
+        if (lane == 0) s_sc[2] = 0.5 * tau_prev * a;
+      }
+      const T pk_raw = __ldcg(Pk + k);
+      if (threadIdx.x < p1)
+        for (int j = k + threadIdx.x; j < n; j += p1) {
+          wv[j] = __ldcg(Pk + j);
+          x[j] = __ldcg(pb + j);
+        }
+      __syncthreads();
+      const T gam = (T)s_sc[2];
+      const T vk = vprev[k], wk = pk_raw - gam * vk;
+      if (threadIdx.x < p1)
+        for (int j = k + threadIdx.x; j < n; j += p1) {
+          const T wj = wv[j] - gam * vprev[j];
+          wv[j] = wj;
+          const T xj = fma(-vk, wj, fma(-wk, vprev[j], x[j]));
+          x[j] = xj;
+          if (j >= k + 2) s2 = fma(xj, xj, s2);
+          if (j < k + 2) s_sc[j - k] = (double)xj;
+        }
+    }
+    if (warp < p1w) {
+      s2 = warp_sum(s2);
+      if (lane == 0) wbuf[warp] = s2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T r = (lane < p1w) ? wbuf[lane] : (T)0;
+      r = warp_sum(r);
+      if (lane == 0) {   // the reflector's scalars, once (FP64 sqrt and divisions are slow here)
+        const double sigma = (double)r, alpha = s_sc[1];
+        double t = 0.0, beta = alpha, sc = 0.0;
+        if (sigma != 0.0) {
+          const double nrm = sqrt(alpha * alpha + sigma);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          t = (beta - alpha) / beta;
+          sc = 1.0 / (alpha - beta);
+        }
+        s_rf[0] = t; s_rf[1] = beta; s_rf[2] = sc;
+      }
+    }
+    __syncthreads();
+    const double t = s_rf[0], beta = s_rf[1], sc = s_rf[2], dk = s_sc[0];
+    const T scT = (T)sc;
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const T v = (j == k + 1) ? (T)1 : x[j] * scT;
+      x[j] = v;
+      if (b == 0) g.V[(int64_t)k * n + j] = v;
+    }
+    if (b == 0 && threadIdx.x == 0) {
+      g.d[k] = dk;
+      g.e[k] = beta;
+      g.tau[k] = t;
+    }
+    __syncthreads();
+    // ---- phase 2: own rows r > k: update k-1 (k > 0) fused with p_k[r]
+    T pv = 0;
+    {
+      const int lr0 = (k + 1 > b) ? (k + 1 - b + G - 1) / G : 0;
+      const int nact = n_own - lr0;
+      if (nact > 0) {
+        const int wpr = max(1, nwarp / nact);     // warps per row when rows are few
+        const int L = n - k - 1;
+        const int seglen = (((L + wpr - 1) / wpr) + 31) & ~31;
+        T *Pk = g.P + (size_t)(k & 1) * n;
+        for (int task = warp; task < nact * wpr; task += nwarp) {
+          const int lr = lr0 + task / wpr, seg = task % wpr;
+          const int r = lr * G + b;
+          T *row = SMEM ? rows + (int64_t)lr * n : g.A + (int64_t)r * n;
+          const int j0 = k + 1 + seg * seglen, j1 = min(n, j0 + seglen);
+          T acc = 0;
+          if (j0 < j1) {
+            if (k == 0) acc = row_pass<T, false>(row, j0, j1, vprev, wv, x, (T)0, (T)0);
+            else acc = row_pass<T, true>(row, j0, j1, vprev, wv, x, vprev[r], wv[r]);
+          }
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+          if (wpr == 1) {
+            if (lane == 0) {
+              const T pr = (T)t * acc;
+              Pk[r] = pr;
+              pv = fma(pr, x[r], pv);
+            }
+          } else if (lane == 0) {
+            s_seg[task] = acc;
+          }
+        }
+        if (wpr > 1) {
+          __syncthreads();
+          if (threadIdx.x < nact) {
+            const int lr = lr0 + threadIdx.x, r = lr * G + b;
+            T a = 0;
+            for (int q = 0; q < wpr; ++q) a += s_seg[threadIdx.x * wpr + q];
+            const T pr = (T)t * a;
+            Pk[r] = pr;
+            pv = fma(pr, x[r], pv);
+          }
+        }
+      }
+    }
+    // pv is non-zero only in lane 0 of each warp, or in lanes of warp 0
+    if (warp == 0) pv = warp_sum(pv);
+    if (lane == 0) wbuf[warp] = pv;
+    __syncthreads();   // also completes every row update of this step
+    if (warp == 0) {
+      T r = (lane < nwarp) ? wbuf[lane] : (T)0;
+      r = warp_sum(r);
+      if (lane == 0) g.part[(size_t)(k & 1) * G + b] = (double)r;
+    }
+    // the owner of row k+1 publishes it (A^(k) values, columns k+1..n-1); at the
+    // last step the owner of row n-1 also hands over that row's last two entries
+    if ((k + 1) % G == b) {
+      const int lr = (k + 1) / G;
+      const T *rp = SMEM ? rows + (int64_t)lr * n : g.A + (int64_t)(k + 1) * n;
+      T *pubp = g.pub + (size_t)((k + 1) & 1) * n;
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) pubp[j] = rp[j];
+    }
+    if (k == n - 3 && (n - 1) % G == b && threadIdx.x == 0) {
+      const T *rp = SMEM ? rows + (int64_t)((n - 1) / G) * n : g.A + (int64_t)(n - 1) * n;
+      g.tail[0] = rp[n - 2];
+      g.tail[1] = rp[n - 1];
+    }
+    if (!grid_barrier(g.gb, (unsigned)k, g.flags)) return;
+    tau_prev = t;
+    T *tmp = vprev; vprev = vcur; vcur = tmp;
+  }
+  // ---- the last 2 x 2 block: apply update n-3 to rows n-2, n-1
+  if (b == 0 && n >= 3) {
+    const int kl = n - 3;
+    const double s = sum_partials(g.part + (size_t)(kl & 1) * G, sh);
+    if (threadIdx.x == 0) {
+      const T gam = (T)(0.5 * tau_prev * s);
+      const T *Pk = g.P + (size_t)(kl & 1) * n;
+      const T *pb = g.pub + (size_t)((kl + 1) & 1) * n;
+      const T v2 = vprev[n - 2], v1 = vprev[n - 1];
+      const T w2 = __ldcg(Pk + n - 2) - gam * v2, w1 = __ldcg(Pk + n - 1) - gam * v1;
+      const T a22 = __ldcg(pb + n - 2), a21 = __ldcg(pb + n - 1), a11 = (T)__ldcg(g.tail + 1);
+      g.d[n - 2] = fma(-v2, w2, fma(-w2, v2, a22));
+      g.e[n - 2] = fma(-v2, w1, fma(-w2, v1, a21));
+      g.d[n - 1] = fma(-v1, w1, fma(-w1, v1, a11));
+      g.e[n - 1] = 0.0;
+    }
+  }
+}
+
+// FP32 working copy of the input for the in-place FP32 reduction.
+__global__ void to_f32_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// 1/q from the hardware reciprocal estimate refined by three Newton steps
+// y <- y (2 - q y) (each step squares the relative error), about 1 ulp: the
+// Sturm count below is exact for a matrix perturbed by a few ulps anyway, and
+// this avoids the IEEE division sequence, which is costly on this part's
+// FP64 pipe.  |q| >= pivmin > 0 keeps q away from zero and subnormals.
+__device__ __forceinline__ double recip_nr(double q) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
+  y = y * fma(-q, y, 2.0);
+  y = y * fma(-q, y, 2.0);
+  y = y * fma(-q, y, 2.0);
+  return y;
+}
+
+// Number of eigenvalues of T below x (signs of the LDL^T pivots of T - x).
+__device__ int sturm_count(const double *d, const double *e2, int n, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++c;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] * recip_nr(q);
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+// The same count in FP32 (IEEE division: FP32 runs at full rate).
+__device__ int sturm_count32(const float *d, const float *e2, int n, float x, float pivmin) {
+  int c = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  if (q < 0.0f) ++c;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    if (q < 0.0f) ++c;
+  }
+  return c;
+}
+
+// scal[1..3] = lower / upper Gershgorin bound, pivmin; scal[4] = ||T|| bound;
+// scal[5] = max e^2; count[0] = #eig > thresh.
+__global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *d, const double *e,
+                                                            int n, double thresh, double *scal,
+                                                            double *e2, int *count) {
+  __shared__ double s_lo[RB], s_hi[RB], s_e[RB];
+  double lo = DBL_MAX, hi = -DBL_MAX, em = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < n - 1) {
+      e2[i] = e[i] * e[i];
+      em = fmax(em, e2[i]);
+    }
+  }
+  s_lo[threadIdx.x] = lo; s_hi[threadIdx.x] = hi; s_e[threadIdx.x] = em;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + s]);
+      s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + s]);
+      s_e[threadIdx.x] = fmax(s_e[threadIdx.x], s_e[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double pivmin = DBL_MIN * fmax(1.0, s_e[0]);
+    scal[1] = s_lo[0] - 2.0 * DBL_EPSILON * fabs(s_lo[0]) - 4.0 * pivmin - 1e-300;
+    scal[2] = s_hi[0] + 2.0 * DBL_EPSILON * fabs(s_hi[0]) + 4.0 * pivmin + 1e-300;
+    scal[3] = pivmin;
+    scal[4] = fmax(fabs(s_lo[0]), fabs(s_hi[0]));  // ||T|| bound
+    scal[5] = s_e[0];
+    int below = sturm_count(d, e2, n, thresh, pivmin);
+    count[0] = n - below;
+    // eigenvalues within 1e-12 * ||T|| of the threshold (tie diagnostics)
+    double tol = 1e-12 * scal[4];
+    count[1] = sturm_count(d, e2, n, thresh + tol, pivmin) - sturm_count(d, e2, n, thresh - tol, pivmin);
+  }
+}
+
+// lam[r] = (n-1-r)-th smallest eigenvalue (r-th largest), r < k, by
+// multisection with BIS_L lanes per eigenvalue: each lane counts the
+// eigenvalues below one of BIS_L interior points, so an interval shrinks
+// (BIS_L + 1)-fold per step.  Few lanes per eigenvalue keep the total number
+// of FP64 divisions (the cost on this part) near that of plain bisection while
+// giving enough threads to hide their latency.  d and e^2 live in shared memory.
+constexpr int BIS_L = 4;
+__global__ void bisect_kernel(const double *d, const double *e2g, const double *scal, int n,
+                              int k, int epw, double *lam) {
+  extern __shared__ double sm[];
+  double *sd = sm, *se2 = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = d[i];
+    se2[i] = (i < n - 1) ? e2g[i] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % BIS_L, grp = lane / BIS_L;
+  const unsigned gmask = ((1u << BIS_L) - 1u) << (grp * BIS_L);
+  const int r = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * epw + grp;
+  const bool live = grp < epw && r < k;
+  const int idx = n - 1 - (live ? r : 0);  // ascending index of the wanted eigenvalue
+  double lo = scal[1], hi = scal[2];
+  const double pivmin = scal[3];
+  bool done = !live;
+  for (int it = 0; it < 200; ++it) {
+    if (!done && hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
+    if (__all_sync(0xffffffffu, done)) break;
+    const double x = lo + (hi - lo) * (double)(sub + 1) / (double)(BIS_L + 1);
+    const bool above = !done && sturm_count(sd, se2, n, x, pivmin) > idx;  // eigenvalue idx < x
+    const unsigned b = (__ballot_sync(0xffffffffu, above) & gmask) >> (grp * BIS_L);
+    if (!done) {
+      const int j = b ? (__ffs(b) - 1) : BIS_L;
+      const double nlo = (j == 0) ? lo : lo + (hi - lo) * (double)j / (double)(BIS_L + 1);
+      const double nhi = (j == BIS_L) ? hi : lo + (hi - lo) * (double)(j + 1) / (double)(BIS_L + 1);
+      if (!(nlo > lo || nhi < hi)) done = true;  // no progress at this resolution
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  if (live && sub == 0) lam[r] = 0.5 * (lo + hi);
+}
+
+// FP32 form: one warp per eigenvalue, 32 interior points per step (the
+// interval shrinks 33-fold), so about five steps reach FP32 resolution.
+__global__ void bisect32_kernel(const double *d, const double *e2g, const double *scal, int n, int k,
+                                double *lam) {
+  extern __shared__ float smf[];
+  float *sd = smf, *se2 = smf + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = (float)d[i];
+    se2[i] = (i < n - 1) ? (float)e2g[i] : 0.0f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= k) return;
+  const int idx = n - 1 - r;
+  const float emax = (float)scal[5];
+  const float pivmin = FLT_MIN * fmaxf(1.0f, emax);
+  const float tn = (float)scal[4];
+  float lo = (float)scal[1] - 4.0f * FLT_EPSILON * tn - 4.0f * pivmin;
+  float hi = (float)scal[2] + 4.0f * FLT_EPSILON * tn + 4.0f * pivmin;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
+    const float x = lo + (hi - lo) * (float)(lane + 1) * (1.0f / 33.0f);
+    const bool above = x < hi && sturm_count32(sd, se2, n, x, pivmin) > idx;
+    const unsigned bm = __ballot_sync(0xffffffffu, above);
+    const int j = bm ? (__ffs(bm) - 1) : 32;   // first point above the eigenvalue
+    const float xj = __shfl_sync(0xffffffffu, x, j & 31), xj1 = __shfl_sync(0xffffffffu, x, (j + 31) & 31);
+    const float nlo = (j == 0) ? lo : xj1;
+    const float nhi = (j == 32) ? hi : xj;
+    if (!(nlo > lo || nhi < hi)) break;   // no progress at this resolution
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) lam[r] = 0.5 * ((double)lo + (double)hi);
+}
+
+// Inverse iteration for the eigenvectors of T, one thread per group of
+// consecutive eigenvalues closer than gtol (groups are orthogonalised
+// internally).  X[i*k + r] receives the vector of lam[r].
+template <typename T>
+__global__ void inverse_iteration_kernel(const double *dg, const double *eg, const double *lam,
+                                         const double *scal, int n, int k, T *X, T *lu, int *flags) {
+  extern __shared__ __align__(16) unsigned char sde_raw[];
+  T *d = reinterpret_cast<T *>(sde_raw), *e = d + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { d[i] = (T)dg[i]; e[i] = (T)eg[i]; }
+  __syncthreads();
+  const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r0 >= k) return;
+  const double tnorm = scal[4];
+  const double gtol = Lim<T>::group_tol * tnorm;
+  if (r0 > 0 && lam[r0 - 1] - lam[r0] <= gtol) return;  // not the first of its group
+  int r1 = r0 + 1;
+  while (r1 < k && lam[r1 - 1] - lam[r1] <= gtol) ++r1;
+  // scratch for this thread: dl, dd, du, du2, piv (strided by k for coalescing)
+  T *dl = lu, *dd = lu + (int64_t)n * k, *du = lu + 2 * (int64_t)n * k;
+  T *du2 = lu + 3 * (int64_t)n * k, *pv = lu + 4 * (int64_t)n * k;
+  const T tiny = Lim<T>::eps() * fmax((T)tnorm, Lim<T>::tiny());
+  double prev = 0.0;
+  for (int r = r0; r < r1; ++r) {
+    double lmd = lam[r];
+    if (r > r0) {
+      double pert = 10.0 * (double)Lim<T>::eps() * fmax(fabs(lmd), tnorm * 1e-3);
+      if (prev - lmd < pert) lmd = prev - pert;
+    }
+    prev = lmd;
+    const T lm = (T)lmd;
+#define S(a, i) a[(int64_t)(i) * k + r]
+    // LU of T - lm with row interchanges
+    for (int i = 0; i < n; ++i) {
+      S(dd, i) = d[i] - lm;
+      if (i < n - 1) { S(dl, i) = e[i]; S(du, i) = e[i]; }
+      S(du2, i) = 0;
+    }
+    for (int i = 0; i < n - 1; ++i) {
+      T di = S(dd, i), li = S(dl, i);
+      if (fabs(di) >= fabs(li)) {
+        S(pv, i) = 0;
+        if (di == (T)0) { di = tiny; S(dd, i) = di; }
+        T f = li / di;
+        S(dl, i) = f;
+        S(dd, i + 1) -= f * S(du, i);
+      } else {
+        S(pv, i) = 1;
+        T f = di / li;
+        S(dd, i) = li;
+        S(dl, i) = f;
+        T tmp = S(du, i);
+        S(du, i) = S(dd, i + 1);
+        S(dd, i + 1) = tmp - f * S(dd, i + 1);
+        if (i < n - 2) {
+          S(du2, i) = S(du, i + 1);
+          S(du, i + 1) = -f * S(du, i + 1);
+        }
+      }
+    }
+    if (S(dd, n - 1) == (T)0) S(dd, n - 1) = tiny;
+    for (int i = 0; i < n; ++i)
+      if (fabs(S(dd, i)) < tiny) S(dd, i) = copysign(tiny, S(dd, i));
+    // start vector: deterministic, no special structure
+    for (int i = 0; i < n; ++i) S(X, i) = (T)(1.0 + 0.5 * sin(0.7548776662 * (i + 1) + 0.5698402910 * (r + 1)));
+    for (int iter = 0; iter < 2; ++iter) {
+      // forward: apply L^-1 with the interchanges
+      for (int i = 0; i < n - 1; ++i) {
+        if (S(pv, i) == (T)0) {
+          S(X, i + 1) -= S(dl, i) * S(X, i);
+        } else {
+          T t = S(X, i);
+          S(X, i) = S(X, i + 1);
+          S(X, i + 1) = t - S(dl, i) * S(X, i);
+        }
+      }
+      // backward: U^-1
+      for (int i = n - 1; i >= 0; --i) {
+        T s = S(X, i);
+        if (i + 1 < n) s -= S(du, i) * S(X, i + 1);
+        if (i + 2 < n) s -= S(du2, i) * S(X, i + 2);
+        S(X, i) = s / S(dd, i);
+      }
+      // orthogonalise against the earlier vectors of this group
+      for (int q = r0; q < r; ++q) {
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot += (double)X[(int64_t)i * k + q] * (double)S(X, i);
+        const T dt = (T)dot;
+        for (int i = 0; i < n; ++i) S(X, i) -= dt * X[(int64_t)i * k + q];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) nrm += (double)S(X, i) * (double)S(X, i);
+      nrm = sqrt(nrm);
+      if (!(nrm > 0.0) || !isfinite(nrm)) { atomicExch(&flags[FLAG_EIG], 1); break; }
+      const T inv = (T)(1.0 / nrm);
+      for (int i = 0; i < n; ++i) S(X, i) *= inv;
+    }
+#undef S
+  }
+}
+
+// F = (3 I - G) / 2 for a k x k Gram matrix G (in place).
+template <typename T>
+__global__ void lowdin_factor_kernel(T *G, int k) {
+  int64_t kk = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kk;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), j = (int)(e - (int64_t)i * k);
+    G[e] = (T)(((i == j) ? 1.5 : 0.0) - 0.5 * (double)G[e]);
+  }
+}
+
+// ---- compact-WY back-transformation: U = H_0 H_1 ... H_{n-3} X ----
+// For a block of nb consecutive reflectors j0..j0+nb-1 (rows of V, zero
+// outside j+1..n-1), H_j0 ... H_{j0+nb-1} = 1 - V_b T V_b^T with T upper
+// triangular (T_ii = tau_i, T[0:l, l] = -tau_l T[0:l, 0:l] G[0:l, l],
+// G = V_b^T V_b).  Blocks are applied from the last to the first:
+// Y <- Y - V_b (T (V_b^T Y)).
+constexpr int WY_NB = 64;
+constexpr int64_t WY_KSPLIT = 64;
+
+// dst[i] = sum_s src[s * stride + i]
+template <typename T>
+__global__ void sum_partials_kernel(const T *__restrict__ src, int nsplit, int64_t stride,
+                                    int64_t n, T *__restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T a = 0;
+    for (int q = 0; q < nsplit; ++q) a += src[q * stride + i];
+    dst[i] = a;
+  }
+}
+
+// T (nb x nb, row-major, upper) from G = V_b^T V_b and tau[j0..j0+nb).
+template <typename T>
+__global__ void wy_build_t_kernel(const T *__restrict__ G, const double *__restrict__ tau,
+                                  int j0, int nb, T *__restrict__ Tm) {
+  __shared__ T sT[WY_NB][WY_NB + 1];
+  const int i = threadIdx.x;
+  for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) sT[q / WY_NB][q % WY_NB] = 0;
+  __syncthreads();
+  if (i < nb) sT[i][i] = (T)tau[j0 + i];
+  __syncthreads();
+  for (int l = 1; l < nb; ++l) {
+    T v = 0;
+    if (i < l) {
+      for (int m = i; m < l; ++m) v += sT[i][m] * G[m * nb + l];
+      v *= -(T)tau[j0 + l];
+    }
+    __syncthreads();
+    if (i < l) sT[i][l] = v;
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) Tm[q] = sT[q / nb][q % nb];
+}
+
+// Ut[c][r] = X[r][c]
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ X, int n, int k, double *__restrict__ Ut) {
+  __shared__ T tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    int r = r0 + q, c = c0 + threadIdx.x;
+    if (r < n && c < k) tile[q][threadIdx.x] = X[(int64_t)r * k + c];
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    int c = c0 + q, r = r0 + threadIdx.x;
+    if (r < n && c < k) Ut[(int64_t)c * n + r] = tile[threadIdx.x][q];
+  }
+}
+
+// Raise a kernel's dynamic shared-memory limit once, to the most any call
+// may use; setting it per call races between host threads (one thread could
+// lower it between another thread's set and launch).
+cudaError_t allow_max_dynamic_smem(const void *kernel, std::once_flag &flag) {
+  cudaError_t result = cudaSuccess;
+  std::call_once(flag, [&] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if ((result = cudaGetDevice(&dev)) != cudaSuccess) return;
+    if ((result = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return;
+    if ((result = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return;
+    result = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes);
+  });
+  return result;
+}
+std::once_flag g_smem_hh[4], g_smem_bisect, g_smem_bisect32, g_smem_invit[2];
+
+// Try the fused reduction in arithmetic T; false when it cannot be launched.
+template <typename T>
+bool launch_fused(EigWork &w, int n, cudaStream_t s, int *launches, cudaError_t *err) {
+  int dev = 0, nsm = 0, coop = 0, optin = 0;
+  *err = cudaSuccess;
+  bool ok = n > 2 && w.grid_ws != nullptr && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess;
+  cudaGetLastError();
+  if (!ok) return false;
+  const int G = std::min(nsm, std::max(1, (n + HH_MIN_ROWS - 1) / HH_MIN_ROWS));
+  const int R = (n + G - 1) / G;
+  const size_t reserve = 1024;   // static shared memory of the kernel
+  const size_t s_rows = (size_t)(3 + R) * n * sizeof(T), s_vec = (size_t)3 * n * sizeof(T);
+  const bool in_smem = s_rows + reserve <= (size_t)optin;
+  const size_t smem = in_smem ? s_rows : s_vec;
+  if (smem + reserve > (size_t)optin) return false;
+  const int fi = (sizeof(T) == 4 ? 2 : 0) + (in_smem ? 1 : 0);
+  const void *kern = in_smem ? (const void *)hh_fused_kernel<T, true> : (const void *)hh_fused_kernel<T, false>;
+  int per_sm = 0;
+  ok = allow_max_dynamic_smem(kern, g_smem_hh[fi]) == cudaSuccess &&
+       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem) == cudaSuccess && per_sm >= 1;
+  cudaGetLastError();
+  if (!ok) return false;
+  HhFusedArgs<T> g;
+  g.A0 = w.A;
+  if (sizeof(T) == sizeof(double)) {
+    g.A = reinterpret_cast<T *>(w.A);       // reduced in place
+  } else {
+    g.A = reinterpret_cast<T *>(w.X);       // FP32 working copy (X is free until step 4)
+    if (!in_smem) {
+      to_f32_kernel<<<152 * 4, 256, 0, s>>>(w.A, reinterpret_cast<float *>(w.X), (int64_t)n * n);
+      *launches += 1;
+    }
+  }
+  g.V = reinterpret_cast<T *>(w.V);
+  g.d = w.d; g.e = w.e; g.tau = w.tau;
+  g.P = reinterpret_cast<T *>(w.grid_ws);
+  g.pub = g.P + 2 * (size_t)n;
+  double *after = w.grid_ws + (4 * (size_t)n * sizeof(T) + sizeof(double) - 1) / sizeof(double);
+  g.tail = after;
+  g.part = after + 2;
+  g.gb = reinterpret_cast<GridBar *>(g.part + 2 * (size_t)nsm);
+  g.flags = w.flags;
+  g.n = n; g.R = R;
+  *err = cudaMemsetAsync(g.gb, 0, sizeof(GridBar), s);
+  if (*err != cudaSuccess) return true;
+  void *args[] = {&g};
+  *err = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(512), args, smem, s);
+  if (*err == cudaSuccess) *launches += 1;
+  return true;
+}
+
+// Steps 3-6 in arithmetic T.
+template <typename T>
+cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, cudaStream_t s, int *launches) {
+  const size_t smem = 2 * (size_t)n * sizeof(T);
+  const bool f32 = sizeof(T) == 4;
+  {
+    cudaError_t e = allow_max_dynamic_smem(f32 ? (const void *)bisect32_kernel : (const void *)bisect_kernel,
+                                           f32 ? g_smem_bisect32 : g_smem_bisect);
+    if (e != cudaSuccess) return e;
+    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T>, g_smem_invit[f32 ? 1 : 0]);
+    if (e != cudaSuccess) return e;
+  }
+  if (f32) {
+    bisect32_kernel<<<(k + 3) / 4, 128, smem, s>>>(w.d, w.p, w.scal, n, k, w.lam);
+  } else {
+    // one warp per block and at most 32 / BIS_L eigenvalues per warp, spread
+    // so that every SM gets work: the FP64 divisions of the Sturm counts are
+    // the cost on this part
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 148;
+    cudaGetLastError();
+    const int epw = std::max(1, std::min(32 / BIS_L, (k + nsm - 1) / nsm));
+    bisect_kernel<<<(k + epw - 1) / epw, 32, smem, s>>>(w.d, w.p, w.scal, n, k, epw, w.lam);
+  }
+  T *X = reinterpret_cast<T *>(w.X), *lu = reinterpret_cast<T *>(w.lu), *V = reinterpret_cast<T *>(w.V);
+  inverse_iteration_kernel<T><<<(k + 31) / 32, 32, smem, s>>>(w.d, w.e, w.lam, w.scal, n, k, X, lu, flags);
+  *launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // re-orthonormalise twice: G = X^T X, F = (3 - G)/2, X <- X F
+  T *G = lu;                       // k*k scratch (inverse-iteration scratch is free now)
+  T *Xn = lu + (int64_t)k * k;     // n*k scratch
+  for (int pass = 0; pass < 2; ++pass) {
+    GemmArgs<T> g;
+    g.M = k; g.N = k; g.K = n;
+    g.A = X; g.lda = k;   // A[kidx][m] = X[i][m]  (M-major)
+    g.B = X; g.ldb = k;   // B[kidx][n] = X[i][n]  (N-major)
+    g.C = G; g.ldc = k;
+    g.syrk = 1;
+    e = launch_gemm<T>(g, 1, false, false, s);
+    if (e != cudaSuccess) return e;
+    lowdin_factor_kernel<T><<<152, 256, 0, s>>>(G, k);
+    GemmArgs<T> h;
+    h.M = n; h.N = k; h.K = k;
+    h.A = X; h.lda = k;   // K-major rows of X
+    h.B = G; h.ldb = k;   // N-major
+    h.C = Xn; h.ldc = k;
+    e = launch_gemm<T>(h, 1, true, false, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(X, Xn, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    *launches += 3;
+  }
+  // compact-WY back-transformation, blocks of WY_NB reflectors from the last
+  const int nref = n - 2;  // reflectors 0 .. n-3
+  T *Gp = reinterpret_cast<T *>(w.wy);                         // [nsplit][nb][nb]
+  const int nsplit_max = (int)((n + WY_KSPLIT - 1) / WY_KSPLIT);
+  T *W1p = Gp + (int64_t)nsplit_max * WY_NB * WY_NB;           // [nsplit][nb][k]
+  T *Gs = W1p + (int64_t)nsplit_max * WY_NB * k;               // [nb][nb]
+  T *W1 = Gs + WY_NB * WY_NB;                                  // [nb][k]
+  T *Tm = W1 + (int64_t)WY_NB * k;                             // [nb][nb]
+  T *W2 = Tm + WY_NB * WY_NB;                                  // [nb][k]
+  for (int j0 = ((nref - 1) / WY_NB) * WY_NB; nref > 0 && j0 >= 0; j0 -= WY_NB) {
+    const int nb = std::min(WY_NB, nref - j0);
+    const int r0 = j0 + 1;              // first row where this block's V is non-zero
+    const int64_t len = n - r0;
+    const int nsplit = (int)((len + WY_KSPLIT - 1) / WY_KSPLIT);
+    GemmArgs<T> g;                      // G partials = V_b V_b^T over row chunks
+    g.M = nb; g.N = nb; g.K = len; g.ksplit = WY_KSPLIT;
+    g.A = V + (int64_t)j0 * n + r0; g.lda = n;
+    g.B = V + (int64_t)j0 * n + r0; g.ldb = n;
+    g.C = Gp; g.ldc = nb; g.strideC = (int64_t)nb * nb;
+    e = launch_gemm<T>(g, nsplit, true, true, s);
+    if (e != cudaSuccess) return e;
+    GemmArgs<T> h;                      // W1 partials = V_b^T Y over row chunks
+    h.M = nb; h.N = k; h.K = len; h.ksplit = WY_KSPLIT;
+    h.A = V + (int64_t)j0 * n + r0; h.lda = n;
+    h.B = X + (int64_t)r0 * k; h.ldb = k;
+    h.C = W1p; h.ldc = k; h.strideC = (int64_t)nb * k;
+    e = launch_gemm<T>(h, nsplit, true, false, s);
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<T><<<64, 256, 0, s>>>(Gp, nsplit, (int64_t)nb * nb, (int64_t)nb * nb, Gs);
+    sum_partials_kernel<T><<<152, 256, 0, s>>>(W1p, nsplit, (int64_t)nb * k, (int64_t)nb * k, W1);
+    wy_build_t_kernel<T><<<1, WY_NB, 0, s>>>(Gs, w.tau, j0, nb, Tm);
+    GemmArgs<T> t2;                     // W2 = T W1
+    t2.M = nb; t2.N = k; t2.K = nb;
+    t2.A = Tm; t2.lda = nb; t2.B = W1; t2.ldb = k; t2.C = W2; t2.ldc = k;
+    e = launch_gemm<T>(t2, 1, true, false, s);
+    if (e != cudaSuccess) return e;
+    GemmArgs<T> u;                      // Y[r0:, :] -= V_b^T W2
+    u.M = (int)len; u.N = k; u.K = nb;
+    u.A = V + (int64_t)j0 * n + r0; u.lda = n;   // A[kidx=i][m=r] = V[j0+i][r0+r]
+    u.B = W2; u.ldb = k;
+    u.C = X + (int64_t)r0 * k; u.ldc = k;
+    u.alpha = -1.0; u.beta = 1.0;
+    e = launch_gemm<T>(u, 1, false, false, s);
+    if (e != cudaSuccess) return e;
+    *launches += 7;
+  }
+  dim3 tb(32, 8), tg((k + 31) / 32, (n + 31) / 32);
+  transpose_kernel<T><<<tg, tb, 0, s>>>(X, n, k, Ut);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches, bool *f32) {
+  cudaError_t e = cudaSuccess;
+  bool fused = false;
+  if (*f32) fused = launch_fused<float>(w, n, s, launches, &e);
+  if (!fused) {
+    *f32 = false;
+    fused = launch_fused<double>(w, n, s, launches, &e);
+  }
+  if (e != cudaSuccess) return e;
+  if (!fused) {
+    for (int k = 0; k + 2 < n; ++k) {
+      const int L = n - k - 1;
+      hh_reflector_kernel<<<1, RB, 0, s>>>(w.A, w.V, w.d, w.e, w.tau, w.scal, n, k);
+      int symv_blocks = (L * 32 + 255) / 256;
+      hh_symv_kernel<<<symv_blocks, 256, 0, s>>>(w.A, w.V, w.p, w.scal, n, k);
+      hh_w_kernel<<<1, RB, 0, s>>>(w.V, w.p, w.w, w.scal, n, k);
+      int64_t LL = (int64_t)L * L;
+      int ub = (int)((LL + 255) / 256);
+      if (ub > 152 * 8) ub = 152 * 8;
+      hh_update_kernel<<<ub, 256, 0, s>>>(w.A, w.V, w.w, n, k);
+      *launches += 4;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    hh_finalize_kernel<<<1, 32, 0, s>>>(w.A, w.d, w.e, n);
+    *launches += 1;
+  }
+  // e2 reuses w.p (length n)
+  tridiag_bounds_kernel<<<1, RB, 0, s>>>(w.d, w.e, n, thresh, w.scal, w.p, w.count);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags, cudaStream_t s,
+                               int *launches, bool f32) {
+  if (k <= 0) return cudaSuccess;
+  return f32 ? eig_vectors_impl<float>(w, n, k, Ut, flags, s, launches)
+             : eig_vectors_impl<double>(w, n, k, Ut, flags, s, launches);
+}
+
+}  // namespace ltgw

@@ -10,7 +10,9 @@
 //
 // GB300's FP64 rate is about 2 DFMA per clock per SM, so a 64x64 tile with a
 // 4x4 register micro-tile per thread keeps the FP64 pipe saturated with
-// ~0.5 B/clk/SM of global traffic; the tiles stay simple on purpose.
+// ~0.5 B/clk/SM of global traffic; the tiles stay simple on purpose.  The
+// plain GEMM / SYRK is also instantiated in FP32 for the mixed-precision
+// eigensolver's small contractions.
 #include <math.h>
 
 #include "common.cuh"
@@ -23,10 +25,11 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 constexpr int PAD = 1;
 
+template <typename T>
 struct TileSmem {
-  double As[BK][BM + PAD];
-  double Bs[BK][BN + PAD];
-  double sc[BK];
+  T As[BK][BM + PAD];
+  T Bs[BK][BN + PAD];
+  T sc[BK];
 };
 
 // Scale applied to pair (column) k of the A operand for batch entry b.
@@ -39,9 +42,9 @@ __device__ __forceinline__ double pair_scale(int mode, double d, double p0, doub
 // Accumulate one BMxBN output tile over the full K range into acc.
 // A is MxK (K-major: A[m*lda+k]; else A[k*lda+m]); B is KxN (K-major:
 // B[n*ldb+k]; else B[k*ldb+n]).  Scale s(k) multiplies the A operand.
-template <bool A_KMAJ, bool B_KMAJ>
-__device__ __forceinline__ void tile_accumulate(double acc[4][4], TileSmem &sm, const double *A,
-                                                int64_t lda, const double *B, int64_t ldb,
+template <typename T, bool A_KMAJ, bool B_KMAJ>
+__device__ __forceinline__ void tile_accumulate(T acc[4][4], TileSmem<T> &sm, const T *A,
+                                                int64_t lda, const T *B, int64_t ldb,
                                                 int m0, int n0, int M, int N, int64_t K,
                                                 int scale_mode, const double *delta, double p0,
                                                 double p1) {
@@ -50,7 +53,7 @@ __device__ __forceinline__ void tile_accumulate(double acc[4][4], TileSmem &sm, 
   for (int64_t k0 = 0; k0 < K; k0 += BK) {
     if (scale_mode != SCALE_NONE && tid < BK) {
       int64_t k = k0 + tid;
-      sm.sc[tid] = (k < K) ? pair_scale(scale_mode, delta[k], p0, p1) : 0.0;
+      sm.sc[tid] = (k < K) ? (T)pair_scale(scale_mode, delta[k], p0, p1) : (T)0;
     }
     if (scale_mode != SCALE_NONE) __syncthreads();
 #pragma unroll
@@ -60,7 +63,7 @@ __device__ __forceinline__ void tile_accumulate(double acc[4][4], TileSmem &sm, 
       if (A_KMAJ) { m = idx / BK; k = idx % BK; } else { k = idx / BM; m = idx % BM; }
       int gm = m0 + m;
       int64_t gk = k0 + k;
-      double v = 0.0;
+      T v = 0;
       if (gm < M && gk < K) v = A_KMAJ ? A[(int64_t)gm * lda + gk] : A[gk * lda + gm];
       if (scale_mode != SCALE_NONE) v *= sm.sc[k];
       sm.As[k][m] = v;
@@ -72,14 +75,14 @@ __device__ __forceinline__ void tile_accumulate(double acc[4][4], TileSmem &sm, 
       if (B_KMAJ) { n = idx / BK; k = idx % BK; } else { k = idx / BN; n = idx % BN; }
       int gn = n0 + n;
       int64_t gk = k0 + k;
-      double v = 0.0;
+      T v = 0;
       if (gn < N && gk < K) v = B_KMAJ ? B[(int64_t)gn * ldb + gk] : B[gk * ldb + gn];
       sm.Bs[k][n] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = sm.As[k][ty + 16 * i];
 #pragma unroll
@@ -93,9 +96,9 @@ __device__ __forceinline__ void tile_accumulate(double acc[4][4], TileSmem &sm, 
   }
 }
 
-template <bool A_KMAJ, bool B_KMAJ>
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
-  __shared__ TileSmem sm;
+template <typename T, bool A_KMAJ, bool B_KMAJ>
+__global__ void __launch_bounds__(NT) gemm_tile_kernel(GemmArgs<T> g) {
+  __shared__ TileSmem<T> sm;
   const int b = blockIdx.z;
   int m0, n0;
   if (g.syrk) {
@@ -111,8 +114,8 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
     m0 = blockIdx.y * BM;
     n0 = blockIdx.x * BN;
   }
-  const double *A, *B;
-  double *C = g.C + (int64_t)b * g.strideC;
+  const T *A, *B;
+  T *C = g.C + (int64_t)b * g.strideC;
   int64_t K = g.K;
   const double *delta = g.delta;
   double p0 = 0.0, p1 = 0.0;
@@ -128,9 +131,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
     p0 = g.batch_p0 ? g.batch_p0[b] : 0.0;
     p1 = g.batch_p1 ? g.batch_p1[b] : 0.0;
   }
-  double acc[4][4] = {};
-  tile_accumulate<A_KMAJ, B_KMAJ>(acc, sm, A, g.lda, B, g.ldb, m0, n0, g.M, g.N, K,
-                                  g.scale_mode, delta, p0, p1);
+  T acc[4][4] = {};
+  tile_accumulate<T, A_KMAJ, B_KMAJ>(acc, sm, A, g.lda, B, g.ldb, m0, n0, g.M, g.N, K,
+                                     g.scale_mode, delta, p0, p1);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -140,8 +143,8 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
     for (int j = 0; j < 4; ++j) {
       int gn = n0 + tx + 16 * j;
       if (gn >= g.N) continue;
-      double v = g.alpha * acc[i][j];
-      if (g.beta != 0.0) v += g.beta * C[(int64_t)gm * g.ldc + gn];
+      T v = (T)g.alpha * acc[i][j];
+      if (g.beta != 0.0) v += (T)g.beta * C[(int64_t)gm * g.ldc + gn];
       if (g.syrk) {
         if (gm >= gn) {
           C[(int64_t)gm * g.ldc + gn] = v;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64Args g) {
 // W[b][t][m] = sum_P Bt[t][P][m] * sum_Q C[b][P][Q] Bt[t][Q][m]
 // grid: x = column tile of m, y = target t, z = frequency b.
 __global__ void __launch_bounds__(NT) gemm_coldot_kernel(ColDotArgs g) {
-  __shared__ TileSmem sm;
+  __shared__ TileSmem<double> sm;
   __shared__ double red[16][BN];
   const int b = blockIdx.z, t = blockIdx.y;
   const int n0 = blockIdx.x * BN;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(NT) gemm_coldot_kernel(ColDotArgs g) {
   double part[4] = {0, 0, 0, 0};
   for (int m0 = 0; m0 < g.N; m0 += BM) {
     double acc[4][4] = {};
-    tile_accumulate<true, false>(acc, sm, Cb, g.ldc, Bt, g.ldb, m0, n0, g.N, g.ncols, g.N,
+    tile_accumulate<double, true, false>(acc, sm, Cb, g.ldc, Bt, g.ldb, m0, n0, g.N, g.ncols, g.N,
                                  SCALE_NONE, nullptr, 0.0, 0.0);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -194,9 +197,10 @@ __global__ void __launch_bounds__(NT) gemm_coldot_kernel(ColDotArgs g) {
 
 }  // namespace
 
-cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b_kmaj,
-                            cudaStream_t s) {
+template <typename T>
+cudaError_t launch_gemm(const GemmArgs<T> &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return cudaSuccess;
+  if (sizeof(T) != sizeof(double) && g.scale_mode != SCALE_NONE) return cudaErrorInvalidValue;
   dim3 grid;
   if (g.syrk) {
     int tm = ceil_div(g.M, BM);
@@ -204,12 +208,14 @@ cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b
   } else {
     grid = dim3((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM), (unsigned)batch);
   }
-  if (a_kmaj && b_kmaj) gemm_f64_kernel<true, true><<<grid, NT, 0, s>>>(g);
-  else if (a_kmaj && !b_kmaj) gemm_f64_kernel<true, false><<<grid, NT, 0, s>>>(g);
-  else if (!a_kmaj && b_kmaj) gemm_f64_kernel<false, true><<<grid, NT, 0, s>>>(g);
-  else gemm_f64_kernel<false, false><<<grid, NT, 0, s>>>(g);
+  if (a_kmaj && b_kmaj) gemm_tile_kernel<T, true, true><<<grid, NT, 0, s>>>(g);
+  else if (a_kmaj && !b_kmaj) gemm_tile_kernel<T, true, false><<<grid, NT, 0, s>>>(g);
+  else if (!a_kmaj && b_kmaj) gemm_tile_kernel<T, false, true><<<grid, NT, 0, s>>>(g);
+  else gemm_tile_kernel<T, false, false><<<grid, NT, 0, s>>>(g);
   return cudaGetLastError();
 }
+template cudaError_t launch_gemm<double>(const GemmArgs<double> &, int, bool, bool, cudaStream_t);
+template cudaError_t launch_gemm<float>(const GemmArgs<float> &, int, bool, bool, cudaStream_t);
 
 cudaError_t launch_gemm_coldot(const ColDotArgs &g, int n_batch, cudaStream_t s) {
   if (g.N <= 0 || g.ncols <= 0 || g.n_tgt <= 0 || n_batch <= 0) return cudaSuccess;

@@ -12,14 +12,15 @@ enum ScaleMode { SCALE_NONE = 0, SCALE_DIRECT = 1, SCALE_LAPLACE = 2 };
 
 // C_b = alpha * A_b diag(s_b) B_b for b in [0, batch).  With syrk = 1 only the
 // lower-triangle tiles are computed and each value is mirrored (A == B^T).
-struct GemmF64Args {
+template <typename T>
+struct GemmArgs {
   int M = 0, N = 0;
   int64_t K = 0;
-  const double *A = nullptr; int64_t lda = 0, strideA = 0;
-  const double *B = nullptr; int64_t ldb = 0, strideB = 0;
-  double *C = nullptr; int64_t ldc = 0, strideC = 0;
+  const T *A = nullptr; int64_t lda = 0, strideA = 0;
+  const T *B = nullptr; int64_t ldb = 0, strideB = 0;
+  T *C = nullptr; int64_t ldc = 0, strideC = 0;
   double alpha = 1.0;
-  int scale_mode = SCALE_NONE;
+  int scale_mode = SCALE_NONE;       // FP64 only
   const double *delta = nullptr;     // [K] pair gaps
   const double *batch_p0 = nullptr;  // [batch] omega (direct) or x_m (Laplace), device
   const double *batch_p1 = nullptr;  // [batch] w_m (Laplace), device
@@ -27,8 +28,14 @@ struct GemmF64Args {
   double beta = 0.0;      // C = alpha * acc + beta * C
   int64_t ksplit = 0;     // > 0: batch index b covers k in [b*ksplit, (b+1)*ksplit), C_b at b*strideC
 };
-cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b_kmaj,
-                            cudaStream_t s);
+using GemmF64Args = GemmArgs<double>;
+using GemmF32Args = GemmArgs<float>;
+// Tiled GEMM / SYRK on the CUDA cores, FP64 or FP32 (no pair scale in FP32).
+template <typename T>
+cudaError_t launch_gemm(const GemmArgs<T> &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s);
+inline cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s) {
+  return launch_gemm<double>(g, batch, a_kmaj, b_kmaj, s);
+}
 
 // W[b][t][m] = sum_P Bt[t][P][m] (C_b Bt[t])[P][m], C_b is N x N (K-major rows).
 struct ColDotArgs {
@@ -62,7 +69,7 @@ size_t screen_blocked_scratch(int N, int n_omega);
 cudaError_t launch_screen_blocked(const double *Pi, int N, int n_omega, double *work, double *C, int *flags,
                                   cudaStream_t s, int *launches);
 
-// ---- eigensolver (eig_f64.cu) ----
+// ---- eigensolver (eig.cu) ----
 struct EigWork {
   double *A = nullptr;      // [n][n] symmetric in, destroyed
   double *V = nullptr;      // [n][n] Householder vectors (row k = v_k)
@@ -73,16 +80,20 @@ struct EigWork {
   double *X = nullptr;                                // [n][kcap] tridiagonal eigenvectors
   double *lu = nullptr;                               // [5 n kcap] inverse-iteration scratch
   int *count = nullptr;                               // [2]
-  double *wy = nullptr;                               // [WY scratch] see eig_f64.cu
-  double *grid_ws = nullptr;                          // [n + 2 * n_sm + 2] persistent-reduction scratch
+  double *wy = nullptr;                               // [WY scratch] see eig.cu
+  double *grid_ws = nullptr;                          // [4 n + 2 n_sm + 8] fused-reduction scratch
   int *flags = nullptr;                               // device error flags
 };
 // Tridiagonalise A, count eigenvalues > thresh (returned through count[0]).
-// V must be zeroed by the caller before the call.
-cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches);
-// Eigenvalues (descending) and eigenvectors for the k largest, Ut = rows [k][n].
+// V must be zeroed by the caller before the call.  *f32 asks for the FP32
+// form of the reduction (mixed precision); it is cleared when that form
+// cannot run and the FP64 form was used instead.  In the FP32 form V, X, lu
+// and wy hold floats (in the same buffers).
+cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches, bool *f32);
+// Eigenvalues (descending) and eigenvectors for the k largest, Ut = rows [k][n];
+// f32 as returned by launch_eig_tridiag.
 cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
-                               cudaStream_t s, int *launches);
+                               cudaStream_t s, int *launches, bool f32);
 
 // ---- split-BF16 tensor-core contraction (tc_gemm.cu) ----
 // D_t = A diag(s_t) B^T for t < n_t; A [*][Kp], B [*][Kp], scale [n_t][Kp] FP32,

@@ -80,6 +80,7 @@ SIGNATURES = {
     "ltgw_gl_grid": (_I, [_I, _D, _P, _P]),
     "ltgw_laplace_grid": (_I, [_I, _D, _D, _P, _P, _P]),
     "ltgw_naf_basis": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
+    "ltgw_naf_basis_mixed": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_polarizability_mixed": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -234,10 +235,11 @@ class Context:
             raise errors[0]
         return self._check(st, allow=(LTGW_ERR_NO_CONVERGE,) if allow_no_converge else ())
 
-    def naf_basis(self, B, n_pairs: int, ld: int, thresh: float, Ut, lam, stream=None) -> int:
+    def naf_basis(self, B, n_pairs: int, ld: int, thresh: float, Ut, lam, stream=None, mixed: bool = False) -> int:
         k = ctypes.c_int()
-        st = self._lib.ltgw_naf_basis(self.handle, int(B.shape[0]), n_pairs, _ptr(B), ld, thresh, _ptr(Ut),
-                                      _ptr(lam), ctypes.byref(k), _stream_ptr(stream))
+        fn = self._lib.ltgw_naf_basis_mixed if mixed else self._lib.ltgw_naf_basis
+        st = fn(self.handle, int(B.shape[0]), n_pairs, _ptr(B), ld, thresh, _ptr(Ut), _ptr(lam), ctypes.byref(k),
+                _stream_ptr(stream))
         self._check(st)
         return k.value
 
