@@ -859,7 +859,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
 
   // ---- screening
   int nl = 0;
-  cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl);
+  cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl, mixed);
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
   ctx->mark(EV_SCREEN, s);

@@ -530,19 +530,30 @@ __device__ int sturm_count32(const float *d, const float *e2, int n, float x, fl
 }
 
 // scal[1..3] = lower / upper Gershgorin bound, pivmin; scal[4] = ||T|| bound;
-// scal[5] = max e^2; count[0] = #eig > thresh.
-__global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *d, const double *e,
+// scal[5] = max e^2; count[0] = #eig > thresh, count[1] = #eig within
+// 1e-12 ||T|| of it (1e-6 ||T|| in the FP32 form).
+__global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *dg, const double *e,
                                                             int n, double thresh, double *scal,
-                                                            double *e2, int *count) {
+                                                            double *e2g, int *count, bool f32, bool staged) {
   __shared__ double s_lo[RB], s_hi[RB], s_e[RB];
+  // the Sturm counts below walk d and e^2 sequentially: staged in shared
+  // memory when they fit, so that each step is not an L2 round trip
+  extern __shared__ double s_de[];
+  double *sd = staged ? s_de : nullptr, *se2 = staged ? s_de + n : e2g;
+  const double *d = staged ? sd : dg;
+  double *e2 = se2;
+  if (staged)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sd[i] = dg[i];
   double lo = DBL_MAX, hi = -DBL_MAX, em = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
+    lo = fmin(lo, dg[i] - r);
+    hi = fmax(hi, dg[i] + r);
     if (i < n - 1) {
-      e2[i] = e[i] * e[i];
-      em = fmax(em, e2[i]);
+      const double ee = e[i] * e[i];
+      e2[i] = ee;
+      if (staged) e2g[i] = ee;
+      em = fmax(em, ee);
     }
   }
   s_lo[threadIdx.x] = lo; s_hi[threadIdx.x] = hi; s_e[threadIdx.x] = em;
@@ -555,18 +566,41 @@ __global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *d, con
     }
     __syncthreads();
   }
+  // the three counts (at the threshold and at thresh -/+ tol) run in three
+  // warps at once; f32: in FP32 with a 1e-6 window (the FP32 form's resolution)
+  __shared__ int s_cnt[3];
+  const double pivmin = DBL_MIN * fmax(1.0, s_e[0]);
+  const double tn = fmax(fabs(s_lo[0]), fabs(s_hi[0]));  // ||T|| bound
+  const double tol = (f32 ? 1e-6 : 1e-12) * tn;
+  const int w = threadIdx.x >> 5;
+  if (w < 3 && (threadIdx.x & 31) == 0) {
+    const double x = thresh + (w == 0 ? 0.0 : (w == 1 ? tol : -tol));
+    if (f32) {
+      const float piv32 = FLT_MIN * fmaxf(1.0f, (float)s_e[0]);
+      int c = 0;
+      float q = (float)d[0] - (float)x;
+      if (fabsf(q) < piv32) q = -piv32;
+      if (q < 0.0f) ++c;
+      for (int i = 1; i < n; ++i) {
+        q = ((float)d[i] - (float)x) - (float)e2[i - 1] / q;
+        if (fabsf(q) < piv32) q = -piv32;
+        if (q < 0.0f) ++c;
+      }
+      s_cnt[w] = c;
+    } else {
+      s_cnt[w] = sturm_count(d, e2, n, x, pivmin);
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double pivmin = DBL_MIN * fmax(1.0, s_e[0]);
     scal[1] = s_lo[0] - 2.0 * DBL_EPSILON * fabs(s_lo[0]) - 4.0 * pivmin - 1e-300;
     scal[2] = s_hi[0] + 2.0 * DBL_EPSILON * fabs(s_hi[0]) + 4.0 * pivmin + 1e-300;
     scal[3] = pivmin;
-    scal[4] = fmax(fabs(s_lo[0]), fabs(s_hi[0]));  // ||T|| bound
+    scal[4] = tn;
     scal[5] = s_e[0];
-    int below = sturm_count(d, e2, n, thresh, pivmin);
-    count[0] = n - below;
-    // eigenvalues within 1e-12 * ||T|| of the threshold (tie diagnostics)
-    double tol = 1e-12 * scal[4];
-    count[1] = sturm_count(d, e2, n, thresh + tol, pivmin) - sturm_count(d, e2, n, thresh - tol, pivmin);
+    count[0] = n - s_cnt[0];
+    // eigenvalues within tol of the threshold (tie diagnostics)
+    count[1] = s_cnt[1] - s_cnt[2];
   }
 }
 
@@ -652,13 +686,37 @@ __global__ void bisect32_kernel(const double *d, const double *e2g, const double
 // Inverse iteration for the eigenvectors of T, one thread per group of
 // consecutive eigenvalues closer than gtol (groups are orthogonalised
 // internally).  X[i*k + r] receives the vector of lam[r].
+//
+// The LU factorisation of T - lambda (row interchanges) runs with its
+// recurrence carried in registers, so it only reads T and writes the factors:
+// multipliers, reciprocals of U's diagonal, U's two super-diagonals and the
+// interchange flags.  SMEM: those five arrays and the working vector live in
+// shared memory, interleaved by thread (TPB threads per block); otherwise in
+// the global scratch lu (strided by k) and X.  The start vector comes from an
+// integer hash of (i, r).
+constexpr int IV_DL = 0, IV_RDD = 1, IV_DU = 2, IV_DU2 = 3, IV_PV = 4, IV_X = 5;
+
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x ^= x >> 16; x *= 0x7feb352du;
+  x ^= x >> 15; x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
 template <typename T>
+__device__ __forceinline__ T iv_start(int i, int r) {
+  return (T)0.5 + (T)(mix32((unsigned)i * 0x9e3779b9u ^ mix32((unsigned)r + 0x632be5abu)) >> 8) * (T)(1.0 / 16777216.0);
+}
+
+template <typename T, bool SMEM>
 __global__ void inverse_iteration_kernel(const double *dg, const double *eg, const double *lam,
                                          const double *scal, int n, int k, T *X, T *lu, int *flags) {
   extern __shared__ __align__(16) unsigned char sde_raw[];
   T *d = reinterpret_cast<T *>(sde_raw), *e = d + n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { d[i] = (T)dg[i]; e[i] = (T)eg[i]; }
+  T *ws = e + n;                                   // SMEM: [6][n][blockDim.x]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { d[i] = (T)dg[i]; e[i] = (i < n - 1) ? (T)eg[i] : (T)0; }
   __syncthreads();
+  const int tl = threadIdx.x, tpb = blockDim.x;
   const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (r0 >= k) return;
   const double tnorm = scal[4];
@@ -666,12 +724,13 @@ __global__ void inverse_iteration_kernel(const double *dg, const double *eg, con
   if (r0 > 0 && lam[r0 - 1] - lam[r0] <= gtol) return;  // not the first of its group
   int r1 = r0 + 1;
   while (r1 < k && lam[r1 - 1] - lam[r1] <= gtol) ++r1;
-  // scratch for this thread: dl, dd, du, du2, piv (strided by k for coalescing)
-  T *dl = lu, *dd = lu + (int64_t)n * k, *du = lu + 2 * (int64_t)n * k;
-  T *du2 = lu + 3 * (int64_t)n * k, *pv = lu + 4 * (int64_t)n * k;
   const T tiny = Lim<T>::eps() * fmax((T)tnorm, Lim<T>::tiny());
+  auto fix = [&](T x) -> T { return (x == (T)0) ? tiny : ((fabs(x) < tiny) ? copysign(tiny, x) : x); };
   double prev = 0.0;
   for (int r = r0; r < r1; ++r) {
+    // element i of array a of this thread's vector
+#define S(a, i) (SMEM ? ws[((int64_t)(a) * n + (i)) * tpb + tl] : lu[((int64_t)(a) * n + (i)) * k + r])
+#define XV(i) (SMEM ? ws[((int64_t)IV_X * n + (i)) * tpb + tl] : X[(int64_t)(i) * k + r])
     double lmd = lam[r];
     if (r > r0) {
       double pert = 10.0 * (double)Lim<T>::eps() * fmax(fabs(lmd), tnorm * 1e-3);
@@ -679,73 +738,74 @@ __global__ void inverse_iteration_kernel(const double *dg, const double *eg, con
     }
     prev = lmd;
     const T lm = (T)lmd;
-#define S(a, i) a[(int64_t)(i) * k + r]
-    // LU of T - lm with row interchanges
-    for (int i = 0; i < n; ++i) {
-      S(dd, i) = d[i] - lm;
-      if (i < n - 1) { S(dl, i) = e[i]; S(du, i) = e[i]; }
-      S(du2, i) = 0;
-    }
-    for (int i = 0; i < n - 1; ++i) {
-      T di = S(dd, i), li = S(dl, i);
-      if (fabs(di) >= fabs(li)) {
-        S(pv, i) = 0;
-        if (di == (T)0) { di = tiny; S(dd, i) = di; }
-        T f = li / di;
-        S(dl, i) = f;
-        S(dd, i + 1) -= f * S(du, i);
-      } else {
-        S(pv, i) = 1;
-        T f = di / li;
-        S(dd, i) = li;
-        S(dl, i) = f;
-        T tmp = S(du, i);
-        S(du, i) = S(dd, i + 1);
-        S(dd, i + 1) = tmp - f * S(dd, i + 1);
-        if (i < n - 2) {
-          S(du2, i) = S(du, i + 1);
-          S(du, i + 1) = -f * S(du, i + 1);
-        }
-      }
-    }
-    if (S(dd, n - 1) == (T)0) S(dd, n - 1) = tiny;
-    for (int i = 0; i < n; ++i)
-      if (fabs(S(dd, i)) < tiny) S(dd, i) = copysign(tiny, S(dd, i));
-    // start vector: deterministic, no special structure
-    for (int i = 0; i < n; ++i) S(X, i) = (T)(1.0 + 0.5 * sin(0.7548776662 * (i + 1) + 0.5698402910 * (r + 1)));
-    for (int iter = 0; iter < 2; ++iter) {
-      // forward: apply L^-1 with the interchanges
+    // LU of T - lm with row interchanges; a, b = current diagonal and super-diagonal
+    {
+      T a = d[0] - lm, b = e[0];
       for (int i = 0; i < n - 1; ++i) {
-        if (S(pv, i) == (T)0) {
-          S(X, i + 1) -= S(dl, i) * S(X, i);
+        const T c = e[i], dn = d[i + 1] - lm, bn = e[i + 1];   // e[n-1] = 0
+        T f, ddi, dui, du2i, an, bnx;
+        const bool sw = fabs(a) < fabs(c);
+        if (!sw) {
+          if (a == (T)0) a = tiny;
+          f = c / a; ddi = a; dui = b; du2i = 0; an = dn - f * b; bnx = bn;
         } else {
-          T t = S(X, i);
-          S(X, i) = S(X, i + 1);
-          S(X, i + 1) = t - S(dl, i) * S(X, i);
+          f = a / c; ddi = c; dui = dn; du2i = bn; an = b - f * dn; bnx = -f * bn;
         }
+        S(IV_DL, i) = f;
+        S(IV_RDD, i) = (T)1 / fix(ddi);
+        S(IV_DU, i) = dui;
+        S(IV_DU2, i) = du2i;
+        S(IV_PV, i) = sw ? (T)1 : (T)0;
+        a = an;
+        b = bnx;
       }
+      S(IV_RDD, n - 1) = (T)1 / fix(a);
+      S(IV_DU, n - 1) = 0;
+      S(IV_DU2, n - 1) = 0;
+      if (n >= 2) S(IV_DU2, n - 2) = 0;   // U has two super-diagonals above row n-3 only
+    }
+    for (int iter = 0; iter < 2; ++iter) {
+      // forward: apply L^-1 with the interchanges (the start vector on the first pass)
+      T xc = (iter == 0) ? iv_start<T>(0, r) : XV(0);
+      for (int i = 0; i < n - 1; ++i) {
+        T xn = (iter == 0) ? iv_start<T>(i + 1, r) : XV(i + 1);
+        const T f = S(IV_DL, i);
+        T out;
+        if (S(IV_PV, i) == (T)0) { out = xc; xn = xn - f * xc; }
+        else { out = xn; xn = xc - f * xn; }
+        XV(i) = out;
+        xc = xn;
+      }
+      XV(n - 1) = xc;
       // backward: U^-1
+      T x1 = 0, x2 = 0;
       for (int i = n - 1; i >= 0; --i) {
-        T s = S(X, i);
-        if (i + 1 < n) s -= S(du, i) * S(X, i + 1);
-        if (i + 2 < n) s -= S(du2, i) * S(X, i + 2);
-        S(X, i) = s / S(dd, i);
+        const T sv = (XV(i) - S(IV_DU, i) * x1 - S(IV_DU2, i) * x2) * S(IV_RDD, i);
+        XV(i) = sv;
+        x2 = x1;
+        x1 = sv;
       }
-      // orthogonalise against the earlier vectors of this group
+      // orthogonalise against the earlier vectors of this group (already in X)
       for (int q = r0; q < r; ++q) {
         double dot = 0.0;
-        for (int i = 0; i < n; ++i) dot += (double)X[(int64_t)i * k + q] * (double)S(X, i);
+        for (int i = 0; i < n; ++i) dot += (double)X[(int64_t)i * k + q] * (double)XV(i);
         const T dt = (T)dot;
-        for (int i = 0; i < n; ++i) S(X, i) -= dt * X[(int64_t)i * k + q];
+        for (int i = 0; i < n; ++i) XV(i) -= dt * X[(int64_t)i * k + q];
       }
-      double nrm = 0.0;
-      for (int i = 0; i < n; ++i) nrm += (double)S(X, i) * (double)S(X, i);
-      nrm = sqrt(nrm);
+      T s0 = 0, s1 = 0;
+      for (int i = 0; i + 1 < n; i += 2) { s0 = fma(XV(i), XV(i), s0); s1 = fma(XV(i + 1), XV(i + 1), s1); }
+      if (n & 1) s0 = fma(XV(n - 1), XV(n - 1), s0);
+      const double nrm = sqrt((double)s0 + (double)s1);
       if (!(nrm > 0.0) || !isfinite(nrm)) { atomicExch(&flags[FLAG_EIG], 1); break; }
       const T inv = (T)(1.0 / nrm);
-      for (int i = 0; i < n; ++i) S(X, i) *= inv;
+      if (SMEM && iter == 1) {
+        for (int i = 0; i < n; ++i) X[(int64_t)i * k + r] = XV(i) * inv;
+      } else {
+        for (int i = 0; i < n; ++i) XV(i) *= inv;
+      }
     }
 #undef S
+#undef XV
   }
 }
 
@@ -783,11 +843,15 @@ __global__ void sum_partials_kernel(const T *__restrict__ src, int nsplit, int64
 
 // T (nb x nb, row-major, upper) from G = V_b^T V_b and tau[j0..j0+nb).
 template <typename T>
-__global__ void wy_build_t_kernel(const T *__restrict__ G, const double *__restrict__ tau,
+__global__ void wy_build_t_kernel(const T *__restrict__ Gg, const double *__restrict__ tau,
                                   int j0, int nb, T *__restrict__ Tm) {
   __shared__ T sT[WY_NB][WY_NB + 1];
+  __shared__ T G[WY_NB * WY_NB];   // staged: the recurrence below reads it column by column
   const int i = threadIdx.x;
-  for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) sT[q / WY_NB][q % WY_NB] = 0;
+  for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) {
+    sT[q / WY_NB][q % WY_NB] = 0;
+    if (q < nb * nb) G[q] = Gg[q];
+  }
   __syncthreads();
   if (i < nb) sT[i][i] = (T)tau[j0 + i];
   __syncthreads();
@@ -836,7 +900,7 @@ cudaError_t allow_max_dynamic_smem(const void *kernel, std::once_flag &flag) {
   });
   return result;
 }
-std::once_flag g_smem_hh[4], g_smem_bisect, g_smem_bisect32, g_smem_invit[2];
+std::once_flag g_smem_hh[4], g_smem_bisect, g_smem_bisect32, g_smem_invit[4], g_smem_bounds;
 
 // Try the fused reduction in arithmetic T; false when it cannot be launched.
 template <typename T>
@@ -901,7 +965,9 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
     cudaError_t e = allow_max_dynamic_smem(f32 ? (const void *)bisect32_kernel : (const void *)bisect_kernel,
                                            f32 ? g_smem_bisect32 : g_smem_bisect);
     if (e != cudaSuccess) return e;
-    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T>, g_smem_invit[f32 ? 1 : 0]);
+    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, true>, g_smem_invit[f32 ? 1 : 0]);
+    if (e != cudaSuccess) return e;
+    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, false>, g_smem_invit[f32 ? 3 : 2]);
     if (e != cudaSuccess) return e;
   }
   if (f32) {
@@ -918,7 +984,21 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
     bisect_kernel<<<(k + epw - 1) / epw, 32, smem, s>>>(w.d, w.p, w.scal, n, k, epw, w.lam);
   }
   T *X = reinterpret_cast<T *>(w.X), *lu = reinterpret_cast<T *>(w.lu), *V = reinterpret_cast<T *>(w.V);
-  inverse_iteration_kernel<T><<<(k + 31) / 32, 32, smem, s>>>(w.d, w.e, w.lam, w.scal, n, k, X, lu, flags);
+  {
+    // factors in shared memory when at least one thread's share fits
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      optin = 48 * 1024;
+    cudaGetLastError();
+    const size_t budget = (size_t)optin - 1024, per_thread = 6 * (size_t)n * sizeof(T);
+    const int tpb = smem + per_thread <= budget ? (int)std::min<size_t>(32, (budget - smem) / per_thread) : 0;
+    if (tpb >= 1)
+      inverse_iteration_kernel<T, true><<<(k + tpb - 1) / tpb, tpb, smem + tpb * per_thread, s>>>(
+          w.d, w.e, w.lam, w.scal, n, k, X, lu, flags);
+    else
+      inverse_iteration_kernel<T, false><<<(k + 31) / 32, 32, smem, s>>>(w.d, w.e, w.lam, w.scal, n, k, X, lu, flags);
+  }
   *launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1028,7 +1108,13 @@ cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s,
     *launches += 1;
   }
   // e2 reuses w.p (length n)
-  tridiag_bounds_kernel<<<1, RB, 0, s>>>(w.d, w.e, n, thresh, w.scal, w.p, w.count);
+  {
+    const size_t st = 2 * (size_t)n * sizeof(double);
+    const bool staged = st <= 180 * 1024 &&
+                        allow_max_dynamic_smem((const void *)tridiag_bounds_kernel, g_smem_bounds) == cudaSuccess;
+    cudaGetLastError();
+    tridiag_bounds_kernel<<<1, RB, staged ? st : 0, s>>>(w.d, w.e, n, thresh, w.scal, w.p, w.count, *f32, staged);
+  }
   *launches += 1;
   return cudaGetLastError();
 }

@@ -64,10 +64,11 @@ cudaError_t launch_copy_cols(const double *src, int64_t lds, int64_t c0, double 
 cudaError_t launch_screen(const double *Pi, int N, int n_omega, double *X0, double *X1,
                           double *C, int *flags, cudaStream_t s, int *launches);
 
-// Blocked form: work = screen_blocked_scratch(N, n_omega) doubles.
+// Blocked form: work = screen_blocked_scratch(N, n_omega) doubles; f32 runs
+// the sweep in FP32 (the work buffer then holds floats).
 size_t screen_blocked_scratch(int N, int n_omega);
 cudaError_t launch_screen_blocked(const double *Pi, int N, int n_omega, double *work, double *C, int *flags,
-                                  cudaStream_t s, int *launches);
+                                  cudaStream_t s, int *launches, bool f32 = false);
 
 // ---- eigensolver (eig.cu) ----
 struct EigWork {

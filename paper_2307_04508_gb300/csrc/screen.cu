@@ -8,7 +8,8 @@
 //    between two buffers (first step forms A = 1 - Pi, last writes C = -X - 1);
 //  * launch_screen_blocked: pivot blocks of 64 - the block is inverted in
 //    shared memory, and the rank-64 update A -= A[:,P] A_PP^-1 A[P,:] runs on
-//    the FP64 GEMM (about N/64 x 5 launches instead of N).
+//    the tiled GEMM (about N/64 x 5 launches instead of N), in FP64 or, for
+//    the mixed form, FP32.
 #include <math.h>
 
 #include <algorithm>
@@ -57,43 +58,48 @@ __global__ void __launch_bounds__(256) sweep_step_kernel(const double *__restric
   }
 }
 
-// ---- blocked sweep: pivot blocks of SB_B, rank-SB_B updates on the FP64 GEMM ----
+// ---- blocked sweep: pivot blocks of SB_B, rank-SB_B updates on the tiled GEMM ----
+// Instantiated in FP64 (the plain form) and FP32 (the mixed form: 1 - Pi has
+// every eigenvalue >= 1, so the FP32 inverse keeps its ~1e-7 relative accuracy).
 constexpr int SB_B = 64;
 
 // X = I - Pi
-__global__ void form_a_kernel(const double *__restrict__ Pi, double *__restrict__ X, int N, int64_t total) {
+template <typename T>
+__global__ void form_a_kernel(const double *__restrict__ Pi, T *__restrict__ X, int N, int64_t total) {
   const int64_t NN = (int64_t)N * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t f = e % NN;
     const int i = (int)(f / N), j = (int)(f - (int64_t)i * N);
-    X[e] = (i == j ? 1.0 : 0.0) - Pi[e];
+    X[e] = (T)((i == j ? 1.0 : 0.0) - Pi[e]);
   }
 }
 
 // Z = X[P,P]^-1 for each frequency (one block each): sweep in shared memory.
-__global__ void __launch_bounds__(256) block_inverse_kernel(const double *__restrict__ X, int N, int p0, int bs,
-                                                            double *__restrict__ Z, int *flags) {
-  __shared__ double a[SB_B][SB_B + 1];
-  __shared__ double piv;
+template <typename T>
+__global__ void __launch_bounds__(256) block_inverse_kernel(const T *__restrict__ X, int N, int p0, int bs,
+                                                            T *__restrict__ Z, int *flags) {
+  __shared__ T a[SB_B][SB_B + 1];
+  __shared__ T s_rp;
   const int b = blockIdx.x;
-  const double *Xb = X + (int64_t)b * N * N;
+  const T *Xb = X + (int64_t)b * N * N;
   for (int q = threadIdx.x; q < bs * bs; q += blockDim.x) {
     const int i = q / bs, j = q % bs;
     a[i][j] = Xb[(int64_t)(p0 + i) * N + (p0 + j)];
   }
   __syncthreads();
   for (int k = 0; k < bs; ++k) {
-    if (threadIdx.x == 0) {
-      piv = a[k][k];
-      if (!(piv > 0.0 && isfinite(piv))) atomicExch(&flags[FLAG_NOT_SPD], 1);
+    if (threadIdx.x == 0) {   // one reciprocal per pivot
+      const T piv = a[k][k];
+      if (!(piv > (T)0 && isfinite(piv))) atomicExch(&flags[FLAG_NOT_SPD], 1);
+      s_rp = (T)1 / piv;
     }
     __syncthreads();
-    const double rp = 1.0 / piv;
-    double nv[16];
+    const T rp = s_rp;
+    T nv[16];
     int cnt = 0;
     for (int q = threadIdx.x; q < bs * bs; q += blockDim.x, ++cnt) {
       const int i = q / bs, j = q % bs;
-      double r;
+      T r;
       if (i == k && j == k) r = -rp;
       else if (i == k) r = a[k][j] * rp;
       else if (j == k) r = a[i][k] * rp;
@@ -105,43 +111,88 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(const double *__rest
     for (int q = threadIdx.x; q < bs * bs; q += blockDim.x, ++cnt) a[q / bs][q % bs] = nv[cnt];
     __syncthreads();
   }
-  double *Zb = Z + (int64_t)b * SB_B * SB_B;
+  T *Zb = Z + (int64_t)b * SB_B * SB_B;
   for (int q = threadIdx.x; q < bs * bs; q += blockDim.x) Zb[(q / bs) * SB_B + (q % bs)] = -a[q / bs][q % bs];
 }
 
 // rowsP[b][r][j] = X[b][p0 + r][j]
-__global__ void copy_rows_kernel(const double *__restrict__ X, int N, int p0, int bs, double *__restrict__ rowsP) {
+template <typename T>
+__global__ void copy_rows_kernel(const T *__restrict__ X, int N, int p0, int bs, T *__restrict__ rowsP) {
   const int b = blockIdx.z, r = blockIdx.y;
-  const double *src = X + (int64_t)b * N * N + (int64_t)(p0 + r) * N;
-  double *dst = rowsP + ((int64_t)b * SB_B + r) * N;
+  const T *src = X + (int64_t)b * N * N + (int64_t)(p0 + r) * N;
+  T *dst = rowsP + ((int64_t)b * SB_B + r) * N;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) dst[j] = src[j];
 }
 
 // X[:, P] = R, X[P, :] = R^T, X[P, P] = -Z
-__global__ void fix_block_kernel(double *__restrict__ X, int N, int p0, int bs, const double *__restrict__ R,
-                                 const double *__restrict__ Z) {
+template <typename T>
+__global__ void fix_block_kernel(T *__restrict__ X, int N, int p0, int bs, const T *__restrict__ R,
+                                 const T *__restrict__ Z) {
   const int b = blockIdx.y;
-  double *Xb = X + (int64_t)b * N * N;
-  const double *Rb = R + (int64_t)b * N * SB_B;
-  const double *Zb = Z + (int64_t)b * SB_B * SB_B;
+  T *Xb = X + (int64_t)b * N * N;
+  const T *Rb = R + (int64_t)b * N * SB_B;
+  const T *Zb = Z + (int64_t)b * SB_B * SB_B;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)N * bs;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(q / bs), c = (int)(q % bs);
     const bool inP = i >= p0 && i < p0 + bs;
-    const double v = inP ? -Zb[(i - p0) * SB_B + c] : Rb[(int64_t)i * SB_B + c];
+    const T v = inP ? -Zb[(i - p0) * SB_B + c] : Rb[(int64_t)i * SB_B + c];
     Xb[(int64_t)i * N + p0 + c] = v;
     if (!inP) Xb[(int64_t)(p0 + c) * N + i] = v;   // the P x P block is written once
   }
 }
 
 // C = -X - I
-__global__ void finish_c_kernel(const double *__restrict__ X, double *__restrict__ C, int N, int64_t total) {
+template <typename T>
+__global__ void finish_c_kernel(const T *__restrict__ X, double *__restrict__ C, int N, int64_t total) {
   const int64_t NN = (int64_t)N * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t f = e % NN;
     const int i = (int)(f / N), j = (int)(f - (int64_t)i * N);
-    C[e] = -X[e] - (i == j ? 1.0 : 0.0);
+    C[e] = -(double)X[e] - (i == j ? 1.0 : 0.0);
   }
+}
+
+template <typename T>
+cudaError_t screen_blocked_impl(const double *Pi, int N, int n_omega, T *work, double *C, int *flags,
+                                cudaStream_t s, int *launches) {
+  const int64_t NN = (int64_t)N * N, total = NN * n_omega;
+  T *X = work;
+  T *R = X + total;
+  T *rowsP = R + (int64_t)n_omega * N * SB_B;
+  T *Z = rowsP + (int64_t)n_omega * SB_B * N;
+  int eb = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  form_a_kernel<T><<<eb, 256, 0, s>>>(Pi, X, N, total);
+  ++*launches;
+  for (int p0 = 0; p0 < N; p0 += SB_B) {
+    const int bs = std::min(SB_B, N - p0);
+    block_inverse_kernel<T><<<n_omega, 256, 0, s>>>(X, N, p0, bs, Z, flags);
+    dim3 cg((N + 255) / 256 < 8 ? (N + 255) / 256 : 8, bs, n_omega);
+    copy_rows_kernel<T><<<cg, 256, 0, s>>>(X, N, p0, bs, rowsP);
+    GemmArgs<T> g;   // R = X[:, P] Z
+    g.M = N; g.N = bs; g.K = bs;
+    g.A = X + p0; g.lda = N; g.strideA = NN;
+    g.B = Z; g.ldb = SB_B; g.strideB = (int64_t)SB_B * SB_B;
+    g.C = R; g.ldc = SB_B; g.strideC = (int64_t)N * SB_B;
+    cudaError_t e = launch_gemm<T>(g, n_omega, true, false, s);
+    if (e != cudaSuccess) return e;
+    GemmArgs<T> u;   // X -= R X[P, :]
+    u.M = N; u.N = N; u.K = bs;
+    u.A = R; u.lda = SB_B; u.strideA = (int64_t)N * SB_B;
+    u.B = rowsP; u.ldb = N; u.strideB = (int64_t)SB_B * N;
+    u.C = X; u.ldc = N; u.strideC = NN;
+    u.alpha = -1.0; u.beta = 1.0;
+    e = launch_gemm<T>(u, n_omega, true, false, s);
+    if (e != cudaSuccess) return e;
+    dim3 fg((int)std::min<int64_t>(((int64_t)N * bs + 255) / 256, 64), n_omega);
+    fix_block_kernel<T><<<fg, 256, 0, s>>>(X, N, p0, bs, R, Z);
+    *launches += 5;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  finish_c_kernel<T><<<eb, 256, 0, s>>>(X, C, N, total);
+  ++*launches;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -173,45 +224,10 @@ size_t screen_blocked_scratch(int N, int n_omega) {
 }
 
 cudaError_t launch_screen_blocked(const double *Pi, int N, int n_omega, double *work, double *C, int *flags,
-                                  cudaStream_t s, int *launches) {
+                                  cudaStream_t s, int *launches, bool f32) {
   if (N <= 0 || n_omega <= 0) return cudaSuccess;
-  const int64_t NN = (int64_t)N * N, total = NN * n_omega;
-  double *X = work;
-  double *R = X + total;
-  double *rowsP = R + (int64_t)n_omega * N * SB_B;
-  double *Z = rowsP + (int64_t)n_omega * SB_B * N;
-  int eb = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  form_a_kernel<<<eb, 256, 0, s>>>(Pi, X, N, total);
-  ++*launches;
-  for (int p0 = 0; p0 < N; p0 += SB_B) {
-    const int bs = std::min(SB_B, N - p0);
-    block_inverse_kernel<<<n_omega, 256, 0, s>>>(X, N, p0, bs, Z, flags);
-    dim3 cg((N + 255) / 256 < 8 ? (N + 255) / 256 : 8, bs, n_omega);
-    copy_rows_kernel<<<cg, 256, 0, s>>>(X, N, p0, bs, rowsP);
-    GemmF64Args g;   // R = X[:, P] Z
-    g.M = N; g.N = bs; g.K = bs;
-    g.A = X + p0; g.lda = N; g.strideA = NN;
-    g.B = Z; g.ldb = SB_B; g.strideB = (int64_t)SB_B * SB_B;
-    g.C = R; g.ldc = SB_B; g.strideC = (int64_t)N * SB_B;
-    cudaError_t e = launch_gemm_f64(g, n_omega, true, false, s);
-    if (e != cudaSuccess) return e;
-    GemmF64Args u;   // X -= R X[P, :]
-    u.M = N; u.N = N; u.K = bs;
-    u.A = R; u.lda = SB_B; u.strideA = (int64_t)N * SB_B;
-    u.B = rowsP; u.ldb = N; u.strideB = (int64_t)SB_B * N;
-    u.C = X; u.ldc = N; u.strideC = NN;
-    u.alpha = -1.0; u.beta = 1.0;
-    e = launch_gemm_f64(u, n_omega, true, false, s);
-    if (e != cudaSuccess) return e;
-    dim3 fg((int)std::min<int64_t>(((int64_t)N * bs + 255) / 256, 64), n_omega);
-    fix_block_kernel<<<fg, 256, 0, s>>>(X, N, p0, bs, R, Z);
-    *launches += 5;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  finish_c_kernel<<<eb, 256, 0, s>>>(X, C, N, total);
-  ++*launches;
-  return cudaGetLastError();
+  return f32 ? screen_blocked_impl<float>(Pi, N, n_omega, reinterpret_cast<float *>(work), C, flags, s, launches)
+             : screen_blocked_impl<double>(Pi, N, n_omega, work, C, flags, s, launches);
 }
 
 }  // namespace ltgw
