@@ -161,17 +161,20 @@ __global__ void hh_finalize_kernel(const double *A, double *d, double *e, int n)
 // memory when the block's rows fit there, else in place in global memory).
 // Step k:
 //  phase 1 (every block, identical arithmetic, so every block holds the same
-//    v_k): w_{k-1} from the full p_{k-1} and the per-block partials of
-//    p_{k-1}.v_{k-1}; row k of A^(k) from row k of A^(k-1), which its owner
-//    published during step k-1, minus update k-1; reflector k from it;
+//    vectors): normalise v_{k-1}; p_{k-1}.v_{k-1} from the full p_{k-1} (so
+//    no per-block partial sums are exchanged); w_{k-1}; row k of A^(k) from
+//    row k of A^(k-1), which its owner published during step k-1, minus
+//    update k-1; the coefficients of reflector k.  The reflector is kept
+//    unnormalised, x = (alpha, x_{k+2}, ...), with v = (1, sc x_{k+2}, ...) and
+//    sc = 1/(alpha - beta), so no extra pass is needed before phase 2;
 //  phase 2 (own rows r > k): one pass that applies update k-1 and accumulates
-//    p_k[r] = tau_k sum_j A^(k)[r][j] v_k[j]; then the owner of row k+1
-//    copies that row to the published buffer;
+//    s_r = sum_j A^(k)[r][j] x_j, then p_k[r] = tau sc (s_r - beta A^(k)[r][k+1]);
+//    the owner of row k+1 copies that row to the published buffer;
 //  grid barrier.
-// p, the published row and the partials are double-buffered by step parity, so
-// a block still reading step k-1's copies never sees step k's writes.  Data
-// crossing blocks goes through L2 (ld.global.cg).  The barrier is bounded
-// (about two seconds) and reports through flags.
+// p and the published row are double-buffered by step parity, so a block
+// still reading step k-1's copies never sees step k's writes.  Data crossing
+// blocks goes through L2 (ld.global.cg).  The barrier is bounded (about two
+// seconds) and reports through flags.
 struct GridBar {
   unsigned count;   // arrivals so far; barrier j (0-based) is passed at count >= G (j + 1)
   int abort;
@@ -229,13 +232,6 @@ __device__ __forceinline__ A warp_sum(A v) {
   return v;   // in lane 0
 }
 
-// Fixed-order sum of the per-block partials (identical in every block).
-__device__ double sum_partials(const double *part, double *sh) {
-  double v = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(part + b);
-  return block_sum(v, sh);
-}
-
 template <typename T>
 struct HhFusedArgs {
   const double *A0;   // the input matrix (row 0 is read from here at step 0)
@@ -245,7 +241,6 @@ struct HhFusedArgs {
   T *P;               // [2][n] p of the step, by parity
   T *pub;             // [2][n] the next reflector's row, by parity
   double *tail;       // [2] A^(n-3)[n-1][n-2 .. n-1], for the last 2 x 2 block
-  double *part;       // [2][G] per-block partials of p.v, by parity
   GridBar *gb;
   int *flags;
   int n, R;           // R = rows per block
@@ -286,20 +281,18 @@ __device__ __forceinline__ T row_pass(T *row, int j0, int j1, const T *vp, const
 }
 
 // FP64 instructions are scarce on this part (about 2 per clock per SM), so
-// the per-step bookkeeping keeps them off paths that every thread runs: in
-// the FP32 form the norm and p.v accumulate in FP32, reductions finish in
-// warp 0, and in the FP64 form phase 1 runs on HH_P1_FP64 threads only.
+// the per-step bookkeeping keeps them off paths that every thread runs: the
+// scalars are computed by one thread, and in the FP64 form phase 1 runs on
+// HH_P1_FP64 threads only (the FP32 form does all of it in FP32).
 constexpr int HH_P1_FP64 = 128;
 
 template <typename T, bool SMEM>
 __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *smem = reinterpret_cast<T *>(smem_raw);
-  __shared__ double sh[32];
-  __shared__ T wbuf[16];          // per-warp partials
-  __shared__ T s_seg[16];
-  __shared__ double s_sc[3];      // x[k], x[k+1], gamma of the step
-  __shared__ double s_rf[3];      // tau, beta, 1 / (alpha - beta) of the reflector
+  __shared__ T wbuf[2][16];       // per-warp partials: p.v, |x|^2
+  __shared__ T s_seg[16], s_a1[16];
+  __shared__ T s_st[5];           // x[k], alpha; tau, beta, sc of the step
   const int n = g.n, G = gridDim.x, b = blockIdx.x, R = g.R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int p1 = (sizeof(T) == 8) ? min(HH_P1_FP64, (int)blockDim.x) : (int)blockDim.x;  // phase-1 team
@@ -314,11 +307,10 @@ __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
     }
   }
   T *vprev = smem + n, *vcur = smem;
-  double tau_prev = 0.0;
+  T tau_prev = 0, sc_prev = 0;
   for (int k = 0; k + 2 < n; ++k) {
-    // ---- phase 1: row k of A^(k) into vcur, then reflector k in place.
-    // Team thread t owns x[j] for j = k + t + m * p1 (no barrier between
-    // writing x and its norm); the owners of j = k, k+1 stash them.
+    // ---- phase 1.  Team thread t owns element j = k + t + m * p1 of every
+    // vector it touches, so the loops below need no barrier between them.
     T *x = vcur;
     T s2 = 0;
     if (k == 0) {
@@ -327,123 +319,104 @@ __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
           const T xj = (T)__ldcg(g.A0 + j);
           x[j] = xj;
           if (j >= 2) s2 = fma(xj, xj, s2);
-          if (j < 2) s_sc[j] = (double)xj;
+          if (j < 2) s_st[j] = xj;
         }
     } else {
       const T *Pk = g.P + (size_t)((k - 1) & 1) * n;
       const T *pb = g.pub + (size_t)(k & 1) * n;
-      // one round trip: warp 0 sums the partials while the team loads p, row k
-      if (warp == 0) {
-        double a = 0.0;
-        for (int q = lane; q < G; q += 32) a += __ldcg(g.part + (size_t)((k - 1) & 1) * G + q);
-        a = warp_sum(a);
-        if (lane == 0) s_sc[2] = 0.5 * tau_prev * a;
-      }
-      const T pk_raw = __ldcg(Pk + k);
+      T dsum = 0;
       if (threadIdx.x < p1)
         for (int j = k + threadIdx.x; j < n; j += p1) {
-          wv[j] = __ldcg(Pk + j);
+          const T vj = (j == k) ? (T)1 : vprev[j] * sc_prev;   // normalise v_{k-1}
+          vprev[j] = vj;
+          if (b == 0) g.V[(int64_t)(k - 1) * n + j] = vj;
+          const T pj = __ldcg(Pk + j);
+          wv[j] = pj;
           x[j] = __ldcg(pb + j);
+          dsum = fma(pj, vj, dsum);
         }
+      if (warp < p1w) {
+        dsum = warp_sum(dsum);
+        if (lane == 0) wbuf[0][warp] = dsum;
+      }
       __syncthreads();
-      const T gam = (T)s_sc[2];
-      const T vk = vprev[k], wk = pk_raw - gam * vk;
-      if (threadIdx.x < p1)
+      if (threadIdx.x < p1) {
+        T pv = 0;
+        for (int q = 0; q < p1w; ++q) pv += wbuf[0][q];
+        const T gam = (T)0.5 * tau_prev * pv;
+        const T wk = __ldcg(Pk + k) - gam;   // v_{k-1}[k] = 1
         for (int j = k + threadIdx.x; j < n; j += p1) {
           const T wj = wv[j] - gam * vprev[j];
           wv[j] = wj;
-          const T xj = fma(-vk, wj, fma(-wk, vprev[j], x[j]));
+          const T xj = x[j] - wj - wk * vprev[j];
           x[j] = xj;
           if (j >= k + 2) s2 = fma(xj, xj, s2);
-          if (j < k + 2) s_sc[j - k] = (double)xj;
+          if (j < k + 2) s_st[j - k] = xj;
         }
+      }
     }
     if (warp < p1w) {
       s2 = warp_sum(s2);
-      if (lane == 0) wbuf[warp] = s2;
+      if (lane == 0) wbuf[1][warp] = s2;
     }
     __syncthreads();
-    if (warp == 0) {
-      T r = (lane < p1w) ? wbuf[lane] : (T)0;
-      r = warp_sum(r);
-      if (lane == 0) {   // the reflector's scalars, once (FP64 sqrt and divisions are slow here)
-        const double sigma = (double)r, alpha = s_sc[1];
-        double t = 0.0, beta = alpha, sc = 0.0;
-        if (sigma != 0.0) {
-          const double nrm = sqrt(alpha * alpha + sigma);
-          beta = (alpha >= 0.0) ? -nrm : nrm;
-          t = (beta - alpha) / beta;
-          sc = 1.0 / (alpha - beta);
-        }
-        s_rf[0] = t; s_rf[1] = beta; s_rf[2] = sc;
+    if (threadIdx.x == 0) {   // the reflector's scalars, once
+      T sigma = 0;
+      for (int q = 0; q < p1w; ++q) sigma += wbuf[1][q];
+      const T alpha = s_st[1];
+      T t = 0, beta = alpha, sc = 0;
+      if (sigma != (T)0) {
+        const T nrm = sqrt(alpha * alpha + sigma);
+        beta = (alpha >= (T)0) ? -nrm : nrm;
+        t = (beta - alpha) / beta;
+        sc = (T)1 / (alpha - beta);
+      }
+      s_st[2] = t; s_st[3] = beta; s_st[4] = sc;
+      if (b == 0) {
+        g.d[k] = s_st[0];
+        g.e[k] = beta;
+        g.tau[k] = t;
       }
     }
     __syncthreads();
-    const double t = s_rf[0], beta = s_rf[1], sc = s_rf[2], dk = s_sc[0];
-    const T scT = (T)sc;
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      const T v = (j == k + 1) ? (T)1 : x[j] * scT;
-      x[j] = v;
-      if (b == 0) g.V[(int64_t)k * n + j] = v;
-    }
-    if (b == 0 && threadIdx.x == 0) {
-      g.d[k] = dk;
-      g.e[k] = beta;
-      g.tau[k] = t;
-    }
-    __syncthreads();
-    // ---- phase 2: own rows r > k: update k-1 (k > 0) fused with p_k[r]
-    T pv = 0;
-    {
-      const int lr0 = (k + 1 > b) ? (k + 1 - b + G - 1) / G : 0;
-      const int nact = n_own - lr0;
-      if (nact > 0) {
-        const int wpr = max(1, nwarp / nact);     // warps per row when rows are few
-        const int L = n - k - 1;
-        const int seglen = (((L + wpr - 1) / wpr) + 31) & ~31;
-        T *Pk = g.P + (size_t)(k & 1) * n;
-        for (int task = warp; task < nact * wpr; task += nwarp) {
-          const int lr = lr0 + task / wpr, seg = task % wpr;
-          const int r = lr * G + b;
-          T *row = SMEM ? rows + (int64_t)lr * n : g.A + (int64_t)r * n;
-          const int j0 = k + 1 + seg * seglen, j1 = min(n, j0 + seglen);
-          T acc = 0;
-          if (j0 < j1) {
-            if (k == 0) acc = row_pass<T, false>(row, j0, j1, vprev, wv, x, (T)0, (T)0);
-            else acc = row_pass<T, true>(row, j0, j1, vprev, wv, x, vprev[r], wv[r]);
-          }
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-          if (wpr == 1) {
-            if (lane == 0) {
-              const T pr = (T)t * acc;
-              Pk[r] = pr;
-              pv = fma(pr, x[r], pv);
-            }
-          } else if (lane == 0) {
-            s_seg[task] = acc;
-          }
+    const T t = s_st[2], beta = s_st[3], sc = s_st[4], tsc = t * sc;
+    // ---- phase 2: own rows r > k: update k-1 (k > 0) fused with s_r
+    const int lr0 = (k + 1 > b) ? (k + 1 - b + G - 1) / G : 0;
+    const int nact = n_own - lr0;
+    const int wpr = nact > 0 ? max(1, nwarp / nact) : 1;   // warps per row when rows are few
+    T *Pk = g.P + (size_t)(k & 1) * n;
+    if (nact > 0) {
+      const int L = n - k - 1;
+      const int seglen = (((L + wpr - 1) / wpr) + 31) & ~31;
+      for (int task = warp; task < nact * wpr; task += nwarp) {
+        const int lr = lr0 + task / wpr, seg = task % wpr;
+        const int r = lr * G + b;
+        T *row = SMEM ? rows + (int64_t)lr * n : g.A + (int64_t)r * n;
+        const int j0 = k + 1 + seg * seglen, j1 = min(n, j0 + seglen);
+        T acc = 0, a1 = 0;
+        if (j0 < j1) {
+          if (k == 0) acc = row_pass<T, false>(row, j0, j1, vprev, wv, x, (T)0, (T)0);
+          else acc = row_pass<T, true>(row, j0, j1, vprev, wv, x, vprev[r], wv[r]);
         }
-        if (wpr > 1) {
-          __syncthreads();
-          if (threadIdx.x < nact) {
-            const int lr = lr0 + threadIdx.x, r = lr * G + b;
-            T a = 0;
-            for (int q = 0; q < wpr; ++q) a += s_seg[threadIdx.x * wpr + q];
-            const T pr = (T)t * a;
-            Pk[r] = pr;
-            pv = fma(pr, x[r], pv);
-          }
+        acc = warp_sum(acc);
+        if (seg == 0) {   // A^(k)[r][k+1], written by this warp's lane 0
+          __syncwarp();
+          a1 = row[k + 1];
+        }
+        if (wpr == 1) {
+          if (lane == 0) Pk[r] = tsc * (acc - beta * a1);
+        } else if (lane == 0) {
+          s_seg[task] = acc;
+          if (seg == 0) s_a1[task / wpr] = a1;
         }
       }
     }
-    // pv is non-zero only in lane 0 of each warp, or in lanes of warp 0
-    if (warp == 0) pv = warp_sum(pv);
-    if (lane == 0) wbuf[warp] = pv;
-    __syncthreads();   // also completes every row update of this step
-    if (warp == 0) {
-      T r = (lane < nwarp) ? wbuf[lane] : (T)0;
-      r = warp_sum(r);
-      if (lane == 0) g.part[(size_t)(k & 1) * G + b] = (double)r;
+    __syncthreads();   // every row update of this step is complete
+    if (nact > 0 && wpr > 1 && threadIdx.x < nact) {
+      const int r = (lr0 + threadIdx.x) * G + b;
+      T a = 0;
+      for (int q = 0; q < wpr; ++q) a += s_seg[threadIdx.x * wpr + q];
+      Pk[r] = tsc * (a - beta * s_a1[threadIdx.x]);
     }
     // the owner of row k+1 publishes it (A^(k) values, columns k+1..n-1); at the
     // last step the owner of row n-1 also hands over that row's last two entries
@@ -460,24 +433,25 @@ __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
     }
     if (!grid_barrier(g.gb, (unsigned)k, g.flags)) return;
     tau_prev = t;
+    sc_prev = sc;
     T *tmp = vprev; vprev = vcur; vcur = tmp;
   }
-  // ---- the last 2 x 2 block: apply update n-3 to rows n-2, n-1
-  if (b == 0 && n >= 3) {
+  // ---- the last 2 x 2 block: normalise v_{n-3}, apply update n-3 to rows n-2, n-1
+  if (b == 0 && n >= 3 && threadIdx.x == 0) {
     const int kl = n - 3;
-    const double s = sum_partials(g.part + (size_t)(kl & 1) * G, sh);
-    if (threadIdx.x == 0) {
-      const T gam = (T)(0.5 * tau_prev * s);
-      const T *Pk = g.P + (size_t)(kl & 1) * n;
-      const T *pb = g.pub + (size_t)((kl + 1) & 1) * n;
-      const T v2 = vprev[n - 2], v1 = vprev[n - 1];
-      const T w2 = __ldcg(Pk + n - 2) - gam * v2, w1 = __ldcg(Pk + n - 1) - gam * v1;
-      const T a22 = __ldcg(pb + n - 2), a21 = __ldcg(pb + n - 1), a11 = (T)__ldcg(g.tail + 1);
-      g.d[n - 2] = fma(-v2, w2, fma(-w2, v2, a22));
-      g.e[n - 2] = fma(-v2, w1, fma(-w2, v1, a21));
-      g.d[n - 1] = fma(-v1, w1, fma(-w1, v1, a11));
-      g.e[n - 1] = 0.0;
-    }
+    const T *Pk = g.P + (size_t)(kl & 1) * n;
+    const T *pb = g.pub + (size_t)((kl + 1) & 1) * n;
+    const T v2 = 1, v1 = vprev[n - 1] * sc_prev;
+    g.V[(int64_t)kl * n + n - 2] = v2;
+    g.V[(int64_t)kl * n + n - 1] = v1;
+    const T p2 = __ldcg(Pk + n - 2), p1v = __ldcg(Pk + n - 1);
+    const T gam = (T)0.5 * tau_prev * (p2 * v2 + p1v * v1);
+    const T w2 = p2 - gam * v2, w1 = p1v - gam * v1;
+    const T a22 = __ldcg(pb + n - 2), a21 = __ldcg(pb + n - 1), a11 = (T)__ldcg(g.tail + 1);
+    g.d[n - 2] = fma(-v2, w2, fma(-w2, v2, a22));
+    g.e[n - 2] = fma(-v2, w1, fma(-w2, v1, a21));
+    g.d[n - 1] = fma(-v1, w1, fma(-w1, v1, a11));
+    g.e[n - 1] = 0.0;
   }
 }
 
@@ -845,12 +819,14 @@ __global__ void sum_partials_kernel(const T *__restrict__ src, int nsplit, int64
 template <typename T>
 __global__ void wy_build_t_kernel(const T *__restrict__ Gg, const double *__restrict__ tau,
                                   int j0, int nb, T *__restrict__ Tm) {
-  __shared__ T sT[WY_NB][WY_NB + 1];
-  __shared__ T G[WY_NB * WY_NB];   // staged: the recurrence below reads it column by column
+  // dynamic: [2][WY_NB][WY_NB + 1] (over the static limit in FP64)
+  extern __shared__ __align__(16) unsigned char wy_raw[];
+  T (*sT)[WY_NB + 1] = reinterpret_cast<T (*)[WY_NB + 1]>(wy_raw);
+  T (*Gt)[WY_NB + 1] = sT + WY_NB;   // G transposed: the recurrence reads column l of G across threads
   const int i = threadIdx.x;
   for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) {
     sT[q / WY_NB][q % WY_NB] = 0;
-    if (q < nb * nb) G[q] = Gg[q];
+    if (q < nb * nb) Gt[q % nb][q / nb] = Gg[q];
   }
   __syncthreads();
   if (i < nb) sT[i][i] = (T)tau[j0 + i];
@@ -858,7 +834,7 @@ __global__ void wy_build_t_kernel(const T *__restrict__ Gg, const double *__rest
   for (int l = 1; l < nb; ++l) {
     T v = 0;
     if (i < l) {
-      for (int m = i; m < l; ++m) v += sT[i][m] * G[m * nb + l];
+      for (int m = i; m < l; ++m) v += sT[i][m] * Gt[l][m];
       v *= -(T)tau[j0 + l];
     }
     __syncthreads();
@@ -900,7 +876,7 @@ cudaError_t allow_max_dynamic_smem(const void *kernel, std::once_flag &flag) {
   });
   return result;
 }
-std::once_flag g_smem_hh[4], g_smem_bisect, g_smem_bisect32, g_smem_invit[4], g_smem_bounds;
+std::once_flag g_smem_hh[4], g_smem_bisect, g_smem_bisect32, g_smem_invit[4], g_smem_bounds, g_smem_wy[2];
 
 // Try the fused reduction in arithmetic T; false when it cannot be launched.
 template <typename T>
@@ -944,8 +920,7 @@ bool launch_fused(EigWork &w, int n, cudaStream_t s, int *launches, cudaError_t 
   g.pub = g.P + 2 * (size_t)n;
   double *after = w.grid_ws + (4 * (size_t)n * sizeof(T) + sizeof(double) - 1) / sizeof(double);
   g.tail = after;
-  g.part = after + 2;
-  g.gb = reinterpret_cast<GridBar *>(g.part + 2 * (size_t)nsm);
+  g.gb = reinterpret_cast<GridBar *>(after + 2);
   g.flags = w.flags;
   g.n = n; g.R = R;
   *err = cudaMemsetAsync(g.gb, 0, sizeof(GridBar), s);
@@ -968,6 +943,8 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
     e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, true>, g_smem_invit[f32 ? 1 : 0]);
     if (e != cudaSuccess) return e;
     e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, false>, g_smem_invit[f32 ? 3 : 2]);
+    if (e != cudaSuccess) return e;
+    e = allow_max_dynamic_smem((const void *)wy_build_t_kernel<T>, g_smem_wy[f32 ? 1 : 0]);
     if (e != cudaSuccess) return e;
   }
   if (f32) {
@@ -1056,7 +1033,7 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
     if (e != cudaSuccess) return e;
     sum_partials_kernel<T><<<64, 256, 0, s>>>(Gp, nsplit, (int64_t)nb * nb, (int64_t)nb * nb, Gs);
     sum_partials_kernel<T><<<152, 256, 0, s>>>(W1p, nsplit, (int64_t)nb * k, (int64_t)nb * k, W1);
-    wy_build_t_kernel<T><<<1, WY_NB, 0, s>>>(Gs, w.tau, j0, nb, Tm);
+    wy_build_t_kernel<T><<<1, WY_NB, 2 * WY_NB * (WY_NB + 1) * sizeof(T), s>>>(Gs, w.tau, j0, nb, Tm);
     GemmArgs<T> t2;                     // W2 = T W1
     t2.M = nb; t2.N = k; t2.K = nb;
     t2.A = Tm; t2.lda = nb; t2.B = W1; t2.ldb = k; t2.C = W2; t2.ldc = k;

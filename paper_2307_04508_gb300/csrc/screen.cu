@@ -74,45 +74,53 @@ __global__ void form_a_kernel(const double *__restrict__ Pi, T *__restrict__ X, 
   }
 }
 
-// Z = X[P,P]^-1 for each frequency (one block each): sweep in shared memory.
+// Z = X[P,P]^-1 for each frequency (one block of 256 threads each): sweep
+// with each thread's 16 elements of the bs x bs block held in registers;
+// only the pivot row and column go through shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) block_inverse_kernel(const T *__restrict__ X, int N, int p0, int bs,
                                                             T *__restrict__ Z, int *flags) {
-  __shared__ T a[SB_B][SB_B + 1];
+  constexpr int PER = SB_B * SB_B / 256;
+  __shared__ T rowk[SB_B], colk[SB_B];
   __shared__ T s_rp;
   const int b = blockIdx.x;
   const T *Xb = X + (int64_t)b * N * N;
-  for (int q = threadIdx.x; q < bs * bs; q += blockDim.x) {
-    const int i = q / bs, j = q % bs;
-    a[i][j] = Xb[(int64_t)(p0 + i) * N + (p0 + j)];
+  T v[PER];
+#pragma unroll
+  for (int c = 0; c < PER; ++c) {
+    const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
+    v[c] = (i < bs && j < bs) ? Xb[(int64_t)(p0 + i) * N + (p0 + j)] : (T)0;
   }
-  __syncthreads();
   for (int k = 0; k < bs; ++k) {
-    if (threadIdx.x == 0) {   // one reciprocal per pivot
-      const T piv = a[k][k];
-      if (!(piv > (T)0 && isfinite(piv))) atomicExch(&flags[FLAG_NOT_SPD], 1);
-      s_rp = (T)1 / piv;
+#pragma unroll
+    for (int c = 0; c < PER; ++c) {
+      const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
+      if (j == k && i < bs) colk[i] = v[c];
+      if (i == k && j < bs) rowk[j] = v[c];
+      if (i == k && j == k) {   // one reciprocal per pivot
+        if (!(v[c] > (T)0 && isfinite(v[c]))) atomicExch(&flags[FLAG_NOT_SPD], 1);
+        s_rp = (T)1 / v[c];
+      }
     }
     __syncthreads();
     const T rp = s_rp;
-    T nv[16];
-    int cnt = 0;
-    for (int q = threadIdx.x; q < bs * bs; q += blockDim.x, ++cnt) {
-      const int i = q / bs, j = q % bs;
-      T r;
-      if (i == k && j == k) r = -rp;
-      else if (i == k) r = a[k][j] * rp;
-      else if (j == k) r = a[i][k] * rp;
-      else r = a[i][j] - a[i][k] * a[k][j] * rp;
-      nv[cnt] = r;
+#pragma unroll
+    for (int c = 0; c < PER; ++c) {
+      const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
+      if (i >= bs || j >= bs) continue;
+      if (i == k && j == k) v[c] = -rp;
+      else if (i == k) v[c] = rowk[j] * rp;
+      else if (j == k) v[c] = colk[i] * rp;
+      else v[c] = v[c] - colk[i] * rowk[j] * rp;
     }
-    __syncthreads();
-    cnt = 0;
-    for (int q = threadIdx.x; q < bs * bs; q += blockDim.x, ++cnt) a[q / bs][q % bs] = nv[cnt];
     __syncthreads();
   }
   T *Zb = Z + (int64_t)b * SB_B * SB_B;
-  for (int q = threadIdx.x; q < bs * bs; q += blockDim.x) Zb[(q / bs) * SB_B + (q % bs)] = -a[q / bs][q % bs];
+#pragma unroll
+  for (int c = 0; c < PER; ++c) {
+    const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
+    if (i < bs && j < bs) Zb[i * SB_B + j] = -v[c];
+  }
 }
 
 // rowsP[b][r][j] = X[b][p0 + r][j]
