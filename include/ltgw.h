@@ -175,13 +175,11 @@ ltgw_status ltgw_naf_basis(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const doub
                            int64_t ld, double thresh, double *Ut, double *lambda,
                            int *n_naf, void *stream);
 
-/* The same NAF basis in the mixed-precision form used by LTGW_BF16X3 solves:
- * K on the tensor cores with split-BF16 operands (as ltgw_polarizability_mixed,
- * unit scale), and the Householder reduction, bisection, inverse iteration,
- * re-orthonormalisation and back-transformation in FP32 (norms and reflector
- * coefficients in FP64).  Eigenvalues carry an absolute error of about
- * 1e-6 * lambda_max; eigenvectors are accurate to that error over the gap to
- * their neighbours.  Same arguments, layouts and errors as ltgw_naf_basis. */
+/* The same NAF basis as LTGW_BF16X3 solves form it: K on the tensor cores
+ * with split-BF16 operands (as ltgw_polarizability_mixed, unit scale), then
+ * the same FP64 eigensolver as ltgw_naf_basis.  K carries a relative error of
+ * about 1e-6, so the eigenvalues carry about 1e-6 * lambda_max.  Same
+ * arguments, layouts and errors as ltgw_naf_basis. */
 ltgw_status ltgw_naf_basis_mixed(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, const double *B,
                                  int64_t ld, double thresh, double *Ut, double *lambda,
                                  int *n_naf, void *stream);

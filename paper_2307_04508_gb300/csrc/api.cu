@@ -158,7 +158,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   EigWork w;
   auto layout = [&](Arena &A) {
     w.A = A.take<double>((size_t)n * n);
-    w.V = A.take<double>((size_t)n * n);
+    w.V = A.take<double>((size_t)(n + 64) * n);   // 64 zero rows past the last reflector (compact-WY blocks)
     w.d = A.take<double>(n);
     w.e = A.take<double>(n);
     w.tau = A.take<double>(n);
@@ -169,8 +169,10 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     w.X = A.take<double>((size_t)n * n);
     w.lu = A.take<double>((size_t)5 * n * n);
     w.count = A.take<int>(2);
-    const int64_t nsplit = (n + 63) / 64;
-    w.wy = A.take<double>((size_t)(nsplit + 3) * 64 * (64 + (size_t)n));
+    const int64_t nsplit = (n + 63) / 64, nblk = (n + 63) / 64;
+    // compact-WY scratch: split partials of G and W1, W1, every block's G, T and M_b
+    w.wy = A.take<double>((size_t)nsplit * 64 * (64 + (size_t)n) + 64 * (size_t)n + 2 * (size_t)nblk * 64 * 64 +
+                          (size_t)nblk * n * 64);
     w.grid_ws = A.take<double>((size_t)4 * n + 2 * (size_t)ctx->n_sm + 8);
   };
   ar.begin_sizing();
@@ -193,11 +195,10 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     g.syrk = 1;
     CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
   }
-  LTGW_CUDA(ctx, cudaMemsetAsync(w.V, 0, (size_t)n * n * sizeof(double), s));
+  LTGW_CUDA(ctx, cudaMemsetAsync(w.V, 0, (size_t)(n + 64) * n * sizeof(double), s));
   int nl = 0;
   ctx->mark(EV_TRI0, s);
-  bool f32 = mixed;
-  cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl, &f32);
+  cudaError_t e = launch_eig_tridiag(w, n, thresh, s, &nl);
   ctx->mark(EV_TRI1, s);
   ctx->tri_n = n;
   ctx->launches += nl;
@@ -209,7 +210,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   if (near_out) *near_out = cnt[1];
   if (k <= 0) { ctx->fail(LTGW_ERR_NO_NAF, "NAF threshold kept no auxiliary function"); return ctx->status(); }
   nl = 0;
-  e = launch_eig_vectors(w, n, k, Ut, ctx->flags, s, &nl, f32);
+  e = launch_eig_vectors(w, n, k, Ut, ctx->flags, s, &nl);
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("eig_vectors: ") + cudaGetErrorString(e)); return ctx->status(); }
   if (lam_out) LTGW_CUDA(ctx, cudaMemcpyAsync(lam_out, w.lam, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -859,7 +860,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
 
   // ---- screening
   int nl = 0;
-  cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl, mixed);
+  cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl);
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
   ctx->mark(EV_SCREEN, s);

@@ -14,12 +14,15 @@
 //  6. back-transformation U = Q X in compact-WY blocks of 64 reflectors
 //     (split-K GEMMs), written transposed as the rows of Ut.
 //
-// Two arithmetic forms share this code: FP64 throughout (the plain form), and
-// FP32 for steps 1 and 3-6 (the mixed form, whose metric K already carries the
-// split-BF16 contraction's ~1e-6 relative error; FP32 runs at 64x the FP64
-// rate on this part).  Scalars of the reductions (norms, Householder
-// coefficients, partial sums) stay FP64 in both.  Only the kept eigenvectors
-// are formed.  Householder convention: H = 1 - tau v v^T, v_0 = 1, H x = beta e_1.
+// FP64 throughout (both the plain and the mixed-precision solve: only the
+// dense contractions around the eigensolver change precision).  Only the kept
+// eigenvectors are formed.  Householder convention: H = 1 - tau v v^T,
+// v_0 = 1, H x = beta e_1.
+//
+// On this part an FP64 FMA has a dependent latency of about 64 cycles and an
+// IEEE FP64 division about 400 (FP32 FMA: 4), so the sequential recurrences
+// (Sturm counts, tridiagonal LU) are written to keep as few operations as
+// possible on their dependency chains.
 #include <float.h>
 
 #include <algorithm>
@@ -40,11 +43,6 @@ template <> struct Lim<double> {
   static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
   static __device__ __forceinline__ double tiny() { return DBL_MIN; }
   static constexpr double group_tol = 1e-7;   // inverse-iteration groups, relative to ||T||
-};
-template <> struct Lim<float> {
-  static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
-  static __device__ __forceinline__ float tiny() { return FLT_MIN; }
-  static constexpr double group_tol = 1e-5;
 };
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -455,60 +453,88 @@ __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
   }
 }
 
-// FP32 working copy of the input for the in-place FP32 reduction.
-__global__ void to_f32_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t count) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
+// Number of eigenvalues of T below x (Sturm): the sign changes along the
+// leading principal minors p_0 = 1, p_i = det(T_i - x) with
+// p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2}.  This is the LDL^T pivot
+// count q_i = p_i / p_{i-1} without the division: one FMA per step sits on the
+// dependency chain (e^2 p_{i-2} is ready a step early), against a reciprocal
+// and its Newton steps in the quotient form.  The pair (p_{i-1}, p_i) is
+// rescaled by an exact power of two whenever the larger exponent leaves
+// [-400, 400] (integer operations on the high words), and a minor that comes
+// out exactly zero is replaced by pivmin with the sign opposite to p_{i-1}
+// (counted as a sign change, like the quotient form's pivot -pivmin).  The range check runs every 8 steps, off
+// the chain.
+__device__ __forceinline__ bool is_zero_bits(double v) {   // +0 or -0, on the integer pipe
+  return ((__double2hiint(v) & 0x7fffffff) | __double2loint(v)) == 0;
 }
 
-// 1/q from the hardware reciprocal estimate refined by three Newton steps
-// y <- y (2 - q y) (each step squares the relative error), about 1 ulp: the
-// Sturm count below is exact for a matrix perturbed by a few ulps anyway, and
-// this avoids the IEEE division sequence, which is costly on this part's
-// FP64 pipe.  |q| >= pivmin > 0 keeps q away from zero and subnormals.
+__device__ int sturm_count(const double *d, const double *e2, int n, double x, double pivmin) {
+  double pm = 1.0, p = d[0] - x;
+  if (p == 0.0) p = -pivmin;
+  bool neg = __double2hiint(p) < 0;
+  int c = neg;
+  int i = 1;
+  while (i < n) {
+    // 8 steps between range checks: |p| grows at most 2 (|d| + |e| + |x|) per
+    // step and shrinks by at most e^2 per two, so +-400 stays far from overflow.
+    // The block's d_i - x and e^2 are formed first, off the FMA chain.
+    double dx[8], ee[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = min(i + u, n - 1);
+      dx[u] = d[j] - x;
+      ee[u] = e2[j - 1];
+    }
+    const int m = min(8, n - i);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u < m) {
+        double pn = fma(dx[u], p, -(ee[u] * pm));
+        if (is_zero_bits(pn))   // -pivmin with the sign opposite to p, on the integer pipe
+          pn = __longlong_as_double((~__double_as_longlong(p) & (long long)0x8000000000000000ull) |
+                                    __double_as_longlong(pivmin));
+        const bool nn = __double2hiint(pn) < 0;
+        c += (nn != neg);
+        neg = nn;
+        pm = p;
+        p = pn;
+      }
+    }
+    i += m;
+    const int em = max((__double2hiint(p) >> 20) & 0x7ff, (__double2hiint(pm) >> 20) & 0x7ff);
+    if (em > 1023 + 400 || em < 1023 - 400) {
+      const double f = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em), exact
+      p *= f;
+      pm *= f;
+    }
+  }
+  return c;
+}
+
+// 1/q from the hardware reciprocal estimate and Newton steps y <- y (2 - q y)
+// (each squares the relative error): two give a few ulps, one about 2^-46, at
+// a fraction of the latency of the IEEE division on this part.  |q| is kept
+// away from zero and subnormals by the caller.
+template <int STEPS = 2>
 __device__ __forceinline__ double recip_nr(double q) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
-  y = y * fma(-q, y, 2.0);
-  y = y * fma(-q, y, 2.0);
-  y = y * fma(-q, y, 2.0);
+#pragma unroll
+  for (int s = 0; s < STEPS; ++s) y = y * fma(-q, y, 2.0);
   return y;
 }
 
-// Number of eigenvalues of T below x (signs of the LDL^T pivots of T - x).
-__device__ int sturm_count(const double *d, const double *e2, int n, double x, double pivmin) {
-  int c = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0.0) ++c;
-  for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e2[i - 1] * recip_nr(q);
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++c;
-  }
-  return c;
-}
-
-// The same count in FP32 (IEEE division: FP32 runs at full rate).
-__device__ int sturm_count32(const float *d, const float *e2, int n, float x, float pivmin) {
-  int c = 0;
-  float q = d[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
-  if (q < 0.0f) ++c;
-  for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
-    if (fabsf(q) < pivmin) q = -pivmin;
-    if (q < 0.0f) ++c;
-  }
-  return c;
+// |a| < |b| on the integer pipe (finite doubles: magnitude order = bit order)
+__device__ __forceinline__ bool abs_less(double a, double b) {
+  return (__double_as_longlong(a) & 0x7fffffffffffffffll) < (__double_as_longlong(b) & 0x7fffffffffffffffll);
 }
 
 // scal[1..3] = lower / upper Gershgorin bound, pivmin; scal[4] = ||T|| bound;
 // scal[5] = max e^2; count[0] = #eig > thresh, count[1] = #eig within
-// 1e-12 ||T|| of it (1e-6 ||T|| in the FP32 form).
+// 1e-12 ||T|| of it.
 __global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *dg, const double *e,
                                                             int n, double thresh, double *scal,
-                                                            double *e2g, int *count, bool f32, bool staged) {
+                                                            double *e2g, int *count, bool staged) {
   __shared__ double s_lo[RB], s_hi[RB], s_e[RB];
   // the Sturm counts below walk d and e^2 sequentially: staged in shared
   // memory when they fit, so that each step is not an L2 round trip
@@ -540,30 +566,15 @@ __global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *dg, co
     }
     __syncthreads();
   }
-  // the three counts (at the threshold and at thresh -/+ tol) run in three
-  // warps at once; f32: in FP32 with a 1e-6 window (the FP32 form's resolution)
+  // the three counts (at the threshold and at thresh -/+ tol) run in three warps at once
   __shared__ int s_cnt[3];
   const double pivmin = DBL_MIN * fmax(1.0, s_e[0]);
   const double tn = fmax(fabs(s_lo[0]), fabs(s_hi[0]));  // ||T|| bound
-  const double tol = (f32 ? 1e-6 : 1e-12) * tn;
+  const double tol = 1e-12 * tn;
   const int w = threadIdx.x >> 5;
   if (w < 3 && (threadIdx.x & 31) == 0) {
     const double x = thresh + (w == 0 ? 0.0 : (w == 1 ? tol : -tol));
-    if (f32) {
-      const float piv32 = FLT_MIN * fmaxf(1.0f, (float)s_e[0]);
-      int c = 0;
-      float q = (float)d[0] - (float)x;
-      if (fabsf(q) < piv32) q = -piv32;
-      if (q < 0.0f) ++c;
-      for (int i = 1; i < n; ++i) {
-        q = ((float)d[i] - (float)x) - (float)e2[i - 1] / q;
-        if (fabsf(q) < piv32) q = -piv32;
-        if (q < 0.0f) ++c;
-      }
-      s_cnt[w] = c;
-    } else {
-      s_cnt[w] = sturm_count(d, e2, n, x, pivmin);
-    }
+    s_cnt[w] = sturm_count(d, e2, n, x, pivmin);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -581,10 +592,11 @@ __global__ void __launch_bounds__(RB) tridiag_bounds_kernel(const double *dg, co
 // lam[r] = (n-1-r)-th smallest eigenvalue (r-th largest), r < k, by
 // multisection with BIS_L lanes per eigenvalue: each lane counts the
 // eigenvalues below one of BIS_L interior points, so an interval shrinks
-// (BIS_L + 1)-fold per step.  Few lanes per eigenvalue keep the total number
-// of FP64 divisions (the cost on this part) near that of plain bisection while
-// giving enough threads to hide their latency.  d and e^2 live in shared memory.
-constexpr int BIS_L = 4;
+// (BIS_L + 1)-fold per step.  On this part a warp's FP64 instructions run one
+// after another whatever their dependences, so a whole warp per eigenvalue
+// (33-fold per step, about 11 steps to full precision) beats fewer lanes with
+// more steps.  d and e^2 live in shared memory.
+constexpr int BIS_L = 32;
 __global__ void bisect_kernel(const double *d, const double *e2g, const double *scal, int n,
                               int k, int epw, double *lam) {
   extern __shared__ double sm[];
@@ -596,7 +608,7 @@ __global__ void bisect_kernel(const double *d, const double *e2g, const double *
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int sub = lane % BIS_L, grp = lane / BIS_L;
-  const unsigned gmask = ((1u << BIS_L) - 1u) << (grp * BIS_L);
+  const unsigned gmask = (BIS_L >= 32) ? 0xffffffffu : (((1u << (BIS_L & 31)) - 1u) << (grp * BIS_L));
   const int r = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * epw + grp;
   const bool live = grp < epw && r < k;
   const int idx = n - 1 - (live ? r : 0);  // ascending index of the wanted eigenvalue
@@ -606,55 +618,20 @@ __global__ void bisect_kernel(const double *d, const double *e2g, const double *
   for (int it = 0; it < 200; ++it) {
     if (!done && hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
     if (__all_sync(0xffffffffu, done)) break;
-    const double x = lo + (hi - lo) * (double)(sub + 1) / (double)(BIS_L + 1);
+    const double x = lo + (hi - lo) * ((double)(sub + 1) * (1.0 / (BIS_L + 1)));
     const bool above = !done && sturm_count(sd, se2, n, x, pivmin) > idx;  // eigenvalue idx < x
     const unsigned b = (__ballot_sync(0xffffffffu, above) & gmask) >> (grp * BIS_L);
     if (!done) {
       const int j = b ? (__ffs(b) - 1) : BIS_L;
-      const double nlo = (j == 0) ? lo : lo + (hi - lo) * (double)j / (double)(BIS_L + 1);
-      const double nhi = (j == BIS_L) ? hi : lo + (hi - lo) * (double)(j + 1) / (double)(BIS_L + 1);
+      // the same expressions as the lanes' points, so the bracket is exactly two of them
+      const double nlo = (j == 0) ? lo : lo + (hi - lo) * ((double)j * (1.0 / (BIS_L + 1)));
+      const double nhi = (j == BIS_L) ? hi : lo + (hi - lo) * ((double)(j + 1) * (1.0 / (BIS_L + 1)));
       if (!(nlo > lo || nhi < hi)) done = true;  // no progress at this resolution
       lo = nlo;
       hi = nhi;
     }
   }
   if (live && sub == 0) lam[r] = 0.5 * (lo + hi);
-}
-
-// FP32 form: one warp per eigenvalue, 32 interior points per step (the
-// interval shrinks 33-fold), so about five steps reach FP32 resolution.
-__global__ void bisect32_kernel(const double *d, const double *e2g, const double *scal, int n, int k,
-                                double *lam) {
-  extern __shared__ float smf[];
-  float *sd = smf, *se2 = smf + n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sd[i] = (float)d[i];
-    se2[i] = (i < n - 1) ? (float)e2g[i] : 0.0f;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= k) return;
-  const int idx = n - 1 - r;
-  const float emax = (float)scal[5];
-  const float pivmin = FLT_MIN * fmaxf(1.0f, emax);
-  const float tn = (float)scal[4];
-  float lo = (float)scal[1] - 4.0f * FLT_EPSILON * tn - 4.0f * pivmin;
-  float hi = (float)scal[2] + 4.0f * FLT_EPSILON * tn + 4.0f * pivmin;
-  for (int it = 0; it < 64; ++it) {
-    if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
-    const float x = lo + (hi - lo) * (float)(lane + 1) * (1.0f / 33.0f);
-    const bool above = x < hi && sturm_count32(sd, se2, n, x, pivmin) > idx;
-    const unsigned bm = __ballot_sync(0xffffffffu, above);
-    const int j = bm ? (__ffs(bm) - 1) : 32;   // first point above the eigenvalue
-    const float xj = __shfl_sync(0xffffffffu, x, j & 31), xj1 = __shfl_sync(0xffffffffu, x, (j + 31) & 31);
-    const float nlo = (j == 0) ? lo : xj1;
-    const float nhi = (j == 32) ? hi : xj;
-    if (!(nlo > lo || nhi < hi)) break;   // no progress at this resolution
-    lo = nlo;
-    hi = nhi;
-  }
-  if (lane == 0) lam[r] = 0.5 * ((double)lo + (double)hi);
 }
 
 // Inverse iteration for the eigenvectors of T, one thread per group of
@@ -699,7 +676,13 @@ __global__ void inverse_iteration_kernel(const double *dg, const double *eg, con
   int r1 = r0 + 1;
   while (r1 < k && lam[r1 - 1] - lam[r1] <= gtol) ++r1;
   const T tiny = Lim<T>::eps() * fmax((T)tnorm, Lim<T>::tiny());
-  auto fix = [&](T x) -> T { return (x == (T)0) ? tiny : ((fabs(x) < tiny) ? copysign(tiny, x) : x); };
+  // pivots below tiny in magnitude (zero included) become +-tiny; integer compare
+  const long long tiny_bits = __double_as_longlong(tiny);
+  auto fix = [&](T x) -> T {
+    const long long xb = __double_as_longlong(x);
+    return ((xb & 0x7fffffffffffffffll) < tiny_bits) ? __longlong_as_double((xb & (long long)0x8000000000000000ull) | tiny_bits)
+                                                   : x;
+  };
   double prev = 0.0;
   for (int r = r0; r < r1; ++r) {
     // element i of array a of this thread's vector
@@ -712,52 +695,95 @@ __global__ void inverse_iteration_kernel(const double *dg, const double *eg, con
     }
     prev = lmd;
     const T lm = (T)lmd;
-    // LU of T - lm with row interchanges; a, b = current diagonal and super-diagonal
+    // LU of T - lm with row interchanges; a, b = current diagonal and super-diagonal.
+    // One reciprocal per step (of the pivot); U's super-diagonals are stored
+    // pre-scaled by it, so the backward sweep has one FMA on its chain.
     {
+      // chain per step: pivot choice (integer compare), reciprocal, one FMA;
+      // the block's d - lm, c b and a dn are formed beside it
       T a = d[0] - lm, b = e[0];
-      for (int i = 0; i < n - 1; ++i) {
-        const T c = e[i], dn = d[i + 1] - lm, bn = e[i + 1];   // e[n-1] = 0
-        T f, ddi, dui, du2i, an, bnx;
-        const bool sw = fabs(a) < fabs(c);
-        if (!sw) {
-          if (a == (T)0) a = tiny;
-          f = c / a; ddi = a; dui = b; du2i = 0; an = dn - f * b; bnx = bn;
-        } else {
-          f = a / c; ddi = c; dui = dn; du2i = bn; an = b - f * dn; bnx = -f * bn;
+      for (int i0 = 0; i0 < n - 1; i0 += 8) {
+        T dn8[8], c8[8], bn8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = min(i0 + u, n - 2);
+          dn8[u] = d[i + 1] - lm;
+          c8[u] = e[i];
+          bn8[u] = e[i + 1];   // e[n-1] = 0
         }
-        S(IV_DL, i) = f;
-        S(IV_RDD, i) = (T)1 / fix(ddi);
-        S(IV_DU, i) = dui;
-        S(IV_DU2, i) = du2i;
-        S(IV_PV, i) = sw ? (T)1 : (T)0;
-        a = an;
-        b = bnx;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u;
+          if (i < n - 1) {
+            const T c = c8[u], dn = dn8[u], bn = bn8[u];
+            const T cb = c * b, adn = a * dn;
+            const bool sw = abs_less(a, c);
+            const T piv = fix(sw ? c : a);
+            const T rp = recip_nr<1>(piv);   // 2^-46: ample for an iteration that refines itself
+            const T f = (sw ? a : c) * rp;
+            S(IV_DL, i) = f;
+            S(IV_RDD, i) = rp;
+            S(IV_DU, i) = (sw ? dn : b) * rp;
+            S(IV_DU2, i) = sw ? bn * rp : (T)0;
+            S(IV_PV, i) = sw ? (T)1 : (T)0;
+            const T an = sw ? fma(-adn, rp, b) : fma(-cb, rp, dn);
+            b = sw ? -f * bn : bn;
+            a = an;
+          }
+        }
       }
-      S(IV_RDD, n - 1) = (T)1 / fix(a);
+      S(IV_RDD, n - 1) = recip_nr<1>(fix(a));
       S(IV_DU, n - 1) = 0;
       S(IV_DU2, n - 1) = 0;
-      if (n >= 2) S(IV_DU2, n - 2) = 0;   // U has two super-diagonals above row n-3 only
     }
     for (int iter = 0; iter < 2; ++iter) {
-      // forward: apply L^-1 with the interchanges (the start vector on the first pass)
+      // forward: apply L^-1 with the interchanges (the start vector on the first
+      // pass).  Eight steps' factors and entries are loaded before the chain.
       T xc = (iter == 0) ? iv_start<T>(0, r) : XV(0);
-      for (int i = 0; i < n - 1; ++i) {
-        T xn = (iter == 0) ? iv_start<T>(i + 1, r) : XV(i + 1);
-        const T f = S(IV_DL, i);
-        T out;
-        if (S(IV_PV, i) == (T)0) { out = xc; xn = xn - f * xc; }
-        else { out = xn; xn = xc - f * xn; }
-        XV(i) = out;
-        xc = xn;
+      for (int i0 = 0; i0 < n - 1; i0 += 8) {
+        T f8[8], p8[8], x8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = min(i0 + u, n - 2);
+          f8[u] = S(IV_DL, i);
+          p8[u] = S(IV_PV, i);
+          x8[u] = (iter == 0) ? iv_start<T>(i + 1, r) : XV(i + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u;
+          if (i < n - 1) {
+            T xn = x8[u], out;
+            if (p8[u] == (T)0) { out = xc; xn = xn - f8[u] * xc; }
+            else { out = xn; xn = xc - f8[u] * xn; }
+            XV(i) = out;
+            xc = xn;
+          }
+        }
       }
       XV(n - 1) = xc;
-      // backward: U^-1
+      // backward: U^-1 (rows scaled by 1 / pivot), eight steps' data loaded first
       T x1 = 0, x2 = 0;
-      for (int i = n - 1; i >= 0; --i) {
-        const T sv = (XV(i) - S(IV_DU, i) * x1 - S(IV_DU2, i) * x2) * S(IV_RDD, i);
-        XV(i) = sv;
-        x2 = x1;
-        x1 = sv;
+      for (int i0 = n - 1; i0 >= 0; i0 -= 8) {
+        T du8[8], dv8[8], rd8[8], xv8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = max(i0 - u, 0);
+          du8[u] = S(IV_DU, i);
+          dv8[u] = S(IV_DU2, i);
+          rd8[u] = S(IV_RDD, i);
+          xv8[u] = XV(i);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 - u;
+          if (i >= 0) {
+            const T sv = fma(-du8[u], x1, fma(-dv8[u], x2, xv8[u] * rd8[u]));
+            XV(i) = sv;
+            x2 = x1;
+            x1 = sv;
+          }
+        }
       }
       // orthogonalise against the earlier vectors of this group (already in X)
       for (int q = r0; q < r; ++q) {
@@ -766,10 +792,14 @@ __global__ void inverse_iteration_kernel(const double *dg, const double *eg, con
         const T dt = (T)dot;
         for (int i = 0; i < n; ++i) XV(i) -= dt * X[(int64_t)i * k + q];
       }
-      T s0 = 0, s1 = 0;
-      for (int i = 0; i + 1 < n; i += 2) { s0 = fma(XV(i), XV(i), s0); s1 = fma(XV(i + 1), XV(i + 1), s1); }
-      if (n & 1) s0 = fma(XV(n - 1), XV(n - 1), s0);
-      const double nrm = sqrt((double)s0 + (double)s1);
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;   // four chains: FP64 FMA latency is long here
+      int i = 0;
+      for (; i + 3 < n; i += 4) {
+        s0 = fma(XV(i), XV(i), s0); s1 = fma(XV(i + 1), XV(i + 1), s1);
+        s2 = fma(XV(i + 2), XV(i + 2), s2); s3 = fma(XV(i + 3), XV(i + 3), s3);
+      }
+      for (; i < n; ++i) s0 = fma(XV(i), XV(i), s0);
+      const double nrm = sqrt((double)((s0 + s1) + (s2 + s3)));
       if (!(nrm > 0.0) || !isfinite(nrm)) { atomicExch(&flags[FLAG_EIG], 1); break; }
       const T inv = (T)(1.0 / nrm);
       if (SMEM && iter == 1) {
@@ -815,33 +845,40 @@ __global__ void sum_partials_kernel(const T *__restrict__ src, int nsplit, int64
   }
 }
 
-// T (nb x nb, row-major, upper) from G = V_b^T V_b and tau[j0..j0+nb).
+// T (row-major, upper, zero-padded to WY_NB x WY_NB) of reflector block b (one
+// CTA each) from G_b = V_b^T V_b (Gg + b*WY_NB^2, ld nb) and tau[j0..j0+nb),
+// j0 = b*WY_NB.
+// Column l: T[0:l, l] = -tau_l T[0:l, 0:l] G[0:l, l]; four threads share
+// each row's sum (shorter FMA chains).
 template <typename T>
-__global__ void wy_build_t_kernel(const T *__restrict__ Gg, const double *__restrict__ tau,
-                                  int j0, int nb, T *__restrict__ Tm) {
+__global__ void wy_build_t_kernel(const T *__restrict__ Gall, const double *__restrict__ tau, int nref,
+                                  T *__restrict__ Tall) {
   // dynamic: [2][WY_NB][WY_NB + 1] (over the static limit in FP64)
   extern __shared__ __align__(16) unsigned char wy_raw[];
   T (*sT)[WY_NB + 1] = reinterpret_cast<T (*)[WY_NB + 1]>(wy_raw);
-  T (*Gt)[WY_NB + 1] = sT + WY_NB;   // G transposed: the recurrence reads column l of G across threads
-  const int i = threadIdx.x;
+  T (*Gt)[WY_NB + 1] = sT + WY_NB;   // G transposed: column l of G is read along a row
+  const int j0 = blockIdx.x * WY_NB, nb = min(WY_NB, nref - j0);
+  const T *Gg = Gall + (int64_t)blockIdx.x * WY_NB * WY_NB;
+  T *Tm = Tall + (int64_t)blockIdx.x * WY_NB * WY_NB;
   for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) {
     sT[q / WY_NB][q % WY_NB] = 0;
     if (q < nb * nb) Gt[q % nb][q / nb] = Gg[q];
   }
   __syncthreads();
-  if (i < nb) sT[i][i] = (T)tau[j0 + i];
+  if (threadIdx.x < nb) sT[threadIdx.x][threadIdx.x] = (T)tau[j0 + threadIdx.x];
   __syncthreads();
+  const int i = threadIdx.x >> 2, part = threadIdx.x & 3;   // blockDim = 4 * WY_NB
   for (int l = 1; l < nb; ++l) {
     T v = 0;
-    if (i < l) {
-      for (int m = i; m < l; ++m) v += sT[i][m] * Gt[l][m];
-      v *= -(T)tau[j0 + l];
-    }
+    if (i < l)
+      for (int m = i + part; m < l; m += 4) v = fma(sT[i][m], Gt[l][m], v);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
     __syncthreads();
-    if (i < l) sT[i][l] = v;
+    if (i < l && part == 0) sT[i][l] = -(T)tau[j0 + l] * v;
     __syncthreads();
   }
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) Tm[q] = sT[q / nb][q % nb];
+  for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) Tm[q] = sT[q / WY_NB][q % WY_NB];   // zero-padded
 }
 
 // Ut[c][r] = X[r][c]
@@ -876,7 +913,7 @@ cudaError_t allow_max_dynamic_smem(const void *kernel, std::once_flag &flag) {
   });
   return result;
 }
-std::once_flag g_smem_hh[4], g_smem_bisect, g_smem_bisect32, g_smem_invit[4], g_smem_bounds, g_smem_wy[2];
+std::once_flag g_smem_hh[2], g_smem_bisect, g_smem_invit[2], g_smem_bounds, g_smem_wy;
 
 // Try the fused reduction in arithmetic T; false when it cannot be launched.
 template <typename T>
@@ -896,7 +933,7 @@ bool launch_fused(EigWork &w, int n, cudaStream_t s, int *launches, cudaError_t 
   const bool in_smem = s_rows + reserve <= (size_t)optin;
   const size_t smem = in_smem ? s_rows : s_vec;
   if (smem + reserve > (size_t)optin) return false;
-  const int fi = (sizeof(T) == 4 ? 2 : 0) + (in_smem ? 1 : 0);
+  const int fi = in_smem ? 1 : 0;
   const void *kern = in_smem ? (const void *)hh_fused_kernel<T, true> : (const void *)hh_fused_kernel<T, false>;
   int per_sm = 0;
   ok = allow_max_dynamic_smem(kern, g_smem_hh[fi]) == cudaSuccess &&
@@ -905,15 +942,7 @@ bool launch_fused(EigWork &w, int n, cudaStream_t s, int *launches, cudaError_t 
   if (!ok) return false;
   HhFusedArgs<T> g;
   g.A0 = w.A;
-  if (sizeof(T) == sizeof(double)) {
-    g.A = reinterpret_cast<T *>(w.A);       // reduced in place
-  } else {
-    g.A = reinterpret_cast<T *>(w.X);       // FP32 working copy (X is free until step 4)
-    if (!in_smem) {
-      to_f32_kernel<<<152 * 4, 256, 0, s>>>(w.A, reinterpret_cast<float *>(w.X), (int64_t)n * n);
-      *launches += 1;
-    }
-  }
+  g.A = w.A;   // reduced in place when the rows do not fit in shared memory
   g.V = reinterpret_cast<T *>(w.V);
   g.d = w.d; g.e = w.e; g.tau = w.tau;
   g.P = reinterpret_cast<T *>(w.grid_ws);
@@ -935,24 +964,19 @@ bool launch_fused(EigWork &w, int n, cudaStream_t s, int *launches, cudaError_t 
 template <typename T>
 cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, cudaStream_t s, int *launches) {
   const size_t smem = 2 * (size_t)n * sizeof(T);
-  const bool f32 = sizeof(T) == 4;
   {
-    cudaError_t e = allow_max_dynamic_smem(f32 ? (const void *)bisect32_kernel : (const void *)bisect_kernel,
-                                           f32 ? g_smem_bisect32 : g_smem_bisect);
+    cudaError_t e = allow_max_dynamic_smem((const void *)bisect_kernel, g_smem_bisect);
     if (e != cudaSuccess) return e;
-    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, true>, g_smem_invit[f32 ? 1 : 0]);
+    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, true>, g_smem_invit[0]);
     if (e != cudaSuccess) return e;
-    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, false>, g_smem_invit[f32 ? 3 : 2]);
+    e = allow_max_dynamic_smem((const void *)inverse_iteration_kernel<T, false>, g_smem_invit[1]);
     if (e != cudaSuccess) return e;
-    e = allow_max_dynamic_smem((const void *)wy_build_t_kernel<T>, g_smem_wy[f32 ? 1 : 0]);
+    e = allow_max_dynamic_smem((const void *)wy_build_t_kernel<T>, g_smem_wy);
     if (e != cudaSuccess) return e;
   }
-  if (f32) {
-    bisect32_kernel<<<(k + 3) / 4, 128, smem, s>>>(w.d, w.p, w.scal, n, k, w.lam);
-  } else {
+  {
     // one warp per block and at most 32 / BIS_L eigenvalues per warp, spread
-    // so that every SM gets work: the FP64 divisions of the Sturm counts are
-    // the cost on this part
+    // so that every SM gets work
     int dev = 0, nsm = 148;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       nsm = 148;
@@ -968,8 +992,17 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       optin = 48 * 1024;
     cudaGetLastError();
+    // shared-memory factors only when every vector then runs in one wave; FP64
+    // instructions cost a warp the same with 2 active lanes as with 32, so
+    // otherwise 32 vectors per warp with the factors in L2 is faster
     const size_t budget = (size_t)optin - 1024, per_thread = 6 * (size_t)n * sizeof(T);
-    const int tpb = smem + per_thread <= budget ? (int)std::min<size_t>(32, (budget - smem) / per_thread) : 0;
+    int tpb = smem + per_thread <= budget ? (int)std::min<size_t>(32, (budget - smem) / per_thread) : 0;
+    int nsm_iv = 148, dev_iv = 0;
+    if (cudaGetDevice(&dev_iv) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm_iv, cudaDevAttrMultiProcessorCount, dev_iv) != cudaSuccess)
+      nsm_iv = 148;
+    cudaGetLastError();
+    if (tpb >= 1 && (k + tpb - 1) / tpb > nsm_iv) tpb = 0;
     if (tpb >= 1)
       inverse_iteration_kernel<T, true><<<(k + tpb - 1) / tpb, tpb, smem + tpb * per_thread, s>>>(
           w.d, w.e, w.lam, w.scal, n, k, X, lu, flags);
@@ -979,18 +1012,28 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
   *launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // re-orthonormalise twice: G = X^T X, F = (3 - G)/2, X <- X F
+  // re-orthonormalise: G = X^T X, F = (3 - G)/2, X <- X F.  One pass squares
+  // the non-orthogonality inverse iteration leaves (about 1e-12 here).  X^T X
+  // is split over its length-n sum (partials in the free inverse-iteration
+  // scratch): a 64 x 64 FP64 tile over all n rows would keep one SM busy for
+  // milliseconds.
   T *G = lu;                       // k*k scratch (inverse-iteration scratch is free now)
   T *Xn = lu + (int64_t)k * k;     // n*k scratch
-  for (int pass = 0; pass < 2; ++pass) {
+  {
+    T *Gpart = Xn + (int64_t)n * k;
+    const int64_t room = 5 * (int64_t)n * n - (int64_t)k * k - (int64_t)n * k;
+    int nsp = (int)std::min<int64_t>((n + 63) / 64, std::max<int64_t>(1, room / ((int64_t)k * k)));
+    const int64_t ks = (n + nsp - 1) / nsp;
+    nsp = (int)((n + ks - 1) / ks);
     GemmArgs<T> g;
-    g.M = k; g.N = k; g.K = n;
+    g.M = k; g.N = k; g.K = n; g.ksplit = ks;
     g.A = X; g.lda = k;   // A[kidx][m] = X[i][m]  (M-major)
     g.B = X; g.ldb = k;   // B[kidx][n] = X[i][n]  (N-major)
-    g.C = G; g.ldc = k;
+    g.C = Gpart; g.ldc = k; g.strideC = (int64_t)k * k;
     g.syrk = 1;
-    e = launch_gemm<T>(g, 1, false, false, s);
+    e = launch_gemm<T>(g, nsp, false, false, s);
     if (e != cudaSuccess) return e;
+    sum_partials_kernel<T><<<152, 256, 0, s>>>(Gpart, nsp, (int64_t)k * k, (int64_t)k * k, G);
     lowdin_factor_kernel<T><<<152, 256, 0, s>>>(G, k);
     GemmArgs<T> h;
     h.M = n; h.N = k; h.K = k;
@@ -1001,53 +1044,73 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(X, Xn, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
-    *launches += 3;
+    *launches += 4;
   }
-  // compact-WY back-transformation, blocks of WY_NB reflectors from the last
+  // compact-WY back-transformation, blocks of WY_NB reflectors from the last:
+  // Y <- Y - M_b (V_b^T Y) with M_b = V_b T_b.  Every block's G, T and M_b are
+  // formed first (the T recurrences in one launch, all M_b in one batched
+  // GEMM over rows 1..n-1; V carries WY_NB zero rows past its end for the
+  // last block), then the blocks are applied in order: two GEMMs each.
   const int nref = n - 2;  // reflectors 0 .. n-3
-  T *Gp = reinterpret_cast<T *>(w.wy);                         // [nsplit][nb][nb]
-  const int nsplit_max = (int)((n + WY_KSPLIT - 1) / WY_KSPLIT);
-  T *W1p = Gp + (int64_t)nsplit_max * WY_NB * WY_NB;           // [nsplit][nb][k]
-  T *Gs = W1p + (int64_t)nsplit_max * WY_NB * k;               // [nb][nb]
-  T *W1 = Gs + WY_NB * WY_NB;                                  // [nb][k]
-  T *Tm = W1 + (int64_t)WY_NB * k;                             // [nb][nb]
-  T *W2 = Tm + WY_NB * WY_NB;                                  // [nb][k]
-  for (int j0 = ((nref - 1) / WY_NB) * WY_NB; nref > 0 && j0 >= 0; j0 -= WY_NB) {
-    const int nb = std::min(WY_NB, nref - j0);
-    const int r0 = j0 + 1;              // first row where this block's V is non-zero
-    const int64_t len = n - r0;
-    const int nsplit = (int)((len + WY_KSPLIT - 1) / WY_KSPLIT);
-    GemmArgs<T> g;                      // G partials = V_b V_b^T over row chunks
-    g.M = nb; g.N = nb; g.K = len; g.ksplit = WY_KSPLIT;
-    g.A = V + (int64_t)j0 * n + r0; g.lda = n;
-    g.B = V + (int64_t)j0 * n + r0; g.ldb = n;
-    g.C = Gp; g.ldc = nb; g.strideC = (int64_t)nb * nb;
-    e = launch_gemm<T>(g, nsplit, true, true, s);
-    if (e != cudaSuccess) return e;
-    GemmArgs<T> h;                      // W1 partials = V_b^T Y over row chunks
-    h.M = nb; h.N = k; h.K = len; h.ksplit = WY_KSPLIT;
-    h.A = V + (int64_t)j0 * n + r0; h.lda = n;
-    h.B = X + (int64_t)r0 * k; h.ldb = k;
-    h.C = W1p; h.ldc = k; h.strideC = (int64_t)nb * k;
-    e = launch_gemm<T>(h, nsplit, true, false, s);
-    if (e != cudaSuccess) return e;
-    sum_partials_kernel<T><<<64, 256, 0, s>>>(Gp, nsplit, (int64_t)nb * nb, (int64_t)nb * nb, Gs);
-    sum_partials_kernel<T><<<152, 256, 0, s>>>(W1p, nsplit, (int64_t)nb * k, (int64_t)nb * k, W1);
-    wy_build_t_kernel<T><<<1, WY_NB, 2 * WY_NB * (WY_NB + 1) * sizeof(T), s>>>(Gs, w.tau, j0, nb, Tm);
-    GemmArgs<T> t2;                     // W2 = T W1
-    t2.M = nb; t2.N = k; t2.K = nb;
-    t2.A = Tm; t2.lda = nb; t2.B = W1; t2.ldb = k; t2.C = W2; t2.ldc = k;
-    e = launch_gemm<T>(t2, 1, true, false, s);
-    if (e != cudaSuccess) return e;
-    GemmArgs<T> u;                      // Y[r0:, :] -= V_b^T W2
-    u.M = (int)len; u.N = k; u.K = nb;
-    u.A = V + (int64_t)j0 * n + r0; u.lda = n;   // A[kidx=i][m=r] = V[j0+i][r0+r]
-    u.B = W2; u.ldb = k;
-    u.C = X + (int64_t)r0 * k; u.ldc = k;
-    u.alpha = -1.0; u.beta = 1.0;
-    e = launch_gemm<T>(u, 1, false, false, s);
-    if (e != cudaSuccess) return e;
-    *launches += 7;
+  if (nref > 0) {
+    const int nblk = (nref + WY_NB - 1) / WY_NB;
+    const int nsplit_max = (int)((n + WY_KSPLIT - 1) / WY_KSPLIT);
+    T *Gp = reinterpret_cast<T *>(w.wy);                         // [nsplit][nb][nb], reused per block
+    T *W1p = Gp + (int64_t)nsplit_max * WY_NB * WY_NB;           // [nsplit][nb][k]
+    T *W1 = W1p + (int64_t)nsplit_max * WY_NB * k;               // [nb][k]
+    T *Gs = W1 + (int64_t)WY_NB * k;                             // [nblk][nb][nb]
+    T *Tm = Gs + (int64_t)nblk * WY_NB * WY_NB;                  // [nblk][WY_NB][WY_NB]
+    T *Mall = Tm + (int64_t)nblk * WY_NB * WY_NB;                // [nblk][n-1][WY_NB]
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int j0 = bi * WY_NB, nb = std::min(WY_NB, nref - j0);
+      const int r0 = j0 + 1;              // first row where this block's V is non-zero
+      const int64_t len = n - r0;
+      const int nsplit = (int)((len + WY_KSPLIT - 1) / WY_KSPLIT);
+      GemmArgs<T> g;                      // G partials = V_b V_b^T over row chunks
+      g.M = nb; g.N = nb; g.K = len; g.ksplit = WY_KSPLIT;
+      g.A = V + (int64_t)j0 * n + r0; g.lda = n;
+      g.B = V + (int64_t)j0 * n + r0; g.ldb = n;
+      g.C = Gp; g.ldc = nb; g.strideC = (int64_t)nb * nb;
+      e = launch_gemm<T>(g, nsplit, true, true, s);
+      if (e != cudaSuccess) return e;
+      sum_partials_kernel<T><<<64, 256, 0, s>>>(Gp, nsplit, (int64_t)nb * nb, (int64_t)nb * nb,
+                                                Gs + (int64_t)bi * WY_NB * WY_NB);
+      *launches += 2;
+    }
+    wy_build_t_kernel<T><<<nblk, 4 * WY_NB, 2 * WY_NB * (WY_NB + 1) * sizeof(T), s>>>(Gs, w.tau, nref, Tm);
+    {
+      GemmArgs<T> m;                      // M_b[r-1][c] = sum_i V[j0+i][r] T_b[i][c], r = 1..n-1
+      m.M = n - 1; m.N = WY_NB; m.K = WY_NB;
+      m.A = V + 1; m.lda = n; m.strideA = (int64_t)WY_NB * n;        // A[kidx=i][m] = V[j0+i][1+m]
+      m.B = Tm; m.ldb = WY_NB; m.strideB = (int64_t)WY_NB * WY_NB;
+      m.C = Mall; m.ldc = WY_NB; m.strideC = (int64_t)(n - 1) * WY_NB;
+      e = launch_gemm<T>(m, nblk, false, false, s);
+      if (e != cudaSuccess) return e;
+    }
+    *launches += 2;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+      const int j0 = bi * WY_NB, nb = std::min(WY_NB, nref - j0);
+      const int r0 = j0 + 1;
+      const int64_t len = n - r0;
+      const int nsplit = (int)((len + WY_KSPLIT - 1) / WY_KSPLIT);
+      GemmArgs<T> h;                      // W1 partials = V_b^T Y over row chunks
+      h.M = nb; h.N = k; h.K = len; h.ksplit = WY_KSPLIT;
+      h.A = V + (int64_t)j0 * n + r0; h.lda = n;
+      h.B = X + (int64_t)r0 * k; h.ldb = k;
+      h.C = W1p; h.ldc = k; h.strideC = (int64_t)nb * k;
+      e = launch_gemm<T>(h, nsplit, true, false, s);
+      if (e != cudaSuccess) return e;
+      sum_partials_kernel<T><<<152, 256, 0, s>>>(W1p, nsplit, (int64_t)nb * k, (int64_t)nb * k, W1);
+      GemmArgs<T> u;                      // Y[r0:, :] -= M_b[r0:, 0:nb] W1
+      u.M = (int)len; u.N = k; u.K = nb;
+      u.A = Mall + (int64_t)bi * (n - 1) * WY_NB + (int64_t)(r0 - 1) * WY_NB; u.lda = WY_NB;   // K-major
+      u.B = W1; u.ldb = k;
+      u.C = X + (int64_t)r0 * k; u.ldc = k;
+      u.alpha = -1.0; u.beta = 1.0;
+      e = launch_gemm<T>(u, 1, true, false, s);
+      if (e != cudaSuccess) return e;
+      *launches += 3;
+    }
   }
   dim3 tb(32, 8), tg((k + 31) / 32, (n + 31) / 32);
   transpose_kernel<T><<<tg, tb, 0, s>>>(X, n, k, Ut);
@@ -1057,14 +1120,9 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
 
 }  // namespace
 
-cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches, bool *f32) {
+cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches) {
   cudaError_t e = cudaSuccess;
-  bool fused = false;
-  if (*f32) fused = launch_fused<float>(w, n, s, launches, &e);
-  if (!fused) {
-    *f32 = false;
-    fused = launch_fused<double>(w, n, s, launches, &e);
-  }
+  const bool fused = launch_fused<double>(w, n, s, launches, &e);
   if (e != cudaSuccess) return e;
   if (!fused) {
     for (int k = 0; k + 2 < n; ++k) {
@@ -1090,17 +1148,16 @@ cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s,
     const bool staged = st <= 180 * 1024 &&
                         allow_max_dynamic_smem((const void *)tridiag_bounds_kernel, g_smem_bounds) == cudaSuccess;
     cudaGetLastError();
-    tridiag_bounds_kernel<<<1, RB, staged ? st : 0, s>>>(w.d, w.e, n, thresh, w.scal, w.p, w.count, *f32, staged);
+    tridiag_bounds_kernel<<<1, RB, staged ? st : 0, s>>>(w.d, w.e, n, thresh, w.scal, w.p, w.count, staged);
   }
   *launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags, cudaStream_t s,
-                               int *launches, bool f32) {
+                               int *launches) {
   if (k <= 0) return cudaSuccess;
-  return f32 ? eig_vectors_impl<float>(w, n, k, Ut, flags, s, launches)
-             : eig_vectors_impl<double>(w, n, k, Ut, flags, s, launches);
+  return eig_vectors_impl<double>(w, n, k, Ut, flags, s, launches);
 }
 
 }  // namespace ltgw

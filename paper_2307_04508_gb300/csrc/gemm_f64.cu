@@ -10,9 +10,7 @@
 //
 // GB300's FP64 rate is about 2 DFMA per clock per SM, so a 64x64 tile with a
 // 4x4 register micro-tile per thread keeps the FP64 pipe saturated with
-// ~0.5 B/clk/SM of global traffic; the tiles stay simple on purpose.  The
-// plain GEMM / SYRK is also instantiated in FP32 for the mixed-precision
-// eigensolver's small contractions.
+// ~0.5 B/clk/SM of global traffic; the tiles stay simple on purpose.
 #include <math.h>
 
 #include "common.cuh"
@@ -215,7 +213,6 @@ cudaError_t launch_gemm(const GemmArgs<T> &g, int batch, bool a_kmaj, bool b_kma
   return cudaGetLastError();
 }
 template cudaError_t launch_gemm<double>(const GemmArgs<double> &, int, bool, bool, cudaStream_t);
-template cudaError_t launch_gemm<float>(const GemmArgs<float> &, int, bool, bool, cudaStream_t);
 
 cudaError_t launch_gemm_coldot(const ColDotArgs &g, int n_batch, cudaStream_t s) {
   if (g.N <= 0 || g.ncols <= 0 || g.n_tgt <= 0 || n_batch <= 0) return cudaSuccess;

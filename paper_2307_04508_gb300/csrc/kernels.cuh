@@ -29,8 +29,7 @@ struct GemmArgs {
   int64_t ksplit = 0;     // > 0: batch index b covers k in [b*ksplit, (b+1)*ksplit), C_b at b*strideC
 };
 using GemmF64Args = GemmArgs<double>;
-using GemmF32Args = GemmArgs<float>;
-// Tiled GEMM / SYRK on the CUDA cores, FP64 or FP32 (no pair scale in FP32).
+// Tiled GEMM / SYRK on the CUDA cores (instantiated in FP64).
 template <typename T>
 cudaError_t launch_gemm(const GemmArgs<T> &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s);
 inline cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s) {
@@ -64,16 +63,15 @@ cudaError_t launch_copy_cols(const double *src, int64_t lds, int64_t c0, double 
 cudaError_t launch_screen(const double *Pi, int N, int n_omega, double *X0, double *X1,
                           double *C, int *flags, cudaStream_t s, int *launches);
 
-// Blocked form: work = screen_blocked_scratch(N, n_omega) doubles; f32 runs
-// the sweep in FP32 (the work buffer then holds floats).
+// Blocked form: work = screen_blocked_scratch(N, n_omega) doubles.
 size_t screen_blocked_scratch(int N, int n_omega);
 cudaError_t launch_screen_blocked(const double *Pi, int N, int n_omega, double *work, double *C, int *flags,
-                                  cudaStream_t s, int *launches, bool f32 = false);
+                                  cudaStream_t s, int *launches);
 
 // ---- eigensolver (eig.cu) ----
 struct EigWork {
   double *A = nullptr;      // [n][n] symmetric in, destroyed
-  double *V = nullptr;      // [n][n] Householder vectors (row k = v_k)
+  double *V = nullptr;      // [n + 64][n] Householder vectors (row k = v_k; rows >= n-2 zero)
   double *d = nullptr, *e = nullptr, *tau = nullptr;  // [n]
   double *p = nullptr, *w = nullptr;                  // [n] symv / update vectors
   double *scal = nullptr;                             // [8]
@@ -86,15 +84,11 @@ struct EigWork {
   int *flags = nullptr;                               // device error flags
 };
 // Tridiagonalise A, count eigenvalues > thresh (returned through count[0]).
-// V must be zeroed by the caller before the call.  *f32 asks for the FP32
-// form of the reduction (mixed precision); it is cleared when that form
-// cannot run and the FP64 form was used instead.  In the FP32 form V, X, lu
-// and wy hold floats (in the same buffers).
-cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches, bool *f32);
-// Eigenvalues (descending) and eigenvectors for the k largest, Ut = rows [k][n];
-// f32 as returned by launch_eig_tridiag.
+// V must be zeroed by the caller before the call.
+cudaError_t launch_eig_tridiag(EigWork &w, int n, double thresh, cudaStream_t s, int *launches);
+// Eigenvalues (descending) and eigenvectors for the k largest, Ut = rows [k][n].
 cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
-                               cudaStream_t s, int *launches, bool f32);
+                               cudaStream_t s, int *launches);
 
 // ---- split-BF16 tensor-core contraction (tc_gemm.cu) ----
 // D_t = A diag(s_t) B^T for t < n_t; A [*][Kp], B [*][Kp], scale [n_t][Kp] FP32,

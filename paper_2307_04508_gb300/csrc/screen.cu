@@ -8,8 +8,7 @@
 //    between two buffers (first step forms A = 1 - Pi, last writes C = -X - 1);
 //  * launch_screen_blocked: pivot blocks of 64 - the block is inverted in
 //    shared memory, and the rank-64 update A -= A[:,P] A_PP^-1 A[P,:] runs on
-//    the tiled GEMM (about N/64 x 5 launches instead of N), in FP64 or, for
-//    the mixed form, FP32.
+//    the FP64 tiled GEMM (about N/64 x 5 launches instead of N).
 #include <math.h>
 
 #include <algorithm>
@@ -59,8 +58,6 @@ __global__ void __launch_bounds__(256) sweep_step_kernel(const double *__restric
 }
 
 // ---- blocked sweep: pivot blocks of SB_B, rank-SB_B updates on the tiled GEMM ----
-// Instantiated in FP64 (the plain form) and FP32 (the mixed form: 1 - Pi has
-// every eigenvalue >= 1, so the FP32 inverse keeps its ~1e-7 relative accuracy).
 constexpr int SB_B = 64;
 
 // X = I - Pi
@@ -92,26 +89,36 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(const T *__restrict_
     v[c] = (i < bs && j < bs) ? Xb[(int64_t)(p0 + i) * N + (p0 + j)] : (T)0;
   }
   for (int k = 0; k < bs; ++k) {
+    // publish column k and row k scaled by the pivot's reciprocal (computed
+    // once, by the pivot's owner), so each update below is one FMA
+    bool own = false;
+    T piv = 0;
 #pragma unroll
-    for (int c = 0; c < PER; ++c) {
+    for (int c = 0; c < PER; ++c) {   // constant indices keep v[] in registers
       const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
       if (j == k && i < bs) colk[i] = v[c];
-      if (i == k && j < bs) rowk[j] = v[c];
-      if (i == k && j == k) {   // one reciprocal per pivot
-        if (!(v[c] > (T)0 && isfinite(v[c]))) atomicExch(&flags[FLAG_NOT_SPD], 1);
-        s_rp = (T)1 / v[c];
-      }
+      if (i == k && j == k) { own = true; piv = v[c]; }
+    }
+    if (own) {
+      if (!(piv > (T)0 && isfinite(piv))) atomicExch(&flags[FLAG_NOT_SPD], 1);
+      s_rp = (T)1 / piv;
     }
     __syncthreads();
     const T rp = s_rp;
 #pragma unroll
     for (int c = 0; c < PER; ++c) {
       const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
+      if (i == k && j < bs) rowk[j] = v[c] * rp;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < PER; ++c) {
+      const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
       if (i >= bs || j >= bs) continue;
       if (i == k && j == k) v[c] = -rp;
-      else if (i == k) v[c] = rowk[j] * rp;
+      else if (i == k) v[c] = rowk[j];
       else if (j == k) v[c] = colk[i] * rp;
-      else v[c] = v[c] - colk[i] * rowk[j] * rp;
+      else v[c] = fma(-colk[i], rowk[j], v[c]);
     }
     __syncthreads();
   }
@@ -184,8 +191,8 @@ cudaError_t screen_blocked_impl(const double *Pi, int N, int n_omega, T *work, d
     g.C = R; g.ldc = SB_B; g.strideC = (int64_t)N * SB_B;
     cudaError_t e = launch_gemm<T>(g, n_omega, true, false, s);
     if (e != cudaSuccess) return e;
-    GemmArgs<T> u;   // X -= R X[P, :]
-    u.M = N; u.N = N; u.K = bs;
+    GemmArgs<T> u;   // X -= R X[P, :]  (= X[:, P] Z X[P, :], symmetric: lower tiles, mirrored)
+    u.M = N; u.N = N; u.K = bs; u.syrk = 1;
     u.A = R; u.lda = SB_B; u.strideA = (int64_t)N * SB_B;
     u.B = rowsP; u.ldb = N; u.strideB = (int64_t)SB_B * N;
     u.C = X; u.ldc = N; u.strideC = NN;
@@ -232,10 +239,9 @@ size_t screen_blocked_scratch(int N, int n_omega) {
 }
 
 cudaError_t launch_screen_blocked(const double *Pi, int N, int n_omega, double *work, double *C, int *flags,
-                                  cudaStream_t s, int *launches, bool f32) {
+                                  cudaStream_t s, int *launches) {
   if (N <= 0 || n_omega <= 0) return cudaSuccess;
-  return f32 ? screen_blocked_impl<float>(Pi, N, n_omega, reinterpret_cast<float *>(work), C, flags, s, launches)
-             : screen_blocked_impl<double>(Pi, N, n_omega, work, C, flags, s, launches);
+  return screen_blocked_impl<double>(Pi, N, n_omega, work, C, flags, s, launches);
 }
 
 }  // namespace ltgw

@@ -55,7 +55,7 @@ def test_naf_basis_paths(ctx, mixed, n):
     U = Ut[:k].cpu().numpy().T
     lg = lam[:k].cpu().numpy()
     lmax = lam_all.max()
-    # FP32 reduction of a split-BF16 metric: errors of a few 1e-6 * lambda_max
+    # the mixed form builds K from split-BF16 products: errors of a few 1e-6 * lambda_max
     tol_lam, tol_res, tol_orth = (2e-5, 2e-5, 1e-5) if mixed else (1e-13, 1e-12, 1e-12)
     assert np.all(np.diff(lg) <= 0.0), "eigenvalues must come out descending"
     assert np.abs(lg - lam_kept[::-1]).max() <= tol_lam * lmax
