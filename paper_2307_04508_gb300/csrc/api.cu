@@ -343,10 +343,13 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   std::vector<int> tindex;
   std::vector<int> tiles = lower_tiles(nI, &tindex);
   float *Af = nullptr, *scale;
+  __nv_bfloat16 *Bhi, *Blo;   // the unscaled operand, pre-split for the TMA-fed kernel
   int *d_tindex;
   auto layout = [&](Arena &A) {
     Af = Af_in ? nullptr : A.take<float>((size_t)Mp * Kp);
     scale = A.take<float>((size_t)n_t * Kp);
+    Bhi = A.take<__nv_bfloat16>((size_t)Mp * Kp);
+    Blo = A.take<__nv_bfloat16>((size_t)Mp * Kp);
     d_tindex = A.take<int>(tindex.size());
   };
   ctx->a5.begin_sizing();
@@ -358,8 +361,10 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   if (!Af_in) CHECK_LAUNCH(ctx, launch_to_f32_padded(Bt, ldb, N, n_pairs, Af, Mp, Kp, s), 1);
   CHECK_LAUNCH(ctx, launch_scale_table(delta, n_pairs, Kp, n_t, n_tau ? d_x : d_omega, n_tau ? d_w : nullptr,
                                        n_tau ? SCALE_LAPLACE : SCALE_DIRECT, scale, s), 1);
+  CHECK_LAUNCH(ctx, launch_split_bf16(A, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
   TcGemmArgs g;
   g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.n_t = n_t; g.nt_group = 4;
+  g.B_hi = Bhi; g.B_lo = Blo; g.rows_a = Mp; g.rows_b = Mp;
   TcRun run;
   ctx->mark(EV_PI0, s);
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();

@@ -3,6 +3,8 @@
 // synchronises.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,8 +117,14 @@ struct TcGemmArgs {
   int n_tile_rows = 0, cd_cols_p = 0;
   float *cd_out = nullptr;
   int *err = nullptr;
+  // Pre-split B (BF16 hi and lo, row-major [rows_b][Kp]) selects the TMA-fed
+  // kernel: operands arrive by tiled bulk copies (not for TC_OUT_COLDOT or A groups).
+  const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
+  int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
 };
 cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s);
+// hi = bf16(x), lo = bf16(x - hi) elementwise: the split the tensor-core kernels use.
+cudaError_t launch_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t n, cudaStream_t s);
 size_t tc_gemm_smem_bytes();
 
 // ---- mixed-precision helpers (mixed.cu) ----

@@ -6,6 +6,10 @@
 
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -225,6 +229,26 @@ cudaError_t launch_tc_reduce_coldot(const float *cd_out, int splits, int groups,
   if (bx > 64) bx = 64;
   dim3 grid(bx, groups);
   tc_reduce_coldot_kernel<<<grid, 256, 0, s>>>(cd_out, splits, groups, n_tile_rows, cols_p, cols, W, ldw);
+  return cudaGetLastError();
+}
+
+
+namespace {
+__global__ void split_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+}  // namespace
+
+cudaError_t launch_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  split_bf16_kernel<<<(int)blocks, 256, 0, s>>>(x, hi, lo, n);
   return cudaGetLastError();
 }
 

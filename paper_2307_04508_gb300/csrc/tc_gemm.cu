@@ -24,6 +24,7 @@
 //   warps 17-20  epilogue: tcgen05.ld of the accumulators, FP64 partial sums
 // Every mbarrier wait is bounded (about two seconds of wall time); on expiry
 // the CTA records an error flag and unwinds.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stddef.h>
 
@@ -80,7 +81,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
 
 // Bounded wait for the phase with the given parity; false on time-out (or, when
 // honor_abort, as soon as another role of the CTA has given up).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Bars *bars, int *err,
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *abort, int *err,
                                           bool honor_abort = true) {
   uint32_t done = 0;
   uint64_t t0 = 0;
@@ -92,12 +93,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Bars *ba
         : "memory");
     if (done) return true;
     if ((it & 1023) == 0) {
-      if (honor_abort && *(volatile int *)&bars->abort) return false;
+      if (honor_abort && *(volatile int *)abort) return false;
       uint64_t t = globaltimer();
       if (it == 0) t0 = t;
       else if (t - t0 > 2000000000ull) {
         atomicExch(&err[FLAG_TC_TIMEOUT], 1);
-        *(volatile int *)&bars->abort = 1;
+        *(volatile int *)abort = 1;
         return false;
       }
     }
@@ -159,12 +160,139 @@ __device__ __forceinline__ void load8(const float *p, float v[8]) {
   v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
+// ---- roles shared by both kernels ----
+
+// MMA issue (one thread): per K-chunk, the B stage then nt A stages, three
+// products each (hi*hi, hi*lo, lo*hi); the TMEM accumulators are drained every
+// chunks_per_drain chunks.
+template <int NSA, int NSB>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, const uint8_t *sA, const uint8_t *sB, uint64_t *a_full, uint64_t *a_empty,
+                          uint64_t *b_full, uint64_t *b_empty, uint64_t *acc_full, uint64_t *acc_empty,
+                          uint64_t *fin, int nchunks, int chunks_per_drain, int ndrains, int nt, int *abort,
+                          int *err) {
+  int ia = 0, ib = 0;
+  uint32_t pa = 0, pb = 0;
+  bool ok = true;
+  for (int dr = 0; dr < ndrains && ok; ++dr) {
+    ok = mbar_wait(acc_empty, (dr & 1) ^ 1, abort, err);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
+    for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
+      ok = mbar_wait(&b_full[ib], pb, abort, err);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t bhi = smem_u32(sB + ib * B_STAGE), blo = bhi + B_BYTES;
+      for (int t = 0; t < nt; ++t) {
+        ok = mbar_wait(&a_full[ia], pa, abort, err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ahi = smem_u32(sA + ia * A_STAGE), alo = ahi + A_BYTES;
+        const uint32_t d = tmem + (uint32_t)(t * TN);
+#pragma unroll
+        for (int kk = 0; kk < TK / 16; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint32_t first = (c == dr * chunks_per_drain && kk == 0) ? 0u : 1u;
+          mma_bf16(d, make_desc(ahi + off), make_desc(bhi + off), first);
+          mma_bf16(d, make_desc(ahi + off), make_desc(blo + off), 1u);
+          mma_bf16(d, make_desc(alo + off), make_desc(bhi + off), 1u);
+        }
+        mma_commit(&a_empty[ia]);
+        if (++ia == NSA) { ia = 0; pa ^= 1; }
+      }
+      mma_commit(&b_empty[ib]);
+      if (++ib == NSB) { ib = 0; pb ^= 1; }
+    }
+    if (ok) mma_commit(acc_full);
+  }
+  // all issued MMAs complete before the CTA tears down
+  mma_commit(fin);
+  mbar_wait(fin, 0, abort, err, false);
+}
+
+// Epilogue (EPI_WARPS warps): tcgen05.ld of the accumulators after each drain
+// window, into FP64 / FP32 partial tiles or the column-dot reduction.
+__device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tmem, uint64_t *acc_full, uint64_t *acc_empty,
+                               int *abort, int ndrains, int nt, int tile, int grp, int split, int ti, int tj,
+                               float (*cd_red)[TN]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ew = warp & 3;                   // TMEM lane quarter this warp may read
+  const int row = ew * 32 + lane;
+  const int64_t tile_elems = (int64_t)TM * TN;
+  const int64_t base = (((int64_t)split * gridDim.y + grp) * MAXT * gridDim.x + tile) * tile_elems;
+  const int64_t tstride = (int64_t)gridDim.x * tile_elems;   // between scales
+  for (int dr = 0; dr < ndrains; ++dr) {
+    if (!mbar_wait(acc_full, dr & 1, abort, g.err)) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    for (int t = 0; t < nt; ++t) {
+      for (int h = 0; h < TN / 32; ++h) {
+        uint32_t r[32];
+        const uint32_t a = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(t * TN + h * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+              "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(a));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (g.out_mode == TC_OUT_F64) {
+          double *oh = g.partial + base + t * tstride + (int64_t)row * TN + h * 32;
+          if (dr == 0) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 2)
+              *reinterpret_cast<double2 *>(oh + q) =
+                  make_double2((double)__uint_as_float(r[q]), (double)__uint_as_float(r[q + 1]));
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; q += 2) {
+              double2 v = *reinterpret_cast<double2 *>(oh + q);
+              v.x += (double)__uint_as_float(r[q]);
+              v.y += (double)__uint_as_float(r[q + 1]);
+              *reinterpret_cast<double2 *>(oh + q) = v;
+            }
+          }
+        } else if (g.out_mode == TC_OUT_F32) {
+          float *oh = g.partial32 + base + t * tstride + (int64_t)row * TN + h * 32;
+#pragma unroll
+          for (int q = 0; q < 32; q += 4)
+            *reinterpret_cast<uint4 *>(oh + q) = make_uint4(r[q], r[q + 1], r[q + 2], r[q + 3]);
+        } else {
+          // column dot: D[row][col] * cd_B[col][row], summed over the 128 rows
+          const int grow = ti * TM + row;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int col = tj * TN + h * 32 + q;
+            float prod = 0.0f;
+            if (grow < g.cd_rows && col < g.cd_cols)
+              prod = __uint_as_float(r[q]) * (float)g.cd_B[(int64_t)col * g.cd_ld + grow];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) prod += __shfl_xor_sync(0xffffffffu, prod, o);
+            if (lane == 0) cd_red[ew][h * 32 + q] = prod;
+          }
+        }
+      }
+    }
+    if (g.out_mode == TC_OUT_COLDOT) {
+      asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI_WARPS) : "memory");   // epilogue warps only
+      if (row < TN) {
+        const float v = cd_red[0][row] + cd_red[1][row] + cd_red[2][row] + cd_red[3][row];
+        g.cd_out[(((int64_t)split * gridDim.y + grp) * g.n_tile_rows + ti) * g.cd_cols_p + tj * TN + row] = v;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    mbar_arrive(acc_empty);
+  }
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;                       // SA stages of [hi | lo]
   uint8_t *sB = smem + SA * A_STAGE;        // SB stages of [hi | lo]
   __shared__ __align__(16) Bars bars;
+  __shared__ float cd_red[EPI_WARPS][TN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x, grp = blockIdx.y, split = blockIdx.z;
@@ -199,46 +327,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
   const uint32_t tmem = bars.tmem_base;
 
   if (warp == 0) {
-    // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      int ia = 0, ib = 0;
-      uint32_t pa = 0, pb = 0;
-      bool ok = true;
-      for (int dr = 0; dr < ndrains && ok; ++dr) {
-        ok = mbar_wait(&bars.acc_empty, (dr & 1) ^ 1, &bars, g.err);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
-        for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
-          ok = mbar_wait(&bars.b_full[ib], pb, &bars, g.err);
-          if (!ok) break;
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t bhi = smem_u32(sB + ib * B_STAGE), blo = bhi + B_BYTES;
-          for (int t = 0; t < nt; ++t) {
-            ok = mbar_wait(&bars.a_full[ia], pa, &bars, g.err);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t ahi = smem_u32(sA + ia * A_STAGE), alo = ahi + A_BYTES;
-            const uint32_t d = tmem + (uint32_t)(t * TN);
-#pragma unroll
-            for (int kk = 0; kk < TK / 16; ++kk) {
-              const uint32_t off = kk * 32;
-              const uint32_t first = (c == dr * chunks_per_drain && kk == 0) ? 0u : 1u;
-              mma_bf16(d, make_desc(ahi + off), make_desc(bhi + off), first);
-              mma_bf16(d, make_desc(ahi + off), make_desc(blo + off), 1u);
-              mma_bf16(d, make_desc(alo + off), make_desc(bhi + off), 1u);
-            }
-            mma_commit(&bars.a_empty[ia]);
-            if (++ia == SA) { ia = 0; pa ^= 1; }
-          }
-          mma_commit(&bars.b_empty[ib]);
-          if (++ib == SB) { ib = 0; pb ^= 1; }
-        }
-        if (ok) mma_commit(&bars.acc_full);
-      }
-      // all issued MMAs complete before the CTA tears down
-      mma_commit(&bars.fin);
-      mbar_wait(&bars.fin, 0, &bars, g.err, false);
-    }
+    if (lane == 0)
+      mma_issue<SA, SB>(tmem, sA, sB, bars.a_full, bars.a_empty, bars.b_full, bars.b_empty, &bars.acc_full,
+                        &bars.acc_empty, &bars.fin, nchunks, chunks_per_drain, ndrains, nt, &bars.abort, g.err);
     __syncwarp();
   } else if (warp <= CONV_WARPS) {
     // ---------------------------------------------------------------- converters
@@ -286,7 +377,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
         load8(Br1 + k0 + TK, m1);
         snext = st_live ? __ldg(Sg + k0 + TK) : 0.0f;
       }
-      if (!mbar_wait(&bars.b_empty[ib], pb ^ 1, &bars, g.err)) break;
+      if (!mbar_wait(&bars.b_empty[ib], pb ^ 1, &bars.abort, g.err)) break;
       {
         uint8_t *hi = sB + ib * B_STAGE;
         split_store(b0, hi + o0, hi + B_BYTES + o0);
@@ -296,7 +387,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars.b_full[ib]);
       if (++ib == SB) { ib = 0; pb ^= 1; }
-      if (!mbar_wait(&bars.s_full[sb], (c >> 1) & 1, &bars, g.err)) break;
+      if (!mbar_wait(&bars.s_full[sb], (c >> 1) & 1, &bars.abort, g.err)) break;
       for (int t = 0; t < nt; ++t) {
         float sc[8], v0[8], v1[8];
         {
@@ -307,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) { v0[q] = a0[q] * sc[q]; v1[q] = a1[q] * sc[q]; }
-        if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars, g.err)) { ok = false; break; }
+        if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars.abort, g.err)) { ok = false; break; }
         uint8_t *hi = sA + ia * A_STAGE;
         split_store(v0, hi + o0, hi + A_BYTES + o0);
         split_store(v1, hi + o1, hi + A_BYTES + o1);
@@ -321,84 +412,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
       if (lane == 0) mbar_arrive(&bars.s_empty[sb]);   // this warp is done with chunk c's scales
       if (c + 1 < nchunks && st_writer) {              // publish chunk c+1's scales
         const int nbuf = (c + 1) & 1;
-        if (!mbar_wait(&bars.s_empty[nbuf], (((c + 1) >> 1) & 1) ^ 1, &bars, g.err)) break;
+        if (!mbar_wait(&bars.s_empty[nbuf], (((c + 1) >> 1) & 1) ^ 1, &bars.abort, g.err)) break;
         bars.scale[nbuf][st_t][st_k] = snext;
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars.s_full[nbuf]);
       }
     }
   } else {
-    // ---------------------------------------------------------------- epilogue
-    const int ew = warp & 3;                   // TMEM lane quarter this warp may read
-    const int row = ew * 32 + lane;
-    const int64_t tile_elems = (int64_t)TM * TN;
-    const int64_t base = (((int64_t)split * gridDim.y + grp) * MAXT * gridDim.x + tile) * tile_elems;
-    const int64_t tstride = (int64_t)gridDim.x * tile_elems;   // between scales
-    __shared__ float cd_red[EPI_WARPS][TN];
-    for (int dr = 0; dr < ndrains; ++dr) {
-      if (!mbar_wait(&bars.acc_full, dr & 1, &bars, g.err)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int t = 0; t < nt; ++t) {
-        for (int h = 0; h < TN / 32; ++h) {
-          uint32_t r[32];
-          const uint32_t a = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(t * TN + h * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-              : "r"(a));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (g.out_mode == TC_OUT_F64) {
-            double *oh = g.partial + base + t * tstride + (int64_t)row * TN + h * 32;
-            if (dr == 0) {
-#pragma unroll
-              for (int q = 0; q < 32; q += 2)
-                *reinterpret_cast<double2 *>(oh + q) =
-                    make_double2((double)__uint_as_float(r[q]), (double)__uint_as_float(r[q + 1]));
-            } else {
-#pragma unroll
-              for (int q = 0; q < 32; q += 2) {
-                double2 v = *reinterpret_cast<double2 *>(oh + q);
-                v.x += (double)__uint_as_float(r[q]);
-                v.y += (double)__uint_as_float(r[q + 1]);
-                *reinterpret_cast<double2 *>(oh + q) = v;
-              }
-            }
-          } else if (g.out_mode == TC_OUT_F32) {
-            float *oh = g.partial32 + base + t * tstride + (int64_t)row * TN + h * 32;
-#pragma unroll
-            for (int q = 0; q < 32; q += 4)
-              *reinterpret_cast<uint4 *>(oh + q) = make_uint4(r[q], r[q + 1], r[q + 2], r[q + 3]);
-          } else {
-            // column dot: D[row][col] * cd_B[col][row], summed over the 128 rows
-            const int grow = ti * TM + row;
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              const int col = tj * TN + h * 32 + q;
-              float prod = 0.0f;
-              if (grow < g.cd_rows && col < g.cd_cols)
-                prod = __uint_as_float(r[q]) * (float)g.cd_B[(int64_t)col * g.cd_ld + grow];
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) prod += __shfl_xor_sync(0xffffffffu, prod, o);
-              if (lane == 0) cd_red[ew][h * 32 + q] = prod;
-            }
-          }
-        }
-      }
-      if (g.out_mode == TC_OUT_COLDOT) {
-        asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI_WARPS) : "memory");   // epilogue warps only
-        if (row < TN) {
-          const float v = cd_red[0][row] + cd_red[1][row] + cd_red[2][row] + cd_red[3][row];
-          g.cd_out[(((int64_t)split * gridDim.y + grp) * g.n_tile_rows + ti) * g.cd_cols_p + tj * TN + row] = v;
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      mbar_arrive(&bars.acc_empty);
-    }
+    epilogue_drain(g, tmem, &bars.acc_full, &bars.acc_empty, &bars.abort, ndrains, nt, tile, grp, split, ti, tj,
+                   cd_red);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -408,14 +430,251 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
   }
 }
 
+// ---- the same contraction with the operands brought in by TMA ----
+// B arrives pre-split (BF16 hi and lo arrays, row-major [rows][Kp]) as two
+// tiled TMA copies per chunk with the 128-byte swizzle the tensor core reads,
+// so no thread touches it.  A arrives as FP32 tiles in a staging ring (one
+// tiled TMA copy, plus the chunk's scale rows as bulk copies), and the
+// converter warps only scale and split it from shared memory: no warp issues
+// operand loads.  Warp roles (22 warps): 0 TMEM + MMA issue, 1 TMA producer,
+// 2-17 converters, 18-21 epilogue.
+constexpr int T2_SF = 2, T2_SA = 2, T2_SB = 2;
+constexpr int T2_THREADS = 32 * (2 + CONV_WARPS + EPI_WARPS);
+constexpr uint32_t F_BYTES = TM * TK * 4;                 // FP32 A tile, 32 KB
+constexpr uint32_t F_STAGE = F_BYTES + MAXT * TK * 4;     // + the chunk's scale rows (1 KB)
+constexpr uint32_t T2_SMEM = T2_SF * F_STAGE + T2_SA * A_STAGE + T2_SB * B_STAGE + 1024;
+static_assert(F_STAGE % 1024 == 0, "A / B stages after the staging ring must stay 1024-byte aligned");
+
+struct Bars2 {
+  uint64_t f_full[T2_SF], f_empty[T2_SF], a_full[T2_SA], a_empty[T2_SA], b_full[T2_SB], b_empty[T2_SB];
+  uint64_t acc_full, acc_empty, fin;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(T2_THREADS, 1)
+    tc_tma_scaled_kernel(TcGemmArgs g, const __grid_constant__ CUtensorMap tmA,
+                         const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sF = smem;                                 // T2_SF staging slots: FP32 A tile + scales
+  uint8_t *sA = smem + T2_SF * F_STAGE;               // T2_SA stages of [hi | lo]
+  uint8_t *sB = sA + T2_SA * A_STAGE;                 // T2_SB stages of [hi | lo]
+  __shared__ __align__(16) Bars2 bars;
+  __shared__ float cd_red[EPI_WARPS][TN];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, grp = blockIdx.y, split = blockIdx.z;
+  const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
+  const int t0 = grp * g.nt_group;
+  const int nt = min(g.nt_group, g.n_t - t0);
+  const int64_t kb = (int64_t)split * g.k_per_split;
+  const int64_t ke = min(g.Kp, kb + g.k_per_split);
+  const int nchunks = (int)((ke - kb) / TK);
+  const int chunks_per_drain = (int)(g.drain_k / TK);
+  const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T2_SF; ++s) { mbar_init(&bars.f_full[s], 1); mbar_init(&bars.f_empty[s], CONV_WARPS); }
+    for (int s = 0; s < T2_SA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
+    for (int s = 0; s < T2_SB; ++s) { mbar_init(&bars.b_full[s], 1); mbar_init(&bars.b_empty[s], 1); }
+    mbar_init(&bars.acc_full, 1);
+    mbar_init(&bars.acc_empty, 32 * EPI_WARPS);
+    mbar_init(&bars.fin, 1);
+    bars.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        smem_u32(&bars.tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = bars.tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0)
+      mma_issue<T2_SA, T2_SB>(tmem, sA, sB, bars.a_full, bars.a_empty, bars.b_full, bars.b_empty, &bars.acc_full,
+                              &bars.acc_empty, &bars.fin, nchunks, chunks_per_drain, ndrains, nt, &bars.abort, g.err);
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int jf = 0, jb = 0;
+      uint32_t pf = 0, pb = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int k0 = (int)(kb + (int64_t)c * TK);   // multiple of 64: 16-byte aligned x for both element sizes
+        if (!mbar_wait(&bars.f_empty[jf], pf ^ 1, &bars.abort, g.err)) break;
+        uint8_t *slot = sF + jf * F_STAGE;
+        mbar_expect_tx(&bars.f_full[jf], F_BYTES + (uint32_t)nt * TK * 4);
+        tma_load_2d(slot, &tmA, k0, ti * TM, &bars.f_full[jf]);
+        for (int t = 0; t < nt; ++t)
+          bulk_load(slot + F_BYTES + t * TK * 4, g.scale + (int64_t)(t0 + t) * g.Kp + k0, TK * 4, &bars.f_full[jf]);
+        if (++jf == T2_SF) { jf = 0; pf ^= 1; }
+        if (!mbar_wait(&bars.b_empty[jb], pb ^ 1, &bars.abort, g.err)) break;
+        uint8_t *bs = sB + jb * B_STAGE;
+        mbar_expect_tx(&bars.b_full[jb], B_STAGE);
+        tma_load_2d(bs, &tmBhi, k0, tj * TN, &bars.b_full[jb]);
+        tma_load_2d(bs + B_BYTES, &tmBlo, k0, tj * TN, &bars.b_full[jb]);
+        if (++jb == T2_SB) { jb = 0; pb ^= 1; }
+      }
+    }
+    __syncwarp();
+  } else if (warp < 2 + CONV_WARPS) {
+    // ---------------------------------------------------------------- converters
+    // Each thread owns rows r and r + 64 of the tile at one 16-byte chunk
+    // (8 k values): it reads them once per chunk from the staging slot, then
+    // writes the nt scaled and split copies.
+    const int ct = threadIdx.x - 64;
+    const int cc = ct & 7;
+    const int r0 = ct >> 3, r1 = r0 + 64;
+    const uint32_t o0 = swz(r0, cc), o1 = swz(r1, cc);
+    int jf = 0, ia = 0;
+    uint32_t pf = 0, pa = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      if (!mbar_wait(&bars.f_full[jf], pf, &bars.abort, g.err)) break;
+      const float *slot = reinterpret_cast<const float *>(sF + jf * F_STAGE);
+      float a0[8], a1[8], sc[MAXT][8];
+      {
+        const float4 *p0 = reinterpret_cast<const float4 *>(slot + r0 * TK + cc * 8);
+        const float4 *p1 = reinterpret_cast<const float4 *>(slot + r1 * TK + cc * 8);
+        float4 x0 = p0[0], y0 = p0[1], x1 = p1[0], y1 = p1[1];
+        a0[0] = x0.x; a0[1] = x0.y; a0[2] = x0.z; a0[3] = x0.w; a0[4] = y0.x; a0[5] = y0.y; a0[6] = y0.z; a0[7] = y0.w;
+        a1[0] = x1.x; a1[1] = x1.y; a1[2] = x1.z; a1[3] = x1.w; a1[4] = y1.x; a1[5] = y1.y; a1[6] = y1.z; a1[7] = y1.w;
+      }
+#pragma unroll
+      for (int t = 0; t < MAXT; ++t) {
+        if (t < nt) {
+          const float4 *ps = reinterpret_cast<const float4 *>(slot + TM * TK + t * TK + cc * 8);
+          float4 x = ps[0], y = ps[1];
+          sc[t][0] = x.x; sc[t][1] = x.y; sc[t][2] = x.z; sc[t][3] = x.w;
+          sc[t][4] = y.x; sc[t][5] = y.y; sc[t][6] = y.z; sc[t][7] = y.w;
+        }
+      }
+      // the slot is refilled by TMA (the async proxy): order these reads before it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.f_empty[jf]);   // this warp is done with the slot
+      if (++jf == T2_SF) { jf = 0; pf ^= 1; }
+#pragma unroll
+      for (int t = 0; t < MAXT; ++t) {
+        if (t < nt) {
+          float v0[8], v1[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) { v0[q] = a0[q] * sc[t][q]; v1[q] = a1[q] * sc[t][q]; }
+          if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars.abort, g.err)) { ok = false; break; }
+          uint8_t *hi = sA + ia * A_STAGE;
+          split_store(v0, hi + o0, hi + A_BYTES + o0);
+          split_store(v1, hi + o1, hi + A_BYTES + o1);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars.a_full[ia]);
+          if (++ia == T2_SA) { ia = 0; pa ^= 1; }
+        }
+      }
+    }
+  } else {
+    epilogue_drain(g, tmem, &bars.acc_full, &bars.acc_empty, &bars.abort, ndrains, nt, tile, grp, split, ti, tj,
+                   cd_red);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+using TmapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmapEncodeFn tmap_encoder() {
+  static TmapEncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmapEncodeFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D row-major [rows][cols] map with a [box_rows][box_cols] box.
+bool encode_2d(CUtensorMap *m, CUtensorMapDataType dt, size_t esize, const void *base, int64_t cols, int64_t rows,
+               uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
+  const TmapEncodeFn f = tmap_encoder();
+  if (!f || ((uintptr_t)base & 15) || (cols * (int64_t)esize) % 16) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(cols * (int64_t)esize)};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  return f(m, dt, 2, const_cast<void *>(base), dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return SMEM_BYTES; }
+size_t tc_gemm_smem_bytes() { return SMEM_BYTES > T2_SMEM ? SMEM_BYTES : T2_SMEM; }
 
 cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
   if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
   if (g.Kp % TK || g.k_per_split % TK || g.drain_k % TK || g.k_per_split <= 0 || g.drain_k <= 0)
     return cudaErrorInvalidValue;
+  if (g.nt_group < 1 || g.nt_group > MAXT) return cudaErrorInvalidValue;
+  if (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) return cudaErrorInvalidValue;
+  if (g.out_mode == TC_OUT_COLDOT && (g.nt_group != 1 || g.k_per_split > g.drain_k)) return cudaErrorInvalidValue;
+  const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
+  const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
+  dim3 grid(n_tiles, groups, splits);
+  if (g.B_hi && g.B_lo) {
+    if (g.out_mode == TC_OUT_COLDOT || g.a_group_stride != 0 || g.rows_a < TM || g.rows_b < TN ||
+        g.rows_a % TM || g.rows_b % TN)
+      return cudaErrorInvalidValue;
+    CUtensorMap ta, tbh, tbl;
+    if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, g.Kp, g.rows_a, TK, TM,
+                   CU_TENSOR_MAP_SWIZZLE_NONE) ||
+        !encode_2d(&tbh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_hi, g.Kp, g.rows_b, TK, TN,
+                   CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_2d(&tbl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_lo, g.Kp, g.rows_b, TK, TN,
+                   CU_TENSOR_MAP_SWIZZLE_128B))
+      return cudaErrorNotSupported;
+    static std::once_flag once2;
+    static cudaError_t attr_err2 = cudaSuccess;
+    std::call_once(once2, [] {
+      attr_err2 = cudaFuncSetAttribute(tc_tma_scaled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)T2_SMEM);
+    });
+    if (attr_err2 != cudaSuccess) return attr_err2;
+    tc_tma_scaled_kernel<<<grid, T2_THREADS, T2_SMEM, s>>>(g, ta, tbh, tbl);
+    return cudaGetLastError();
+  }
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -423,12 +682,6 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
                                     (int)SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  if (g.nt_group < 1 || g.nt_group > MAXT) return cudaErrorInvalidValue;
-  if (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) return cudaErrorInvalidValue;
-  if (g.out_mode == TC_OUT_COLDOT && (g.nt_group != 1 || g.k_per_split > g.drain_k)) return cudaErrorInvalidValue;
-  const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
-  const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
-  dim3 grid(n_tiles, groups, splits);
   tc_split_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(g);
   return cudaGetLastError();
 }
