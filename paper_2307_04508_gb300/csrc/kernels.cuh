@@ -96,7 +96,7 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
 // D_t = A diag(s_t) B^T for t < n_t; A [*][Kp], B [*][Kp], scale [n_t][Kp] FP32,
 // zero-padded (rows of A and B to 128, Kp to 64).  tiles: device list of
 // (tile row of A, tile row of B) pairs.  Output: FP64 partial tiles
-// partial[split][group][4][tile][128][128], group = t / 4.
+// partial[split][group][nt_group][tile][128][128], group = t / nt_group.
 enum TcOut { TC_OUT_F64 = 0, TC_OUT_F32 = 1, TC_OUT_COLDOT = 2 };
 struct TcGemmArgs {
   const float *A = nullptr, *B = nullptr, *scale = nullptr;
@@ -118,7 +118,8 @@ struct TcGemmArgs {
   float *cd_out = nullptr;
   int *err = nullptr;
   // Pre-split B (BF16 hi and lo, row-major [rows_b][Kp]) selects the TMA-fed
-  // kernel: operands arrive by tiled bulk copies (not for TC_OUT_COLDOT or A groups).
+  // kernel with A in tensor memory: operands arrive by tiled bulk copies
+  // (nt_group <= 3; not for TC_OUT_COLDOT or A groups).
   const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
   int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
 };
@@ -133,7 +134,8 @@ size_t tc_gemm_smem_bytes();
 cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0, int rows, int cols,
                                      float *dst, int rows_p, int cols_p, int batch, int64_t strideS,
                                      int64_t strideD, cudaStream_t s);
-// out[r][c] = alpha * sum over splits of full-grid partial tiles (tile = I * nJ + J) for
+// out[r][c] = alpha * sum over splits of full-grid partial tiles (tile = I * nJ + J, one
+// scale per group: nt_group = 1) for
 // r < rows, c < cols; FP64 to out64 (ld ld64) and/or FP32 to out32 (ld ld32; columns
 // up to cols32 (default ld32) and rows up to rows_p32 are written, zero beyond the
 // data), per group g (strides in elements).
@@ -151,10 +153,10 @@ cudaError_t launch_to_f32_padded(const double *src, int64_t lds, int rows, int64
 cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n_t, const double *p0,
                                const double *p1, int mode, float *scale, cudaStream_t s);
 // M_t = alpha * sum over splits of the partial tiles (FP64 or FP32), full symmetric
-// [n_t][N][N] FP64, for a lower tile list (tile_index [nI][nJ]).
+// [n_t][N][N] FP64, for a lower tile list (tile_index [nI][nJ]); nt_group scales per group.
 cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
                                  int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
-                                 double *M, cudaStream_t s, double beta = 0.0);
+                                 double *M, cudaStream_t s, double beta, int nt_group);
 // dst[c][r] = src[r][c0 + c] in FP64 (batched)
 cudaError_t launch_transpose_f64(const double *src, int64_t lds, int64_t c0, int rows, int cols, double *dst,
                                  int64_t ldd, int batch, int64_t strideS, int64_t strideD, cudaStream_t s);

@@ -47,9 +47,10 @@ __global__ void scale_table_kernel(const double *__restrict__ delta, int64_t K, 
 // tiles are 128 x 128, four scales per group.
 __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
                                      int splits, int groups, int n_tiles, const int *__restrict__ tile_index,
-                                     int nJ, int N, double alpha, double beta, double *__restrict__ M) {
+                                     int nJ, int N, int nt_group, double alpha, double beta,
+                                     double *__restrict__ M) {
   const int t = blockIdx.y;
-  const int grp = t / 4, slot = t % 4;
+  const int grp = t / nt_group, slot = t % nt_group;
   const int64_t NN = (int64_t)N * N;
   const int64_t ntri = (int64_t)N * (N + 1) / 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ntri;
@@ -62,7 +63,7 @@ __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const f
     const int tile = tile_index[(i / 128) * nJ + (j / 128)];
     double acc = 0.0;
     for (int s = 0; s < splits; ++s) {
-      const int64_t off = ((((int64_t)s * groups + grp) * 4 + slot) * n_tiles + tile) * (128 * 128) +
+      const int64_t off = ((((int64_t)s * groups + grp) * nt_group + slot) * n_tiles + tile) * (128 * 128) +
                           (i % 128) * 128 + (j % 128);
       acc += partial32 ? (double)partial32[off] : partial[off];
     }
@@ -120,7 +121,6 @@ __global__ void tc_reduce_full_kernel(const double *__restrict__ partial, const 
                                       int64_t stride32) {
   const int g = blockIdx.z;
   const int r = blockIdx.y;
-  const int grp = g, slot = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (out32 ? cols32 : cols);
        c += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -128,7 +128,7 @@ __global__ void tc_reduce_full_kernel(const double *__restrict__ partial, const 
       const int tile = (r / 128) * nJ + (int)(c / 128);
       const int64_t off = (int64_t)(r % 128) * 128 + (c % 128);
       for (int s = 0; s < splits; ++s) {
-        const int64_t base = ((((int64_t)s * groups + grp) * 4 + slot) * n_tiles + tile) * (128 * 128);
+        const int64_t base = (((int64_t)s * groups + g) * n_tiles + tile) * (128 * 128);
         acc += partial32 ? (double)partial32[base + off] : partial[base + off];
       }
       acc *= alpha;
@@ -174,14 +174,15 @@ cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n
 
 cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
                                  int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
-                                 double *M, cudaStream_t s, double beta) {
+                                 double *M, cudaStream_t s, double beta, int nt_group) {
   if (N <= 0 || n_t <= 0) return cudaSuccess;
   int64_t ntri = (int64_t)N * (N + 1) / 2;
   int bx = (int)((ntri + 255) / 256);
   if (bx > 152 * 4) bx = 152 * 4;
   dim3 grid(bx, n_t);
+  if (nt_group < 1 || (n_t + nt_group - 1) / nt_group != groups) return cudaErrorInvalidValue;
   tc_reduce_sym_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, tile_index, nJ, N,
-                                            alpha, beta, M);
+                                            nt_group, alpha, beta, M);
   return cudaGetLastError();
 }
 

@@ -218,7 +218,7 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
   const int ew = warp & 3;                   // TMEM lane quarter this warp may read
   const int row = ew * 32 + lane;
   const int64_t tile_elems = (int64_t)TM * TN;
-  const int64_t base = (((int64_t)split * gridDim.y + grp) * MAXT * gridDim.x + tile) * tile_elems;
+  const int64_t base = (((int64_t)split * gridDim.y + grp) * g.nt_group * gridDim.x + tile) * tile_elems;
   const int64_t tstride = (int64_t)gridDim.x * tile_elems;   // between scales
   for (int dr = 0; dr < ndrains; ++dr) {
     if (!mbar_wait(acc_full, dr & 1, abort, g.err)) break;
@@ -430,23 +430,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
   }
 }
 
-// ---- the same contraction with the operands brought in by TMA ----
+// ---- the same contraction with A in tensor memory, operands brought in by TMA ----
 // B arrives pre-split (BF16 hi and lo arrays, row-major [rows][Kp]) as two
 // tiled TMA copies per chunk with the 128-byte swizzle the tensor core reads,
-// so no thread touches it.  A arrives as FP32 tiles in a staging ring (one
-// tiled TMA copy, plus the chunk's scale rows as bulk copies), and the
-// converter warps only scale and split it from shared memory: no warp issues
-// operand loads.  Warp roles (22 warps): 0 TMEM + MMA issue, 1 TMA producer,
-// 2-17 converters, 18-21 epilogue.
-constexpr int T2_SF = 2, T2_SA = 2, T2_SB = 2;
-constexpr int T2_THREADS = 32 * (2 + CONV_WARPS + EPI_WARPS);
+// so no thread touches it.  A arrives as an FP32 tile (two 128B-swizzled
+// boxes of 32 k, so a warp reading 32 consecutive rows at one k offset is
+// free of bank conflicts) plus the chunk's scale rows in a staging ring.  The
+// converter warps scale and split A and write hi / lo straight into tensor
+// memory (tcgen05.st), and the MMA takes A from there: shared memory carries
+// only the TMA copies, the staging reads and the B operand reads of the
+// tensor core.  TMEM columns: nt accumulators of 128, then a ring of A
+// stages of 64 columns (hi: 32 columns of packed k pairs, lo: 32).
+// Warp roles (22 warps): 0 TMEM + MMA issue, 1 TMA producer, 2-17 converters
+// (lane quarter warp % 4, k slice (warp - 2) / 4 of 16 values), 18-21 epilogue.
+constexpr int T3_SF = 3, T3_SB = 3;
+constexpr int T3_MAXT = 3;                                // scales per CTA
+constexpr int T3_MAXSA = (512 - 128) / (TK);              // A stages when nt = 1
+constexpr int T3_THREADS = 32 * (2 + CONV_WARPS + EPI_WARPS);
 constexpr uint32_t F_BYTES = TM * TK * 4;                 // FP32 A tile, 32 KB
-constexpr uint32_t F_STAGE = F_BYTES + MAXT * TK * 4;     // + the chunk's scale rows (1 KB)
-constexpr uint32_t T2_SMEM = T2_SF * F_STAGE + T2_SA * A_STAGE + T2_SB * B_STAGE + 1024;
-static_assert(F_STAGE % 1024 == 0, "A / B stages after the staging ring must stay 1024-byte aligned");
+constexpr uint32_t F_BOX = TM * 32 * 4;                   // one 32-k box, 16 KB
+constexpr uint32_t F_STAGE = F_BYTES + 1024;              // + the chunk's scale rows (nt x 256 B)
+constexpr uint32_t T3_SMEM = T3_SF * F_STAGE + T3_SB * B_STAGE + 1024;
+static_assert(F_STAGE % 1024 == 0, "stages must stay 1024-byte aligned for the 128-byte swizzle");
+static_assert(T3_MAXT * TK * 4 <= 1024, "scale rows must fit the staging slot");
 
-struct Bars2 {
-  uint64_t f_full[T2_SF], f_empty[T2_SF], a_full[T2_SA], a_empty[T2_SA], b_full[T2_SB], b_empty[T2_SB];
+struct Bars3 {
+  uint64_t f_full[T3_SF], f_empty[T3_SF], b_full[T3_SB], b_empty[T3_SB];
+  uint64_t a_full[T3_MAXSA], a_empty[T3_MAXSA];
   uint64_t acc_full, acc_empty, fin;
   uint32_t tmem_base;
   int abort;
@@ -471,15 +481,28 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                : "memory");
 }
 
-__global__ void __launch_bounds__(T2_THREADS, 1)
-    tc_tma_scaled_kernel(TcGemmArgs g, const __grid_constant__ CUtensorMap tmA,
-                         const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo) {
+// D (TMEM) += A (TMEM, M = 128 rows on the 128 lanes, k pairs packed per column) * B (shared memory)
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %3, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %4, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(acc), "r"(IDESC));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
+__global__ void __launch_bounds__(T3_THREADS, 1)
+    tc_tma_ts_kernel(TcGemmArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                     const __grid_constant__ CUtensorMap tmBlo) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *sF = smem;                                 // T2_SF staging slots: FP32 A tile + scales
-  uint8_t *sA = smem + T2_SF * F_STAGE;               // T2_SA stages of [hi | lo]
-  uint8_t *sB = sA + T2_SA * A_STAGE;                 // T2_SB stages of [hi | lo]
-  __shared__ __align__(16) Bars2 bars;
+  uint8_t *sF = smem;                                 // T3_SF staging slots: FP32 A tile + scales
+  uint8_t *sB = sF + T3_SF * F_STAGE;                 // T3_SB stages of [hi | lo]
+  __shared__ __align__(16) Bars3 bars;
   __shared__ float cd_red[EPI_WARPS][TN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -487,6 +510,8 @@ __global__ void __launch_bounds__(T2_THREADS, 1)
   const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
   const int t0 = grp * g.nt_group;
   const int nt = min(g.nt_group, g.n_t - t0);
+  const int nsa = (512 - TN * g.nt_group) / TK;       // A stages in TMEM after the accumulators
+  const uint32_t acol0 = (uint32_t)(TN * g.nt_group); // first A column
   const int64_t kb = (int64_t)split * g.k_per_split;
   const int64_t ke = min(g.Kp, kb + g.k_per_split);
   const int nchunks = (int)((ke - kb) / TK);
@@ -494,9 +519,9 @@ __global__ void __launch_bounds__(T2_THREADS, 1)
   const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < T2_SF; ++s) { mbar_init(&bars.f_full[s], 1); mbar_init(&bars.f_empty[s], CONV_WARPS); }
-    for (int s = 0; s < T2_SA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
-    for (int s = 0; s < T2_SB; ++s) { mbar_init(&bars.b_full[s], 1); mbar_init(&bars.b_empty[s], 1); }
+    for (int s = 0; s < T3_SF; ++s) { mbar_init(&bars.f_full[s], 1); mbar_init(&bars.f_empty[s], CONV_WARPS); }
+    for (int s = 0; s < T3_SB; ++s) { mbar_init(&bars.b_full[s], 1); mbar_init(&bars.b_empty[s], 1); }
+    for (int s = 0; s < T3_MAXSA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
     mbar_init(&bars.acc_full, 1);
     mbar_init(&bars.acc_empty, 32 * EPI_WARPS);
     mbar_init(&bars.fin, 1);
@@ -514,9 +539,45 @@ __global__ void __launch_bounds__(T2_THREADS, 1)
   const uint32_t tmem = bars.tmem_base;
 
   if (warp == 0) {
-    if (lane == 0)
-      mma_issue<T2_SA, T2_SB>(tmem, sA, sB, bars.a_full, bars.a_empty, bars.b_full, bars.b_empty, &bars.acc_full,
-                              &bars.acc_empty, &bars.fin, nchunks, chunks_per_drain, ndrains, nt, &bars.abort, g.err);
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      int ia = 0, ib = 0;
+      uint32_t pa = 0, pb = 0;
+      bool ok = true;
+      for (int dr = 0; dr < ndrains && ok; ++dr) {
+        ok = mbar_wait(&bars.acc_empty, (dr & 1) ^ 1, &bars.abort, g.err);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
+        for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
+          ok = mbar_wait(&bars.b_full[ib], pb, &bars.abort, g.err);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t bhi = smem_u32(sB + ib * B_STAGE), blo = bhi + B_BYTES;
+          for (int t = 0; t < nt; ++t) {
+            ok = mbar_wait(&bars.a_full[ia], pa, &bars.abort, g.err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ahi = tmem + acol0 + (uint32_t)(ia * TK), alo = ahi + TK / 2;
+            const uint32_t d = tmem + (uint32_t)(t * TN);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk) {
+              const uint32_t first = (c == dr * chunks_per_drain && kk == 0) ? 0u : 1u;
+              mma_bf16_ts(d, ahi + kk * 8, make_desc(bhi + kk * 32), first);
+              mma_bf16_ts(d, ahi + kk * 8, make_desc(blo + kk * 32), 1u);
+              mma_bf16_ts(d, alo + kk * 8, make_desc(bhi + kk * 32), 1u);
+            }
+            mma_commit(&bars.a_empty[ia]);
+            if (++ia == nsa) { ia = 0; pa ^= 1; }
+          }
+          mma_commit(&bars.b_empty[ib]);
+          if (++ib == T3_SB) { ib = 0; pb ^= 1; }
+        }
+        if (ok) mma_commit(&bars.acc_full);
+      }
+      // all issued MMAs complete before the CTA tears down
+      mma_commit(&bars.fin);
+      mbar_wait(&bars.fin, 0, &bars.abort, g.err, false);
+    }
     __syncwarp();
   } else if (warp == 1) {
     // ---------------------------------------------------------------- TMA producer
@@ -524,76 +585,79 @@ __global__ void __launch_bounds__(T2_THREADS, 1)
       int jf = 0, jb = 0;
       uint32_t pf = 0, pb = 0;
       for (int c = 0; c < nchunks; ++c) {
-        const int k0 = (int)(kb + (int64_t)c * TK);   // multiple of 64: 16-byte aligned x for both element sizes
+        const int k0 = (int)(kb + (int64_t)c * TK);   // multiple of 64: x stays 16-byte aligned for both types
         if (!mbar_wait(&bars.f_empty[jf], pf ^ 1, &bars.abort, g.err)) break;
         uint8_t *slot = sF + jf * F_STAGE;
         mbar_expect_tx(&bars.f_full[jf], F_BYTES + (uint32_t)nt * TK * 4);
         tma_load_2d(slot, &tmA, k0, ti * TM, &bars.f_full[jf]);
+        tma_load_2d(slot + F_BOX, &tmA, k0 + 32, ti * TM, &bars.f_full[jf]);
         for (int t = 0; t < nt; ++t)
           bulk_load(slot + F_BYTES + t * TK * 4, g.scale + (int64_t)(t0 + t) * g.Kp + k0, TK * 4, &bars.f_full[jf]);
-        if (++jf == T2_SF) { jf = 0; pf ^= 1; }
+        if (++jf == T3_SF) { jf = 0; pf ^= 1; }
         if (!mbar_wait(&bars.b_empty[jb], pb ^ 1, &bars.abort, g.err)) break;
         uint8_t *bs = sB + jb * B_STAGE;
         mbar_expect_tx(&bars.b_full[jb], B_STAGE);
         tma_load_2d(bs, &tmBhi, k0, tj * TN, &bars.b_full[jb]);
         tma_load_2d(bs + B_BYTES, &tmBlo, k0, tj * TN, &bars.b_full[jb]);
-        if (++jb == T2_SB) { jb = 0; pb ^= 1; }
+        if (++jb == T3_SB) { jb = 0; pb ^= 1; }
       }
     }
     __syncwarp();
   } else if (warp < 2 + CONV_WARPS) {
     // ---------------------------------------------------------------- converters
-    // Each thread owns rows r and r + 64 of the tile at one 16-byte chunk
-    // (8 k values): it reads them once per chunk from the staging slot, then
-    // writes the nt scaled and split copies.
-    const int ct = threadIdx.x - 64;
-    const int cc = ct & 7;
-    const int r0 = ct >> 3, r1 = r0 + 64;
-    const uint32_t o0 = swz(r0, cc), o1 = swz(r1, cc);
+    // Thread = tile row r (its TMEM lane) x 16 k values of the chunk: 4 reads
+    // of 16 bytes from the swizzled staging box, then per scale 16 products,
+    // their hi / lo split and two 8-column TMEM stores.
+    const int wq = warp & 3;
+    const int sub = (warp - 2) >> 2;
+    const int r = wq * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(wq * 32) << 16;
+    const uint32_t roff = (uint32_t)(sub >> 1) * F_BOX + (uint32_t)r * 128;
+    const int c0 = (sub & 1) * 4;
     int jf = 0, ia = 0;
     uint32_t pf = 0, pa = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       if (!mbar_wait(&bars.f_full[jf], pf, &bars.abort, g.err)) break;
-      const float *slot = reinterpret_cast<const float *>(sF + jf * F_STAGE);
-      float a0[8], a1[8], sc[MAXT][8];
-      {
-        const float4 *p0 = reinterpret_cast<const float4 *>(slot + r0 * TK + cc * 8);
-        const float4 *p1 = reinterpret_cast<const float4 *>(slot + r1 * TK + cc * 8);
-        float4 x0 = p0[0], y0 = p0[1], x1 = p1[0], y1 = p1[1];
-        a0[0] = x0.x; a0[1] = x0.y; a0[2] = x0.z; a0[3] = x0.w; a0[4] = y0.x; a0[5] = y0.y; a0[6] = y0.z; a0[7] = y0.w;
-        a1[0] = x1.x; a1[1] = x1.y; a1[2] = x1.z; a1[3] = x1.w; a1[4] = y1.x; a1[5] = y1.y; a1[6] = y1.z; a1[7] = y1.w;
-      }
+      const uint8_t *slot = sF + jf * F_STAGE;
+      float a[16];
 #pragma unroll
-      for (int t = 0; t < MAXT; ++t) {
-        if (t < nt) {
-          const float4 *ps = reinterpret_cast<const float4 *>(slot + TM * TK + t * TK + cc * 8);
-          float4 x = ps[0], y = ps[1];
-          sc[t][0] = x.x; sc[t][1] = x.y; sc[t][2] = x.z; sc[t][3] = x.w;
-          sc[t][4] = y.x; sc[t][5] = y.y; sc[t][6] = y.z; sc[t][7] = y.w;
+      for (int j = 0; j < 4; ++j) {
+        const float4 x = *reinterpret_cast<const float4 *>(slot + roff + (((c0 + j) ^ (r & 7)) << 4));
+        a[4 * j] = x.x; a[4 * j + 1] = x.y; a[4 * j + 2] = x.z; a[4 * j + 3] = x.w;
+      }
+      for (int t = 0; t < nt && ok; ++t) {
+        const float4 *ps = reinterpret_cast<const float4 *>(slot + F_BYTES + t * TK * 4 + sub * 64);
+        uint32_t hi[8], lo[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 s4 = ps[j];   // the same address in every lane: one broadcast
+          const float v0 = a[4 * j] * s4.x, v1 = a[4 * j + 1] * s4.y, v2 = a[4 * j + 2] * s4.z,
+                      v3 = a[4 * j + 3] * s4.w;
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(v0, v1), h1 = __floats2bfloat162_rn(v2, v3);
+          const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+          __nv_bfloat162 l0 = __floats2bfloat162_rn(v0 - f0.x, v1 - f0.y), l1 = __floats2bfloat162_rn(v2 - f1.x, v3 - f1.y);
+          hi[2 * j] = *reinterpret_cast<uint32_t *>(&h0);
+          hi[2 * j + 1] = *reinterpret_cast<uint32_t *>(&h1);
+          lo[2 * j] = *reinterpret_cast<uint32_t *>(&l0);
+          lo[2 * j + 1] = *reinterpret_cast<uint32_t *>(&l1);
         }
+        if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars.abort, g.err)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ta = tmem + lane_addr + acol0 + (uint32_t)(ia * TK + sub * 8);
+        tmem_st8(ta, hi);
+        tmem_st8(ta + TK / 2, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.a_full[ia]);
+        if (++ia == nsa) { ia = 0; pa ^= 1; }
       }
       // the slot is refilled by TMA (the async proxy): order these reads before it
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars.f_empty[jf]);   // this warp is done with the slot
-      if (++jf == T2_SF) { jf = 0; pf ^= 1; }
-#pragma unroll
-      for (int t = 0; t < MAXT; ++t) {
-        if (t < nt) {
-          float v0[8], v1[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) { v0[q] = a0[q] * sc[t][q]; v1[q] = a1[q] * sc[t][q]; }
-          if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars.abort, g.err)) { ok = false; break; }
-          uint8_t *hi = sA + ia * A_STAGE;
-          split_store(v0, hi + o0, hi + A_BYTES + o0);
-          split_store(v1, hi + o1, hi + A_BYTES + o1);
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bars.a_full[ia]);
-          if (++ia == T2_SA) { ia = 0; pa ^= 1; }
-        }
-      }
+      if (lane == 0) mbar_arrive(&bars.f_empty[jf]);
+      if (++jf == T3_SF) { jf = 0; pf ^= 1; }
     }
   } else {
     epilogue_drain(g, tmem, &bars.acc_full, &bars.acc_empty, &bars.abort, ndrains, nt, tile, grp, split, ti, tj,
@@ -641,7 +705,7 @@ bool encode_2d(CUtensorMap *m, CUtensorMapDataType dt, size_t esize, const void 
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return SMEM_BYTES > T2_SMEM ? SMEM_BYTES : T2_SMEM; }
+size_t tc_gemm_smem_bytes() { return SMEM_BYTES > T3_SMEM ? SMEM_BYTES : T3_SMEM; }
 
 cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
   if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
@@ -654,12 +718,12 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
   dim3 grid(n_tiles, groups, splits);
   if (g.B_hi && g.B_lo) {
-    if (g.out_mode == TC_OUT_COLDOT || g.a_group_stride != 0 || g.rows_a < TM || g.rows_b < TN ||
-        g.rows_a % TM || g.rows_b % TN)
+    if (g.out_mode == TC_OUT_COLDOT || g.a_group_stride != 0 || g.nt_group > T3_MAXT || g.rows_a < TM ||
+        g.rows_b < TN || g.rows_a % TM || g.rows_b % TN)
       return cudaErrorInvalidValue;
     CUtensorMap ta, tbh, tbl;
-    if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, g.Kp, g.rows_a, TK, TM,
-                   CU_TENSOR_MAP_SWIZZLE_NONE) ||
+    if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, g.Kp, g.rows_a, 32, TM,
+                   CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&tbh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_hi, g.Kp, g.rows_b, TK, TN,
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&tbl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_lo, g.Kp, g.rows_b, TK, TN,
@@ -668,11 +732,11 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
     static std::once_flag once2;
     static cudaError_t attr_err2 = cudaSuccess;
     std::call_once(once2, [] {
-      attr_err2 = cudaFuncSetAttribute(tc_tma_scaled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)T2_SMEM);
+      attr_err2 = cudaFuncSetAttribute(tc_tma_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)T3_SMEM);
     });
     if (attr_err2 != cudaSuccess) return attr_err2;
-    tc_tma_scaled_kernel<<<grid, T2_THREADS, T2_SMEM, s>>>(g, ta, tbh, tbl);
+    tc_tma_ts_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(g, ta, tbh, tbl);
     return cudaGetLastError();
   }
   static std::once_flag once;
