@@ -251,16 +251,21 @@ ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const doub
 
 // Split-K plan: one CTA per SM, so choose the split count that fills whole
 // waves best while keeping at least 1024 pairs per CTA.
-int64_t tc_splits(const ltgw_ctx *ctx, int64_t units, int64_t Kp, int64_t *kps_out) {
-  const int64_t max_split = std::max<int64_t>(1, Kp / 1024);
-  int64_t splits = 1;
-  double best = -1.0;
-  for (int64_t sp = 1; sp <= std::min<int64_t>(max_split, 64); ++sp) {
-    const int64_t ctas = units * sp;
-    const int64_t waves = (ctas + ctx->n_sm - 1) / ctx->n_sm;
-    const double eff = (double)ctas / (double)(waves * ctx->n_sm);
-    const double score = eff - 0.002 * (double)sp;   // prefer fewer splits on ties
-    if (score > best) { best = score; splits = sp; }
+// K-split count for a tensor-core contraction of `units` output tiles x groups:
+// the CTAs of one wave run in lockstep, so the time is about waves x (per-CTA
+// overhead + K chunks per CTA); the overhead (TMEM and barrier setup, pipeline
+// fill, draining the accumulators) costs about as much as ten 64-pair chunks.
+// At least Kp / drain_k splits (up to 64) keep each CTA to one FP32 drain.
+int64_t tc_splits(const ltgw_ctx *ctx, int64_t units, int64_t Kp, int64_t drain_k, int64_t *kps_out) {
+  const int64_t max_split = std::min<int64_t>(64, std::max<int64_t>(1, Kp / 1024));
+  const int64_t min_split = std::min<int64_t>(max_split, (Kp + drain_k - 1) / drain_k);
+  const int64_t nchunk = Kp / 64;
+  int64_t splits = min_split;
+  double best = 1e300;
+  for (int64_t sp = min_split; sp <= max_split; ++sp) {
+    const int64_t waves = (units * sp + ctx->n_sm - 1) / ctx->n_sm;
+    const double cost = (double)waves * (10.0 + (double)((nchunk + sp - 1) / sp));
+    if (cost < best) { best = cost; splits = sp; }   // fewer splits on ties
   }
   int64_t kps = ((Kp + splits - 1) / splits + 63) / 64 * 64;
   *kps_out = kps;
@@ -299,8 +304,9 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
   const int n_tiles = (int)(tiles.size() / 2);
   const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
   int64_t kps = 0;
-  int64_t splits = tc_splits(ctx, (int64_t)n_tiles * groups, g.Kp, &kps);
-  if (g.out_mode == TC_OUT_COLDOT) { kps = g.Kp; splits = 1; }
+  int64_t splits = tc_splits(ctx, (int64_t)n_tiles * groups, g.Kp, g.drain_k, &kps);
+  // the column dot needs the whole contraction (K = the NAF count) in one drain
+  if (g.out_mode == TC_OUT_COLDOT) { kps = g.Kp; splits = 1; g.drain_k = std::max<int64_t>(g.drain_k, g.Kp); }
   const bool f32 = g.out_mode != TC_OUT_COLDOT && kps <= g.drain_k;
   if (g.out_mode != TC_OUT_COLDOT) g.out_mode = f32 ? TC_OUT_F32 : TC_OUT_F64;
   int *d_tiles;

@@ -105,7 +105,8 @@ struct TcGemmArgs {
   int nt_group = 4;              // scales per CTA (1..4); group = blockIdx.y
   int64_t a_group_stride = 0;    // A of group g starts at A + g * a_group_stride
   const int *tiles = nullptr;
-  int64_t k_per_split = 0, drain_k = 16384;
+  int64_t k_per_split = 0;
+  int64_t drain_k = 2048;        // pairs per FP32 accumulation (bounds its rounding bias)
   int out_mode = TC_OUT_F64;     // F32 requires k_per_split <= drain_k
   double *partial = nullptr;     // TC_OUT_F64
   float *partial32 = nullptr;    // TC_OUT_F32
@@ -119,7 +120,7 @@ struct TcGemmArgs {
   int *err = nullptr;
   // Pre-split B (BF16 hi and lo, row-major [rows_b][Kp]) selects the TMA-fed
   // kernel with A in tensor memory: operands arrive by tiled bulk copies
-  // (nt_group <= 3; not for TC_OUT_COLDOT or A groups).
+  // (nt_group <= 2; not for TC_OUT_COLDOT or A groups).
   const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
   int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
 };

@@ -7,7 +7,13 @@
 // contraction, Eqs. naftrafo and ScreenedCoulombOrbital) in the mixed
 // precision form: each operand value x is split into x_hi = bf16(x) and
 // x_lo = bf16(x - x_hi), and D accumulates hi*hi + hi*lo + lo*hi with FP32
-// accumulation in tensor memory, drained into FP64 every `drain_k` pairs.
+// accumulation in tensor memory, drained into FP64 every `drain_k` pairs.  The
+// drain length bounds the FP32 accumulation error: each MMA adds its products
+// into D with an FP32 rounding that loses about half an ulp on average, all in
+// the same direction for sums of one sign, so the relative bias grows with
+// the number of MMAs into one accumulator (about 1.7e-5 after 2048 pairs of
+// three products).  With at most two scales per CTA and more than one drain,
+// two accumulator sets alternate, so a drain overlaps the next window's MMAs.
 //
 // Operands are FP32, K-major, zero-padded to multiples of the tile (rows to
 // 128 / 64, K to 64) so the kernel needs no bounds checks.  The scale s_t is
@@ -51,7 +57,7 @@ constexpr uint32_t SMEM_BYTES = SA * A_STAGE + SB * B_STAGE + 1024;  // + alignm
 
 struct Bars {
   alignas(16) float scale[2][MAXT][TK];   // scale ring (converters only), read as float4
-  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full, acc_empty, fin;
+  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[2], acc_empty[2], fin;
   uint64_t s_full[2], s_empty[2];
   uint32_t tmem_base;
   int abort;
@@ -81,28 +87,39 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
 
 // Bounded wait for the phase with the given parity; false on time-out (or, when
 // honor_abort, as soon as another role of the CTA has given up).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *abort, int *err,
-                                          bool honor_abort = true) {
-  uint32_t done = 0;
-  uint64_t t0 = 0;
-  for (uint32_t it = 0;; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ uint32_t mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return done;
+}
+
+// Bounded wait for the phase with the given parity; false on time-out (or, when
+// honor_abort, as soon as another role of the CTA has given up).  A phase that
+// has already completed costs one try_wait: the MMA issue thread waits once per
+// stage, and anything it executes between MMAs leaves the tensor pipe idle.
+__device__ __forceinline__ bool mbar_wait_slow(uint64_t *b, uint32_t parity, int *abort, int *err, bool honor_abort) {
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(b, parity)) return true;
     if ((it & 1023) == 0) {
       if (honor_abort && *(volatile int *)abort) return false;
-      uint64_t t = globaltimer();
-      if (it == 0) t0 = t;
-      else if (t - t0 > 2000000000ull) {
+      if (globaltimer() - t0 > 2000000000ull) {
         atomicExch(&err[FLAG_TC_TIMEOUT], 1);
         *(volatile int *)abort = 1;
         return false;
       }
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *abort, int *err,
+                                          bool honor_abort = true) {
+  if (mbar_try(b, parity)) return true;
+  return mbar_wait_slow(b, parity, abort, err, honor_abort);
 }
 
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
@@ -164,17 +181,18 @@ __device__ __forceinline__ void load8(const float *p, float v[8]) {
 
 // MMA issue (one thread): per K-chunk, the B stage then nt A stages, three
 // products each (hi*hi, hi*lo, lo*hi); the TMEM accumulators are drained every
-// chunks_per_drain chunks.
+// chunks_per_drain chunks, window dr into accumulator set dr % nbuf.
 template <int NSA, int NSB>
 __device__ __forceinline__ void mma_issue(uint32_t tmem, const uint8_t *sA, const uint8_t *sB, uint64_t *a_full, uint64_t *a_empty,
                           uint64_t *b_full, uint64_t *b_empty, uint64_t *acc_full, uint64_t *acc_empty,
-                          uint64_t *fin, int nchunks, int chunks_per_drain, int ndrains, int nt, int *abort,
-                          int *err) {
+                          uint64_t *fin, int nchunks, int chunks_per_drain, int ndrains, int nt, int nbuf,
+                          int *abort, int *err) {
   int ia = 0, ib = 0;
   uint32_t pa = 0, pb = 0;
   bool ok = true;
   for (int dr = 0; dr < ndrains && ok; ++dr) {
-    ok = mbar_wait(acc_empty, (dr & 1) ^ 1, abort, err);
+    const int buf = dr % nbuf;
+    ok = mbar_wait(&acc_empty[buf], ((dr / nbuf) & 1) ^ 1, abort, err);
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
     for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
@@ -187,7 +205,7 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem, const uint8_t *sA, cons
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t ahi = smem_u32(sA + ia * A_STAGE), alo = ahi + A_BYTES;
-        const uint32_t d = tmem + (uint32_t)(t * TN);
+        const uint32_t d = tmem + (uint32_t)((buf * nt + t) * TN);
 #pragma unroll
         for (int kk = 0; kk < TK / 16; ++kk) {
           const uint32_t off = kk * 32;
@@ -202,7 +220,7 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem, const uint8_t *sA, cons
       mma_commit(&b_empty[ib]);
       if (++ib == NSB) { ib = 0; pb ^= 1; }
     }
-    if (ok) mma_commit(acc_full);
+    if (ok) mma_commit(&acc_full[buf]);
   }
   // all issued MMAs complete before the CTA tears down
   mma_commit(fin);
@@ -210,10 +228,10 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem, const uint8_t *sA, cons
 }
 
 // Epilogue (EPI_WARPS warps): tcgen05.ld of the accumulators after each drain
-// window, into FP64 / FP32 partial tiles or the column-dot reduction.
+// window (set dr % nbuf), into FP64 / FP32 partial tiles or the column-dot reduction.
 __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tmem, uint64_t *acc_full, uint64_t *acc_empty,
-                               int *abort, int ndrains, int nt, int tile, int grp, int split, int ti, int tj,
-                               float (*cd_red)[TN]) {
+                               int *abort, int ndrains, int nt, int nbuf, int tile, int grp, int split, int ti,
+                               int tj, float (*cd_red)[TN]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ew = warp & 3;                   // TMEM lane quarter this warp may read
   const int row = ew * 32 + lane;
@@ -221,12 +239,13 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
   const int64_t base = (((int64_t)split * gridDim.y + grp) * g.nt_group * gridDim.x + tile) * tile_elems;
   const int64_t tstride = (int64_t)gridDim.x * tile_elems;   // between scales
   for (int dr = 0; dr < ndrains; ++dr) {
-    if (!mbar_wait(acc_full, dr & 1, abort, g.err)) break;
+    const int buf = dr % nbuf;
+    if (!mbar_wait(&acc_full[buf], (dr / nbuf) & 1, abort, g.err)) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     for (int t = 0; t < nt; ++t) {
       for (int h = 0; h < TN / 32; ++h) {
         uint32_t r[32];
-        const uint32_t a = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(t * TN + h * 32);
+        const uint32_t a = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((buf * nt + t) * TN + h * 32);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -282,7 +301,7 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    mbar_arrive(acc_empty);
+    mbar_arrive(&acc_empty[buf]);
   }
 }
 
@@ -305,13 +324,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
   const int nchunks = (int)((ke - kb) / TK);
   const int chunks_per_drain = (int)(g.drain_k / TK);
   const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
+  const int nbuf = (ndrains > 1 && 2 * g.nt_group <= MAXT) ? 2 : 1;   // accumulator sets
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < SA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
     for (int s = 0; s < SB; ++s) { mbar_init(&bars.b_full[s], CONV_WARPS); mbar_init(&bars.b_empty[s], 1); }
     for (int s = 0; s < 2; ++s) { mbar_init(&bars.s_full[s], 8); mbar_init(&bars.s_empty[s], CONV_WARPS); }
-    mbar_init(&bars.acc_full, 1);
-    mbar_init(&bars.acc_empty, 32 * EPI_WARPS);
+    for (int s = 0; s < 2; ++s) { mbar_init(&bars.acc_full[s], 1); mbar_init(&bars.acc_empty[s], 32 * EPI_WARPS); }
     mbar_init(&bars.fin, 1);
     bars.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -328,8 +347,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
 
   if (warp == 0) {
     if (lane == 0)
-      mma_issue<SA, SB>(tmem, sA, sB, bars.a_full, bars.a_empty, bars.b_full, bars.b_empty, &bars.acc_full,
-                        &bars.acc_empty, &bars.fin, nchunks, chunks_per_drain, ndrains, nt, &bars.abort, g.err);
+      mma_issue<SA, SB>(tmem, sA, sB, bars.a_full, bars.a_empty, bars.b_full, bars.b_empty, bars.acc_full,
+                        bars.acc_empty, &bars.fin, nchunks, chunks_per_drain, ndrains, nt, nbuf, &bars.abort, g.err);
     __syncwarp();
   } else if (warp <= CONV_WARPS) {
     // ---------------------------------------------------------------- converters
@@ -419,7 +438,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
       }
     }
   } else {
-    epilogue_drain(g, tmem, &bars.acc_full, &bars.acc_empty, &bars.abort, ndrains, nt, tile, grp, split, ti, tj,
+    epilogue_drain(g, tmem, bars.acc_full, bars.acc_empty, &bars.abort, ndrains, nt, nbuf, tile, grp, split, ti, tj,
                    cd_red);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -441,23 +460,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g
 // only the TMA copies, the staging reads and the B operand reads of the
 // tensor core.  TMEM columns: nt accumulators of 128, then a ring of A
 // stages of 64 columns (hi: 32 columns of packed k pairs, lo: 32).
-// Warp roles (22 warps): 0 TMEM + MMA issue, 1 TMA producer, 2-17 converters
-// (lane quarter warp % 4, k slice (warp - 2) / 4 of 16 values), 18-21 epilogue.
+// Warp roles (23 warps): 0 TMEM allocation and MMA issue for scale 0, 1 TMA
+// producer, 2-17 converters (lane quarter warp % 4, k slice (warp - 2) / 4 of
+// 16 values), 18-21 epilogue, 22 MMA issue for scale 1.  One issuing thread
+// per accumulator: a thread's MMAs reach the tensor pipe at full rate only when
+// they are issued back to back, so each stage's twelve MMAs form one
+// instruction block and the per-stage waits of the two issuers overlap.  Each
+// A stage belongs to one issuer (the stage count is a multiple of the scales
+// per CTA), so an issuer never waits on a phase more than one ahead of its
+// stage's barrier, where the parity test would alias.
 constexpr int T3_SF = 3, T3_SB = 3;
-constexpr int T3_MAXT = 3;                                // scales per CTA
+constexpr int T3_MAXT = 2;                                // scales per CTA
 constexpr int T3_MAXSA = (512 - 128) / (TK);              // A stages when nt = 1
-constexpr int T3_THREADS = 32 * (2 + CONV_WARPS + EPI_WARPS);
+constexpr int T3_ISSUE1 = 2 + CONV_WARPS + EPI_WARPS;     // issuer warp of scale 1
+constexpr int T3_THREADS = 32 * (T3_ISSUE1 + T3_MAXT - 1);
+static_assert(((512 - 128 * 1) / TK) % 1 == 0 && ((512 - 128 * 2) / TK) % 2 == 0,
+              "every A stage must belong to one issuer");
 constexpr uint32_t F_BYTES = TM * TK * 4;                 // FP32 A tile, 32 KB
 constexpr uint32_t F_BOX = TM * 32 * 4;                   // one 32-k box, 16 KB
 constexpr uint32_t F_STAGE = F_BYTES + 1024;              // + the chunk's scale rows (nt x 256 B)
 constexpr uint32_t T3_SMEM = T3_SF * F_STAGE + T3_SB * B_STAGE + 1024;
 static_assert(F_STAGE % 1024 == 0, "stages must stay 1024-byte aligned for the 128-byte swizzle");
 static_assert(T3_MAXT * TK * 4 <= 1024, "scale rows must fit the staging slot");
+static_assert(TK == 64, "the stage MMA block covers four K = 16 steps and A_lo 32 columns after A_hi");
 
 struct Bars3 {
   uint64_t f_full[T3_SF], f_empty[T3_SF], b_full[T3_SB], b_empty[T3_SB];
   uint64_t a_full[T3_MAXSA], a_empty[T3_MAXSA];
-  uint64_t acc_full, acc_empty, fin;
+  uint64_t acc_full[1], acc_empty[1], fin;
   uint32_t tmem_base;
   int abort;
 };
@@ -481,12 +511,34 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                : "memory");
 }
 
-// D (TMEM) += A (TMEM, M = 128 rows on the 128 lanes, k pairs packed per column) * B (shared memory)
-__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+// A operand in tensor memory: M = 128 rows on the 128 lanes, k pairs packed
+// per 32-bit column.  One stage of one scale: D += A_hi B_hi + A_hi B_lo + A_lo B_hi over the 64 k
+// of a chunk as four K = 16 steps.  a: TMEM column of A_hi (A_lo 32 columns
+// on); bh / bl: descriptors of B_hi / B_lo (a 32-byte k step adds 2 to the
+// start-address field).  acc0 = 0 overwrites D with the first product.
+__device__ __forceinline__ void mma_stage_ts(uint32_t d, uint32_t a, uint64_t bh, uint64_t bl, uint32_t acc0) {
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %3, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %4, p;\n}\n" ::"r"(d),
-      "r"(a), "l"(b), "r"(acc), "r"(IDESC));
+      "{\n.reg .pred p;\n.reg .b32 a1, a2, a3, l0, l1, l2, l3;\n.reg .b64 h1, h2, h3, m1, m2, m3;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "add.u32 a1, %1, 8;\nadd.u32 a2, %1, 16;\nadd.u32 a3, %1, 24;\n"
+      "add.u32 l0, %1, 32;\nadd.u32 l1, %1, 40;\nadd.u32 l2, %1, 48;\nadd.u32 l3, %1, 56;\n"
+      "add.u64 h1, %2, 2;\nadd.u64 h2, %2, 4;\nadd.u64 h3, %2, 6;\n"
+      "add.u64 m1, %3, 2;\nadd.u64 m2, %3, 4;\nadd.u64 m3, %3, 6;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %5, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %3, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [l0], %2, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], h1, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], m1, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [l1], h1, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], h2, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], m2, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [l2], h2, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], h3, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], m3, %5, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [l3], h3, %5, 1;\n"
+      "}\n" ::"r"(d),
+      "r"(a), "l"(bh), "l"(bl), "r"(acc0), "r"(IDESC)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
@@ -519,12 +571,13 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
 
   if (threadIdx.x == 0) {
+    // b_empty, acc_full and fin collect one commit from each of the nt issuers
     for (int s = 0; s < T3_SF; ++s) { mbar_init(&bars.f_full[s], 1); mbar_init(&bars.f_empty[s], CONV_WARPS); }
-    for (int s = 0; s < T3_SB; ++s) { mbar_init(&bars.b_full[s], 1); mbar_init(&bars.b_empty[s], 1); }
+    for (int s = 0; s < T3_SB; ++s) { mbar_init(&bars.b_full[s], 1); mbar_init(&bars.b_empty[s], nt); }
     for (int s = 0; s < T3_MAXSA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
-    mbar_init(&bars.acc_full, 1);
-    mbar_init(&bars.acc_empty, 32 * EPI_WARPS);
-    mbar_init(&bars.fin, 1);
+    mbar_init(&bars.acc_full[0], nt);
+    mbar_init(&bars.acc_empty[0], 32 * EPI_WARPS);
+    mbar_init(&bars.fin, nt);
     bars.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -538,41 +591,35 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = bars.tmem_base;
 
-  if (warp == 0) {
-    // ---------------------------------------------------------------- MMA issue
-    if (lane == 0) {
-      int ia = 0, ib = 0;
+  const int issue_t = warp == 0 ? 0 : (warp >= T3_ISSUE1 ? warp - T3_ISSUE1 + 1 : -1);
+  if (issue_t >= 0) {
+    // ---------------------------------------------------------------- MMA issue, scale issue_t
+    // Stages of A come in the order (chunk, scale): this scale's stage of
+    // chunk c is (c nt + issue_t) mod nsa.
+    if (lane == 0 && issue_t < nt) {
+      const uint64_t db0 = make_desc(smem_u32(sB));
+      const uint32_t d = tmem + (uint32_t)(issue_t * TN);
+      int ia = issue_t, ib = 0;
       uint32_t pa = 0, pb = 0;
+      while (ia >= nsa) { ia -= nsa; pa ^= 1; }
       bool ok = true;
       for (int dr = 0; dr < ndrains && ok; ++dr) {
-        ok = mbar_wait(&bars.acc_empty, (dr & 1) ^ 1, &bars.abort, g.err);
+        ok = mbar_wait(&bars.acc_empty[0], (dr & 1) ^ 1, &bars.abort, g.err);
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
         for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
-          ok = mbar_wait(&bars.b_full[ib], pb, &bars.abort, g.err);
+          ok = mbar_wait(&bars.b_full[ib], pb, &bars.abort, g.err) && mbar_wait(&bars.a_full[ia], pa, &bars.abort, g.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t bhi = smem_u32(sB + ib * B_STAGE), blo = bhi + B_BYTES;
-          for (int t = 0; t < nt; ++t) {
-            ok = mbar_wait(&bars.a_full[ia], pa, &bars.abort, g.err);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t ahi = tmem + acol0 + (uint32_t)(ia * TK), alo = ahi + TK / 2;
-            const uint32_t d = tmem + (uint32_t)(t * TN);
-#pragma unroll
-            for (int kk = 0; kk < TK / 16; ++kk) {
-              const uint32_t first = (c == dr * chunks_per_drain && kk == 0) ? 0u : 1u;
-              mma_bf16_ts(d, ahi + kk * 8, make_desc(bhi + kk * 32), first);
-              mma_bf16_ts(d, ahi + kk * 8, make_desc(blo + kk * 32), 1u);
-              mma_bf16_ts(d, alo + kk * 8, make_desc(bhi + kk * 32), 1u);
-            }
-            mma_commit(&bars.a_empty[ia]);
-            if (++ia == nsa) { ia = 0; pa ^= 1; }
-          }
+          const uint64_t bh = db0 + (uint64_t)((ib * B_STAGE) >> 4);
+          mma_stage_ts(d, tmem + acol0 + (uint32_t)(ia * TK), bh, bh + (B_BYTES >> 4),
+                       c == dr * chunks_per_drain ? 0u : 1u);
+          mma_commit(&bars.a_empty[ia]);
           mma_commit(&bars.b_empty[ib]);
+          for (ia += nt; ia >= nsa;) { ia -= nsa; pa ^= 1; }
           if (++ib == T3_SB) { ib = 0; pb ^= 1; }
         }
-        if (ok) mma_commit(&bars.acc_full);
+        if (ok) mma_commit(&bars.acc_full[0]);
       }
       // all issued MMAs complete before the CTA tears down
       mma_commit(&bars.fin);
@@ -660,7 +707,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
       if (++jf == T3_SF) { jf = 0; pf ^= 1; }
     }
   } else {
-    epilogue_drain(g, tmem, &bars.acc_full, &bars.acc_empty, &bars.abort, ndrains, nt, tile, grp, split, ti, tj,
+    epilogue_drain(g, tmem, bars.acc_full, bars.acc_empty, &bars.abort, ndrains, nt, 1, tile, grp, split, ti, tj,
                    cd_red);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");

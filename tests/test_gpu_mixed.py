@@ -1,9 +1,10 @@
 """Mixed-precision (split-BF16 on tcgen05) polarisability against the FP64 oracle.
 
 The mixed form keeps about 16 bits per operand (x = bf16(x) + bf16(x - bf16(x)),
-three products) with FP32 accumulation drained to FP64 every 16384 pairs, so
+three products) with FP32 accumulation drained to FP64 every 2048 pairs, so
 the bar here is a relative Frobenius error of 5e-5 on Pi and 1 meV on the
-quasi-particle energies (the mixed-precision target)."""
+quasi-particle energies (the mixed-precision target).  140,000 pairs take more
+K-splits than a launch allows, so every CTA drains its accumulators twice."""
 import numpy as np
 import pytest
 
@@ -34,7 +35,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("N,P,n_om", [(1, 1, 3), (37, 301, 12), (130, 2000, 9), (200, 9000, 20)])
+@pytest.mark.parametrize("N,P,n_om", [(1, 1, 3), (37, 301, 12), (130, 2000, 9), (200, 9000, 20), (130, 140000, 5)])
 def test_mixed_polarizability_direct_and_laplace(ctx, N, P, n_om):
     rng = np.random.default_rng(N + P)
     Bt = rng.standard_normal((N, P)) * 0.05

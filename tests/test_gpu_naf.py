@@ -28,11 +28,13 @@ def ctx():
     c.close()
 
 
-def _case(n: int, seed: int):
-    """B with an exponentially decaying spectrum of K (like the RI workloads)
-    and a threshold in the widest gap among the top 20-50 % of eigenvalues."""
+def _case(n: int, seed: int, pairs: int = 0):
+    """B (n x pairs, default 2n) with an exponentially decaying spectrum of
+    K (like the RI workloads) and a threshold in the widest gap among the top
+    20-50 % of eigenvalues."""
     rng = np.random.default_rng(seed)
-    B = rng.standard_normal((n, 2 * n)) / np.sqrt(2 * n)
+    pairs = pairs or 2 * n
+    B = rng.standard_normal((n, pairs)) / np.sqrt(pairs)
     B *= np.exp(-3.0 * np.arange(n) / n)[:, None]
     K = B @ B.T
     lam = np.sort(np.linalg.eigvalsh(K))[::-1]
@@ -64,3 +66,20 @@ def test_naf_basis_paths(ctx, mixed, n):
     assert np.abs(U.T @ U - np.eye(k)).max() <= tol_orth
     if not mixed:
         assert np.abs(U @ U.T - U_ref @ U_ref.T).max() <= 1e-10
+
+
+def test_naf_basis_mixed_multidrain(ctx):
+    """140,000 pairs: more K-splits than a launch takes, so every CTA of the
+    metric drains its FP32 accumulators twice (alternating accumulator sets);
+    the result must match the single-drain accuracy."""
+    n, P = 130, 140000
+    B, K, thr = _case(n, 77, P)
+    U_ref, lam_kept, lam_all = O.naf_basis(K, thr)
+    Ut = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    lam = torch.zeros(n, dtype=torch.float64, device="cuda")
+    k = ctx.naf_basis(torch.from_numpy(B).cuda(), P, P, thr, Ut, lam, mixed=True)
+    assert k == U_ref.shape[1]
+    lg = lam[:k].cpu().numpy()
+    assert np.abs(lg - lam_kept[::-1]).max() <= 2e-5 * lam_all.max()
+    U = Ut[:k].cpu().numpy().T
+    assert np.linalg.norm(K @ U - U * lg[None, :], axis=0).max() <= 2e-5 * lam_all.max()
