@@ -224,13 +224,19 @@ def run_gpu(args):
     tri_ms = float(np.mean([x["ms_tridiag"] for x in stats]))
     pk, src = peaks()
     alu_peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    # DRAM bytes per launch (read + write) from the ncu captures summarised in profiles/
+    # (tc_tma_ts_pi_mid.md, hh_fused_double_mid.md); mid workload only
+    traffic_pi = 112.06e6 + 44.71e6 if args.workload == "mid" and mixed else None
+    traffic_tri = 26.0e6 + 0.01e6 if args.workload == "mid" else None
     if mixed:
         # three BF16 products (hi*hi, hi*lo, lo*hi) per useful product
         tc = 3 * pi_flops / (pi_ms / 1e3) / 1e12
-        roof_pi = {"bound": "tensor", "kernel": "tc_split_gemm_kernel (Pi(tau_k) moments, split-BF16 tcgen05)",
+        roof_pi = {"bound": "tensor", "kernel": "tc_tma_ts_kernel (Pi(tau_k) moments, split-BF16 tcgen05, A in TMEM)",
                    "achieved": tc, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tc / pk["bf16_tflops"],
                    "peak_source": f"bf16_tflops (burst, kernel of {pi_ms:.3f} ms) of {src} MEASURED_PEAKS.json",
-                   "flops_per_launch": 3 * pi_flops, "ms_per_launch": pi_ms, "traffic": None}
+                   "flops_per_launch": 3 * pi_flops, "ms_per_launch": pi_ms, "traffic": traffic_pi,
+                   "note": "algorithmic flops (SYRK as N^2 K, 453 NAFs); the padded 128 x 128 tiles do 1.59x "
+                           "this in MMA work"}
     else:
         a = pi_flops / (pi_ms / 1e3) / 1e12
         roof_pi = {"bound": "alu", "kernel": "gemm_f64_kernel (Pi(tau_k) moments, FP64 SYRK)", "achieved": a,
@@ -250,7 +256,7 @@ def run_gpu(args):
                 "note": "full-storage fused form does 2 N^3 FP64 flops (the 4/3 N^3 counted here exploit "
                         "symmetry); one grid barrier (1.2 us measured alone) and three block barriers per "
                         "reflector on top",
-                "traffic": None}
+                "traffic": traffic_tri}
     roofline = roof_tri if tri_ms > pi_ms else roof_pi
     clocks = clk.summary()
     line = {"metric": "G0W0 solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

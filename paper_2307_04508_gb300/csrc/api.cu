@@ -371,7 +371,7 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   CHECK_LAUNCH(ctx, launch_split_bf16(A, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
   TcGemmArgs g;
   g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.n_t = n_t; g.nt_group = 2;
-  g.B_hi = Bhi; g.B_lo = Blo; g.rows_a = Mp; g.rows_b = Mp;
+  g.B_hi = Bhi; g.B_lo = Blo; g.rows_a = Mp; g.rows_b = Mp; g.out_colmajor = 1;
   TcRun run;
   ctx->mark(EV_PI0, s);
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
@@ -379,10 +379,10 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   ctx->pi_tc_flops = 3.0 * 2.0 * (double)run.n_tiles * 128 * 128 * (double)Kp * n_t;
   if (n_tau == 0) {
     CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                           nI, n_t, N, -2.0 * spin, Pi, s, 0.0, g.nt_group), 1);
+                                           nI, n_t, N, -2.0 * spin, Pi, s, 0.0, g.nt_group, 1), 1);
   } else {
     CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                           nI, n_t, N, 1.0, M, s, 0.0, g.nt_group), 1);
+                                           nI, n_t, N, 1.0, M, s, 0.0, g.nt_group, 1), 1);
     CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
   }
   return LTGW_OK;
@@ -414,7 +414,7 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
   TcRun run;
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
   CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                         nI, 1, n, 1.0, K, s, beta, g.nt_group), 1);
+                                         nI, 1, n, 1.0, K, s, beta, g.nt_group, 0), 1);
   return LTGW_OK;
 }
 

@@ -108,6 +108,7 @@ struct TcGemmArgs {
   int64_t k_per_split = 0;
   int64_t drain_k = 2048;        // pairs per FP32 accumulation (bounds its rounding bias)
   int out_mode = TC_OUT_F64;     // F32 requires k_per_split <= drain_k
+  int out_colmajor = 0;          // F64 / F32 partial tiles stored [col][row] (coalesced drains)
   double *partial = nullptr;     // TC_OUT_F64
   float *partial32 = nullptr;    // TC_OUT_F32
   // TC_OUT_COLDOT (nt_group = 1): out[split][group][tile row][col] =
@@ -154,10 +155,11 @@ cudaError_t launch_to_f32_padded(const double *src, int64_t lds, int rows, int64
 cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n_t, const double *p0,
                                const double *p1, int mode, float *scale, cudaStream_t s);
 // M_t = alpha * sum over splits of the partial tiles (FP64 or FP32), full symmetric
-// [n_t][N][N] FP64, for a lower tile list (tile_index [nI][nJ]); nt_group scales per group.
+// [n_t][N][N] FP64, for a lower tile list (tile_index [nI][nJ]); nt_group scales per
+// group; colmajor: partial tiles stored [col][row].
 cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
                                  int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
-                                 double *M, cudaStream_t s, double beta, int nt_group);
+                                 double *M, cudaStream_t s, double beta, int nt_group, int colmajor);
 // dst[c][r] = src[r][c0 + c] in FP64 (batched)
 cudaError_t launch_transpose_f64(const double *src, int64_t lds, int64_t c0, int rows, int cols, double *dst,
                                  int64_t ldd, int batch, int64_t strideS, int64_t strideD, cudaStream_t s);

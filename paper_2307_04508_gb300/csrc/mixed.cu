@@ -47,7 +47,7 @@ __global__ void scale_table_kernel(const double *__restrict__ delta, int64_t K, 
 // tiles are 128 x 128, four scales per group.
 __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
                                      int splits, int groups, int n_tiles, const int *__restrict__ tile_index,
-                                     int nJ, int N, int nt_group, double alpha, double beta,
+                                     int nJ, int N, int nt_group, int colmajor, double alpha, double beta,
                                      double *__restrict__ M) {
   const int t = blockIdx.y;
   const int grp = t / nt_group, slot = t % nt_group;
@@ -56,15 +56,18 @@ __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const f
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ntri;
        e += (int64_t)gridDim.x * blockDim.x) {
     // e -> (i, j), i >= j, row-major lower triangle
-    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
-    while ((int64_t)i * (i + 1) / 2 > e) --i;
-    const int j = (int)(e - (int64_t)i * (i + 1) / 2);
+    int a = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= e) ++a;
+    while ((int64_t)a * (a + 1) / 2 > e) --a;
+    const int b = (int)(e - (int64_t)a * (a + 1) / 2);
+    // (a, b), a >= b, b fastest; column-major tiles take (i, j) = (N-1-b, N-1-a) so that
+    // consecutive threads read consecutive rows of one column
+    const int i = colmajor ? N - 1 - b : a, j = colmajor ? N - 1 - a : b;
     const int tile = tile_index[(i / 128) * nJ + (j / 128)];
+    const int64_t in_tile = colmajor ? (int64_t)(j % 128) * 128 + (i % 128) : (int64_t)(i % 128) * 128 + (j % 128);
     double acc = 0.0;
     for (int s = 0; s < splits; ++s) {
-      const int64_t off = ((((int64_t)s * groups + grp) * nt_group + slot) * n_tiles + tile) * (128 * 128) +
-                          (i % 128) * 128 + (j % 128);
+      const int64_t off = ((((int64_t)s * groups + grp) * nt_group + slot) * n_tiles + tile) * (128 * 128) + in_tile;
       acc += partial32 ? (double)partial32[off] : partial[off];
     }
     acc *= alpha;
@@ -174,7 +177,7 @@ cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n
 
 cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, int splits, int groups,
                                  int n_tiles, const int *tile_index, int nJ, int n_t, int N, double alpha,
-                                 double *M, cudaStream_t s, double beta, int nt_group) {
+                                 double *M, cudaStream_t s, double beta, int nt_group, int colmajor) {
   if (N <= 0 || n_t <= 0) return cudaSuccess;
   int64_t ntri = (int64_t)N * (N + 1) / 2;
   int bx = (int)((ntri + 255) / 256);
@@ -182,7 +185,7 @@ cudaError_t launch_tc_reduce_sym(const double *partial, const float *partial32, 
   dim3 grid(bx, n_t);
   if (nt_group < 1 || (n_t + nt_group - 1) / nt_group != groups) return cudaErrorInvalidValue;
   tc_reduce_sym_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, tile_index, nJ, N,
-                                            nt_group, alpha, beta, M);
+                                            nt_group, colmajor, alpha, beta, M);
   return cudaGetLastError();
 }
 

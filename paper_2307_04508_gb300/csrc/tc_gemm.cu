@@ -256,7 +256,20 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
               "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(a));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (g.out_mode == TC_OUT_F64) {
+        if (g.out_colmajor && g.out_mode != TC_OUT_COLDOT) {
+          // [col][row]: for each column the warp's 32 rows are one contiguous store
+          const int64_t o = base + t * tstride + (int64_t)(h * 32) * TM + row;
+          if (g.out_mode == TC_OUT_F32) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) g.partial32[o + (int64_t)q * TM] = __uint_as_float(r[q]);
+          } else if (dr == 0) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) g.partial[o + (int64_t)q * TM] = (double)__uint_as_float(r[q]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) g.partial[o + (int64_t)q * TM] += (double)__uint_as_float(r[q]);
+          }
+        } else if (g.out_mode == TC_OUT_F64) {
           double *oh = g.partial + base + t * tstride + (int64_t)row * TN + h * 32;
           if (dr == 0) {
 #pragma unroll
