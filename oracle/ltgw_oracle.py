@@ -49,6 +49,7 @@ __all__ = [
     "pair_gaps", "polarizability_direct", "laplace_moments", "polarizability_lt",
     "screened_interaction", "w_nm", "sigma_iw", "pade_coefficients", "pade_eval",
     "qp_newton", "solve", "sinc_laplace_grid", "pade_nodes",
+    "E4M3_MAX", "e4m3_round", "fp8_row_quantize", "pi_scale_table", "polarizability_fp8",
 ]
 
 
@@ -151,6 +152,79 @@ def polarizability_lt(M: np.ndarray, omegas: np.ndarray, x: np.ndarray, spin: in
         e = np.exp(-om * om * x)
         out[j] = -2.0 * spin * np.tensordot(e, M, axes=(0, 0))
     return out
+
+
+# ----------------------------------------------------------------------------
+# FP8 E4M3 form of the Pi contraction (per-auxiliary-row scales)
+# ----------------------------------------------------------------------------
+# Not a step of the paper: the low-precision variant of the Pi contraction.
+# Its plain definition: every operand value is rounded to the FP8 E4M3 grid
+# after a per-row scale that maps the row's largest magnitude to the largest
+# finite E4M3 value, and the products of the rounded values are summed
+# exactly.  The values fed to the rounding are formed in FP32 exactly as a
+# GPU forms them (FP32 copy of R~, FP32 per-pair scale, FP32 products), so
+# that both sides take every rounding decision on the same number.
+E4M3_MAX = 448.0
+
+
+def e4m3_round(v) -> np.ndarray:
+    """Round to the FP8 E4M3 grid (OCP 8-bit floating point: 4 exponent bits,
+    bias 7, 3 mantissa bits, subnormals below 2^-6 with spacing 2^-9, largest
+    finite value 448, no infinities), round half to even, saturating at +-448."""
+    v = np.asarray(v, dtype=np.float64)
+    a = np.abs(v)
+    _, e = np.frexp(a)                      # a = f 2^e with f in [0.5, 1)
+    e = np.maximum(e - 1, -6)               # binade 2^e <= a < 2^(e+1); subnormals share 2^-6's spacing
+    q = np.ldexp(1.0, e - 3)                # 3 mantissa bits: spacing 2^(e-3)
+    r = np.minimum(np.rint(a / q) * q, E4M3_MAX)
+    return np.copysign(r, v)
+
+
+def fp8_row_quantize(X):
+    """Per-row scaling onto the E4M3 grid: inv_r = 448 / max_j |X_rj| (FP32;
+    0 for a zero row), codes = e4m3(X_rj * inv_r) with the product in FP32.
+    X ~ codes / inv_r.  Returns (codes as float64, inv as float32)."""
+    X = np.asarray(X, dtype=np.float32)
+    m = np.abs(X).max(axis=1)
+    inv = np.zeros_like(m)
+    nz = m > 0
+    inv[nz] = np.float32(E4M3_MAX) / m[nz]
+    return e4m3_round(X * inv[:, None]), inv
+
+
+def pi_scale_table(delta, omegas=None, x=None, w=None) -> np.ndarray:
+    """Per-pair factors in FP32: Delta / (w_j^2 + Delta^2) per frequency (Eq. Pi)
+    or w_m Delta exp(-Delta^2 x_m) per Laplace point (the M^m form), each
+    formed in FP64 and rounded once."""
+    delta = np.asarray(delta, dtype=np.float64)
+    if x is None:
+        rows = [delta / (om * om + delta * delta) for om in omegas]
+    else:
+        rows = [w[m] * delta * np.exp(-delta * delta * x[m]) for m in range(len(x))]
+    return np.array(rows).astype(np.float32)
+
+
+def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None) -> np.ndarray:
+    """Pi in the FP8 E4M3 form: B32 = fp32(R~); for each frequency (Eq. Pi) or
+    Laplace point (M^m form) with FP32 factors s_k, A_k = fp32(B32 * s_k);
+    A_k and B32 are quantised per auxiliary row (fp8_row_quantize) and
+    M_k = (qA_k / invA_k) (qB / invB)^T summed exactly, lower triangle
+    mirrored; then Pi as in polarizability_direct or polarizability_lt."""
+    B32 = np.asarray(Bt, dtype=np.float32)
+    S = pi_scale_table(delta, omegas, x, w)
+    qb, invb = fp8_row_quantize(B32)
+    Bd = qb / np.where(invb > 0, invb, 1.0).astype(np.float64)[:, None]
+    M = np.empty((len(S), B32.shape[0], B32.shape[0]))
+    for k in range(len(S)):
+        qa, inva = fp8_row_quantize(B32 * S[k][None, :])
+        Ad = qa / np.where(inva > 0, inva, 1.0).astype(np.float64)[:, None]
+        Mk = Ad @ Bd.T
+        # qA qB^T is not exactly symmetric (the two operands carry different
+        # scales): the lower triangle (P >= Q) is formed and mirrored
+        M[k] = np.tril(Mk) + np.tril(Mk, -1).T
+    if x is None:
+        return -2.0 * spin * M
+    return polarizability_lt(M, omegas, x, spin)
 
 
 # ----------------------------------------------------------------------------
