@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--compare-prefix", type=int, default=32,
                     help="serving: requests of the stream solved back to back in both forms for the ratio")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"],
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "fp8"],
                     help="bf16x3: every contraction on the tensor cores with split-BF16 operands (eigensolver, "
                          "screening, Pade, Newton in FP64); fp64: every step in FP64")
     return ap.parse_args()
@@ -168,6 +168,59 @@ def _solve_loop(ctx, p, dev, out_dev, stream, flush, steps, clk=None):
     return np.array([a.elapsed_time(b) for a, b in ev]), stats
 
 
+PREC = {"fp64": 0, "bf16x3": 1, "fp8": 2}                  # ltgw.LTGW_FP64 / LTGW_BF16X3 / LTGW_FP8
+DTYPE = {"fp64": "f64", "bf16x3": "bf16x3", "fp8": "fp8e4m3"}
+
+
+def pi_roofline(prec, pi_flops, pi_ms, pk, src, traffic=None):
+    """Roofline of the Pi-build kernel: algorithmic flops (SYRK as N^2 K) per launch
+    over its CUDA-event time; split-BF16 does three tensor products per useful one."""
+    if prec == "fp64":
+        a = pi_flops / (pi_ms / 1e3) / 1e12
+        peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+        return {"bound": "alu", "kernel": "gemm_tile_kernel<double> (Pi(tau_k) moments, FP64 SYRK)", "achieved": a,
+                "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
+                "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": traffic}
+    if prec == "fp8":
+        a = pi_flops / (pi_ms / 1e3) / 1e12
+        peak = 2.0 * pk["bf16_tflops"]
+        return {"bound": "tensor", "kernel": "tc_fp8_kernel (Pi(tau_k) moments, FP8 E4M3 tcgen05 kind::f8f6f4)",
+                "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "peak_source": f"2 x bf16_tflops (the nominal fp8 / bf16 dense ratio, 4.5 / 2.25 PFLOP/s) of {src} "
+                               "MEASURED_PEAKS.json",
+                "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": traffic,
+                "note": "algorithmic flops (SYRK as N^2 K); the padded 128 x 128 tiles do more MMA work; the "
+                        "quantisation pass before the kernel is not in ms_per_launch"}
+    tc = 3 * pi_flops / (pi_ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "tc_tma_ts_kernel (Pi(tau_k) moments, split-BF16 tcgen05, A in TMEM)",
+            "achieved": tc, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tc / pk["bf16_tflops"],
+            "peak_source": f"bf16_tflops (burst, kernel of {pi_ms:.3f} ms) of {src} MEASURED_PEAKS.json",
+            "flops_per_launch": 3 * pi_flops, "ms_per_launch": pi_ms, "traffic": traffic,
+            "note": "algorithmic flops (SYRK as N^2 K, three BF16 products per useful one); the padded "
+                    "128 x 128 tiles do more MMA work"}
+
+
+def pi_error_vs_fp64(ctx, prob, N, n_omega, prec, stream):
+    """Relative Frobenius error of Pi(i w_j) in the given tensor-core form against
+    the FP64 form, both through the library's entry points, on the first N
+    auxiliary rows of the active pairs (the NAF-basis Pi's shape), direct form
+    (Eq. Pi) on the n_omega GL frequencies."""
+    import torch
+    from paper_2307_04508_gb300 import ltgw
+    nf, no, nv = prob.n_frozen, prob.n_occ, prob.n_virt
+    Bs = torch.from_numpy(np.ascontiguousarray(prob.B_ov[:N, nf * nv:])).cuda()
+    delta = torch.from_numpy(np.ascontiguousarray(
+        (prob.eps[no:][None, :] - prob.eps[nf:no][:, None]).reshape(-1))).cuda()
+    om, _ = ltgw.gl_grid(n_omega, 0.5)
+    ref = torch.empty((n_omega, N, N), dtype=torch.float64, device="cuda")
+    got = torch.empty_like(ref)
+    ctx.polarizability(Bs, delta, om, ref, spin=2, stream=stream)
+    ctx.polarizability_mixed(Bs, delta, om, got, spin=2, stream=stream, fp8=prec == "fp8")
+    torch.cuda.synchronize()
+    return float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+
+
 def run_gpu(args):
     import torch
     from paper_2307_04508_gb300 import ltgw
@@ -184,13 +237,13 @@ def run_gpu(args):
     ctx = ltgw.Context(local)
     stream = torch.cuda.Stream()
     T = len(prob.targets)
-    mixed = args.precision == "bf16x3"
+    mixed = args.precision != "fp64"
 
     def params(prec):
         return ltgw.make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, cfg["n_omega"], cfg["n_tau"],
                                 0.5, cfg["naf_thresh"], 2, True, prec)
 
-    p = params(ltgw.LTGW_BF16X3 if mixed else ltgw.LTGW_FP64)
+    p = params(PREC[args.precision])
     p64 = params(ltgw.LTGW_FP64)
     dev = {"eps": torch.from_numpy(prob.eps).cuda(), "B_ov": torch.from_numpy(prob.B_ov).cuda(),
            "B_tgt": torch.from_numpy(prob.B_tgt).cuda(),
@@ -226,23 +279,9 @@ def run_gpu(args):
     alu_peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
     # DRAM bytes per launch (read + write) from the ncu captures summarised in profiles/
     # (tc_tma_ts_pi_mid.md, hh_fused_double_mid.md); mid workload only
-    traffic_pi = 112.06e6 + 44.71e6 if args.workload == "mid" and mixed else None
+    traffic_pi = 112.06e6 + 44.71e6 if args.workload == "mid" and args.precision == "bf16x3" else None
     traffic_tri = 26.0e6 + 0.01e6 if args.workload == "mid" else None
-    if mixed:
-        # three BF16 products (hi*hi, hi*lo, lo*hi) per useful product
-        tc = 3 * pi_flops / (pi_ms / 1e3) / 1e12
-        roof_pi = {"bound": "tensor", "kernel": "tc_tma_ts_kernel (Pi(tau_k) moments, split-BF16 tcgen05, A in TMEM)",
-                   "achieved": tc, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tc / pk["bf16_tflops"],
-                   "peak_source": f"bf16_tflops (burst, kernel of {pi_ms:.3f} ms) of {src} MEASURED_PEAKS.json",
-                   "flops_per_launch": 3 * pi_flops, "ms_per_launch": pi_ms, "traffic": traffic_pi,
-                   "note": "algorithmic flops (SYRK as N^2 K, 453 NAFs); the padded 128 x 128 tiles do 1.59x "
-                           "this in MMA work"}
-    else:
-        a = pi_flops / (pi_ms / 1e3) / 1e12
-        roof_pi = {"bound": "alu", "kernel": "gemm_f64_kernel (Pi(tau_k) moments, FP64 SYRK)", "achieved": a,
-                   "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
-                   "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
-                   "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": None}
+    roof_pi = pi_roofline(args.precision, pi_flops, pi_ms, pk, src, traffic_pi)
     # Householder reduction of the N_aux x N_aux metric: 4/3 N^3 algorithmic flops,
     # N - 2 steps of one grid barrier each (latency-bound at mid size)
     tri_flops = 4.0 / 3.0 * prob.n_aux ** 3
@@ -261,7 +300,7 @@ def run_gpu(args):
     clocks = clk.summary()
     line = {"metric": "G0W0 solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if mixed else "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": desc, "precision": args.precision,
                        "l2": "256 MB buffer written between steps; inputs 553 MB > L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -278,6 +317,8 @@ def run_gpu(args):
         line["fp64_form"] = {"solves_per_s": len(ms64) / (ms64.sum() / 1e3), "ms_per_solve": float(ms64.mean())}
         line["speedup_vs_fp64_form"] = value / line["fp64_form"]["solves_per_s"]
         line["qp_max_mev_vs_fp64_form"] = float(np.abs(e_main - e64).max() * HA2MEV)
+        line["qp_mev_vs_fp64_form_per_state"] = (np.abs(e_main - e64) * HA2MEV).tolist()
+        line["pi_rel_frob_vs_fp64_form"] = pi_error_vs_fp64(ctx, prob, N, cfg["n_omega"], args.precision, stream)
     # end-to-end: host (pinned) inputs and outputs through the same C ABI call
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
            {"eps": prob.eps, "B_ov": prob.B_ov, "B_tgt": prob.B_tgt,
@@ -390,9 +431,13 @@ def run_large(args):
     targets = torch.from_numpy(law.targets.astype(np.int32)).cuda()
     shift = torch.from_numpy(law.shift).cuda()
     T = len(law.targets)
-    mixed = args.precision == "bf16x3"
-    p = ltgw.make_params(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["n_omega"], cfg["n_tau"],
-                         0.5, cfg["naf_thresh"], 2, True, ltgw.LTGW_BF16X3 if mixed else ltgw.LTGW_FP64)
+    mixed = args.precision != "fp64"
+
+    def params(prec):
+        return ltgw.make_params(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["n_omega"],
+                                cfg["n_tau"], 0.5, cfg["naf_thresh"], 2, True, PREC[prec])
+
+    p = params(args.precision)
     ctx = ltgw.Context(0)
     ctx.set_timing(True)
     stream = torch.cuda.Stream()
@@ -402,9 +447,9 @@ def run_large(args):
     def fill(i0, i1, dst, strm):
         return law.fill_block(i0, i1, dst)
 
-    def one():
+    def one(pp=p):
         t0 = time.perf_counter()
-        ctx.solve_streamed(p, eps, fill, args.occ_block, B_tgt, targets, shift, *out, stream=stream)
+        ctx.solve_streamed(pp, eps, fill, args.occ_block, B_tgt, targets, shift, *out, stream=stream)
         return time.perf_counter() - t0, ctx.stats()
 
     for _ in range(max(args.warmup, 3)):
@@ -421,11 +466,11 @@ def run_large(args):
     pi_flops = cfg["n_tau"] * N * N * n_ov
     pi_ms = float(np.mean([r[1]["ms_pi_kernel"] for r in res]))
     pk, src = peaks()
-    tc = 3 * pi_flops / (pi_ms / 1e3) / 1e12
+    e_main = out[1].cpu().numpy().copy()
     line = {"metric": "G0W0 solves/s (large system, streamed)", "value": len(res) / solve_s.sum(),
             "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(solve_s.mean()), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3" if mixed else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "large: n_occ=320 (60 frozen), n_virt=3500, N_aux=9000, NAF 1e-2, N_omega=32, "
                                    f"N_tau=10, 20 QP states; RI tensor generated on the device in blocks of "
                                    f"{args.occ_block} occupied orbitals inside the solve (FP32 loading GEMM), "
@@ -435,15 +480,13 @@ def run_large(args):
             "n_naf": N, "pi_build_tflops": pi_flops / (pi_ms / 1e3) / 1e12,
             "stage_ms": {k: st[k] for k in ("ms_naf", "ms_tridiag", "ms_pi", "ms_screen", "ms_wnm", "ms_sigma_qp",
                                             "ms_total")},
-            "roofline_pi_build": {"bound": "tensor" if mixed else "alu",
-                                  "kernel": "tc_split_gemm_kernel (Pi(tau_k) moments, split-BF16 tcgen05)",
-                                  "achieved": tc if mixed else pi_flops / (pi_ms / 1e3) / 1e12,
-                                  "peak": pk["bf16_tflops"] if mixed else fp64_alu_peak_tflops(),
-                                  "unit": "TFLOP/s", "ms_per_launch": pi_ms,
-                                  "frac": (tc / pk["bf16_tflops"]) if mixed else
-                                  pi_flops / (pi_ms / 1e3) / 1e12 / fp64_alu_peak_tflops()},
-            "e_qp_ha": out[1].cpu().numpy().tolist(), "qp_status": out[2].cpu().numpy().tolist(),
+            "roofline_pi_build": pi_roofline(args.precision, pi_flops, pi_ms, pk, src),
+            "e_qp_ha": e_main.tolist(), "qp_status": out[2].cpu().numpy().tolist(),
             "clocks": clk.summary()}
+    if args.precision == "fp8":
+        # the same solve in the split-BF16 form (within a few 0.01 meV of FP64 at the mid size)
+        one(params("bf16x3"))
+        line["qp_mev_vs_bf16x3_form_per_state"] = (np.abs(e_main - out[1].cpu().numpy()) * HA2MEV).tolist()
     print(json.dumps(line), flush=True)
     ctx.close()
 

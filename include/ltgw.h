@@ -76,8 +76,12 @@ typedef struct {
   double naf_thresh;  /* < 0: no NAF; >= 0: keep eigenvalues of K above it        */
   int spin;           /* 1 (spin orbitals) or 2 (closed shell)                    */
   int use_laplace;    /* 0: Pi from Eq. Pi; 1: Pi from the Laplace moments M^m     */
-  int precision;      /* LTGW_FP64, or LTGW_BF16X3: Pi on the tensor cores with    */
-                      /* split-BF16 operands (see ltgw_polarizability_mixed)      */
+  int precision;      /* LTGW_FP64; LTGW_BF16X3: the dense contractions (NAF       */
+                      /* metric, projections, Pi, W_nm) on the tensor cores with  */
+                      /* split-BF16 operands (see ltgw_polarizability_mixed);     */
+                      /* LTGW_FP8: the same with the Pi build in FP8 E4M3 with    */
+                      /* per-auxiliary-row scales (ltgw_polarizability_fp8).      */
+                      /* The eigensolver, screening, Pade and Newton stay FP64.   */
   int reserved;       /* must be 0                                                */
 } ltgw_params;
 
@@ -197,12 +201,29 @@ ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const dou
  * pair sum runs on the tensor cores with BF16 hi/lo split operands
  * (x = bf16(x) + bf16(x - bf16(x)); hi*hi + hi*lo + lo*hi), the per-pair scale
  * applied while the operands are loaded, FP32 accumulation drained to FP64
- * every 16384 pairs.  Same arguments and layout as ltgw_polarizability;
- * relative error about 1e-5.  Synchronises. */
+ * every 2048 pairs (each MMA's FP32 rounding biases sums of one sign by about
+ * half an ulp, so the drain length bounds the drift).  Same arguments and
+ * layout as ltgw_polarizability; relative error about 1e-5.  Synchronises. */
 ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
                                       const double *delta, int n_omega, const double *omegas,
                                       int n_tau, const double *x, const double *w, int spin,
                                       double *Pi, void *stream);
+
+/* The same polarisability in FP8 E4M3 (not a step of the paper: the
+ * low-precision variant of its Pi contraction).  R~ is rounded to FP32, the
+ * per-pair factors of Eq. Pi (or of the M^m form) are formed in FP64 and
+ * rounded to FP32, and every row of R~ and of each R~ diag(factor) (FP32
+ * products) is scaled so that its largest magnitude maps to 448, the largest
+ * finite E4M3 value, then rounded to E4M3 (nearest even, saturating).  The
+ * products of the codes are summed on the tensor cores (kind::f8f6f4) in FP32,
+ * drained every 4096 pairs, de-scaled per row and summed over K-splits in
+ * FP64; each Pi_j (or M^m) is formed on its lower triangle and mirrored.
+ * Relative error against the exact Pi about 1e-3 (E4M3 keeps 3 mantissa
+ * bits).  Same arguments and layout as ltgw_polarizability.  Synchronises. */
+ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                    const double *delta, int n_omega, const double *omegas,
+                                    int n_tau, const double *x, const double *w, int spin,
+                                    double *Pi, void *stream);
 
 /* Screening (Eq. ScreenedCoulombOrbital): C_j = [1 - Pi_j]^-1 - 1 for each of
  * n_omega matrices (device [n_omega][N][N] in and out, may not alias).

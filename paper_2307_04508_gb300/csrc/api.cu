@@ -255,8 +255,9 @@ ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const doub
 // the CTAs of one wave run in lockstep, so the time is about waves x (per-CTA
 // overhead + K chunks per CTA); the overhead (TMEM and barrier setup, pipeline
 // fill, draining the accumulators) costs about as much as ten 64-pair chunks.
-// At least Kp / drain_k splits (up to 64) keep each CTA to one FP32 drain.
-int64_t tc_splits(const ltgw_ctx *ctx, int64_t units, int64_t Kp, int64_t drain_k, int64_t *kps_out) {
+// At least Kp / drain_k splits (up to 64) keep each CTA to one FP32 drain; the
+// split length is a multiple of `align` pairs.
+int64_t tc_splits(const ltgw_ctx *ctx, int64_t units, int64_t Kp, int64_t drain_k, int64_t align, int64_t *kps_out) {
   const int64_t max_split = std::min<int64_t>(64, std::max<int64_t>(1, Kp / 1024));
   const int64_t min_split = std::min<int64_t>(max_split, (Kp + drain_k - 1) / drain_k);
   const int64_t nchunk = Kp / 64;
@@ -267,7 +268,7 @@ int64_t tc_splits(const ltgw_ctx *ctx, int64_t units, int64_t Kp, int64_t drain_
     const double cost = (double)waves * (10.0 + (double)((nchunk + sp - 1) / sp));
     if (cost < best) { best = cost; splits = sp; }   // fewer splits on ties
   }
-  int64_t kps = ((Kp + splits - 1) / splits + 63) / 64 * 64;
+  int64_t kps = ((Kp + splits - 1) / splits + align - 1) / align * align;
   *kps_out = kps;
   return (Kp + kps - 1) / kps;
 }
@@ -304,7 +305,7 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
   const int n_tiles = (int)(tiles.size() / 2);
   const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
   int64_t kps = 0;
-  int64_t splits = tc_splits(ctx, (int64_t)n_tiles * groups, g.Kp, g.drain_k, &kps);
+  int64_t splits = tc_splits(ctx, (int64_t)n_tiles * groups, g.Kp, g.drain_k, g.A8 ? 128 : 64, &kps);
   // the column dot needs the whole contraction (K = the NAF count) in one drain
   if (g.out_mode == TC_OUT_COLDOT) { kps = g.Kp; splits = 1; g.drain_k = std::max<int64_t>(g.drain_k, g.Kp); }
   const bool f32 = g.out_mode != TC_OUT_COLDOT && kps <= g.drain_k;
@@ -329,34 +330,44 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
   g.cd_out = run->cd_out;
   g.n_tile_rows = coldot_rows;
   g.err = ctx->flags;
-  CHECK_LAUNCH(ctx, launch_tc_split_gemm(g, n_tiles, s), 1);
+  CHECK_LAUNCH(ctx, g.A8 ? launch_tc_fp8_gemm(g, n_tiles, s) : launch_tc_split_gemm(g, n_tiles, s), 1);
   run->splits = (int)splits;
   run->groups = groups;
   run->n_tiles = n_tiles;
   return LTGW_OK;
 }
 
-// Pi (direct) or the Laplace moments M^k in the split-BF16 form on the tensor
-// cores.  Operand: Af (FP32 [roundup(N,128)][roundup(n_pairs,64)]) when given,
-// else converted from the FP64 block Bt.  Scale table (the per-pair factor of
-// Eq. Pi or of the M^m form) is applied by the converter warps.
+// Pi (direct) or the Laplace moments M^k on the tensor cores, split-BF16 or
+// (fp8) FP8 E4M3 with per-row scales.  Operand: Af (FP32
+// [roundup(N,128)][roundup(n_pairs,64)]) when given, else converted from the
+// FP64 block Bt.  Scale table: the per-pair factor of Eq. Pi or of the M^m
+// form, applied by the converter warps (split-BF16) or before quantisation (FP8).
 ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, int64_t ldb,
                               const float *Af_in, const double *delta, int n_omega, const double *d_omega,
                               int n_tau, const double *d_x, const double *d_w, const double *d_E,
-                              double *M, int spin, double *Pi, cudaStream_t s) {
-  const int64_t Kp = (n_pairs + 63) / 64 * 64;
+                              double *M, int spin, double *Pi, cudaStream_t s, bool fp8) {
+  const int64_t Kp = (n_pairs + 63) / 64 * 64, Kq = (n_pairs + 127) / 128 * 128;
   const int nI = (N + 127) / 128, Mp = nI * 128;
   const int n_t = n_tau ? n_tau : n_omega;
   std::vector<int> tindex;
   std::vector<int> tiles = lower_tiles(nI, &tindex);
   float *Af = nullptr, *scale;
-  __nv_bfloat16 *Bhi, *Blo;   // the unscaled operand, pre-split for the TMA-fed kernel
+  __nv_bfloat16 *Bhi = nullptr, *Blo = nullptr;   // the unscaled operand, pre-split for the TMA-fed kernel
+  uint8_t *qa = nullptr, *qb = nullptr;           // FP8 codes: scaled operands [n_t][Mp][Kq], B [Mp][Kq]
+  float *ds_a = nullptr, *ds_b = nullptr;         // FP8 per-row de-scales
   int *d_tindex;
   auto layout = [&](Arena &A) {
     Af = Af_in ? nullptr : A.take<float>((size_t)Mp * Kp);
     scale = A.take<float>((size_t)n_t * Kp);
-    Bhi = A.take<__nv_bfloat16>((size_t)Mp * Kp);
-    Blo = A.take<__nv_bfloat16>((size_t)Mp * Kp);
+    if (fp8) {
+      qa = A.take<uint8_t>((size_t)n_t * Mp * Kq);
+      qb = A.take<uint8_t>((size_t)Mp * Kq);
+      ds_a = A.take<float>((size_t)n_t * Mp);
+      ds_b = A.take<float>((size_t)Mp);
+    } else {
+      Bhi = A.take<__nv_bfloat16>((size_t)Mp * Kp);
+      Blo = A.take<__nv_bfloat16>((size_t)Mp * Kp);
+    }
     d_tindex = A.take<int>(tindex.size());
   };
   ctx->a5.begin_sizing();
@@ -368,15 +379,22 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   if (!Af_in) CHECK_LAUNCH(ctx, launch_to_f32_padded(Bt, ldb, N, n_pairs, Af, Mp, Kp, s), 1);
   CHECK_LAUNCH(ctx, launch_scale_table(delta, n_pairs, Kp, n_t, n_tau ? d_x : d_omega, n_tau ? d_w : nullptr,
                                        n_tau ? SCALE_LAPLACE : SCALE_DIRECT, scale, s), 1);
-  CHECK_LAUNCH(ctx, launch_split_bf16(A, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
   TcGemmArgs g;
-  g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.n_t = n_t; g.nt_group = 2;
-  g.B_hi = Bhi; g.B_lo = Blo; g.rows_a = Mp; g.rows_b = Mp; g.out_colmajor = 1;
+  if (fp8) {
+    CHECK_LAUNCH(ctx, launch_fp8_quantize(A, Kp, Kq, scale, n_t, Mp, qa, qb, ds_a, ds_b, s), 1);
+    // FP32 sums of exact E4M3 products: a 4096-pair drain keeps the accumulation
+    // bias (about 4e-6) far below the E4M3 rounding error
+    g.A8 = qa; g.B8 = qb; g.ds_a = ds_a; g.ds_b = ds_b; g.Kp = Kq; g.nt_group = 4; g.drain_k = 4096;
+  } else {
+    CHECK_LAUNCH(ctx, launch_split_bf16(A, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
+    g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.nt_group = 2; g.B_hi = Bhi; g.B_lo = Blo;
+  }
+  g.n_t = n_t; g.rows_a = Mp; g.rows_b = Mp; g.out_colmajor = 1;
   TcRun run;
   ctx->mark(EV_PI0, s);
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
   ctx->mark(EV_PI1, s);
-  ctx->pi_tc_flops = 3.0 * 2.0 * (double)run.n_tiles * 128 * 128 * (double)Kp * n_t;
+  ctx->pi_tc_flops = (fp8 ? 1.0 : 3.0) * 2.0 * (double)run.n_tiles * 128 * 128 * (double)g.Kp * n_t;
   if (n_tau == 0) {
     CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
                                            nI, n_t, N, -2.0 * spin, Pi, s, 0.0, g.nt_group, 1), 1);
@@ -540,8 +558,8 @@ ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
   REQUIRE(ctx, p->spin == 1 || p->spin == 2, "spin must be 1 or 2");
   REQUIRE(ctx, p->use_laplace == 0 || p->use_laplace == 1, "use_laplace must be 0 or 1");
   REQUIRE(ctx, !p->use_laplace || (p->n_tau >= 1 && p->n_tau <= 32), "n_tau must be in [1, 32]");
-  REQUIRE(ctx, p->precision == LTGW_FP64 || p->precision == LTGW_BF16X3,
-          "precision must be LTGW_FP64 or LTGW_BF16X3");
+  REQUIRE(ctx, p->precision == LTGW_FP64 || p->precision == LTGW_BF16X3 || p->precision == LTGW_FP8,
+          "precision must be LTGW_FP64, LTGW_BF16X3 or LTGW_FP8");
   REQUIRE(ctx, p->reserved == 0, "reserved must be 0");
   REQUIRE(ctx, isfinite(p->naf_thresh), "naf_thresh must be finite");
   return LTGW_OK;
@@ -645,7 +663,8 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   const int n_omega = p->n_omega, T = n_tgt;
   const int n_tau = p->use_laplace ? p->n_tau : 0;
   const bool naf = p->naf_thresh >= 0.0;
-  const bool mixed = p->precision == LTGW_BF16X3;
+  const bool mixed = p->precision != LTGW_FP64;   // contractions on the tensor cores
+  const bool fp8 = p->precision == LTGW_FP8;      // ... with the Pi build in FP8 E4M3
   ctx->stats = ltgw_stats{};
   ctx->mark(EV_START, s);
 
@@ -862,7 +881,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   // ---- Pi (Eq. Pi or the Laplace form)
   if (mixed) {
     if (polarizability_tc(ctx, N, n_ov, nullptr, 0, d_Bf, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E,
-                          d_M, p->spin, d_Pi, s) != LTGW_OK)
+                          d_M, p->spin, d_Pi, s, fp8) != LTGW_OK)
       return ctx->status();
   } else if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
                                 p->spin, d_Pi, s) != LTGW_OK) {
@@ -932,6 +951,50 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   for (int t = 0; t < T; ++t)
     if (hs[t] != 0) ctx->fail(LTGW_ERR_NO_CONVERGE, "a quasi-particle Newton solve did not converge");
   return ctx->status();
+}
+
+ltgw_status polarizability_tc_api(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, const double *delta,
+                                  int n_omega, const double *omegas, int n_tau, const double *x, const double *w,
+                                  int spin, double *Pi, void *stream, bool fp8) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
+  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
+  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
+  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
+  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
+  for (int j = 0; j < n_omega; ++j)
+    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
+  double *d_om, *d_x, *d_w, *d_E, *d_M;
+  auto layout = [&](Arena &A) {
+    d_om = A.take<double>(n_omega);
+    d_x = A.take<double>(std::max(n_tau, 1));
+    d_w = A.take<double>(std::max(n_tau, 1));
+    d_E = A.take<double>(h_E.size());
+    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
+  };
+  ctx->a2.begin_sizing();
+  layout(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
+  layout(ctx->a2);
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
+  if (n_tau) {
+    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
+    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
+    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+  }
+  if (ctx->status() != LTGW_OK) return ctx->status();
+  if (polarizability_tc(ctx, N, n_pairs, Bt, n_pairs, nullptr, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                        spin, Pi, s, fp8) != LTGW_OK)
+    return ctx->status();
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->stats.ms_pi_kernel = ctx->ms(EV_PI0, EV_PI1);
+  ctx->stats.pi_kernel_launches = 1;
+  return check_flags(ctx, s);
 }
 
 }  // namespace
@@ -1036,45 +1099,13 @@ ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, con
                                       const double *delta, int n_omega, const double *omegas, int n_tau,
                                       const double *x, const double *w, int spin, double *Pi,
                                       void *stream) {
-  if (!ctx) return LTGW_ERR_BAD_ARG;
-  ctx->reset();
-  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
-  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
-  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
-  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
-  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
-  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
-  for (int j = 0; j < n_omega; ++j)
-    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
-  double *d_om, *d_x, *d_w, *d_E, *d_M;
-  auto layout = [&](Arena &A) {
-    d_om = A.take<double>(n_omega);
-    d_x = A.take<double>(std::max(n_tau, 1));
-    d_w = A.take<double>(std::max(n_tau, 1));
-    d_E = A.take<double>(h_E.size());
-    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
-  };
-  ctx->a2.begin_sizing();
-  layout(ctx->a2);
-  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
-  layout(ctx->a2);
-  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
-  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
-  if (n_tau) {
-    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
-    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
-    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
-  }
-  if (ctx->status() != LTGW_OK) return ctx->status();
-  if (polarizability_tc(ctx, N, n_pairs, Bt, n_pairs, nullptr, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
-                        spin, Pi, s) != LTGW_OK)
-    return ctx->status();
-  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
-  ctx->stats.ms_pi_kernel = ctx->ms(EV_PI0, EV_PI1);
-  ctx->stats.pi_kernel_launches = 1;
-  return check_flags(ctx, s);
+  return polarizability_tc_api(ctx, N, n_pairs, Bt, delta, n_omega, omegas, n_tau, x, w, spin, Pi, stream, false);
+}
+
+ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                    const double *delta, int n_omega, const double *omegas, int n_tau,
+                                    const double *x, const double *w, int spin, double *Pi, void *stream) {
+  return polarizability_tc_api(ctx, N, n_pairs, Bt, delta, n_omega, omegas, n_tau, x, w, spin, Pi, stream, true);
 }
 
 ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C, void *stream) {

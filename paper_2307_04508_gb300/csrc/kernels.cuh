@@ -124,10 +124,24 @@ struct TcGemmArgs {
   // (nt_group <= 2; not for TC_OUT_COLDOT or A groups).
   const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
   int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
+  // FP8 E4M3 form (launch_tc_fp8_gemm): codes qa [n_t][rows_a][Kp], qb [rows_b][Kp] and
+  // per-row de-scales ds_a [n_t][rows_a], ds_b [rows_b], applied in the epilogue.
+  const uint8_t *A8 = nullptr, *B8 = nullptr;
+  const float *ds_a = nullptr, *ds_b = nullptr;
 };
 cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s);
 // hi = bf16(x), lo = bf16(x - hi) elementwise: the split the tensor-core kernels use.
 cudaError_t launch_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t n, cudaStream_t s);
+// FP8 E4M3 operands with per-row scales (mixed.cu): for each row r of X [rows][Kp] (FP32),
+// inv = 448 / max|X_r|, qb[r][k] = e4m3(X_rk inv); for each factor row S[t] ([n_t][Kp])
+// the FP32 products X_rk S_tk get their own row scale, codes qa[t][r][k].  De-scales
+// (1 / inv, 0 for zero rows) in ds_b[r], ds_a[t][r]; code columns Kp..Kq-1 are zero.
+cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const float *S, int n_t, int rows,
+                                uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s);
+// Scaled contraction on FP8 E4M3 codes (tcgen05 kind::f8f6f4): D_t = diag(ds_a[t]) qa[t] qb^T diag(ds_b),
+// up to four scales per CTA (nt_group <= 4), Kp (of the codes) and k_per_split multiples of 128;
+// partial tiles as launch_tc_split_gemm (column-major).
+cudaError_t launch_tc_fp8_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s);
 size_t tc_gemm_smem_bytes();
 
 // ---- mixed-precision helpers (mixed.cu) ----

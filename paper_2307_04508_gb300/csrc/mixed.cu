@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -253,6 +254,107 @@ cudaError_t launch_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
   split_bf16_kernel<<<(int)blocks, 256, 0, s>>>(x, hi, lo, n);
+  return cudaGetLastError();
+}
+
+namespace {
+constexpr int Q8_THREADS = 256;
+constexpr float E4M3_MAX = 448.0f;   // largest finite FP8 E4M3 value
+
+__device__ __forceinline__ float block_max(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float m = 0.0f;
+#pragma unroll
+  for (int i = 0; i < Q8_THREADS / 32; ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+
+// four E4M3 codes (round to nearest even, saturating) of x * inv, packed low byte first
+__device__ __forceinline__ uint32_t e4m3x4(float4 x, float inv) {
+  const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x.x * inv, x.y * inv), __NV_SATFINITE, __NV_E4M3);
+  const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x.z * inv, x.w * inv), __NV_SATFINITE, __NV_E4M3);
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// One block per row r of X [rows][Kp] (FP32; Kp a multiple of 4): the row's
+// scale inv = 448 / max_k |X_rk| and codes qb[r][k] = e4m3(X_rk inv); for each
+// of the n_t factor rows S[t] the products p = X_rk S_tk (FP32) get their own
+// scale and codes qa[t][r][k].  De-scales 1 / inv (0 for a zero row) go to
+// ds_b[r] and ds_a[t][r]; code columns Kp..Kq-1 are zero.
+template <int MAXT>
+__global__ void __launch_bounds__(Q8_THREADS)
+    fp8_quantize_kernel(const float *__restrict__ X, int64_t Kp, int64_t Kq, const float *__restrict__ S, int n_t,
+                        int rows, uint8_t *__restrict__ qa, uint8_t *__restrict__ qb, float *__restrict__ ds_a,
+                        float *__restrict__ ds_b) {
+  __shared__ float red[Q8_THREADS / 32];
+  __shared__ float inv_s[MAXT + 1];
+  const int r = blockIdx.x;
+  const float4 *xr = reinterpret_cast<const float4 *>(X + (int64_t)r * Kp);
+  const int64_t n4 = Kp / 4, q4 = Kq / 4;
+  float mb = 0.0f, ma[MAXT];
+#pragma unroll
+  for (int t = 0; t < MAXT; ++t) ma[t] = 0.0f;
+  for (int64_t k = threadIdx.x; k < n4; k += Q8_THREADS) {
+    const float4 x = xr[k];
+    mb = fmaxf(mb, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t) {
+      if (t < n_t) {
+        const float4 sv = reinterpret_cast<const float4 *>(S + (int64_t)t * Kp)[k];
+        ma[t] = fmaxf(ma[t], fmaxf(fmaxf(fabsf(x.x * sv.x), fabsf(x.y * sv.y)),
+                                   fmaxf(fabsf(x.z * sv.z), fabsf(x.w * sv.w))));
+      }
+    }
+  }
+  mb = block_max(mb, red);
+  if (threadIdx.x == 0) inv_s[MAXT] = mb > 0.0f ? E4M3_MAX / mb : 0.0f;
+#pragma unroll
+  for (int t = 0; t < MAXT; ++t) {
+    if (t < n_t) {
+      const float m = block_max(ma[t], red);
+      if (threadIdx.x == 0) inv_s[t] = m > 0.0f ? E4M3_MAX / m : 0.0f;
+    }
+  }
+  __syncthreads();
+  const float invb = inv_s[MAXT];
+  if (threadIdx.x == 0) {
+    ds_b[r] = invb > 0.0f ? 1.0f / invb : 0.0f;
+    for (int t = 0; t < n_t; ++t) ds_a[(int64_t)t * rows + r] = inv_s[t] > 0.0f ? 1.0f / inv_s[t] : 0.0f;
+  }
+  uint32_t *qbr = reinterpret_cast<uint32_t *>(qb + (int64_t)r * Kq);
+  for (int64_t k = threadIdx.x; k < q4; k += Q8_THREADS) {
+    if (k >= n4) {
+      qbr[k] = 0u;
+      for (int t = 0; t < n_t; ++t) reinterpret_cast<uint32_t *>(qa + ((int64_t)t * rows + r) * Kq)[k] = 0u;
+      continue;
+    }
+    const float4 x = xr[k];
+    qbr[k] = e4m3x4(x, invb);
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t) {
+      if (t < n_t) {
+        const float4 sv = reinterpret_cast<const float4 *>(S + (int64_t)t * Kp)[k];
+        const float4 p = make_float4(x.x * sv.x, x.y * sv.y, x.z * sv.z, x.w * sv.w);
+        reinterpret_cast<uint32_t *>(qa + ((int64_t)t * rows + r) * Kq)[k] = e4m3x4(p, inv_s[t]);
+      }
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const float *S, int n_t, int rows,
+                                uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (Kp % 4 || Kq % 16 || Kq < Kp || n_t < 0 || n_t > 32) return cudaErrorInvalidValue;
+  if (n_t <= 8)
+    fp8_quantize_kernel<8><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b);
+  else
+    fp8_quantize_kernel<32><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b);
   return cudaGetLastError();
 }
 

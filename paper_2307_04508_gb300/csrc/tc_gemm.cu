@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <stddef.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include <stdint.h>
@@ -257,6 +258,12 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
             : "r"(a));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (g.out_colmajor && g.out_mode != TC_OUT_COLDOT) {
+          if (g.ds_a) {   // FP8 form: per-row de-scales of both operands
+            const float ra = g.ds_a[(int64_t)(grp * g.nt_group + t) * g.rows_a + ti * TM + row];
+            const float *cb = g.ds_b + tj * TN + h * 32;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) * (ra * __ldg(cb + q)));
+          }
           // [col][row]: for each column the warp's 32 rows are one contiguous store
           const int64_t o = base + t * tstride + (int64_t)(h * 32) * TM + row;
           if (g.out_mode == TC_OUT_F32) {
@@ -731,6 +738,145 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   }
 }
 
+// ---- FP8 E4M3 form: both operands quantised per row, brought in by TMA ----
+// D_t = qa_t qb^T on tcgen05 kind::f8f6f4 (E4M3 x E4M3, FP32 accumulation),
+// K = 32 per MMA; the per-row de-scales of both operands are applied in the
+// epilogue.  A chunk is 128 pairs (one 128-byte swizzled row per tile row); a
+// stage holds the A tiles of up to four scales and the B tile.  Warp roles
+// (9 warps): 0 TMEM allocation and MMA issue for scale 0, 1 TMA producer,
+// 2-5 epilogue, 6-8 MMA issue for scales 1-3 (one issuing thread per
+// accumulator, each stage's four MMAs back to back).
+constexpr int F8_K = 128;
+constexpr int F8_STAGES = 2;
+constexpr int F8_MAXT = 4;
+constexpr uint32_t F8_TILE = TM * F8_K;                      // 16 KB
+constexpr uint32_t F8_STAGE = (F8_MAXT + 1) * F8_TILE;       // A tiles of four scales + B
+constexpr int F8_ISSUE1 = 2 + EPI_WARPS;                     // issuer warp of scale 1
+constexpr int F8_THREADS = 32 * (F8_ISSUE1 + F8_MAXT - 1);
+constexpr uint32_t F8_SMEM = F8_STAGES * F8_STAGE + 1024;
+// kind::f8f6f4: D = FP32 (bit 4), A = B = E4M3 (format code 0), both K-major, N = 128, M = 128
+constexpr uint32_t IDESC8 = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+static_assert(F8_TILE % 1024 == 0 && F8_STAGE % 1024 == 0, "swizzled tiles must stay 1024-byte aligned");
+
+struct Bars8 {
+  uint64_t full[F8_STAGES], empty[F8_STAGES], acc_full[1], acc_empty[1], fin;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// D += A B^T over one 128-pair chunk: four K = 32 steps (32 bytes: +2 in the
+// descriptors' start-address field).  acc0 = 0 overwrites D first.
+__device__ __forceinline__ void mma_stage_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t acc0) {
+  asm volatile(
+      "{\n.reg .pred p;\n.reg .b64 a1, a2, a3, b1, b2, b3;\n"
+      "setp.ne.b32 p, %3, 0;\n"
+      "add.u64 a1, %1, 2;\nadd.u64 a2, %1, 4;\nadd.u64 a3, %1, 6;\n"
+      "add.u64 b1, %2, 2;\nadd.u64 b2, %2, 4;\nadd.u64 b3, %2, 6;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %4, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], a1, b1, %4, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], a2, b2, %4, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], a3, b3, %4, 1;\n"
+      "}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(acc0), "r"(IDESC8)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(F8_THREADS, 1)
+    tc_fp8_kernel(TcGemmArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sS = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(16) Bars8 bars;
+  __shared__ float cd_red[EPI_WARPS][TN];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, grp = blockIdx.y, split = blockIdx.z;
+  const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
+  const int t0 = grp * g.nt_group;
+  const int nt = min(g.nt_group, g.n_t - t0);
+  const int64_t kb = (int64_t)split * g.k_per_split;
+  const int64_t ke = min(g.Kp, kb + g.k_per_split);
+  const int nchunks = (int)((ke - kb) / F8_K);
+  const int chunks_per_drain = (int)(g.drain_k / F8_K);
+  const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
+
+  if (threadIdx.x == 0) {
+    // empty, acc_full and fin collect one commit from each of the nt issuers
+    for (int s = 0; s < F8_STAGES; ++s) { mbar_init(&bars.full[s], 1); mbar_init(&bars.empty[s], nt); }
+    mbar_init(&bars.acc_full[0], nt);
+    mbar_init(&bars.acc_empty[0], 32 * EPI_WARPS);
+    mbar_init(&bars.fin, nt);
+    bars.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        smem_u32(&bars.tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = bars.tmem_base;
+
+  const int issue_t = warp == 0 ? 0 : (warp >= F8_ISSUE1 ? warp - F8_ISSUE1 + 1 : -1);
+  if (issue_t >= 0) {
+    // ---------------------------------------------------------------- MMA issue, scale issue_t
+    if (lane == 0 && issue_t < nt) {
+      const uint64_t db0 = make_desc(smem_u32(sS));
+      const uint32_t d = tmem + (uint32_t)(issue_t * TN);
+      int js = 0;
+      uint32_t ps = 0;
+      bool ok = true;
+      for (int dr = 0; dr < ndrains && ok; ++dr) {
+        ok = mbar_wait(&bars.acc_empty[0], (dr & 1) ^ 1, &bars.abort, g.err);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
+        for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
+          ok = mbar_wait(&bars.full[js], ps, &bars.abort, g.err);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t st = (uint32_t)js * F8_STAGE;
+          mma_stage_f8(d, db0 + ((st + (uint32_t)issue_t * F8_TILE) >> 4), db0 + ((st + F8_MAXT * F8_TILE) >> 4),
+                       c == dr * chunks_per_drain ? 0u : 1u);
+          mma_commit(&bars.empty[js]);
+          if (++js == F8_STAGES) { js = 0; ps ^= 1; }
+        }
+        if (ok) mma_commit(&bars.acc_full[0]);
+      }
+      // all issued MMAs complete before the CTA tears down
+      mma_commit(&bars.fin);
+      mbar_wait(&bars.fin, 0, &bars.abort, g.err, false);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int js = 0;
+      uint32_t ps = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int k0 = (int)(kb + (int64_t)c * F8_K);   // multiple of 128 bytes
+        if (!mbar_wait(&bars.empty[js], ps ^ 1, &bars.abort, g.err)) break;
+        uint8_t *st = sS + js * F8_STAGE;
+        mbar_expect_tx(&bars.full[js], (uint32_t)(nt + 1) * F8_TILE);
+        for (int t = 0; t < nt; ++t)
+          tma_load_2d(st + t * F8_TILE, &tmA, k0, (int)((t0 + t) * g.rows_a + ti * TM), &bars.full[js]);
+        tma_load_2d(st + F8_MAXT * F8_TILE, &tmB, k0, tj * TN, &bars.full[js]);
+        if (++js == F8_STAGES) { js = 0; ps ^= 1; }
+      }
+    }
+    __syncwarp();
+  } else {
+    epilogue_drain(g, tmem, bars.acc_full, bars.acc_empty, &bars.abort, ndrains, nt, 1, tile, grp, split, ti, tj,
+                   cd_red);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 using TmapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -765,7 +911,31 @@ bool encode_2d(CUtensorMap *m, CUtensorMapDataType dt, size_t esize, const void 
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return SMEM_BYTES > T3_SMEM ? SMEM_BYTES : T3_SMEM; }
+size_t tc_gemm_smem_bytes() { return std::max<size_t>(SMEM_BYTES, std::max<size_t>(T3_SMEM, F8_SMEM)); }
+
+cudaError_t launch_tc_fp8_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
+  if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
+  if (!g.A8 || !g.B8 || !g.ds_a || !g.ds_b || g.Kp % F8_K || g.k_per_split % F8_K || g.drain_k % F8_K ||
+      g.k_per_split <= 0 || g.drain_k <= 0 || g.nt_group < 1 || g.nt_group > F8_MAXT || !g.out_colmajor ||
+      g.out_mode == TC_OUT_COLDOT || (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) || g.rows_a < TM ||
+      g.rows_b < TN || g.rows_a % TM || g.rows_b % TN || (int64_t)g.n_t * g.rows_a > INT32_MAX)
+    return cudaErrorInvalidValue;
+  const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
+  const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
+  CUtensorMap ta, tb;
+  if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g.A8, g.Kp, (int64_t)g.n_t * g.rows_a, F8_K, TM,
+                 CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_2d(&tb, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g.B8, g.Kp, g.rows_b, F8_K, TN, CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorNotSupported;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F8_SMEM);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  tc_fp8_kernel<<<dim3(n_tiles, groups, splits), F8_THREADS, F8_SMEM, s>>>(g, ta, tb);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
   if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;

@@ -83,6 +83,7 @@ SIGNATURES = {
     "ltgw_naf_basis_mixed": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_polarizability_mixed": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "ltgw_polarizability_fp8": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
     "ltgw_screen_static": (_I, [_I, _I, _P, _P, _P]),
     "ltgw_server_create": (_I, [ctypes.POINTER(ctypes.c_void_p), _I, _I, ctypes.c_size_t]),
@@ -254,16 +255,21 @@ class Context:
         self._check(st)
 
     def polarizability_mixed(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None,
-                             stream=None):
+                             stream=None, fp8: bool = False):
+        """Split-BF16 form (ltgw_polarizability_mixed), or with fp8 the FP8 E4M3
+        form (ltgw_polarizability_fp8)."""
         N, n_pairs = int(Bt.shape[0]), int(Bt.shape[1])
         om = np.ascontiguousarray(omegas, dtype=np.float64)
         n_tau = 0 if x is None else len(x)
         xx = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
         ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
-        st = self._lib.ltgw_polarizability_mixed(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om),
-                                                 _ptr(om), n_tau, _ptr(xx), _ptr(ww), spin, _ptr(Pi),
-                                                 _stream_ptr(stream))
+        fn = self._lib.ltgw_polarizability_fp8 if fp8 else self._lib.ltgw_polarizability_mixed
+        st = fn(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om), _ptr(om), n_tau, _ptr(xx), _ptr(ww), spin,
+                _ptr(Pi), _stream_ptr(stream))
         self._check(st)
+
+    def polarizability_fp8(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None, stream=None):
+        self.polarizability_mixed(Bt, delta, omegas, Pi, spin, x, w, stream, fp8=True)
 
     def screen(self, Pi, C, stream=None):
         n_omega, N = int(Pi.shape[0]), int(Pi.shape[1])
