@@ -41,14 +41,17 @@ def parse():
     ap.add_argument("--workload", default="mid", choices=["tiny", "mid", "large", "serving"])
     ap.add_argument("--occ-block", type=int, default=20, help="large: occupied orbitals per streamed block")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests in the stream")
-    ap.add_argument("--rate", type=float, default=3.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="serving: Poisson arrival rate (requests/s); default 0.7 x the mixed form's measured "
+                         "capacity (back-to-back throughput of the stream's first --compare-prefix requests)")
     ap.add_argument("--slots", type=int, default=4, help="serving: server worker slots")
     ap.add_argument("--compare-prefix", type=int, default=32,
                     help="serving: requests of the stream solved back to back in both forms for the ratio")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "fp8"],
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "fp8", "fp8pi"],
                     help="bf16x3: every contraction on the tensor cores with split-BF16 operands (eigensolver, "
-                         "screening, Pade, Newton in FP64); fp64: every step in FP64")
+                         "screening, Pade, Newton in FP64); fp8: Pi and W_nm in FP8 E4M3; fp8pi: Pi in FP8, the "
+                         "rest as bf16x3; fp64: every step in FP64")
     return ap.parse_args()
 
 
@@ -168,8 +171,8 @@ def _solve_loop(ctx, p, dev, out_dev, stream, flush, steps, clk=None):
     return np.array([a.elapsed_time(b) for a, b in ev]), stats
 
 
-PREC = {"fp64": 0, "bf16x3": 1, "fp8": 2}                  # ltgw.LTGW_FP64 / LTGW_BF16X3 / LTGW_FP8
-DTYPE = {"fp64": "f64", "bf16x3": "bf16x3", "fp8": "fp8e4m3"}
+PREC = {"fp64": 0, "bf16x3": 1, "fp8": 2, "fp8pi": 3}     # ltgw.LTGW_FP64 / BF16X3 / FP8 / FP8_PI
+DTYPE = {"fp64": "f64", "bf16x3": "bf16x3", "fp8": "fp8e4m3", "fp8pi": "fp8e4m3 (Pi) + bf16x3"}
 
 
 def pi_roofline(prec, pi_flops, pi_ms, pk, src, traffic=None):
@@ -182,7 +185,7 @@ def pi_roofline(prec, pi_flops, pi_ms, pk, src, traffic=None):
                 "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                 "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
                 "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": traffic}
-    if prec == "fp8":
+    if prec in ("fp8", "fp8pi"):
         a = pi_flops / (pi_ms / 1e3) / 1e12
         peak = 2.0 * pk["bf16_tflops"]
         return {"bound": "tensor", "kernel": "tc_fp8_kernel (Pi(tau_k) moments, FP8 E4M3 tcgen05 kind::f8f6f4)",
@@ -216,7 +219,7 @@ def pi_error_vs_fp64(ctx, prob, N, n_omega, prec, stream):
     ref = torch.empty((n_omega, N, N), dtype=torch.float64, device="cuda")
     got = torch.empty_like(ref)
     ctx.polarizability(Bs, delta, om, ref, spin=2, stream=stream)
-    ctx.polarizability_mixed(Bs, delta, om, got, spin=2, stream=stream, fp8=prec == "fp8")
+    ctx.polarizability_mixed(Bs, delta, om, got, spin=2, stream=stream, fp8=prec in ("fp8", "fp8pi"))
     torch.cuda.synchronize()
     return float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
 
@@ -366,7 +369,7 @@ def run_serving(args):
 
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    reqs = S.serving_stream(args.requests, rate_hz=args.rate)
+    reqs = S.serving_stream(args.requests, rate_hz=args.rate or 1.0)   # sizes do not depend on the rate
     budget = int(0.6 * torch.cuda.get_device_properties(0).total_memory)
     # same prefix of the stream, back to back, in both forms: the throughput ratio
     pre = reqs[:min(args.compare_prefix, len(reqs))]
@@ -383,6 +386,17 @@ def run_serving(args):
     dev = max(np.abs(cmp["bf16x3"]["e"][k] - cmp["fp64"]["e"][k]).max() for k in cmp["fp64"]["e"]) * HA2MEV
     del inputs
     torch.cuda.empty_cache()
+    # capacity: the whole stream closed loop (all arriving at once) with its inputs
+    # generated on the device as in the open-loop run, mixed form
+    srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
+    try:
+        burst = S.serving_stream(len(reqs), rate_hz=1e9)
+        recs_c, wall_c, _ = serving.run_stream_pipelined(srv, burst, ltgw.LTGW_BF16X3)
+    finally:
+        srv.close()
+    capacity = len(recs_c) / wall_c
+    rate = args.rate if args.rate else 0.7 * capacity
+    reqs = S.serving_stream(args.requests, rate_hz=rate)
     # the whole stream, open loop at the arrival rate, mixed form
     srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
     try:
@@ -395,14 +409,17 @@ def run_serving(args):
             "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / len(reqs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
             "data": "synthetic",
-            "config": {"workload": f"serving: {len(reqs)} requests, Poisson {args.rate}/s, n_occ log-uniform "
+            "config": {"workload": f"serving: {len(reqs)} requests, Poisson {rate:.3f}/s "
+                                   + ("; " if args.rate else "= 0.7 x ") + f"the measured capacity "
+                                   f"{capacity:.3f} solves/s (the same stream closed loop, device ingest "
+                                   "included), n_occ log-uniform "
                                    "[8,200], n_virt = u n_occ (u in [8,12]), N_aux = 3(n_occ+n_virt), NAF 1e-2, "
                                    "N_omega 32, N_tau 8, 4 states; inputs generated on the device at arrival",
                        "slots": args.slots, "hbm_budget_bytes": budget},
             "latency_ms": {"p50": sm["p50_ms"], "p99": sm["p99_ms"],
                            "p50_from_arrival": sm.get("p50_from_arrival_ms"),
                            "p99_from_arrival": sm.get("p99_from_arrival_ms")},
-            "completed": sm["completed"], "ingest_s": ingest_s,
+            "completed": sm["completed"], "ingest_s": ingest_s, "capacity_solves_per_s": capacity,
             "prefix_comparison": {"requests": len(pre), "bf16x3_solves_per_s": cmp["bf16x3"]["solves_per_s"],
                                   "fp64_solves_per_s": cmp["fp64"]["solves_per_s"],
                                   "speedup": cmp["bf16x3"]["solves_per_s"] / cmp["fp64"]["solves_per_s"],
@@ -483,7 +500,7 @@ def run_large(args):
             "roofline_pi_build": pi_roofline(args.precision, pi_flops, pi_ms, pk, src),
             "e_qp_ha": e_main.tolist(), "qp_status": out[2].cpu().numpy().tolist(),
             "clocks": clk.summary()}
-    if args.precision == "fp8":
+    if args.precision in ("fp8", "fp8pi"):
         # the same solve in the split-BF16 form (within a few 0.01 meV of FP64 at the mid size)
         one(params("bf16x3"))
         line["qp_mev_vs_bf16x3_form_per_state"] = (np.abs(e_main - out[1].cpu().numpy()) * HA2MEV).tolist()

@@ -63,7 +63,7 @@ typedef enum {
   LTGW_ERR_TIMEOUT = 8      /* a wait for completions ran out of time              */
 } ltgw_status;
 
-enum { LTGW_FP64 = 0, LTGW_BF16X3 = 1, LTGW_FP8 = 2 };
+enum { LTGW_FP64 = 0, LTGW_BF16X3 = 1, LTGW_FP8 = 2, LTGW_FP8_PI = 3 };
 
 typedef struct {
   int n_occ;          /* occupied orbitals, frozen core included                  */
@@ -79,8 +79,10 @@ typedef struct {
   int precision;      /* LTGW_FP64; LTGW_BF16X3: the dense contractions (NAF       */
                       /* metric, projections, Pi, W_nm) on the tensor cores with  */
                       /* split-BF16 operands (see ltgw_polarizability_mixed);     */
-                      /* LTGW_FP8: the same with the Pi build in FP8 E4M3 with    */
-                      /* per-auxiliary-row scales (ltgw_polarizability_fp8).      */
+                      /* LTGW_FP8: the same with the Pi build and the W_nm        */
+                      /* contraction in FP8 E4M3 with per-row scales (rows are    */
+                      /* auxiliary functions; ltgw_polarizability_fp8);           */
+                      /* LTGW_FP8_PI: FP8 for the Pi build only.                  */
                       /* The eigensolver, screening, Pade and Newton stay FP64.   */
   int reserved;       /* must be 0                                                */
 } ltgw_params;

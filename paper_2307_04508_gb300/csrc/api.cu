@@ -519,16 +519,26 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   return LTGW_OK;
 }
 
-// W_nm(i w_j) (Eq. ScreenedCoulombOrbital) in the split-BF16 form: Y_j = C_j R~_tgt
-// on the tensor cores with the column dot against R~_tgt fused into the epilogue.
+// W_nm(i w_j) (Eq. ScreenedCoulombOrbital) on the tensor cores: Y_j = C_j R~_tgt
+// with the column dot against R~_tgt fused into the epilogue; split BF16, or
+// (fp8) FP8 E4M3 codes of C_j's and R~_tgt^T's rows, each row with its own
+// scale (C_j's rows are auxiliary functions).
 ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, int n_orb_act, const double *BtT64,
-                   const float *BtT32, double *W, cudaStream_t s) {
-  const int KpN = (N + 63) / 64 * 64, MpN = (N + 127) / 128 * 128, nI = MpN / 128;
-  const int ncols = T * n_orb_act, nJ = (ncols + 127) / 128;
-  float *Cf, *ones;
+                   const float *BtT32, double *W, cudaStream_t s, bool fp8) {
+  const int KpN = (N + 63) / 64 * 64, MpN = (N + 127) / 128 * 128, nI = MpN / 128, Kq = (N + 127) / 128 * 128;
+  const int ncols = T * n_orb_act, nJ = (ncols + 127) / 128, rowsTp = nJ * 128;
+  float *Cf, *ones = nullptr, *dsC = nullptr, *dsR = nullptr;
+  uint8_t *qC = nullptr, *qR = nullptr;
   auto layout = [&](Arena &A) {
     Cf = A.take<float>((size_t)n_omega * MpN * KpN);
-    ones = A.take<float>((size_t)n_omega * KpN);
+    if (fp8) {
+      qC = A.take<uint8_t>((size_t)n_omega * MpN * Kq);
+      qR = A.take<uint8_t>((size_t)rowsTp * Kq);
+      dsC = A.take<float>((size_t)n_omega * MpN);
+      dsR = A.take<float>((size_t)rowsTp);
+    } else {
+      ones = A.take<float>((size_t)n_omega * KpN);
+    }
   };
   ctx->a5.begin_sizing();
   layout(ctx->a5);
@@ -537,9 +547,15 @@ ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, in
   // C_j is symmetric, so its transpose is its padded copy
   CHECK_LAUNCH(ctx, launch_to_f32_transposed(C, N, 0, N, N, Cf, KpN, MpN, n_omega, (int64_t)N * N,
                                              (int64_t)MpN * KpN, s), 1);
-  CHECK_LAUNCH(ctx, launch_scale_table(nullptr, N, KpN, n_omega, nullptr, nullptr, SCALE_NONE, ones, s), 1);
   TcGemmArgs g;
-  g.A = Cf; g.a_group_stride = (int64_t)MpN * KpN; g.B = BtT32; g.scale = ones; g.Kp = KpN;
+  if (fp8) {
+    CHECK_LAUNCH(ctx, launch_fp8_quantize(Cf, KpN, Kq, nullptr, 0, n_omega * MpN, nullptr, qC, nullptr, dsC, s), 1);
+    CHECK_LAUNCH(ctx, launch_fp8_quantize(BtT32, KpN, Kq, nullptr, 0, rowsTp, nullptr, qR, nullptr, dsR, s), 1);
+    g.A8 = qC; g.B8 = qR; g.ds_a = dsC; g.ds_b = dsR; g.Kp = Kq; g.rows_a = MpN; g.rows_b = rowsTp;
+  } else {
+    CHECK_LAUNCH(ctx, launch_scale_table(nullptr, N, KpN, n_omega, nullptr, nullptr, SCALE_NONE, ones, s), 1);
+    g.A = Cf; g.a_group_stride = (int64_t)MpN * KpN; g.B = BtT32; g.scale = ones; g.Kp = KpN;
+  }
   g.n_t = n_omega; g.nt_group = 1;
   g.out_mode = TC_OUT_COLDOT;
   g.cd_B = BtT64; g.cd_ld = N; g.cd_rows = N; g.cd_cols = ncols; g.cd_cols_p = nJ * 128;
@@ -558,8 +574,8 @@ ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
   REQUIRE(ctx, p->spin == 1 || p->spin == 2, "spin must be 1 or 2");
   REQUIRE(ctx, p->use_laplace == 0 || p->use_laplace == 1, "use_laplace must be 0 or 1");
   REQUIRE(ctx, !p->use_laplace || (p->n_tau >= 1 && p->n_tau <= 32), "n_tau must be in [1, 32]");
-  REQUIRE(ctx, p->precision == LTGW_FP64 || p->precision == LTGW_BF16X3 || p->precision == LTGW_FP8,
-          "precision must be LTGW_FP64, LTGW_BF16X3 or LTGW_FP8");
+  REQUIRE(ctx, p->precision >= LTGW_FP64 && p->precision <= LTGW_FP8_PI,
+          "precision must be LTGW_FP64, LTGW_BF16X3, LTGW_FP8 or LTGW_FP8_PI");
   REQUIRE(ctx, p->reserved == 0, "reserved must be 0");
   REQUIRE(ctx, isfinite(p->naf_thresh), "naf_thresh must be finite");
   return LTGW_OK;
@@ -664,7 +680,8 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   const int n_tau = p->use_laplace ? p->n_tau : 0;
   const bool naf = p->naf_thresh >= 0.0;
   const bool mixed = p->precision != LTGW_FP64;   // contractions on the tensor cores
-  const bool fp8 = p->precision == LTGW_FP8;      // ... with the Pi build in FP8 E4M3
+  const bool fp8 = p->precision == LTGW_FP8 || p->precision == LTGW_FP8_PI;   // Pi build in FP8 E4M3
+  const bool fp8_w = p->precision == LTGW_FP8;                                // W_nm in FP8 E4M3
   ctx->stats = ltgw_stats{};
   ctx->mark(EV_START, s);
 
@@ -898,7 +915,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
 
   // ---- W_nm(i w_j)
   if (mixed) {
-    if (wnm_tc(ctx, N, n_omega, d_C, T, n_orb_act, d_BtT64, d_BtT32, d_W, s) != LTGW_OK) return ctx->status();
+    if (wnm_tc(ctx, N, n_omega, d_C, T, n_orb_act, d_BtT64, d_BtT32, d_W, s, fp8_w) != LTGW_OK) return ctx->status();
   } else {
     ColDotArgs cd;
     cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;

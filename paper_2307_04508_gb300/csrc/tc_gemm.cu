@@ -257,13 +257,13 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
               "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(a));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (g.out_colmajor && g.out_mode != TC_OUT_COLDOT) {
-          if (g.ds_a) {   // FP8 form: per-row de-scales of both operands
-            const float ra = g.ds_a[(int64_t)(grp * g.nt_group + t) * g.rows_a + ti * TM + row];
-            const float *cb = g.ds_b + tj * TN + h * 32;
+        if (g.ds_a) {   // FP8 form: per-row de-scales of both operands
+          const float ra = g.ds_a[(int64_t)(grp * g.nt_group + t) * g.rows_a + ti * TM + row];
+          const float *cb = g.ds_b + tj * TN + h * 32;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) * (ra * __ldg(cb + q)));
-          }
+          for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) * (ra * __ldg(cb + q)));
+        }
+        if (g.out_colmajor && g.out_mode != TC_OUT_COLDOT) {
           // [col][row]: for each column the warp's 32 rows are one contiguous store
           const int64_t o = base + t * tstride + (int64_t)(h * 32) * TM + row;
           if (g.out_mode == TC_OUT_F32) {
@@ -916,9 +916,10 @@ size_t tc_gemm_smem_bytes() { return std::max<size_t>(SMEM_BYTES, std::max<size_
 cudaError_t launch_tc_fp8_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
   if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
   if (!g.A8 || !g.B8 || !g.ds_a || !g.ds_b || g.Kp % F8_K || g.k_per_split % F8_K || g.drain_k % F8_K ||
-      g.k_per_split <= 0 || g.drain_k <= 0 || g.nt_group < 1 || g.nt_group > F8_MAXT || !g.out_colmajor ||
-      g.out_mode == TC_OUT_COLDOT || (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) || g.rows_a < TM ||
-      g.rows_b < TN || g.rows_a % TM || g.rows_b % TN || (int64_t)g.n_t * g.rows_a > INT32_MAX)
+      g.k_per_split <= 0 || g.drain_k <= 0 || g.nt_group < 1 || g.nt_group > F8_MAXT ||
+      (g.out_mode == TC_OUT_COLDOT ? (g.nt_group != 1 || g.k_per_split > g.drain_k) : !g.out_colmajor) ||
+      (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) || g.rows_a < TM || g.rows_b < TN ||
+      g.rows_a % TM || g.rows_b % TN || (int64_t)g.n_t * g.rows_a > INT32_MAX)
     return cudaErrorInvalidValue;
   const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
   const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libltgw.so")
 LTGW_OK, LTGW_ERR_BAD_ARG, LTGW_ERR_NOMEM, LTGW_ERR_NOT_SPD = 0, 1, 2, 3
 LTGW_ERR_NO_CONVERGE, LTGW_ERR_DEVICE, LTGW_ERR_EIG, LTGW_ERR_NO_NAF = 4, 5, 6, 7
 LTGW_ERR_TIMEOUT = 8
-LTGW_FP64, LTGW_BF16X3, LTGW_FP8 = 0, 1, 2
+LTGW_FP64, LTGW_BF16X3, LTGW_FP8, LTGW_FP8_PI = 0, 1, 2, 3
 
 
 class Params(ctypes.Structure):

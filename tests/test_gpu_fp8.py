@@ -4,7 +4,8 @@ which rounds the same FP32 values to E4M3 and sums the products exactly: the
 two differ only by the FP32 accumulation, so the bar is 2e-5 relative
 Frobenius.  The error of the FP8 form itself (against the exact Pi, and in
 the quasi-particle energies of a whole solve against the FP64 oracle) is
-printed and bounded at its measured level."""
+printed and bounded at its measured level: Pi and W_nm in FP8 stay within
+2 meV, Pi alone in FP8 within the 1 meV target."""
 import numpy as np
 import pytest
 
@@ -61,20 +62,24 @@ def test_fp8_polarizability_direct_and_laplace(ctx, N, P, n_om):
     assert errl <= PI_TOL_FP8_VS_ORACLE
 
 
-def test_fp8_solve_mid_workload(ctx):
-    """Mid workload (1800 auxiliary functions, NAF 1e-2) with the Pi build in FP8:
-    per-state QP error against the FP64 oracle fed the same Laplace grid."""
+@pytest.mark.parametrize("mode,bound_mev", [("fp8", 2.0), ("fp8_pi", 1.0)])
+def test_fp8_solve_mid_workload(ctx, mode, bound_mev):
+    """Mid workload (1800 auxiliary functions, NAF 1e-2): per-state QP error
+    against the FP64 oracle fed the same Laplace grid, with Pi and W_nm in FP8
+    (LTGW_FP8; measured 1.07-1.64 meV) or Pi alone in FP8 (LTGW_FP8_PI,
+    W_nm split-BF16; measured 0.79-0.95 meV, inside the 1 meV target)."""
     from paper_2307_04508_gb300 import ltgw
     prob = S.make_workload(S.MID)
     tau = O.sinc_laplace_grid(8, -12.0, 3.0)
     _, e_o, st_o = O.solve(prob.eps, prob.B_ov, prob.B_tgt, prob.targets, prob.shift, 60, 540, 10, n_omega=32,
                            naf_thresh=1e-2, tau_x=tau[0], tau_w=tau[1])
-    p = ltgw.make_params(60, 540, 1800, 10, 32, 8, 0.5, 1e-2, 2, True, ltgw.LTGW_FP8)
+    prec = ltgw.LTGW_FP8 if mode == "fp8" else ltgw.LTGW_FP8_PI
+    p = ltgw.make_params(60, 540, 1800, 10, 32, 8, 0.5, 1e-2, 2, True, prec)
     T = len(prob.targets)
     sig, e, st = np.zeros((T, 32, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
     dev = [_dev(a) for a in (prob.eps, prob.B_ov, prob.B_tgt, prob.targets.astype(np.int32), prob.shift)]
     ctx.solve(p, *dev, sig, e, st, tau_x=np.ascontiguousarray(tau[0]), tau_w=np.ascontiguousarray(tau[1]))
     mev = np.abs(e - e_o) * HA_TO_MEV
-    print("fp8 solve: per-state QP error (meV) " + " ".join(f"{v:.3f}" for v in mev))
+    print(f"{mode} solve: per-state QP error (meV) " + " ".join(f"{v:.3f}" for v in mev))
     assert np.all(st == 0) and np.all(st_o == 0)
-    assert mev.max() <= 1.0   # the mixed-precision target (measured 0.79-0.94 meV)
+    assert mev.max() <= bound_mev
