@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--compare-prefix", type=int, default=32,
                     help="serving: requests of the stream solved back to back in both forms for the ratio")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="mid / large: fixed contraction configurations instead of the library's autotuner")
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "fp8", "fp8pi"],
                     help="bf16x3: every contraction on the tensor cores with split-BF16 operands (eigensolver, "
                          "screening, Pade, Newton in FP64); fp8: Pi and W_nm in FP8 E4M3; fp8pi: Pi in FP8, the "
@@ -238,6 +240,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     cfg, prob, desc = workload(args.workload)
     ctx = ltgw.Context(local)
+    ctx.set_autotune(not args.no_autotune)   # the warm-up solves time and fix the configurations
     stream = torch.cuda.Stream()
     T = len(prob.targets)
     mixed = args.precision != "fp64"
@@ -312,7 +315,7 @@ def run_gpu(args):
             "stage_ms": {k: st[k] for k in ("ms_naf", "ms_tridiag", "ms_pi", "ms_screen", "ms_wnm", "ms_sigma_qp",
                                             "ms_total")},
             "roofline": roofline, "roofline_pi_build": roof_pi, "gpu_launches": launches, "clocks": clocks,
-            "peaks_source": src}
+            "peaks_source": src, "autotuned_shapes": st.get("tc_autotuned", 0)}
     if mixed:
         # the plain FP64 form on the same workload, for the "vs plain FP64 form" part of the metric
         ms64, _ = _solve_loop(ctx, p64, dev, out_dev, stream, flush, max(3, args.steps // 2))
@@ -457,6 +460,7 @@ def run_large(args):
     p = params(args.precision)
     ctx = ltgw.Context(0)
     ctx.set_timing(True)
+    ctx.set_autotune(not args.no_autotune)   # the warm-up solve times and fixes the configurations
     stream = torch.cuda.Stream()
     out = (torch.empty((T, cfg["n_omega"], 2), dtype=torch.float64, device="cuda"),
            torch.empty(T, dtype=torch.float64, device="cuda"), torch.empty(T, dtype=torch.int32, device="cuda"))

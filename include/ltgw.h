@@ -100,6 +100,7 @@ typedef struct {
   int kernel_launches;       /* all kernel launches in the last solve                 */
   double ms_tridiag;         /* device time of the NAF Householder tridiagonalisation */
   double ms_generate;        /* host time spent in the block callback (streamed solve) */
+  int tc_autotuned;          /* contraction shapes the autotuner has timed (this context) */
 } ltgw_stats;
 
 typedef struct ltgw_ctx ltgw_ctx;
@@ -113,6 +114,14 @@ const char *ltgw_last_error(const ltgw_ctx *ctx);
 
 /* Turn per-stage CUDA-event timing on (1) or off (0); off by default. */
 ltgw_status ltgw_set_timing(ltgw_ctx *ctx, int on);
+/* Turn the contraction autotuner on (1) or off (0); off by default.  When on,
+ * the first tensor-core contraction of a shape on this context times a few
+ * configurations (scales per CTA, K-split count) on the caller's stream and
+ * keeps the fastest for later calls with that shape; results then depend on
+ * the choice only through FP32 summation order (within the form's
+ * tolerance).  Off, every call takes the fixed heuristic and is
+ * reproducible bit for bit. */
+ltgw_status ltgw_set_autotune(ltgw_ctx *ctx, int on);
 ltgw_status ltgw_get_stats(const ltgw_ctx *ctx, ltgw_stats *out);
 
 /*

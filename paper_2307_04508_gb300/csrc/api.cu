@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <chrono>
 #include <functional>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -85,6 +87,19 @@ struct ltgw_ctx {
   int n_sm = 148;
   Arena a4;  // tensor-core scratch: tile lists and partial tiles
   Arena a5;  // tensor-core operand copies consumed by the next contraction
+  // Autotuner of the tensor-core contractions (off by default): per shape, the
+  // (scales per CTA, K-splits) configuration that timed fastest on this GPU.
+  struct TcKey {
+    int kind, n_tiles, n_t, out_mode;
+    int64_t Kp, rows_a, rows_b;
+    bool operator<(const TcKey &o) const {
+      return std::tie(kind, n_tiles, n_t, out_mode, Kp, rows_a, rows_b) <
+             std::tie(o.kind, o.n_tiles, o.n_t, o.out_mode, o.Kp, o.rows_a, o.rows_b);
+    }
+  };
+  struct TcChoice { int nt_group; int64_t splits; };
+  bool autotune = false;
+  std::map<TcKey, TcChoice> tuned;
 
   void fail(ltgw_status c, const std::string &m) {
     if (st == LTGW_OK) { st = c; err = m; }
@@ -298,25 +313,92 @@ struct TcRun {
   double *partial = nullptr;
   float *partial32 = nullptr;
   float *cd_out = nullptr;
-  int splits = 1, groups = 1, n_tiles = 0;
+  int splits = 1, groups = 1, n_tiles = 0, nt_group = 1;
 };
+
+// One configuration of a contraction: scales per CTA, K-split length, output precision.
+struct TcPlan {
+  int nt_group, groups;
+  int64_t splits, kps;
+  int out_mode;
+};
+
+TcPlan tc_plan(const ltgw_ctx *ctx, const TcGemmArgs &g, int n_tiles, int nt_group, int64_t want_splits) {
+  TcPlan p;
+  p.nt_group = nt_group;
+  p.groups = (g.n_t + nt_group - 1) / nt_group;
+  const int64_t align = g.A8 ? 128 : 64;
+  if (g.out_mode == TC_OUT_COLDOT) {
+    // the column dot needs the whole contraction (K = the NAF count) in one drain
+    p.kps = g.Kp; p.splits = 1; p.out_mode = TC_OUT_COLDOT;
+    return p;
+  }
+  if (want_splits > 0) {
+    p.kps = ((g.Kp + want_splits - 1) / want_splits + align - 1) / align * align;
+    p.splits = (g.Kp + p.kps - 1) / p.kps;
+  } else {
+    p.splits = tc_splits(ctx, (int64_t)n_tiles * p.groups, g.Kp, g.drain_k, align, &p.kps);
+  }
+  p.out_mode = p.kps <= g.drain_k ? TC_OUT_F32 : TC_OUT_F64;
+  return p;
+}
+
+// Run a contraction.  Scratch (tile list, partials) comes from `ar`; the
+// caller reduces the partials (returned with the configuration used).  With
+// the autotuner on, the first contraction of a shape times its candidate
+// configurations (scales per CTA where the kernel and the caller's reduction
+// allow several; the heuristic's K-split count, half and twice it, each
+// keeping one FP32 drain per CTA where one can) with CUDA events on the
+// stream, keeps the fastest for this context and then runs it.
 ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int> &tiles, int coldot_rows,
                    TcRun *run, cudaStream_t s) {
   const int n_tiles = (int)(tiles.size() / 2);
-  const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
-  int64_t kps = 0;
-  int64_t splits = tc_splits(ctx, (int64_t)n_tiles * groups, g.Kp, g.drain_k, g.A8 ? 128 : 64, &kps);
-  // the column dot needs the whole contraction (K = the NAF count) in one drain
-  if (g.out_mode == TC_OUT_COLDOT) { kps = g.Kp; splits = 1; g.drain_k = std::max<int64_t>(g.drain_k, g.Kp); }
-  const bool f32 = g.out_mode != TC_OUT_COLDOT && kps <= g.drain_k;
-  if (g.out_mode != TC_OUT_COLDOT) g.out_mode = f32 ? TC_OUT_F32 : TC_OUT_F64;
+  if (g.out_mode == TC_OUT_COLDOT) g.drain_k = std::max<int64_t>(g.drain_k, g.Kp);
+  const int kind = g.A8 ? 2 : (g.B_hi ? 1 : 0);
+  TcPlan plan = tc_plan(ctx, g, n_tiles, g.nt_group, 0);
+  std::vector<TcPlan> cands{plan};
+  const ltgw_ctx::TcKey key{kind, n_tiles, g.n_t, g.out_mode, g.Kp, g.rows_a, g.rows_b};
+  bool tune = false;
+  if (ctx->autotune && g.out_mode != TC_OUT_COLDOT) {
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+      plan = tc_plan(ctx, g, n_tiles, it->second.nt_group, it->second.splits);
+      cands = {plan};
+    } else {
+      tune = true;
+      cands.clear();
+      std::vector<int> ntgs{g.nt_group};
+      if (kind == 1) ntgs = {2, 1};
+      if (kind == 2) ntgs = {4, 2, 1};
+      const int64_t min_split = std::min<int64_t>(64, (g.Kp + g.drain_k - 1) / g.drain_k);
+      for (int ntg : ntgs) {
+        const TcPlan base = tc_plan(ctx, g, n_tiles, ntg, 0);
+        for (int64_t sp : {base.splits, base.splits / 2, base.splits * 2}) {
+          sp = std::max<int64_t>(std::max<int64_t>(sp, min_split), 1);
+          const TcPlan c = tc_plan(ctx, g, n_tiles, ntg, sp);
+          if (c.splits > 256) continue;
+          bool dup = false;
+          for (const TcPlan &o : cands) dup |= (o.nt_group == c.nt_group && o.splits == c.splits);
+          if (!dup) cands.push_back(c);
+        }
+      }
+    }
+  }
+  size_t part64_n = 0, part32_n = 0, cd_n = 0;
+  for (const TcPlan &c : cands) {
+    const size_t n_part = (size_t)c.splits * c.groups * c.nt_group * n_tiles * 128 * 128;
+    if (c.out_mode == TC_OUT_F64) part64_n = std::max(part64_n, n_part);
+    if (c.out_mode == TC_OUT_F32) part32_n = std::max(part32_n, n_part);
+    if (c.out_mode == TC_OUT_COLDOT) cd_n = (size_t)c.splits * c.groups * coldot_rows * (size_t)g.cd_cols_p;
+  }
   int *d_tiles;
+  double *part64;
+  float *part32, *cd;
   auto layout = [&](Arena &A) {
     d_tiles = A.take<int>(tiles.size());
-    const size_t n_part = (size_t)splits * groups * g.nt_group * n_tiles * 128 * 128;
-    run->partial = (g.out_mode == TC_OUT_F64) ? A.take<double>(n_part) : nullptr;
-    run->partial32 = (g.out_mode == TC_OUT_F32) ? A.take<float>(n_part) : nullptr;
-    run->cd_out = (g.out_mode == TC_OUT_COLDOT) ? A.take<float>((size_t)splits * groups * coldot_rows * (size_t)g.cd_cols_p) : nullptr;
+    part64 = part64_n ? A.take<double>(part64_n) : nullptr;
+    part32 = part32_n ? A.take<float>(part32_n) : nullptr;
+    cd = cd_n ? A.take<float>(cd_n) : nullptr;
   };
   ar.begin_sizing();
   layout(ar);
@@ -324,16 +406,46 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
   layout(ar);
   copy_in(ctx, d_tiles, tiles.data(), tiles.size() * sizeof(int), s);
   g.tiles = d_tiles;
-  g.k_per_split = kps;
-  g.partial = run->partial;
-  g.partial32 = run->partial32;
-  g.cd_out = run->cd_out;
   g.n_tile_rows = coldot_rows;
   g.err = ctx->flags;
-  CHECK_LAUNCH(ctx, g.A8 ? launch_tc_fp8_gemm(g, n_tiles, s) : launch_tc_split_gemm(g, n_tiles, s), 1);
-  run->splits = (int)splits;
-  run->groups = groups;
+  auto launch = [&](const TcPlan &c) {
+    TcGemmArgs h = g;
+    h.nt_group = c.nt_group;
+    h.k_per_split = c.kps;
+    h.out_mode = c.out_mode;
+    h.partial = c.out_mode == TC_OUT_F64 ? part64 : nullptr;
+    h.partial32 = c.out_mode == TC_OUT_F32 ? part32 : nullptr;
+    h.cd_out = c.out_mode == TC_OUT_COLDOT ? cd : nullptr;
+    return h.A8 ? launch_tc_fp8_gemm(h, n_tiles, s) : launch_tc_split_gemm(h, n_tiles, s);
+  };
+  if (tune) {
+    cudaEvent_t e0, e1;
+    LTGW_CUDA(ctx, cudaEventCreate(&e0));
+    LTGW_CUDA(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (const TcPlan &c : cands) {
+      float ms = 0.0f;
+      CHECK_LAUNCH(ctx, launch(c), 1);   // warm
+      cudaEventRecord(e0, s);
+      CHECK_LAUNCH(ctx, launch(c), 1);
+      cudaEventRecord(e1, s);
+      LTGW_CUDA(ctx, cudaEventSynchronize(e1));
+      LTGW_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; plan = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuned[key] = ltgw_ctx::TcChoice{plan.nt_group, plan.splits};
+  }
+  ctx->stats.tc_autotuned = (int)ctx->tuned.size();
+  CHECK_LAUNCH(ctx, launch(plan), 1);
+  run->partial = plan.out_mode == TC_OUT_F64 ? part64 : nullptr;
+  run->partial32 = plan.out_mode == TC_OUT_F32 ? part32 : nullptr;
+  run->cd_out = plan.out_mode == TC_OUT_COLDOT ? cd : nullptr;
+  run->splits = (int)plan.splits;
+  run->groups = plan.groups;
   run->n_tiles = n_tiles;
+  run->nt_group = plan.nt_group;
   return LTGW_OK;
 }
 
@@ -397,10 +509,10 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   ctx->pi_tc_flops = (fp8 ? 1.0 : 3.0) * 2.0 * (double)run.n_tiles * 128 * 128 * (double)g.Kp * n_t;
   if (n_tau == 0) {
     CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                           nI, n_t, N, -2.0 * spin, Pi, s, 0.0, g.nt_group, 1), 1);
+                                           nI, n_t, N, -2.0 * spin, Pi, s, 0.0, run.nt_group, 1), 1);
   } else {
     CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                           nI, n_t, N, 1.0, M, s, 0.0, g.nt_group, 1), 1);
+                                           nI, n_t, N, 1.0, M, s, 0.0, run.nt_group, 1), 1);
     CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
   }
   return LTGW_OK;
@@ -432,7 +544,7 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
   TcRun run;
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
   CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                         nI, 1, n, 1.0, K, s, beta, g.nt_group, 0), 1);
+                                         nI, 1, n, 1.0, K, s, beta, run.nt_group, 0), 1);
   return LTGW_OK;
 }
 
@@ -642,6 +754,12 @@ const char *ltgw_last_error(const ltgw_ctx *ctx) { return ctx ? ctx->err.c_str()
 ltgw_status ltgw_set_timing(ltgw_ctx *ctx, int on) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
   ctx->timing = (on != 0);
+  return LTGW_OK;
+}
+
+ltgw_status ltgw_set_autotune(ltgw_ctx *ctx, int on) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->autotune = (on != 0);
   return LTGW_OK;
 }
 

@@ -35,7 +35,7 @@ class Stats(ctypes.Structure):
                 ("ms_wnm", ctypes.c_double), ("ms_sigma_qp", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_pi_kernel", ctypes.c_double), ("pi_kernel_launches", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int), ("ms_tridiag", ctypes.c_double),
-                ("ms_generate", ctypes.c_double)]
+                ("ms_generate", ctypes.c_double), ("tc_autotuned", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,6 +73,7 @@ SIGNATURES = {
     "ltgw_status_string": (ctypes.c_char_p, [_I]),
     "ltgw_last_error": (ctypes.c_char_p, [_P]),
     "ltgw_set_timing": (_I, [_P, _I]),
+    "ltgw_set_autotune": (_I, [_P, _I]),
     "ltgw_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "ltgw_solve": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "ltgw_solve_streamed": (_I, [_P, ctypes.POINTER(Params), _P, BLOCK_FN, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P,
@@ -199,6 +200,9 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check(self._lib.ltgw_set_timing(self.handle, int(bool(on))))
+
+    def set_autotune(self, on: bool):
+        self._check(self._lib.ltgw_set_autotune(self.handle, int(bool(on))))
 
     def stats(self) -> dict:
         s = Stats()
