@@ -71,11 +71,13 @@ typedef struct {
   int n_frozen;       /* lowest occupied orbitals frozen (0 <= n_frozen < n_occ)  */
   int n_aux;          /* auxiliary functions                                      */
   int n_omega;        /* modified Gauss-Legendre points (2..256)                  */
-  int n_tau;          /* Laplace points when use_laplace != 0 (1..64)             */
+  int n_tau;          /* Laplace / imaginary-time points, use_laplace != 0 (1..32) */
   double omega0;      /* GL map w = omega0 (1+x)/(1-x), Ha (> 0)                  */
   double naf_thresh;  /* < 0: no NAF; >= 0: keep eigenvalues of K above it        */
   int spin;           /* 1 (spin orbitals) or 2 (closed shell)                    */
   int use_laplace;    /* 0: Pi from Eq. Pi; 1: Pi from the Laplace moments M^m     */
+                      /* (Eq. LT); 2: imaginary-time (cosine-transform) form,     */
+                      /* moments with e^{-Delta tau_k} (ltgw_cosine_grid)         */
   int precision;      /* LTGW_FP64; LTGW_BF16X3: the dense contractions (NAF       */
                       /* metric, projections, Pi, W_nm) on the tensor cores with  */
                       /* split-BF16 operands (see ltgw_polarizability_mixed);     */
@@ -133,7 +135,11 @@ ltgw_status ltgw_get_stats(const ltgw_ctx *ctx, ltgw_stats *out);
  *   targets  any [n_tgt]                   orbital indices, n_frozen <= n < n_occ+n_virt
  *   shift    any [n_tgt]                   (Sigma_x - V_xc)_n, Ha
  *   tau_x, tau_w  any [n_tau] or NULL      Laplace grid; NULL: the library fits a
- *                                          minimax grid on the paper's interval
+ *                                          minimax grid on the paper's interval.
+ *                                          use_laplace = 2: tau_x = tau [n_tau],
+ *                                          tau_w = gamma [n_omega][n_tau]; NULL:
+ *                                          ltgw_cosine_grid on [gap, span] of the
+ *                                          active orbitals
  *   sigma_iw any [n_tgt][n_omega][2]       out: Sigma^c_n(i w_l) (re, im) at the GL nodes
  *   e_qp     any [n_tgt]                   out: quasi-particle energies, Ha
  *   qp_status any [n_tgt]                  out: 0 converged, 1 not
@@ -179,6 +185,23 @@ ltgw_status ltgw_gl_grid(int n, double omega0, double *omega, double *weight);
 ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *x, double *w,
                               double *max_rel_err);
 
+/* Imaginary-time (cosine-transform) grid, the alternative to Eq. LT's
+ * factorisation: Delta / (w^2 + Delta^2) = int_0^inf cos(w tau) e^{-Delta tau} dtau
+ * ~ sum_k gamma[j][k] e^{-Delta tau_k} for Delta in [dmin, dmax] and each of the
+ * n_omega frequencies.  tau (n_tau): geometric from 0.1/dmax to 8/dmin;
+ * gamma ([n_omega][n_tau]): per frequency, the least-squares fit over log-spaced
+ * Delta of the error scaled by the target's largest value on [dmin, dmax], plus
+ * ridge times the squared coefficients of unit-norm columns (a small ridge
+ * trades fit error for less cancellation among the coefficients).  max_err: the
+ * largest such scaled error over the frequencies on a finer sample;
+ * amplification (may be NULL): the largest sum_k |gamma_jk| e^{-Delta tau_k} over
+ * the target's largest value, the factor by which the recombination can
+ * magnify relative errors of the moments.  Solves use ridge 1e-14 in FP64 and
+ * 1e-10 in the tensor-core forms.  Host only. */
+ltgw_status ltgw_cosine_grid(int n_tau, double dmin, double dmax, int n_omega, const double *omegas,
+                             double ridge, double *tau, double *gamma, double *max_err,
+                             double *amplification);
+
 /* ---- single steps on device buffers (for checking and composition) ------ */
 
 /* NAF basis (Eqs. nafeq and NAF eigen-equation): K = B B^T over the n_pairs
@@ -219,6 +242,18 @@ ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, con
                                       const double *delta, int n_omega, const double *omegas,
                                       int n_tau, const double *x, const double *w, int spin,
                                       double *Pi, void *stream);
+
+/* Pi in the imaginary-time (cosine-transform) form, the alternative to Eq. LT's
+ * factorisation (Delta / (w^2 + Delta^2) = int_0^inf cos(w tau) e^{-Delta tau} dtau):
+ * M^k = R~ diag(e^{-Delta tau_k}) R~^T for the n_tau points tau (host) and
+ * Pi_j = -2 spin sum_k gamma[j][k] M^k (gamma host [n_omega][n_tau], e.g. from
+ * ltgw_cosine_grid).  precision: LTGW_FP64, LTGW_BF16X3 (split BF16) or
+ * LTGW_FP8 / LTGW_FP8_PI (FP8 E4M3); other arguments as ltgw_polarizability.
+ * Synchronises. */
+ltgw_status ltgw_polarizability_tau(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                    const double *delta, int n_omega, const double *omegas,
+                                    int n_tau, const double *tau, const double *gamma, int spin,
+                                    int precision, double *Pi, void *stream);
 
 /* The same polarisability in FP8 E4M3 (not a step of the paper: the
  * low-precision variant of its Pi contraction).  R~ is rounded to FP32, the

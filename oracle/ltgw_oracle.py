@@ -50,6 +50,7 @@ __all__ = [
     "screened_interaction", "w_nm", "sigma_iw", "pade_coefficients", "pade_eval",
     "qp_newton", "solve", "sinc_laplace_grid", "pade_nodes",
     "E4M3_MAX", "e4m3_round", "fp8_row_quantize", "pi_scale_table", "polarizability_fp8",
+    "cosine_grid", "tau_moments", "polarizability_tau",
 ]
 
 
@@ -155,6 +156,51 @@ def polarizability_lt(M: np.ndarray, omegas: np.ndarray, x: np.ndarray, spin: in
 
 
 # ----------------------------------------------------------------------------
+# Imaginary-time (cosine-transform) form of Pi
+# ----------------------------------------------------------------------------
+# The alternative to Eq. LT's factorisation in X = w^2 + Delta^2: the
+# Fourier-cosine representation Delta / (w^2 + Delta^2) = int_0^inf cos(w t)
+# e^{-Delta t} dt, discretised on nodes tau_k with per-frequency coefficients
+# gamma_jk, so that Pi_j = -2 s sum_k gamma_jk M^k with
+# M^k = R~ diag(e^{-Delta tau_k}) R~^T.
+def cosine_grid(n_tau: int, dmin: float, dmax: float, omegas, ridge: float = 0.0, n_samples: int = 2000):
+    """A grid for the imaginary-time form: geometric tau from 0.1/dmax to 8/dmin and,
+    per frequency, the least-squares (SVD) coefficients of the error scaled by the
+    target's largest value over log-spaced Delta in [dmin, dmax], optionally with
+    ridge times the squared coefficients of unit-norm columns.  Returns
+    (tau, gamma [n_omega][n_tau], amplification = max sum_k |gamma_jk| e^{-Delta tau_k}
+    over the target's largest value)."""
+    tau = np.geomspace(0.1 / dmax, 8.0 / dmin, n_tau)
+    D = np.geomspace(dmin, dmax, n_samples)
+    E = np.exp(-D[:, None] * tau[None, :])
+    gamma = np.empty((len(omegas), n_tau))
+    amp = 0.0
+    for j, om in enumerate(omegas):
+        f = D / (om * om + D * D)
+        s = f.max()
+        A = E / s
+        cn = np.linalg.norm(A, axis=0)
+        As = np.vstack([A / cn, np.sqrt(ridge) * np.eye(n_tau)])
+        y = np.concatenate([f / s, np.zeros(n_tau)])
+        gamma[j] = np.linalg.lstsq(As, y, rcond=None)[0] / cn
+        amp = max(amp, (np.abs(E * gamma[j][None, :]).sum(1) / s).max())
+    return tau, gamma, amp
+
+
+def tau_moments(Bt: np.ndarray, delta: np.ndarray, tau: np.ndarray) -> np.ndarray:
+    """M^k_PQ = sum_ia R^P_ia exp(-Delta_ia tau_k) R^Q_ia."""
+    out = np.empty((len(tau), Bt.shape[0], Bt.shape[0]))
+    for k in range(len(tau)):
+        out[k] = (Bt * np.exp(-delta * tau[k])[None, :]) @ Bt.T
+    return out
+
+
+def polarizability_tau(M: np.ndarray, gamma: np.ndarray, spin: int = 2) -> np.ndarray:
+    """Pi_j = -2 s sum_k gamma_jk M^k."""
+    return -2.0 * spin * np.tensordot(gamma, M, axes=(1, 0))
+
+
+# ----------------------------------------------------------------------------
 # FP8 E4M3 form of the Pi contraction (per-auxiliary-row scales)
 # ----------------------------------------------------------------------------
 # Not a step of the paper: the low-precision variant of the Pi contraction.
@@ -192,26 +238,29 @@ def fp8_row_quantize(X):
     return e4m3_round(X * inv[:, None]), inv
 
 
-def pi_scale_table(delta, omegas=None, x=None, w=None) -> np.ndarray:
-    """Per-pair factors in FP32: Delta / (w_j^2 + Delta^2) per frequency (Eq. Pi)
-    or w_m Delta exp(-Delta^2 x_m) per Laplace point (the M^m form), each
-    formed in FP64 and rounded once."""
+def pi_scale_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
+    """Per-pair factors in FP32: Delta / (w_j^2 + Delta^2) per frequency (Eq. Pi),
+    w_m Delta exp(-Delta^2 x_m) per Laplace point (the M^m form) or
+    exp(-Delta tau_k) per imaginary-time node, each formed in FP64 and rounded once."""
     delta = np.asarray(delta, dtype=np.float64)
-    if x is None:
+    if tau is not None:
+        rows = [np.exp(-delta * t) for t in tau]
+    elif x is None:
         rows = [delta / (om * om + delta * delta) for om in omegas]
     else:
         rows = [w[m] * delta * np.exp(-delta * delta * x[m]) for m in range(len(x))]
     return np.array(rows).astype(np.float32)
 
 
-def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None) -> np.ndarray:
+def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None, tau=None, gamma=None) -> np.ndarray:
     """Pi in the FP8 E4M3 form: B32 = fp32(R~); for each frequency (Eq. Pi) or
     Laplace point (M^m form) with FP32 factors s_k, A_k = fp32(B32 * s_k);
     A_k and B32 are quantised per auxiliary row (fp8_row_quantize) and
     M_k = (qA_k / invA_k) (qB / invB)^T summed exactly, lower triangle
-    mirrored; then Pi as in polarizability_direct or polarizability_lt."""
+    mirrored; then Pi as in polarizability_direct, polarizability_lt or (tau,
+    gamma) polarizability_tau."""
     B32 = np.asarray(Bt, dtype=np.float32)
-    S = pi_scale_table(delta, omegas, x, w)
+    S = pi_scale_table(delta, omegas, x, w, tau)
     qb, invb = fp8_row_quantize(B32)
     Bd = qb / np.where(invb > 0, invb, 1.0).astype(np.float64)[:, None]
     M = np.empty((len(S), B32.shape[0], B32.shape[0]))
@@ -222,6 +271,8 @@ def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None) -> np.n
         # qA qB^T is not exactly symmetric (the two operands carry different
         # scales): the lower triangle (P >= Q) is formed and mirrored
         M[k] = np.tril(Mk) + np.tril(Mk, -1).T
+    if tau is not None:
+        return polarizability_tau(M, gamma, spin)
     if x is None:
         return -2.0 * spin * M
     return polarizability_lt(M, omegas, x, spin)
@@ -334,9 +385,12 @@ def pade_nodes(n_omega: int) -> np.ndarray:
 
 
 def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=24,
-          omega0=0.5, naf_thresh=-1.0, spin=2, tau_x=None, tau_w=None, return_all=False):
+          omega0=0.5, naf_thresh=-1.0, spin=2, tau_x=None, tau_w=None, return_all=False, cos_tau=None,
+          cos_gamma=None):
     """One G0W0 solve.  Direct Pi (Eq. Pi) unless a Laplace grid (tau_x, tau_w)
-    is given, in which case Pi is built from the moments M^m.
+    is given, in which case Pi is built from the moments M^m, or an
+    imaginary-time grid (cos_tau [n_tau], cos_gamma [n_omega][n_tau]), in which
+    case Pi_j = -2 s sum_k gamma_jk M^k with M^k = R~ diag(e^{-Delta tau_k}) R~^T.
     B_ov [P][i*n_virt+a] (all occupied i), B_tgt [T][P][m] (all orbitals m).
     Returns (sigma [T][n_omega] complex, e_qp [T], status [T]) and, with
     return_all, a dict of intermediates."""
@@ -359,7 +413,11 @@ def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=2
         Bt = B_act
         Bt_tgt = np.ascontiguousarray(B_tgt[:, :, n_frozen:])
         inter.update(U=None, n_naf=Bt.shape[0])
-    if tau_x is None:
+    if cos_tau is not None:
+        M = tau_moments(Bt, delta, np.asarray(cos_tau))
+        Pi = polarizability_tau(M, np.asarray(cos_gamma), spin)
+        inter["M"] = M
+    elif tau_x is None:
         Pi = polarizability_direct(Bt, delta, omegas, spin)
     else:
         M = laplace_moments(Bt, delta, np.asarray(tau_x), np.asarray(tau_w))

@@ -232,11 +232,14 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   return LTGW_OK;
 }
 
-// Pi at the GL frequencies, direct (n_tau == 0) or through Laplace moments.
+// Pi at the GL frequencies, direct (n_tau == 0) or through moments M^k and the
+// recombination d_E [n_omega][n_tau]: lt_form 1 = the M^m form of Eq. LT
+// (factors w_m Delta e^{-Delta^2 x_m}), 2 = imaginary time (factors e^{-Delta tau_k},
+// tau_k in d_x).
 ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, int64_t ldb,
                                const double *delta, int n_omega, const double *d_omega,
                                int n_tau, const double *d_x, const double *d_w, const double *d_E,
-                               double *M, int spin, double *Pi, cudaStream_t s) {
+                               double *M, int spin, double *Pi, cudaStream_t s, int lt_form) {
   GemmF64Args g;
   g.M = N; g.N = N; g.K = n_pairs;
   g.A = Bt; g.lda = ldb; g.B = Bt; g.ldb = ldb;
@@ -254,9 +257,9 @@ ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const doub
   } else {
     g.C = M;
     g.alpha = 1.0;
-    g.scale_mode = SCALE_LAPLACE;
+    g.scale_mode = lt_form == 2 ? SCALE_EXPTAU : SCALE_LAPLACE;
     g.batch_p0 = d_x;
-    g.batch_p1 = d_w;
+    g.batch_p1 = lt_form == 2 ? nullptr : d_w;
     CHECK_LAUNCH(ctx, launch_gemm_f64(g, n_tau, true, true, s), 1);
     ctx->mark(EV_PI1, s);
     CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
@@ -457,7 +460,7 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
 ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, int64_t ldb,
                               const float *Af_in, const double *delta, int n_omega, const double *d_omega,
                               int n_tau, const double *d_x, const double *d_w, const double *d_E,
-                              double *M, int spin, double *Pi, cudaStream_t s, bool fp8) {
+                              double *M, int spin, double *Pi, cudaStream_t s, bool fp8, int lt_form) {
   const int64_t Kp = (n_pairs + 63) / 64 * 64, Kq = (n_pairs + 127) / 128 * 128;
   const int nI = (N + 127) / 128, Mp = nI * 128;
   const int n_t = n_tau ? n_tau : n_omega;
@@ -489,8 +492,9 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   const float *A = Af_in ? Af_in : Af;
   copy_in(ctx, d_tindex, tindex.data(), tindex.size() * sizeof(int), s);
   if (!Af_in) CHECK_LAUNCH(ctx, launch_to_f32_padded(Bt, ldb, N, n_pairs, Af, Mp, Kp, s), 1);
-  CHECK_LAUNCH(ctx, launch_scale_table(delta, n_pairs, Kp, n_t, n_tau ? d_x : d_omega, n_tau ? d_w : nullptr,
-                                       n_tau ? SCALE_LAPLACE : SCALE_DIRECT, scale, s), 1);
+  const int mode = n_tau ? (lt_form == 2 ? SCALE_EXPTAU : SCALE_LAPLACE) : SCALE_DIRECT;
+  CHECK_LAUNCH(ctx, launch_scale_table(delta, n_pairs, Kp, n_t, n_tau ? d_x : d_omega,
+                                       mode == SCALE_LAPLACE ? d_w : nullptr, mode, scale, s), 1);
   TcGemmArgs g;
   if (fp8) {
     CHECK_LAUNCH(ctx, launch_fp8_quantize(A, Kp, Kq, scale, n_t, Mp, qa, qb, ds_a, ds_b, s), 1);
@@ -684,7 +688,7 @@ ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
   REQUIRE(ctx, p->n_omega >= 1 && p->n_omega <= 256, "n_omega must be in [1, 256]");
   REQUIRE(ctx, p->omega0 > 0.0 && isfinite(p->omega0), "omega0 must be positive");
   REQUIRE(ctx, p->spin == 1 || p->spin == 2, "spin must be 1 or 2");
-  REQUIRE(ctx, p->use_laplace == 0 || p->use_laplace == 1, "use_laplace must be 0 or 1");
+  REQUIRE(ctx, p->use_laplace >= 0 && p->use_laplace <= 2, "use_laplace must be 0, 1 or 2");
   REQUIRE(ctx, !p->use_laplace || (p->n_tau >= 1 && p->n_tau <= 32), "n_tau must be in [1, 32]");
   REQUIRE(ctx, p->precision >= LTGW_FP64 && p->precision <= LTGW_FP8_PI,
           "precision must be LTGW_FP64, LTGW_BF16X3, LTGW_FP8 or LTGW_FP8_PI");
@@ -822,7 +826,24 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   }
   std::vector<double> h_x(n_tau), h_w(n_tau), h_E((size_t)n_omega * std::max(n_tau, 1));
   ctx->stats.lt_max_rel_err = NAN;
-  if (n_tau) {
+  if (n_tau && p->use_laplace == 2) {
+    // imaginary-time form: tau_k (tau_x) and the recombination gamma [n_omega][n_tau] (tau_w)
+    if (tau_x) {
+      if (read_small(ctx, h_x.data(), tau_x, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
+      if (read_small(ctx, h_E.data(), tau_w, h_E.size() * sizeof(double), s) != LTGW_OK) return ctx->status();
+    } else {
+      double err = 0.0;
+      // the tensor-core forms carry ~1e-5 relative error in M^k: a larger ridge
+      // keeps the recombination from magnifying it
+      if (ltgw_cosine_grid(n_tau, h_eps[n_occ] - h_eps[n_occ - 1], h_eps[n_orb - 1] - h_eps[n_fc], n_omega,
+                           h_om.data(), mixed ? 1e-10 : 1e-14, h_x.data(), h_E.data(), &err,
+                           nullptr) != LTGW_OK) {
+        ctx->fail(LTGW_ERR_BAD_ARG, "imaginary-time grid fit");
+        return ctx->status();
+      }
+      ctx->stats.lt_max_rel_err = err;
+    }
+  } else if (n_tau) {
     if (tau_x) {
       if (read_small(ctx, h_x.data(), tau_x, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
       if (read_small(ctx, h_w.data(), tau_w, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
@@ -1016,10 +1037,10 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   // ---- Pi (Eq. Pi or the Laplace form)
   if (mixed) {
     if (polarizability_tc(ctx, N, n_ov, nullptr, 0, d_Bf, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E,
-                          d_M, p->spin, d_Pi, s, fp8) != LTGW_OK)
+                          d_M, p->spin, d_Pi, s, fp8, p->use_laplace) != LTGW_OK)
       return ctx->status();
   } else if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
-                                p->spin, d_Pi, s) != LTGW_OK) {
+                                p->spin, d_Pi, s, p->use_laplace) != LTGW_OK) {
     return ctx->status();
   }
   ctx->mark(EV_PI, s);
@@ -1088,21 +1109,69 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   return ctx->status();
 }
 
-ltgw_status polarizability_tc_api(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, const double *delta,
-                                  int n_omega, const double *omegas, int n_tau, const double *x, const double *w,
-                                  int spin, double *Pi, void *stream, bool fp8) {
+ltgw_status polarizability_dev_api(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, const double *delta,
+                                   int n_omega, const double *omegas, int n_tau, const double *x, const double *w,
+                                   int spin, double *Pi, void *stream, int lt_form, const double *gamma) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
   ctx->reset();
   REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
   REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
   REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
-  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
+  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && (lt_form == 2 ? gamma : w) != nullptr)),
+          "a required pointer is NULL");
   REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
   LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
   for (int j = 0; j < n_omega; ++j)
-    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
+    for (int k = 0; k < n_tau; ++k)
+      h_E[(size_t)j * n_tau + k] = lt_form == 2 ? gamma[(size_t)j * n_tau + k] : exp(-h_om[j] * h_om[j] * x[k]);
+  double *d_om, *d_x, *d_w, *d_E, *d_M;
+  auto layout = [&](Arena &A) {
+    d_om = A.take<double>(n_omega);
+    d_x = A.take<double>(std::max(n_tau, 1));
+    d_w = A.take<double>(std::max(n_tau, 1));
+    d_E = A.take<double>(h_E.size());
+    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
+  };
+  ctx->a2.begin_sizing();
+  layout(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
+  layout(ctx->a2);
+  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
+  if (n_tau) {
+    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
+    if (lt_form != 2) copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
+    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+  }
+  if (ctx->status() != LTGW_OK) return ctx->status();
+  if (polarizability_dev(ctx, N, n_pairs, Bt, n_pairs, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                         spin, Pi, s, lt_form) != LTGW_OK)
+    return ctx->status();
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));  // the staged grid lives in the workspace
+  return LTGW_OK;
+}
+
+// lt_form 1: x, w are the Laplace grid of Eq. LT; 2: x holds tau_k and gamma
+// [n_omega][n_tau] the imaginary-time recombination (w unused).
+ltgw_status polarizability_tc_api(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, const double *delta,
+                                  int n_omega, const double *omegas, int n_tau, const double *x, const double *w,
+                                  int spin, double *Pi, void *stream, bool fp8, int lt_form = 1,
+                                  const double *gamma = nullptr) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
+  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
+  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
+  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && (lt_form == 2 ? gamma : w) != nullptr)),
+          "a required pointer is NULL");
+  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
+  for (int j = 0; j < n_omega; ++j)
+    for (int k = 0; k < n_tau; ++k)
+      h_E[(size_t)j * n_tau + k] = lt_form == 2 ? gamma[(size_t)j * n_tau + k] : exp(-h_om[j] * h_om[j] * x[k]);
   double *d_om, *d_x, *d_w, *d_E, *d_M;
   auto layout = [&](Arena &A) {
     d_om = A.take<double>(n_omega);
@@ -1119,12 +1188,12 @@ ltgw_status polarizability_tc_api(ltgw_ctx *ctx, int N, int64_t n_pairs, const d
   copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
   if (n_tau) {
     copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
-    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
+    if (lt_form != 2) copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
     copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
   }
   if (ctx->status() != LTGW_OK) return ctx->status();
   if (polarizability_tc(ctx, N, n_pairs, Bt, n_pairs, nullptr, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
-                        spin, Pi, s, fp8) != LTGW_OK)
+                        spin, Pi, s, fp8, lt_form) != LTGW_OK)
     return ctx->status();
   LTGW_CUDA(ctx, cudaStreamSynchronize(s));
   ctx->stats.ms_pi_kernel = ctx->ms(EV_PI0, EV_PI1);
@@ -1192,42 +1261,25 @@ ltgw_status ltgw_naf_basis_mixed(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, cons
 ltgw_status ltgw_polarizability(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
                                 const double *delta, int n_omega, const double *omegas, int n_tau,
                                 const double *x, const double *w, int spin, double *Pi, void *stream) {
+  return polarizability_dev_api(ctx, N, n_pairs, Bt, delta, n_omega, omegas, n_tau, x, w, spin, Pi, stream, 1,
+                                nullptr);
+}
+
+ltgw_status ltgw_polarizability_tau(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, const double *delta,
+                                    int n_omega, const double *omegas, int n_tau, const double *tau,
+                                    const double *gamma, int spin, int precision, double *Pi, void *stream) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
-  ctx->reset();
-  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
-  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
-  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
-  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
-  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
-  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
-  for (int j = 0; j < n_omega; ++j)
-    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
-  double *d_om, *d_x, *d_w, *d_E, *d_M;
-  auto layout = [&](Arena &A) {
-    d_om = A.take<double>(n_omega);
-    d_x = A.take<double>(std::max(n_tau, 1));
-    d_w = A.take<double>(std::max(n_tau, 1));
-    d_E = A.take<double>(h_E.size());
-    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
-  };
-  ctx->a2.begin_sizing();
-  layout(ctx->a2);
-  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
-  layout(ctx->a2);
-  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
-  if (n_tau) {
-    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
-    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
-    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
-  }
-  if (ctx->status() != LTGW_OK) return ctx->status();
-  if (polarizability_dev(ctx, N, n_pairs, Bt, n_pairs, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
-                         spin, Pi, s) != LTGW_OK)
+  if (n_tau < 1) { ctx->reset(); ctx->fail(LTGW_ERR_BAD_ARG, "n_tau must be >= 1"); return ctx->status(); }
+  if (precision == LTGW_FP64)
+    return polarizability_dev_api(ctx, N, n_pairs, Bt, delta, n_omega, omegas, n_tau, tau, nullptr, spin, Pi,
+                                  stream, 2, gamma);
+  if (precision < LTGW_FP64 || precision > LTGW_FP8_PI) {
+    ctx->reset();
+    ctx->fail(LTGW_ERR_BAD_ARG, "unknown precision");
     return ctx->status();
-  LTGW_CUDA(ctx, cudaStreamSynchronize(s));  // the staged grid lives in the workspace
-  return LTGW_OK;
+  }
+  return polarizability_tc_api(ctx, N, n_pairs, Bt, delta, n_omega, omegas, n_tau, tau, nullptr, spin, Pi, stream,
+                               precision == LTGW_FP8 || precision == LTGW_FP8_PI, 2, gamma);
 }
 
 ltgw_status ltgw_polarizability_mixed(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,

@@ -34,6 +34,7 @@ struct TileSmem {
 __device__ __forceinline__ double pair_scale(int mode, double d, double p0, double p1) {
   if (mode == SCALE_DIRECT) return d / (p0 * p0 + d * d);   // D / (w^2 + D^2)
   if (mode == SCALE_LAPLACE) return p1 * d * exp(-d * d * p0);  // w_m D e^{-D^2 x_m}
+  if (mode == SCALE_EXPTAU) return exp(-d * p0);                // e^{-D tau_k}
   return 1.0;
 }
 

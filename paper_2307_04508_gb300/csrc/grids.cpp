@@ -387,3 +387,107 @@ extern "C" ltgw_status ltgw_laplace_grid(int n_tau, double a, double b, double *
   if (max_err) *max_err = err;
   return LTGW_OK;
 }
+
+namespace {
+// min ||A g - y||^2 + ridge ||C g||^2 for A (m x n, column-major, m >= n),
+// C the diagonal that gives A's columns unit norm, by Householder QR of A's
+// unit-norm columns stacked over sqrt(ridge) I.  The small ridge keeps the
+// coefficients of nearly dependent exponentials from cancelling at large
+// magnitude.  False when a column is zero.
+bool least_squares(const std::vector<double> &A0, int m, int n, const std::vector<double> &y0, double ridge,
+                   std::vector<double> &g) {
+  const int mm = m + n;
+  std::vector<double> A((size_t)mm * n, 0.0), y(mm, 0.0), cs(n);
+  for (int c = 0; c < n; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < m; ++r) s += A0[(size_t)c * m + r] * A0[(size_t)c * m + r];
+    if (!(s > 0.0)) return false;
+    cs[c] = 1.0 / sqrt(s);
+    for (int r = 0; r < m; ++r) A[(size_t)c * mm + r] = A0[(size_t)c * m + r] * cs[c];
+    A[(size_t)c * mm + m + c] = sqrt(ridge);
+  }
+  for (int r = 0; r < m; ++r) y[r] = y0[r];
+  for (int c = 0; c < n; ++c) {
+    double *a = &A[(size_t)c * mm];
+    double nrm = 0.0;
+    for (int r = c; r < mm; ++r) nrm += a[r] * a[r];
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0)) return false;
+    const double alpha = a[c] > 0.0 ? -nrm : nrm;
+    a[c] -= alpha;                                  // v = a - alpha e_c, stored in place
+    const double vtv = -2.0 * alpha * a[c];         // |v|^2 = 2 nrm (nrm + |a_c|)
+    for (int d = c + 1; d < n; ++d) {
+      double *b = &A[(size_t)d * mm];
+      double t = 0.0;
+      for (int r = c; r < mm; ++r) t += a[r] * b[r];
+      t = 2.0 * t / vtv;
+      for (int r = c; r < mm; ++r) b[r] -= t * a[r];
+    }
+    double t = 0.0;
+    for (int r = c; r < mm; ++r) t += a[r] * y[r];
+    t = 2.0 * t / vtv;
+    for (int r = c; r < mm; ++r) y[r] -= t * a[r];
+    a[c] = alpha;                                   // R's diagonal
+  }
+  g.assign(n, 0.0);
+  for (int c = n - 1; c >= 0; --c) {
+    double s = y[c];
+    for (int d = c + 1; d < n; ++d) s -= A[(size_t)d * mm + c] * g[d];
+    g[c] = s / A[(size_t)c * mm + c];
+  }
+  for (int c = 0; c < n; ++c) g[c] *= cs[c];
+  return true;
+}
+}  // namespace
+
+// Imaginary-time (cosine-transform) grid:
+//   Delta / (w^2 + Delta^2) = int_0^inf cos(w tau) exp(-Delta tau) dtau
+//                           ~ sum_k gamma_jk exp(-Delta tau_k)   for Delta in [dmin, dmax].
+// tau_k: geometric from 0.1 / dmax to 8 / dmin (the decay times of the pair
+// exponentials; the short ones carry the nearly linear shape Delta / w^2 of
+// the high frequencies).  gamma_j: for each frequency w_j the least-squares
+// fit over log-spaced Delta of the error scaled by max_Delta of the target,
+// with a ridge term ridge |C g|^2 (C: unit-norm columns).  max_err: max over
+// frequencies of max_Delta |fit - target| / max_Delta target on a four times
+// finer sample; amplification: max over frequencies and Delta of
+// sum_k |gamma_jk| e^{-Delta tau_k} / max target, the factor by which the
+// recombination can magnify relative errors of M^k.
+extern "C" ltgw_status ltgw_cosine_grid(int n_tau, double dmin, double dmax, int n_omega, const double *omegas,
+                                        double ridge, double *tau, double *gamma, double *max_err,
+                                        double *amplification) {
+  if (n_tau < 1 || n_tau > 64 || !(dmin > 0.0) || !(dmax > dmin) || n_omega < 1 || !omegas || !tau || !gamma ||
+      !(ridge >= 0.0))
+    return LTGW_ERR_BAD_ARG;
+  const double t_lo = 0.1 / dmax, t_hi = 8.0 / dmin;
+  for (int k = 0; k < n_tau; ++k)
+    tau[k] = n_tau == 1 ? sqrt(t_lo * t_hi) : t_lo * pow(t_hi / t_lo, (double)k / (n_tau - 1));
+  const int m = 64 * n_tau + 200, mf = 4 * m;
+  const double lr = log(dmax / dmin);
+  double worst = 0.0, amp = 0.0;
+  std::vector<double> A((size_t)m * n_tau), y(m), g;
+  for (int j = 0; j < n_omega; ++j) {
+    const double w2 = omegas[j] * omegas[j];
+    // the target's largest value on [dmin, dmax]: at Delta = w when w lies inside
+    const double dpk = std::min(std::max(omegas[j], dmin), dmax), fmax = dpk / (w2 + dpk * dpk);
+    for (int s = 0; s < m; ++s) {
+      const double d = dmin * exp(lr * s / (m - 1)), f = d / (w2 + d * d);
+      for (int k = 0; k < n_tau; ++k) A[(size_t)k * m + s] = exp(-d * tau[k]) / fmax;
+      y[s] = f / fmax;
+    }
+    if (!least_squares(A, m, n_tau, y, ridge, g)) return LTGW_ERR_BAD_ARG;
+    for (int k = 0; k < n_tau; ++k) gamma[(size_t)j * n_tau + k] = g[k];
+    for (int s = 0; s < mf; ++s) {
+      const double d = dmin * exp(lr * s / (mf - 1)), f = d / (w2 + d * d);
+      double v = 0.0, va = 0.0;
+      for (int k = 0; k < n_tau; ++k) {
+        v += g[k] * exp(-d * tau[k]);
+        va += fabs(g[k]) * exp(-d * tau[k]);
+      }
+      worst = std::max(worst, fabs(v - f) / fmax);
+      amp = std::max(amp, va / fmax);
+    }
+  }
+  if (max_err) *max_err = worst;
+  if (amplification) *amplification = amp;
+  return LTGW_OK;
+}

@@ -10,7 +10,9 @@
 
 namespace ltgw {
 
-enum ScaleMode { SCALE_NONE = 0, SCALE_DIRECT = 1, SCALE_LAPLACE = 2 };
+// per-pair factor of Pi's contraction: Delta / (w^2 + Delta^2) (Eq. Pi), w_m Delta
+// e^{-Delta^2 x_m} (the M^m form of Eq. LT), or e^{-Delta tau_k} (imaginary-time form)
+enum ScaleMode { SCALE_NONE = 0, SCALE_DIRECT = 1, SCALE_LAPLACE = 2, SCALE_EXPTAU = 3 };
 
 // C_b = alpha * A_b diag(s_b) B_b for b in [0, batch).  With syrk = 1 only the
 // lower-triangle tiles are computed and each value is mirrored (A == B^T).
@@ -165,7 +167,8 @@ cudaError_t launch_tc_reduce_coldot(const float *cd_out, int splits, int groups,
 // dst[r][c] = (float)src[r][c] for r < rows, c < cols; zero up to rows_p x cols_p.
 cudaError_t launch_to_f32_padded(const double *src, int64_t lds, int rows, int64_t cols, float *dst,
                                  int rows_p, int64_t cols_p, cudaStream_t s);
-// scale[t][k] (FP32, zero for k >= K): direct w_t -> D/(w^2+D^2); Laplace (x_t, w_t) -> w D e^{-D^2 x}.
+// scale[t][k] (FP32, zero for k >= K): direct w_t -> D/(w^2+D^2); Laplace (x_t, w_t) -> w D e^{-D^2 x};
+// imaginary time tau_t -> e^{-D tau}.
 cudaError_t launch_scale_table(const double *delta, int64_t K, int64_t Kp, int n_t, const double *p0,
                                const double *p1, int mode, float *scale, cudaStream_t s);
 // M_t = alpha * sum over splits of the partial tiles (FP64 or FP32), full symmetric

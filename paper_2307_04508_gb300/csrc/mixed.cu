@@ -38,7 +38,8 @@ __global__ void scale_table_kernel(const double *__restrict__ delta, int64_t K, 
     if (k < K) {
       const double d = delta ? delta[k] : 0.0;
       v = (mode == SCALE_DIRECT) ? d / (a * a + d * d)
-          : (mode == SCALE_LAPLACE) ? b * d * exp(-d * d * a) : 1.0;
+          : (mode == SCALE_LAPLACE) ? b * d * exp(-d * d * a)
+          : (mode == SCALE_EXPTAU) ? exp(-d * a) : 1.0;
     }
     scale[(int64_t)t * Kp + k] = (float)v;
   }

@@ -80,11 +80,13 @@ SIGNATURES = {
                                  _P, _P]),
     "ltgw_gl_grid": (_I, [_I, _D, _P, _P]),
     "ltgw_laplace_grid": (_I, [_I, _D, _D, _P, _P, _P]),
+    "ltgw_cosine_grid": (_I, [_I, _D, _D, _I, _P, _D, _P, _P, _P, _P]),
     "ltgw_naf_basis": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ltgw_naf_basis_mixed": (_I, [_P, _I, _I64, _P, _I64, _D, _P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_polarizability_mixed": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_polarizability_fp8": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "ltgw_polarizability_tau": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
     "ltgw_screen_static": (_I, [_I, _I, _P, _P, _P]),
     "ltgw_server_create": (_I, [ctypes.POINTER(ctypes.c_void_p), _I, _I, ctypes.c_size_t]),
@@ -160,6 +162,17 @@ def gl_grid(n: int, omega0: float = 0.5):
     if st:
         raise LtgwError(st, status_string(st))
     return om, wt
+
+
+def cosine_grid(n_tau: int, dmin: float, dmax: float, omegas, ridge: float = 1e-14):
+    """ltgw_cosine_grid: (tau [n_tau], gamma [n_omega][n_tau], max scaled error, amplification)."""
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    tau, gam, err, amp = np.zeros(n_tau), np.zeros((len(om), n_tau)), ctypes.c_double(), ctypes.c_double()
+    st = load().ltgw_cosine_grid(n_tau, dmin, dmax, len(om), om.ctypes.data, ridge, tau.ctypes.data,
+                                 gam.ctypes.data, ctypes.byref(err), ctypes.byref(amp))
+    if st != 0:
+        raise RuntimeError(f"ltgw_cosine_grid failed ({st})")
+    return tau, gam, err.value, amp.value
 
 
 def laplace_grid(n_tau: int, a: float, b: float):
@@ -272,6 +285,19 @@ class Context:
                 _ptr(Pi), _stream_ptr(stream))
         self._check(st)
 
+    def polarizability_tau(self, Bt, delta, omegas: np.ndarray, tau, gamma, Pi, spin: int = 2,
+                           precision: int = 0, stream=None):
+        """Imaginary-time form (ltgw_polarizability_tau): tau [n_tau], gamma [n_omega][n_tau] on the host."""
+        N, n_pairs = int(Bt.shape[0]), int(Bt.shape[1])
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        tt = np.ascontiguousarray(tau, dtype=np.float64)
+        gg = np.ascontiguousarray(gamma, dtype=np.float64)
+        assert gg.shape == (len(om), len(tt))
+        st = self._lib.ltgw_polarizability_tau(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om), _ptr(om),
+                                               len(tt), _ptr(tt), _ptr(gg), spin, precision, _ptr(Pi),
+                                               _stream_ptr(stream))
+        self._check(st)
+
     def polarizability_fp8(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None, stream=None):
         self.polarizability_mixed(Bt, delta, omegas, Pi, spin, x, w, stream, fp8=True)
 
@@ -346,8 +372,9 @@ def screen_static(Pi, C, stream=None) -> int:
 
 def make_params(n_occ, n_virt, n_aux, n_frozen=0, n_omega=32, n_tau=8, omega0=0.5, naf_thresh=-1.0,
                 spin=2, use_laplace=False, precision=LTGW_FP64) -> Params:
+    """use_laplace: False / 0 direct (Eq. Pi), True / 1 Eq. LT's moments, 2 imaginary time."""
     return Params(n_occ, n_virt, n_frozen, n_aux, n_omega, n_tau if use_laplace else 0, omega0,
-                  naf_thresh, spin, int(bool(use_laplace)), precision, 0)
+                  naf_thresh, spin, int(use_laplace), precision, 0)
 
 
 def solve_problem(ctx: Context, prob, n_omega=32, n_tau=8, naf_thresh=-1.0, use_laplace=False, spin=2,
