@@ -46,10 +46,13 @@ def sigma_analytic(E, eps_m, occ_mask, res, Omega):
 
 
 def g0w0_analytic(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, spin=2,
-                  tol=1e-12, max_iter=200):
+                  tol=1e-12, max_iter=200, eps_ref=None):
     """QP energies E_n = eps_n + Re Sigma^c_n(E_n) + shift_n by Newton from eps_n,
-    together with a callable giving Sigma^c_n at any complex energy."""
+    together with a callable giving Sigma^c_n at any complex energy.  With
+    eps_ref, Sigma^c is built from eps but the equation reads
+    E_n = eps_ref_n + Re Sigma^c_n(E_n) + shift_n (Newton from eps_ref_n)."""
     eps = np.asarray(eps, dtype=np.float64)
+    ref = eps if eps_ref is None else np.asarray(eps_ref, dtype=np.float64)
     B_act = B_ov[:, n_frozen * n_virt:]
     occ = eps[n_frozen:n_occ]
     virt = eps[n_occ:n_occ + n_virt]
@@ -60,11 +63,11 @@ def g0w0_analytic(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, s
     out, status, sig_fns = [], [], []
     for t, n in enumerate(targets):
         res = residues(B_act, B_tgt[t][:, n_frozen:], delta, Omega, Z, spin)
-        E = eps[n]
+        E = ref[n]
         st = 1
         for _ in range(max_iter):
             s, ds = sigma_analytic(E, eps_m, occ_mask, res, Omega)
-            dE = -(E - eps[n] - s.real - shift[t]) / (1.0 - ds.real)
+            dE = -(E - ref[n] - s.real - shift[t]) / (1.0 - ds.real)
             E += dE
             if abs(dE) < tol:
                 st = 0

@@ -50,7 +50,7 @@ __all__ = [
     "screened_interaction", "w_nm", "sigma_iw", "pade_coefficients", "pade_eval",
     "qp_newton", "solve", "sinc_laplace_grid", "pade_nodes",
     "E4M3_MAX", "e4m3_round", "fp8_row_quantize", "pi_scale_table", "polarizability_fp8",
-    "cosine_grid", "tau_moments", "polarizability_tau",
+    "cosine_grid", "tau_moments", "polarizability_tau", "evgw_energies", "evgw",
 ]
 
 
@@ -386,11 +386,13 @@ def pade_nodes(n_omega: int) -> np.ndarray:
 
 def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=24,
           omega0=0.5, naf_thresh=-1.0, spin=2, tau_x=None, tau_w=None, return_all=False, cos_tau=None,
-          cos_gamma=None):
+          cos_gamma=None, eps_qp_ref=None):
     """One G0W0 solve.  Direct Pi (Eq. Pi) unless a Laplace grid (tau_x, tau_w)
     is given, in which case Pi is built from the moments M^m, or an
     imaginary-time grid (cos_tau [n_tau], cos_gamma [n_omega][n_tau]), in which
     case Pi_j = -2 s sum_k gamma_jk M^k with M^k = R~ diag(e^{-Delta tau_k}) R~^T.
+    eps_qp_ref: energies of the quasi-particle equation's reference eps_n (and
+    Newton's start) when they differ from the energies of Pi and Sigma (evGW).
     B_ov [P][i*n_virt+a] (all occupied i), B_tgt [T][P][m] (all orbitals m).
     Returns (sigma [T][n_omega] complex, e_qp [T], status [T]) and, with
     return_all, a dict of intermediates."""
@@ -432,11 +434,68 @@ def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=2
     e_qp = np.empty(len(targets))
     status = np.empty(len(targets), dtype=np.int32)
     coefs = []
+    ref = eps if eps_qp_ref is None else np.asarray(eps_qp_ref, dtype=np.float64)
     for t, n in enumerate(targets):
         a = pade_coefficients(z_nodes, sig[t][sel])
         coefs.append(a)
-        e_qp[t], status[t] = qp_newton(eps[n], shift[t], eF, z_nodes, a)
+        e_qp[t], status[t] = qp_newton(ref[n], shift[t], eF, z_nodes, a)
     if return_all:
         inter.update(Bt=Bt, Bt_tgt=Bt_tgt, Pi=Pi, C=C, W=W, pade=np.array(coefs), delta=delta)
         return sig, e_qp, status, inter
     return sig, e_qp, status
+
+
+# ----------------------------------------------------------------------------
+# Eigenvalue-self-consistent GW (Sec. 3, computational details; the evGW
+# timings table of Sec. 4)
+# ----------------------------------------------------------------------------
+def evgw_energies(eps_ks, targets, e_qp, n_frozen: int = 0) -> np.ndarray:
+    """Orbital energies for the next evGW cycle: the quasi-particle energies for
+    the target states; every other active orbital shifted by the shift
+    (E_QP - eps) of the target nearest to it by orbital index (ties: the lower
+    one), which below and above the window is the shift of the lowest and of
+    the highest target; frozen-core orbitals unchanged."""
+    eps_ks = np.asarray(eps_ks, dtype=np.float64)
+    tg = np.asarray(targets)
+    order = np.argsort(tg)
+    tg = tg[order]
+    sh = (np.asarray(e_qp, dtype=np.float64) - eps_ks[np.asarray(targets)])[order]
+    out = eps_ks.copy()
+    for p in range(n_frozen, len(eps_ks)):
+        k = int(np.searchsorted(tg, p))
+        if k < len(tg) and tg[k] == p:
+            out[p] = eps_ks[p] + sh[k]
+            continue
+        cand = []
+        if k - 1 >= 0:
+            cand.append((p - tg[k - 1], 0, k - 1))
+        if k < len(tg):
+            cand.append((tg[k] - p, 1, k))
+        out[p] = eps_ks[p] + sh[min(cand)[2]]
+    return out
+
+
+def evgw(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_cycles=5, gap_tol=0.0, **solve_kw):
+    """evGW: cycle 0 is G0W0 on the input energies; each of up to n_cycles further
+    cycles recomputes Pi, W and Sigma with evgw_energies of the previous cycle,
+    keeping the input eps_n + (Sigma_x - V_xc)_n as the quasi-particle equation's
+    reference.  With gap_tol > 0 and both HOMO and LUMO among the targets, it
+    stops once the quasi-particle HOMO/LUMO gap changes by less than gap_tol.
+    Returns (sigma, e_qp, status, cycles after G0W0)."""
+    eps0 = np.asarray(eps, dtype=np.float64)
+    targets = np.asarray(targets)
+    sig, e, st = solve(eps0, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen, eps_qp_ref=eps0, **solve_kw)
+    ih = np.where(targets == n_occ - 1)[0]
+    il = np.where(targets == n_occ)[0]
+    done = 0
+    for _ in range(n_cycles):
+        cur = evgw_energies(eps0, targets, e, n_frozen)
+        sig, e_new, st = solve(cur, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen, eps_qp_ref=eps0,
+                               **solve_kw)
+        done += 1
+        conv = (gap_tol > 0 and len(ih) and len(il) and
+                abs((e_new[il[0]] - e_new[ih[0]]) - (e[il[0]] - e[ih[0]])) < gap_tol)
+        e = e_new
+        if conv:
+            break
+    return sig, e, st, done
