@@ -153,6 +153,28 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps,
                        int *qp_status, void *stream);
 
 /*
+ * Eigenvalue-self-consistent GW (evGW, Sec. 3 and the evGW timings of Sec. 4):
+ * ltgw_solve's G0W0, then up to n_cycles further cycles that rebuild Pi, W and
+ * Sigma from the previous cycle's quasi-particle energies for the target
+ * states and, for every other active orbital, its input energy shifted by the
+ * shift (E_QP - eps) of the target nearest to it by orbital index (below and
+ * above the window: the lowest and the highest target's shift; frozen core
+ * unchanged).  The NAF basis and the projected tensors are formed once; the
+ * library's Laplace grid (when tau_x is NULL) is refitted to each cycle's
+ * energies.  The quasi-particle equation keeps the input eps_n +
+ * (Sigma_x - V_xc)_n as its reference.  Stops early once the quasi-particle
+ * HOMO/LUMO gap changes by less than gap_tol (> 0; both states among the
+ * targets).  Outputs are those of the last cycle; cycles_done (may be NULL):
+ * the cycles run after G0W0.  Other arguments as ltgw_solve.
+ */
+ltgw_status ltgw_solve_ev(ltgw_ctx *ctx, const ltgw_params *p, const double *eps,
+                          const double *B_ov, const double *B_tgt, const int *targets,
+                          int n_tgt, const double *shift, const double *tau_x,
+                          const double *tau_w, int n_cycles, double gap_tol,
+                          double *sigma_iw, double *e_qp, int *qp_status, int *cycles_done,
+                          void *stream);
+
+/*
  * The same solve without the occupied-virtual block resident: the caller
  * supplies the RI tensor one block of occupied orbitals at a time.
  *   fill(user, i0, i1, dst, stream) writes R^P_ia for active occupied

@@ -779,10 +779,16 @@ namespace {
 
 // One solve; with `fill` set, B_ov is not given and the occupied blocks are
 // requested from the caller twice (NAF metric, then projection).
+// One solve; ev_cycles > 0 adds evGW cycles (Sec. 3): Pi, W and Sigma rebuilt
+// from the previous quasi-particle energies (targets) and the scissor shift of
+// the nearest target (other active orbitals), the NAF basis and the projected
+// tensors kept, until the HOMO/LUMO quasi-particle gap changes by less than
+// ev_gap_tol (> 0; both states among the targets) or ev_cycles cycles ran.
 ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, const double *B_ov,
                        ltgw_block_fn fill, void *user, int occ_block, const double *B_tgt, const int *targets,
                        int n_tgt, const double *shift, const double *tau_x, const double *tau_w,
-                       double *sigma_iw, double *e_qp, int *qp_status, void *stream) {
+                       double *sigma_iw, double *e_qp, int *qp_status, void *stream, int ev_cycles = 0,
+                       double ev_gap_tol = 0.0, int *ev_done = nullptr) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
   ctx->reset();
   if (validate(ctx, p) != LTGW_OK) return ctx->status();
@@ -793,6 +799,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
           "the streamed solve needs NAF (naf_thresh >= 0) and occ_block >= 1");
   REQUIRE(ctx, n_tgt >= 1, "n_tgt must be >= 1");
   REQUIRE(ctx, (tau_x == nullptr) == (tau_w == nullptr), "tau_x and tau_w must both be given or both NULL");
+  REQUIRE(ctx, ev_cycles >= 0 && ev_cycles <= 100 && ev_gap_tol >= 0.0, "need 0 <= ev_cycles <= 100, ev_gap_tol >= 0");
   LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const int n_occ = p->n_occ, n_virt = p->n_virt, n_fc = p->n_frozen, n_aux = p->n_aux;
@@ -818,7 +825,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   REQUIRE(ctx, h_eps[n_occ] > h_eps[n_occ - 1], "need eps_LUMO > eps_HOMO");
   for (int t = 0; t < T; ++t)
     REQUIRE(ctx, h_tg[t] >= n_fc && h_tg[t] < n_orb, "target outside the active orbitals");
-  const double eF = 0.5 * (h_eps[n_occ - 1] + h_eps[n_occ]);
+  double eF = 0.5 * (h_eps[n_occ - 1] + h_eps[n_occ]);
   std::vector<double> h_om(n_omega), h_wt(n_omega);
   if (ltgw_gl_grid(n_omega, p->omega0, h_om.data(), h_wt.data()) != LTGW_OK) {
     ctx->fail(LTGW_ERR_BAD_ARG, "GL grid");
@@ -826,41 +833,44 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   }
   std::vector<double> h_x(n_tau), h_w(n_tau), h_E((size_t)n_omega * std::max(n_tau, 1));
   ctx->stats.lt_max_rel_err = NAN;
-  if (n_tau && p->use_laplace == 2) {
-    // imaginary-time form: tau_k (tau_x) and the recombination gamma [n_omega][n_tau] (tau_w)
-    if (tau_x) {
-      if (read_small(ctx, h_x.data(), tau_x, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
-      if (read_small(ctx, h_E.data(), tau_w, h_E.size() * sizeof(double), s) != LTGW_OK) return ctx->status();
-    } else {
-      double err = 0.0;
-      // the tensor-core forms carry ~1e-5 relative error in M^k: a larger ridge
-      // keeps the recombination from magnifying it
-      if (ltgw_cosine_grid(n_tau, h_eps[n_occ] - h_eps[n_occ - 1], h_eps[n_orb - 1] - h_eps[n_fc], n_omega,
-                           h_om.data(), mixed ? 1e-10 : 1e-14, h_x.data(), h_E.data(), &err,
-                           nullptr) != LTGW_OK) {
+  // The library's grid for orbital energies e: Eq. LT's bounds of Sec. 3
+  // (a = gap^2 + w_min^2, b = max(span^2, 1e4)), or the imaginary-time fit on
+  // [gap, span] (the tensor-core forms carry ~1e-5 relative error in M^k: a
+  // larger ridge keeps the recombination from magnifying it).
+  auto fit_grid = [&](const std::vector<double> &e) -> ltgw_status {
+    const double gap = e[n_occ] - e[n_occ - 1];
+    const double span = *std::max_element(e.begin() + n_fc, e.end()) - *std::min_element(e.begin() + n_fc, e.end());
+    double err = 0.0;
+    if (p->use_laplace == 2) {
+      if (ltgw_cosine_grid(n_tau, gap, span, n_omega, h_om.data(), mixed ? 1e-10 : 1e-14, h_x.data(), h_E.data(),
+                           &err, nullptr) != LTGW_OK) {
         ctx->fail(LTGW_ERR_BAD_ARG, "imaginary-time grid fit");
         return ctx->status();
       }
-      ctx->stats.lt_max_rel_err = err;
-    }
-  } else if (n_tau) {
-    if (tau_x) {
-      if (read_small(ctx, h_x.data(), tau_x, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
-      if (read_small(ctx, h_w.data(), tau_w, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
     } else {
-      double gap = h_eps[n_occ] - h_eps[n_occ - 1];
-      double lo = gap * gap + h_om[0] * h_om[0];
-      double span = h_eps[n_orb - 1] - h_eps[n_fc];
-      double hi = std::max(span * span, 1e4);
-      double err = 0.0;
-      if (ltgw_laplace_grid(n_tau, lo, hi, h_x.data(), h_w.data(), &err) != LTGW_OK) {
+      if (ltgw_laplace_grid(n_tau, gap * gap + h_om[0] * h_om[0], std::max(span * span, 1e4), h_x.data(), h_w.data(),
+                            &err) != LTGW_OK) {
         ctx->fail(LTGW_ERR_BAD_ARG, "Laplace grid fit");
         return ctx->status();
       }
-      ctx->stats.lt_max_rel_err = err;
+      for (int j = 0; j < n_omega; ++j)
+        for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * h_x[k]);
     }
-    for (int j = 0; j < n_omega; ++j)
-      for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * h_x[k]);
+    ctx->stats.lt_max_rel_err = err;
+    return LTGW_OK;
+  };
+  if (n_tau && tau_x) {
+    // caller's grid: Eq. LT (x, w), or imaginary time (tau_k, gamma [n_omega][n_tau])
+    if (read_small(ctx, h_x.data(), tau_x, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
+    if (p->use_laplace == 2) {
+      if (read_small(ctx, h_E.data(), tau_w, h_E.size() * sizeof(double), s) != LTGW_OK) return ctx->status();
+    } else {
+      if (read_small(ctx, h_w.data(), tau_w, n_tau * sizeof(double), s) != LTGW_OK) return ctx->status();
+      for (int j = 0; j < n_omega; ++j)
+        for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * h_x[k]);
+    }
+  } else if (n_tau && fit_grid(h_eps) != LTGW_OK) {
+    return ctx->status();
   }
   std::vector<double> h_epsn(T);
   for (int t = 0; t < T; ++t) h_epsn[t] = h_eps[h_tg[t]];
@@ -1034,50 +1044,97 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   }
   ctx->mark(EV_NAF, s);
 
-  // ---- Pi (Eq. Pi or the Laplace form)
-  if (mixed) {
-    if (polarizability_tc(ctx, N, n_ov, nullptr, 0, d_Bf, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E,
-                          d_M, p->spin, d_Pi, s, fp8, p->use_laplace) != LTGW_OK)
+  // evGW: the quasi-particle energies of the previous cycle (targets) and the
+  // scissor shift of the nearest target by orbital index (other active orbitals)
+  auto ev_energies = [&](const std::vector<double> &hq) {
+    std::vector<double> e = h_eps;
+    std::vector<std::pair<int, double>> ts(T);
+    for (int t = 0; t < T; ++t) ts[t] = {h_tg[t], hq[t] - h_eps[h_tg[t]]};
+    std::sort(ts.begin(), ts.end());
+    for (int q = n_fc; q < n_orb; ++q) {
+      int best = 0;
+      for (int t = 1; t < T; ++t)
+        if (abs(ts[t].first - q) < abs(ts[best].first - q)) best = t;   // ties keep the lower target
+      e[q] = h_eps[q] + ts[best].second;
+    }
+    return e;
+  };
+  int ih = -1, il = -1;
+  for (int t = 0; t < T; ++t) {
+    if (h_tg[t] == n_occ - 1) ih = t;
+    if (h_tg[t] == n_occ) il = t;
+  }
+  std::vector<double> hq_prev;
+  int cycles = 0;
+  for (int cyc = 0;; ++cyc) {
+    // ---- Pi (Eq. Pi or the Laplace form)
+    if (mixed) {
+      if (polarizability_tc(ctx, N, n_ov, nullptr, 0, d_Bf, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E,
+                            d_M, p->spin, d_Pi, s, fp8, p->use_laplace) != LTGW_OK)
+        return ctx->status();
+    } else if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
+                                  p->spin, d_Pi, s, p->use_laplace) != LTGW_OK) {
       return ctx->status();
-  } else if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
-                                p->spin, d_Pi, s, p->use_laplace) != LTGW_OK) {
-    return ctx->status();
+    }
+    ctx->mark(EV_PI, s);
+
+    // ---- screening
+    int nl = 0;
+    cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
+    ctx->mark(EV_SCREEN, s);
+
+    // ---- W_nm(i w_j)
+    if (mixed) {
+      if (wnm_tc(ctx, N, n_omega, d_C, T, n_orb_act, d_BtT64, d_BtT32, d_W, s, fp8_w) != LTGW_OK) return ctx->status();
+    } else {
+      ColDotArgs cd;
+      cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;
+      cd.C = d_C; cd.ldc = N; cd.strideC = (int64_t)N * N;
+      cd.Bt = Btt; cd.ldb = ld_btt; cd.strideBt = stride_btt;
+      cd.W = d_W; cd.ldw = n_orb_act;
+      CHECK_LAUNCH(ctx, launch_gemm_coldot(cd, n_omega, s), 1);
+    }
+    ctx->mark(EV_WNM, s);
+
+    // ---- Sigma(i w), Pade, Newton
+    SigmaArgs sa;
+    sa.n_tgt = T; sa.n_omega = n_omega; sa.n_orb = n_orb_act;
+    sa.W = d_W; sa.eps_m = d_eps + n_fc; sa.omega = d_om; sa.weight = d_wt;
+    sa.eps_F = eF; sa.sigma = d_sig;
+    CHECK_LAUNCH(ctx, launch_sigma(sa, s), 1);
+    QpArgs q;
+    q.n_tgt = T; q.n_omega = n_omega; q.pade_stride = 2;
+    q.sigma = d_sig; q.omega = d_om; q.eps_n = d_epsn; q.shift = d_shift;
+    q.eps_F = eF; q.eta = 0.0; q.tol = 1e-12; q.max_iter = 100;
+    q.e_qp = d_eqp; q.status = d_st;
+    CHECK_LAUNCH(ctx, launch_qp(q, s), 1);
+    ctx->mark(EV_SIGQP, s);
+
+    if (cyc == ev_cycles) break;
+    // ---- next evGW cycle
+    std::vector<double> hq(T);
+    if (read_small(ctx, hq.data(), d_eqp, T * sizeof(double), s) != LTGW_OK) return ctx->status();
+    if (cyc > 0 && ev_gap_tol > 0.0 && ih >= 0 && il >= 0 &&
+        fabs((hq[il] - hq[ih]) - (hq_prev[il] - hq_prev[ih])) < ev_gap_tol)
+      break;
+    const std::vector<double> e_next = ev_energies(hq);
+    REQUIRE(ctx, e_next[n_occ] > e_next[n_occ - 1], "evGW: the quasi-particle HOMO/LUMO gap closed");
+    eF = 0.5 * (e_next[n_occ - 1] + e_next[n_occ]);
+    copy_in(ctx, d_eps, e_next.data(), n_orb * sizeof(double), s);
+    CHECK_LAUNCH(ctx, launch_pair_gaps(d_eps, n_occ, n_virt, n_fc, d_delta, s), 1);
+    if (n_tau && !tau_x) {
+      if (fit_grid(e_next) != LTGW_OK) return ctx->status();
+      copy_in(ctx, d_x, h_x.data(), n_tau * sizeof(double), s);
+      copy_in(ctx, d_w, h_w.data(), n_tau * sizeof(double), s);
+      copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+    }
+    if (ctx->status() != LTGW_OK) return ctx->status();
+    hq_prev = hq;
+    ++cycles;
   }
-  ctx->mark(EV_PI, s);
-
-  // ---- screening
-  int nl = 0;
-  cudaError_t e = launch_screen_blocked(d_Pi, N, n_omega, d_X0, d_C, ctx->flags, s, &nl);
-  ctx->launches += nl;
-  if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("screen: ") + cudaGetErrorString(e)); return ctx->status(); }
-  ctx->mark(EV_SCREEN, s);
-
-  // ---- W_nm(i w_j)
-  if (mixed) {
-    if (wnm_tc(ctx, N, n_omega, d_C, T, n_orb_act, d_BtT64, d_BtT32, d_W, s, fp8_w) != LTGW_OK) return ctx->status();
-  } else {
-    ColDotArgs cd;
-    cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;
-    cd.C = d_C; cd.ldc = N; cd.strideC = (int64_t)N * N;
-    cd.Bt = Btt; cd.ldb = ld_btt; cd.strideBt = stride_btt;
-    cd.W = d_W; cd.ldw = n_orb_act;
-    CHECK_LAUNCH(ctx, launch_gemm_coldot(cd, n_omega, s), 1);
-  }
-  ctx->mark(EV_WNM, s);
-
-  // ---- Sigma(i w), Pade, Newton
-  SigmaArgs sa;
-  sa.n_tgt = T; sa.n_omega = n_omega; sa.n_orb = n_orb_act;
-  sa.W = d_W; sa.eps_m = d_eps + n_fc; sa.omega = d_om; sa.weight = d_wt;
-  sa.eps_F = eF; sa.sigma = d_sig;
-  CHECK_LAUNCH(ctx, launch_sigma(sa, s), 1);
-  QpArgs q;
-  q.n_tgt = T; q.n_omega = n_omega; q.pade_stride = 2;
-  q.sigma = d_sig; q.omega = d_om; q.eps_n = d_epsn; q.shift = d_shift;
-  q.eps_F = eF; q.eta = 0.0; q.tol = 1e-12; q.max_iter = 100;
-  q.e_qp = d_eqp; q.status = d_st;
-  CHECK_LAUNCH(ctx, launch_qp(q, s), 1);
-  ctx->mark(EV_SIGQP, s);
+  if (ev_done) *ev_done = cycles;
 
   // ---- outputs
   LTGW_CUDA(ctx, cudaMemcpyAsync(sigma_iw, d_sig, (size_t)T * n_omega * 2 * sizeof(double), cudaMemcpyDefault, s));
@@ -1211,6 +1268,14 @@ ltgw_status ltgw_solve(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
                        int *qp_status, void *stream) {
   return solve_impl(ctx, p, eps, B_ov, nullptr, nullptr, 0, B_tgt, targets, n_tgt, shift, tau_x, tau_w, sigma_iw,
                     e_qp, qp_status, stream);
+}
+
+ltgw_status ltgw_solve_ev(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, const double *B_ov,
+                          const double *B_tgt, const int *targets, int n_tgt, const double *shift,
+                          const double *tau_x, const double *tau_w, int n_cycles, double gap_tol,
+                          double *sigma_iw, double *e_qp, int *qp_status, int *cycles_done, void *stream) {
+  return solve_impl(ctx, p, eps, B_ov, nullptr, nullptr, 0, B_tgt, targets, n_tgt, shift, tau_x, tau_w, sigma_iw,
+                    e_qp, qp_status, stream, n_cycles, gap_tol, cycles_done);
 }
 
 ltgw_status ltgw_solve_streamed(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, ltgw_block_fn fill,

@@ -76,6 +76,8 @@ SIGNATURES = {
     "ltgw_set_autotune": (_I, [_P, _I]),
     "ltgw_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "ltgw_solve": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "ltgw_solve_ev": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _I, _D, _P, _P, _P,
+                           _P, _P]),
     "ltgw_solve_streamed": (_I, [_P, ctypes.POINTER(Params), _P, BLOCK_FN, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P,
                                  _P, _P]),
     "ltgw_gl_grid": (_I, [_I, _D, _P, _P]),
@@ -230,6 +232,18 @@ class Context:
                                   _ptr(targets), n_tgt, _ptr(shift), _ptr(tau_x), _ptr(tau_w),
                                   _ptr(sigma_out), _ptr(e_qp_out), _ptr(status_out), _stream_ptr(stream))
         return self._check(st, allow=(LTGW_ERR_NO_CONVERGE,) if allow_no_converge else ())
+
+    def solve_ev(self, params: Params, eps, B_ov, B_tgt, targets, shift, sigma_out, e_qp_out, status_out,
+                 n_cycles: int = 5, gap_tol: float = 0.0, tau_x=None, tau_w=None, stream=None,
+                 allow_no_converge=True) -> int:
+        """ltgw_solve_ev (evGW); returns the number of cycles run after G0W0."""
+        done = ctypes.c_int()
+        st = self._lib.ltgw_solve_ev(self.handle, ctypes.byref(params), _ptr(eps), _ptr(B_ov), _ptr(B_tgt),
+                                     _ptr(targets), int(targets.shape[0]), _ptr(shift), _ptr(tau_x), _ptr(tau_w),
+                                     n_cycles, gap_tol, _ptr(sigma_out), _ptr(e_qp_out), _ptr(status_out),
+                                     ctypes.byref(done), _stream_ptr(stream))
+        self._check(st, allow=(LTGW_ERR_NO_CONVERGE,) if allow_no_converge else ())
+        return done.value
 
     def solve_streamed(self, params: Params, eps, fill, occ_block: int, B_tgt, targets, shift, sigma_out,
                        e_qp_out, status_out, tau_x=None, tau_w=None, stream=None, allow_no_converge=True) -> int:
