@@ -325,6 +325,21 @@ def run_gpu(args):
         line["qp_max_mev_vs_fp64_form"] = float(np.abs(e_main - e64).max() * HA2MEV)
         line["qp_mev_vs_fp64_form_per_state"] = (np.abs(e_main - e64) * HA2MEV).tolist()
         line["pi_rel_frob_vs_fp64_form"] = pi_error_vs_fp64(ctx, prob, N, cfg["n_omega"], args.precision, stream)
+        # evGW, five cycles after G0W0 (the NAF basis and projections formed once), both forms
+        ev = {}
+        for name, pp in (("mixed", p), ("fp64", p64)):
+            T_ = len(prob.targets)
+            sg, ee, ss = (np.zeros((T_, cfg["n_omega"], 2)), np.zeros(T_), np.zeros(T_, dtype=np.int32))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.solve_ev(pp, dev["eps"], dev["B_ov"], dev["B_tgt"], dev["targets"], dev["shift"], sg, ee, ss,
+                         n_cycles=5, stream=stream)
+            ev[name] = {"ms": 1e3 * (time.perf_counter() - t0), "e": ee.copy()}
+        line["evgw_5_cycles"] = {"ms_mixed": ev["mixed"]["ms"], "ms_fp64_form": ev["fp64"]["ms"],
+                                 "speedup": ev["fp64"]["ms"] / ev["mixed"]["ms"],
+                                 "qp_max_mev_vs_fp64_form": float(np.abs(ev["mixed"]["e"] - ev["fp64"]["e"]).max()
+                                                                  * HA2MEV),
+                                 "note": "host wall time of one ltgw_solve_ev call (device inputs)"}
     # end-to-end: host (pinned) inputs and outputs through the same C ABI call
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
            {"eps": prob.eps, "B_ov": prob.B_ov, "B_tgt": prob.B_tgt,
