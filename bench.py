@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="mid", choices=["tiny", "mid", "large", "serving"])
+    ap.add_argument("--workload", default="mid", choices=["tiny", "mid", "large", "serving", "sweep"])
+    ap.add_argument("--sweep-size", default="mid", choices=["mid", "large"],
+                    help="sweep: the workload whose GL x Laplace grids are swept")
     ap.add_argument("--occ-block", type=int, default=20, help="large: occupied orbitals per streamed block")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=None,
@@ -527,6 +529,78 @@ def run_large(args):
     ctx.close()
 
 
+def run_sweep(args):
+    """GL x Laplace grid sweep (the paper's grid comparison of Sec. 4.1, here on
+    the synthetic workloads): for N_omega in {32, 64, 128} and N_tau in
+    {8, 10, 12, 14, 18} (Eq. LT's form, library grid) the solve time and the
+    largest QP deviation from the reference, direct AC (no Laplace transform)
+    with 128 GL points, all in the split-BF16 form.  Times exclude the input
+    generation of the streamed large workload."""
+    import torch
+    from paper_2307_04508_gb300 import ltgw
+    from paper_2307_04508_gb300 import synthetic as S
+
+    torch.cuda.set_device(0)
+    ctx = ltgw.Context(0)
+    ctx.set_timing(True)
+    stream = torch.cuda.Stream()
+    large = args.sweep_size == "large"
+    if large:
+        from paper_2307_04508_gb300.synthetic.device import DeviceLaw
+        cfg = S.LARGE
+        law = DeviceLaw(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["seed"], cfg["n_targets"],
+                        gemm="fp32")
+        dims = (cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"])
+        B_tgt = law.b_tgt()
+        eps = torch.from_numpy(law.eps).cuda()
+        targets = torch.from_numpy(law.targets.astype(np.int32)).cuda()
+        shift = torch.from_numpy(law.shift).cuda()
+        grids = [(32, 0), (32, 8), (32, 12), (32, 18), (128, 8), (128, 12), (128, 18)]
+        reps = 1
+    else:
+        cfg = dict(S.MID)
+        prob = S.make_workload(cfg)
+        dims = (prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen)
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+               (prob.eps, prob.B_ov, prob.B_tgt, prob.targets.astype(np.int32), prob.shift)]
+        grids = [(n_om, n_tau) for n_om in (32, 64, 128) for n_tau in (0, 8, 10, 12, 14, 18)]
+        reps = 3
+    T = cfg["n_targets"] if large else len(prob.targets)
+
+    def run(n_om, n_tau):
+        p = ltgw.make_params(*dims, n_om, n_tau, 0.5, cfg["naf_thresh"], 2, n_tau > 0, ltgw.LTGW_BF16X3)
+        out = (torch.empty((T, n_om, 2), dtype=torch.float64, device="cuda"),
+               torch.empty(T, dtype=torch.float64, device="cuda"), torch.empty(T, dtype=torch.int32, device="cuda"))
+        ms = []
+        for r in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if large:
+                ctx.solve_streamed(p, eps, lambda i0, i1, dst, strm: law.fill_block(i0, i1, dst), args.occ_block,
+                                   B_tgt, targets, shift, *out, stream=stream)
+            else:
+                ctx.solve(p, *dev, *out, stream=stream)
+            torch.cuda.synchronize()
+            if r:   # the first run warms up
+                ms.append(1e3 * (time.perf_counter() - t0) - ctx.stats()["ms_generate"])
+        return float(np.median(ms)), out[1].cpu().numpy().copy(), out[2].cpu().numpy().copy()
+
+    t_ref, e_ref, st_ref = run(128, 0)
+    rows = []
+    with ClockSampler(0) as clk:
+        for n_om, n_tau in grids:
+            t, e, st = run(n_om, n_tau)
+            rows.append({"n_omega": n_om, "n_tau": n_tau, "ms": t, "speedup_vs_reference": t_ref / t,
+                         "qp_max_mev_vs_reference": float(np.abs(e - e_ref).max() * HA2MEV),
+                         "converged": bool(np.all(st == 0))})
+    line = {"metric": "GL x Laplace grid sweep (speed-up and QP deviation vs direct AC, 128 GL)",
+            "unit": "ms per solve", "workload": args.sweep_size, "precision": "bf16x3",
+            "reference": {"n_omega": 128, "n_tau": 0, "ms": t_ref, "converged": bool(np.all(st_ref == 0))},
+            "rows": rows, "clocks": clk.summary(), "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -535,6 +609,8 @@ def main():
         run_serving(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_gpu(args)
 

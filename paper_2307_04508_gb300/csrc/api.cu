@@ -262,7 +262,8 @@ ltgw_status polarizability_dev(ltgw_ctx *ctx, int N, int64_t n_pairs, const doub
     g.batch_p1 = lt_form == 2 ? nullptr : d_w;
     CHECK_LAUNCH(ctx, launch_gemm_f64(g, n_tau, true, true, s), 1);
     ctx->mark(EV_PI1, s);
-    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
+    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
+                 (n_omega + 63) / 64);
   }
   return LTGW_OK;
 }
@@ -517,7 +518,8 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   } else {
     CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
                                            nI, n_t, N, 1.0, M, s, 0.0, run.nt_group, 1), 1);
-    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s), 1);
+    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
+                 (n_omega + 63) / 64);
   }
   return LTGW_OK;
 }

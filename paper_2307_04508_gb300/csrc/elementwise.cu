@@ -67,18 +67,27 @@ cudaError_t launch_pair_gaps(const double *eps, int n_occ, int n_virt, int n_fro
   return cudaGetLastError();
 }
 
+// Frequencies go in launches of up to 64 (the kernel keeps E of one launch in
+// shared memory); each launch re-reads the moments.
 cudaError_t launch_recombine(const double *M, int n_tau, const double *E, int n_omega,
                              int64_t n_elem, double alpha, double *Pi, cudaStream_t s) {
-  if (n_tau > 32 || n_omega > 64) return cudaErrorInvalidValue;
+  if (n_tau > 32 || n_tau < 1 || n_omega < 1) return cudaErrorInvalidValue;
   int blocks = (int)((n_elem + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  if (n_tau <= 8)
-    recombine_kernel<8><<<blocks, 256, 0, s>>>(M, n_tau, E, n_omega, n_elem, alpha, Pi);
-  else if (n_tau <= 16)
-    recombine_kernel<16><<<blocks, 256, 0, s>>>(M, n_tau, E, n_omega, n_elem, alpha, Pi);
-  else
-    recombine_kernel<32><<<blocks, 256, 0, s>>>(M, n_tau, E, n_omega, n_elem, alpha, Pi);
-  return cudaGetLastError();
+  for (int j0 = 0; j0 < n_omega; j0 += 64) {
+    const int nj = n_omega - j0 < 64 ? n_omega - j0 : 64;
+    const double *Ej = E + (int64_t)j0 * n_tau;
+    double *Pj = Pi + (int64_t)j0 * n_elem;
+    if (n_tau <= 8)
+      recombine_kernel<8><<<blocks, 256, 0, s>>>(M, n_tau, Ej, nj, n_elem, alpha, Pj);
+    else if (n_tau <= 16)
+      recombine_kernel<16><<<blocks, 256, 0, s>>>(M, n_tau, Ej, nj, n_elem, alpha, Pj);
+    else
+      recombine_kernel<32><<<blocks, 256, 0, s>>>(M, n_tau, Ej, nj, n_elem, alpha, Pj);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_copy_cols(const double *src, int64_t lds, int64_t c0, double *dst,

@@ -53,7 +53,7 @@ cudaError_t launch_gemm_coldot(const ColDotArgs &g, int n_batch, cudaStream_t s)
 // delta[i*n_virt + a] = eps[n_occ + a] - eps[n_frozen + i], i < n_occ - n_frozen
 cudaError_t launch_pair_gaps(const double *eps, int n_occ, int n_virt, int n_frozen,
                              double *delta, cudaStream_t s);
-// Pi_j = alpha * sum_k E[j][k] M_k over n elements per matrix
+// Pi_j = alpha * sum_k E[j][k] M_k over n elements per matrix (n_tau <= 32, any n_omega)
 cudaError_t launch_recombine(const double *M, int n_tau, const double *E, int n_omega,
                              int64_t n_elem, double alpha, double *Pi, cudaStream_t s);
 // dst[r][c] = src[r][c0 + c] for a strided 2-D copy of rows (batched)

@@ -95,3 +95,17 @@ def test_grid_forms_against_direct_oracle(ctx):
               f"imaginary-time form {errs[3]:.4f}")
     assert rows[-1][2] < 0.01          # the imaginary-time form converges with the node count
     assert rows[-1][2] < rows[0][2]
+
+
+def test_laplace_form_beyond_64_frequencies(ctx):
+    """Eq. LT's recombination over 100 GL frequencies (launched in chunks of 64)."""
+    rng = np.random.default_rng(5)
+    N, P = 40, 2000
+    Bt = rng.standard_normal((N, P)) * 0.05
+    delta = rng.uniform(0.3, 4.0, P)
+    om, _ = O.gl_grid(100, 0.5)
+    x, w = O.sinc_laplace_grid(9, -8.0, 2.0)
+    Pi = torch.empty((len(om), N, N), dtype=torch.float64, device="cuda")
+    ctx.polarizability(_dev(Bt), _dev(delta), om, Pi, spin=2, x=x, w=w)
+    ref = O.polarizability_lt(O.laplace_moments(Bt, delta, x, w), om, x, 2)
+    assert _rel(Pi.cpu().numpy(), ref) <= 1e-11
