@@ -390,7 +390,10 @@ def run_serving(args):
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     reqs = S.serving_stream(args.requests, rate_hz=args.rate or 1.0)   # sizes do not depend on the rate
-    budget = int(0.6 * torch.cuda.get_device_properties(0).total_memory)
+    # the server's admission budget and the ingest thread's budget for generated
+    # inputs share the device: 55 % + 15 % of it, leaving room for the contexts
+    total = torch.cuda.get_device_properties(0).total_memory
+    budget, ingest_budget = int(0.55 * total), int(0.15 * total)
     # same prefix of the stream, back to back, in both forms: the throughput ratio
     pre = reqs[:min(args.compare_prefix, len(reqs))]
     inputs = [serving.ingest(r, device=True) for r in pre]
@@ -411,7 +414,7 @@ def run_serving(args):
     srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
     try:
         burst = S.serving_stream(len(reqs), rate_hz=1e9)
-        recs_c, wall_c, _ = serving.run_stream_pipelined(srv, burst, ltgw.LTGW_BF16X3)
+        recs_c, wall_c, _ = serving.run_stream_pipelined(srv, burst, ltgw.LTGW_BF16X3, mem_budget_bytes=ingest_budget)
     finally:
         srv.close()
     capacity = len(recs_c) / wall_c
@@ -421,10 +424,14 @@ def run_serving(args):
     srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
     try:
         with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-            recs, wall, ingest_s = serving.run_stream_pipelined(srv, reqs, ltgw.LTGW_BF16X3)
+            recs, wall, ingest_s = serving.run_stream_pipelined(srv, reqs, ltgw.LTGW_BF16X3,
+                                                                mem_budget_bytes=ingest_budget)
     finally:
         srv.close()
     sm = serving.summarize(recs, wall, ingest_s)
+    failures = [{"index": k, "status": v.get("status"), "message": v.get("message", ""),
+                 "n_occ": reqs[k]["n_occ"], "n_virt": reqs[k]["n_virt"], "n_aux": reqs[k]["n_aux"]}
+                for k, v in recs.items() if v.get("status") not in (ltgw.LTGW_OK, ltgw.LTGW_ERR_NO_CONVERGE)]
     line = {"metric": "G0W0 solves/s (serving stream)", "value": sm["solves_per_s"], "unit": "solves/s",
             "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / len(reqs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
@@ -439,7 +446,8 @@ def run_serving(args):
             "latency_ms": {"p50": sm["p50_ms"], "p99": sm["p99_ms"],
                            "p50_from_arrival": sm.get("p50_from_arrival_ms"),
                            "p99_from_arrival": sm.get("p99_from_arrival_ms")},
-            "completed": sm["completed"], "ingest_s": ingest_s, "capacity_solves_per_s": capacity,
+            "completed": sm["completed"], "failures": failures, "ingest_s": ingest_s,
+            "capacity_solves_per_s": capacity,
             "prefix_comparison": {"requests": len(pre), "bf16x3_solves_per_s": cmp["bf16x3"]["solves_per_s"],
                                   "fp64_solves_per_s": cmp["fp64"]["solves_per_s"],
                                   "speedup": cmp["bf16x3"]["solves_per_s"] / cmp["fp64"]["solves_per_s"],

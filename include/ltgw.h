@@ -124,6 +124,12 @@ ltgw_status ltgw_set_timing(ltgw_ctx *ctx, int on);
  * tolerance).  Off, every call takes the fixed heuristic and is
  * reproducible bit for bit. */
 ltgw_status ltgw_set_autotune(ltgw_ctx *ctx, int on);
+/* Device workspace a context holds between calls (it grows to the largest
+ * call's need and is kept for the next call). */
+size_t ltgw_workspace_bytes(const ltgw_ctx *ctx);
+/* Free that workspace (no call of this context may be in flight); the next
+ * call allocates again. */
+ltgw_status ltgw_trim(ltgw_ctx *ctx);
 ltgw_status ltgw_get_stats(const ltgw_ctx *ctx, ltgw_stats *out);
 
 /*

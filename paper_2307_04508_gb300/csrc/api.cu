@@ -763,6 +763,22 @@ ltgw_status ltgw_set_timing(ltgw_ctx *ctx, int on) {
   return LTGW_OK;
 }
 
+size_t ltgw_workspace_bytes(const ltgw_ctx *ctx) {
+  if (!ctx) return 0;
+  return ctx->a1.cap + ctx->a2.cap + ctx->a3.cap + ctx->a4.cap + ctx->a5.cap;
+}
+
+ltgw_status ltgw_trim(ltgw_ctx *ctx) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  ctx->a1.release();
+  ctx->a2.release();
+  ctx->a3.release();
+  ctx->a4.release();
+  ctx->a5.release();
+  return LTGW_OK;
+}
+
 ltgw_status ltgw_set_autotune(ltgw_ctx *ctx, int on) {
   if (!ctx) return LTGW_ERR_BAD_ARG;
   ctx->autotune = (on != 0);

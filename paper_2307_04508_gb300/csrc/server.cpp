@@ -36,6 +36,7 @@ struct Slot {
   std::thread th;
   bool has_job = false;
   Pending job;
+  size_t retained = 0;   // workspace its context keeps between requests
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -47,6 +48,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 struct ltgw_server {
   int device = 0;
   size_t budget = 0, in_flight = 0;
+  size_t retained = 0;   // workspace kept by the slots between requests
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Pending> queue;
@@ -64,7 +66,7 @@ struct ltgw_server {
   void dispatch_locked() {
     while (!queue.empty()) {
       Pending &head = queue.front();
-      if (in_flight + head.footprint > budget && running > 0) return;
+      if (in_flight + retained + head.footprint > budget && running > 0) return;
       Slot *free_slot = nullptr;
       for (auto &s : slots)
         if (!s->has_job && !busy_slot(s.get())) { free_slot = s.get(); break; }
@@ -111,9 +113,18 @@ struct ltgw_server {
                         r.sigma_iw, r.e_qp, r.qp_status, stream);
       }
       const Clock::time_point t_end = Clock::now();
+      // a slot keeps at most its share of a quarter of the budget between requests;
+      // what it keeps counts against admission (see dispatch_locked)
+      size_t keep = 0;
+      if (ctx) {
+        if (ltgw_workspace_bytes(ctx) > budget / (4 * slots.size())) ltgw_trim(ctx);
+        keep = ltgw_workspace_bytes(ctx);
+      }
       lock.lock();
       busy.erase(std::find(busy.begin(), busy.end(), slot));
       in_flight -= job.footprint;
+      retained += keep - slot->retained;
+      slot->retained = keep;
       --running;
       ltgw_completion c{};
       c.ticket = job.ticket;
@@ -153,8 +164,13 @@ size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt) {
   d += n_tau * N * N + 2 * n_om * N * N;                       // Laplace moments, Pi, C
   d += n_om * (N * N + 128 * N + 4096);                        // screening sweep scratch
   d += T * N * n_orb + n_om * T * n_orb;                       // projected targets, W
-  if (p->precision == LTGW_BF16X3) d += (2 * n_aux * n_ov + N * n_ov) / 2 + n_om * N * N / 2;  // FP32 copies
-  else d += N * n_ov;                                          // projected ov block
+  if (p->precision != LTGW_FP64) {
+    d += (2 * n_aux * n_ov + N * n_ov) / 2 + n_om * N * N / 2;  // FP32 copies, BF16 hi / lo of the ov block
+    if (p->precision == LTGW_FP8 || p->precision == LTGW_FP8_PI)
+      d += ((n_tau ? n_tau : n_om) + 1) * N * n_ov / 8;         // FP8 codes of the scaled operands and R~
+  } else {
+    d += N * n_ov;                                              // projected ov block
+  }
   return d * sizeof(double) + (64u << 20);                     // + fixed slack
 }
 

@@ -74,6 +74,8 @@ SIGNATURES = {
     "ltgw_last_error": (ctypes.c_char_p, [_P]),
     "ltgw_set_timing": (_I, [_P, _I]),
     "ltgw_set_autotune": (_I, [_P, _I]),
+    "ltgw_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "ltgw_trim": (_I, [_P]),
     "ltgw_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "ltgw_solve": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "ltgw_solve_ev": (_I, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, _I, _P, _P, _P, _I, _D, _P, _P, _P,
@@ -218,6 +220,12 @@ class Context:
 
     def set_autotune(self, on: bool):
         self._check(self._lib.ltgw_set_autotune(self.handle, int(bool(on))))
+
+    def workspace_bytes(self) -> int:
+        return int(self._lib.ltgw_workspace_bytes(self.handle))
+
+    def trim(self):
+        self._check(self._lib.ltgw_trim(self.handle))
 
     def stats(self) -> dict:
         s = Stats()

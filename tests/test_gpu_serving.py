@@ -86,3 +86,27 @@ def test_device_generator_matches_host_law():
     law = DeviceLaw(6, 50, 120, 1, 31, 2, gemm="fp64")
     assert np.abs(law.b_ov().cpu().numpy() - p.B_ov).max() < 1e-12 * np.abs(p.B_ov).max() + 1e-15
     assert np.abs(law.b_tgt().cpu().numpy() - p.B_tgt).max() < 1e-12 * np.abs(p.B_tgt).max() + 1e-15
+
+
+def test_trim_releases_the_workspace():
+    """A context's workspace grows to its largest call and is kept; ltgw_trim
+    frees it and the next call allocates again with the same result."""
+    from paper_2307_04508_gb300 import ltgw
+    c = ltgw.Context(0)
+    try:
+        prob = S.make_problem(9, 70, 150, n_frozen=1, seed=99, n_targets=3)
+        p = ltgw.make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, 17, 0, 0.5, 5e-3, 2, False,
+                             ltgw.LTGW_BF16X3)
+        T = len(prob.targets)
+        outs = []
+        for trim in (False, True):
+            sig, e, st = np.zeros((T, 17, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
+            c.solve(p, prob.eps, prob.B_ov, prob.B_tgt, prob.targets.astype(np.int32), prob.shift, sig, e, st)
+            outs.append(e.copy())
+            assert c.workspace_bytes() > 0
+            if not trim:
+                c.trim()
+                assert c.workspace_bytes() == 0
+        assert np.array_equal(outs[0], outs[1])
+    finally:
+        c.close()
