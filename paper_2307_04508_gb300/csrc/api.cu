@@ -501,7 +501,7 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
     CHECK_LAUNCH(ctx, launch_fp8_quantize(A, Kp, Kq, scale, n_t, Mp, qa, qb, ds_a, ds_b, s), 1);
     // FP32 sums of exact E4M3 products: a 4096-pair drain keeps the accumulation
     // bias (about 4e-6) far below the E4M3 rounding error
-    g.A8 = qa; g.B8 = qb; g.ds_a = ds_a; g.ds_b = ds_b; g.Kp = Kq; g.nt_group = 4; g.drain_k = 4096;
+    g.A8 = qa; g.B8 = qb; g.ds_a = ds_a; g.ds_b = ds_b; g.Kp = Kq; g.nt_group = 2; g.drain_k = 4096;
   } else {
     CHECK_LAUNCH(ctx, launch_split_bf16(A, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
     g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.nt_group = 2; g.B_hi = Bhi; g.B_lo = Blo;

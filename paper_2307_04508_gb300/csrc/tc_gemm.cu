@@ -742,24 +742,32 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 // D_t = qa_t qb^T on tcgen05 kind::f8f6f4 (E4M3 x E4M3, FP32 accumulation),
 // K = 32 per MMA; the per-row de-scales of both operands are applied in the
 // epilogue.  A chunk is 128 pairs (one 128-byte swizzled row per tile row); a
-// stage holds the A tiles of up to four scales and the B tile.  Warp roles
+// stage holds the A tiles of the CTA's nt_group scales and the B tile, and as
+// many stages as fit (2 with four scales, 4 with two, up to 4) keep the
+// loads of later chunks in flight behind the MMAs.  Warp roles
 // (9 warps): 0 TMEM allocation and MMA issue for scale 0, 1 TMA producer,
 // 2-5 epilogue, 6-8 MMA issue for scales 1-3 (one issuing thread per
 // accumulator, each stage's four MMAs back to back).
 constexpr int F8_K = 128;
-constexpr int F8_STAGES = 2;
+constexpr int F8_MAXSTAGES = 4;
 constexpr int F8_MAXT = 4;
 constexpr uint32_t F8_TILE = TM * F8_K;                      // 16 KB
-constexpr uint32_t F8_STAGE = (F8_MAXT + 1) * F8_TILE;       // A tiles of four scales + B
+constexpr uint32_t F8_RING = 12 * F8_TILE;                   // 192 KB of stages
 constexpr int F8_ISSUE1 = 2 + EPI_WARPS;                     // issuer warp of scale 1
 constexpr int F8_THREADS = 32 * (F8_ISSUE1 + F8_MAXT - 1);
-constexpr uint32_t F8_SMEM = F8_STAGES * F8_STAGE + 1024;
+constexpr uint32_t F8_SMEM = F8_RING + 1024;
+// stages of (nt + 1) tiles that fit the ring
+__host__ __device__ constexpr int f8_stages(int nt) {
+  return (int)(F8_RING / ((uint32_t)(nt + 1) * F8_TILE)) < F8_MAXSTAGES ? (int)(F8_RING / ((uint32_t)(nt + 1) * F8_TILE))
+                                                                       : F8_MAXSTAGES;
+}
+static_assert(f8_stages(F8_MAXT) >= 2, "two stages of four scales must fit");
 // kind::f8f6f4: D = FP32 (bit 4), A = B = E4M3 (format code 0), both K-major, N = 128, M = 128
 constexpr uint32_t IDESC8 = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-static_assert(F8_TILE % 1024 == 0 && F8_STAGE % 1024 == 0, "swizzled tiles must stay 1024-byte aligned");
+static_assert(F8_TILE % 1024 == 0, "swizzled tiles must stay 1024-byte aligned");
 
 struct Bars8 {
-  uint64_t full[F8_STAGES], empty[F8_STAGES], acc_full[1], acc_empty[1], fin;
+  uint64_t full[F8_MAXSTAGES], empty[F8_MAXSTAGES], acc_full[1], acc_empty[1], fin;
   uint32_t tmem_base;
   int abort;
 };
@@ -798,10 +806,12 @@ __global__ void __launch_bounds__(F8_THREADS, 1)
   const int nchunks = (int)((ke - kb) / F8_K);
   const int chunks_per_drain = (int)(g.drain_k / F8_K);
   const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
+  const int nst = f8_stages(g.nt_group);                              // stages in the ring
+  const uint32_t stage_bytes = (uint32_t)(g.nt_group + 1) * F8_TILE;  // A tiles, then B
 
   if (threadIdx.x == 0) {
     // empty, acc_full and fin collect one commit from each of the nt issuers
-    for (int s = 0; s < F8_STAGES; ++s) { mbar_init(&bars.full[s], 1); mbar_init(&bars.empty[s], nt); }
+    for (int s = 0; s < F8_MAXSTAGES; ++s) { mbar_init(&bars.full[s], 1); mbar_init(&bars.empty[s], nt); }
     mbar_init(&bars.acc_full[0], nt);
     mbar_init(&bars.acc_empty[0], 32 * EPI_WARPS);
     mbar_init(&bars.fin, nt);
@@ -835,11 +845,11 @@ __global__ void __launch_bounds__(F8_THREADS, 1)
           ok = mbar_wait(&bars.full[js], ps, &bars.abort, g.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t st = (uint32_t)js * F8_STAGE;
-          mma_stage_f8(d, db0 + ((st + (uint32_t)issue_t * F8_TILE) >> 4), db0 + ((st + F8_MAXT * F8_TILE) >> 4),
-                       c == dr * chunks_per_drain ? 0u : 1u);
+          const uint32_t st = (uint32_t)js * stage_bytes;
+          mma_stage_f8(d, db0 + ((st + (uint32_t)issue_t * F8_TILE) >> 4),
+                       db0 + ((st + (uint32_t)g.nt_group * F8_TILE) >> 4), c == dr * chunks_per_drain ? 0u : 1u);
           mma_commit(&bars.empty[js]);
-          if (++js == F8_STAGES) { js = 0; ps ^= 1; }
+          if (++js == nst) { js = 0; ps ^= 1; }
         }
         if (ok) mma_commit(&bars.acc_full[0]);
       }
@@ -856,12 +866,12 @@ __global__ void __launch_bounds__(F8_THREADS, 1)
       for (int c = 0; c < nchunks; ++c) {
         const int k0 = (int)(kb + (int64_t)c * F8_K);   // multiple of 128 bytes
         if (!mbar_wait(&bars.empty[js], ps ^ 1, &bars.abort, g.err)) break;
-        uint8_t *st = sS + js * F8_STAGE;
+        uint8_t *st = sS + js * stage_bytes;
         mbar_expect_tx(&bars.full[js], (uint32_t)(nt + 1) * F8_TILE);
         for (int t = 0; t < nt; ++t)
           tma_load_2d(st + t * F8_TILE, &tmA, k0, (int)((t0 + t) * g.rows_a + ti * TM), &bars.full[js]);
-        tma_load_2d(st + F8_MAXT * F8_TILE, &tmB, k0, tj * TN, &bars.full[js]);
-        if (++js == F8_STAGES) { js = 0; ps ^= 1; }
+        tma_load_2d(st + g.nt_group * F8_TILE, &tmB, k0, tj * TN, &bars.full[js]);
+        if (++js == nst) { js = 0; ps ^= 1; }
       }
     }
     __syncwarp();
