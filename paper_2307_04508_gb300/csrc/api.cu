@@ -372,8 +372,9 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
       tune = true;
       cands.clear();
       std::vector<int> ntgs{g.nt_group};
-      if (kind == 1) ntgs = {2, 1};
-      if (kind == 2) ntgs = {4, 2, 1};
+      // scales per CTA vary only where the caller reduces with reduce_sym (column-major partials)
+      if (g.out_colmajor && g.n_t > 1 && kind == 1) ntgs = {2, 1};
+      if (g.out_colmajor && g.n_t > 1 && kind == 2) ntgs = {4, 2, 1};
       const int64_t min_split = std::min<int64_t>(64, (g.Kp + g.drain_k - 1) / g.drain_k);
       for (int ntg : ntgs) {
         const TcPlan base = tc_plan(ctx, g, n_tiles, ntg, 0);
@@ -532,10 +533,13 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
   std::vector<int> tindex;
   std::vector<int> tiles = lower_tiles(nI, &tindex);
   float *Af, *ones;
+  __nv_bfloat16 *Bhi, *Blo;   // the operand pre-split for the TMA-fed kernel
   int *d_tindex;
   auto layout = [&](Arena &A) {
     Af = A.take<float>((size_t)Mp * Kp);
     ones = A.take<float>((size_t)Kp);
+    Bhi = A.take<__nv_bfloat16>((size_t)Mp * Kp);
+    Blo = A.take<__nv_bfloat16>((size_t)Mp * Kp);
     d_tindex = A.take<int>(tindex.size());
   };
   ctx->a5.begin_sizing();
@@ -545,12 +549,14 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
   copy_in(ctx, d_tindex, tindex.data(), tindex.size() * sizeof(int), s);
   CHECK_LAUNCH(ctx, launch_to_f32_padded(B, ld, n, n_pairs, Af, Mp, Kp, s), 1);
   CHECK_LAUNCH(ctx, launch_scale_table(nullptr, n_pairs, Kp, 1, nullptr, nullptr, SCALE_NONE, ones, s), 1);
+  CHECK_LAUNCH(ctx, launch_split_bf16(Af, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
   TcGemmArgs g;
   g.A = Af; g.B = Af; g.scale = ones; g.Kp = Kp; g.n_t = 1; g.nt_group = 1;
+  g.B_hi = Bhi; g.B_lo = Blo; g.rows_a = Mp; g.rows_b = Mp; g.out_colmajor = 1;
   TcRun run;
   if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
   CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                         nI, 1, n, 1.0, K, s, beta, run.nt_group, 0), 1);
+                                         nI, 1, n, 1.0, K, s, beta, run.nt_group, 1), 1);
   return LTGW_OK;
 }
 
@@ -586,11 +592,18 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   const int nI_ov = (int)((n_ov + 127) / 128);
   const int MpT = (n_orb_act + 127) / 128 * 128;
   float *UtF, *BactT, *BtgT, *ones;
+  __nv_bfloat16 *Bh, *Bl, *Uh = nullptr, *Ul = nullptr;   // B operands pre-split for the TMA-fed kernel
   auto layout = [&](Arena &A) {
     UtF = A.take<float>((size_t)MpN * Kpa);
     BactT = A.take<float>((size_t)nI_ov * 128 * Kpa);
     BtgT = window ? nullptr : A.take<float>((size_t)T * MpT * Kpa);
     ones = A.take<float>((size_t)std::max(T, 1) * Kpa);
+    Bh = A.take<__nv_bfloat16>((size_t)nI_ov * 128 * Kpa);
+    Bl = A.take<__nv_bfloat16>((size_t)nI_ov * 128 * Kpa);
+    if (!window) {
+      Uh = A.take<__nv_bfloat16>((size_t)MpN * Kpa);
+      Ul = A.take<__nv_bfloat16>((size_t)MpN * Kpa);
+    }
   };
   ctx->a5.begin_sizing();
   layout(ctx->a5);
@@ -606,8 +619,10 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   CHECK_LAUNCH(ctx, launch_scale_table(nullptr, n_aux, Kpa, std::max(T, 1), nullptr, nullptr, SCALE_NONE, ones, s), 1);
   // R~_ov = U^T R_ov: rows N (A = U^T), columns n_ov (B rows = R_ov^T)
   if (B_act) {
+    CHECK_LAUNCH(ctx, launch_split_bf16(BactT, Bh, Bl, (int64_t)nI_ov * 128 * Kpa, s), 1);
     TcGemmArgs g;
     g.A = UtF; g.B = BactT; g.scale = ones; g.Kp = Kpa; g.n_t = 1; g.nt_group = 1;
+    g.B_hi = Bh; g.B_lo = Bl; g.rows_a = MpN; g.rows_b = (int64_t)nI_ov * 128;
     TcRun run;
     const int nI = (N + 127) / 128;
     if (tc_run(ctx, ctx->a4, g, full_tiles(nI, nI_ov), 0, &run, s) != LTGW_OK) return ctx->status();
@@ -622,9 +637,11 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   }
   // R~_tgt[t]^T = R_tgt[t]^T U: per target t, rows n_orb_act (A), columns N (B rows = U^T)
   {
+    CHECK_LAUNCH(ctx, launch_split_bf16(UtF, Uh, Ul, (int64_t)MpN * Kpa, s), 1);
     TcGemmArgs g;
     g.A = BtgT; g.a_group_stride = (int64_t)MpT * Kpa; g.B = UtF; g.scale = ones; g.Kp = Kpa;
     g.n_t = T; g.nt_group = 1;
+    g.B_hi = Uh; g.B_lo = Ul; g.rows_a = MpT; g.rows_b = MpN;
     TcRun run;
     const int nJ = (N + 127) / 128;
     if (tc_run(ctx, ctx->a4, g, full_tiles(MpT / 128, nJ), 0, &run, s) != LTGW_OK) return ctx->status();

@@ -649,6 +649,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
+      // stacked A groups (a_group_stride = rows_a Kp): group grp's rows follow grp * rows_a
+      const int arow0 = (g.a_group_stride ? grp * (int)g.rows_a : 0) + ti * TM;
       int jf = 0, jb = 0;
       uint32_t pf = 0, pb = 0;
       for (int c = 0; c < nchunks; ++c) {
@@ -656,8 +658,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         if (!mbar_wait(&bars.f_empty[jf], pf ^ 1, &bars.abort, g.err)) break;
         uint8_t *slot = sF + jf * F_STAGE;
         mbar_expect_tx(&bars.f_full[jf], F_BYTES + (uint32_t)nt * TK * 4);
-        tma_load_2d(slot, &tmA, k0, ti * TM, &bars.f_full[jf]);
-        tma_load_2d(slot + F_BOX, &tmA, k0 + 32, ti * TM, &bars.f_full[jf]);
+        tma_load_2d(slot, &tmA, k0, arow0, &bars.f_full[jf]);
+        tma_load_2d(slot + F_BOX, &tmA, k0 + 32, arow0, &bars.f_full[jf]);
         for (int t = 0; t < nt; ++t)
           bulk_load(slot + F_BYTES + t * TK * 4, g.scale + (int64_t)(t0 + t) * g.Kp + k0, TK * 4, &bars.f_full[jf]);
         if (++jf == T3_SF) { jf = 0; pf ^= 1; }
@@ -959,11 +961,13 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
   dim3 grid(n_tiles, groups, splits);
   if (g.B_hi && g.B_lo) {
-    if (g.out_mode == TC_OUT_COLDOT || g.a_group_stride != 0 || g.nt_group > T3_MAXT || g.rows_a < TM ||
-        g.rows_b < TN || g.rows_a % TM || g.rows_b % TN)
+    if (g.out_mode == TC_OUT_COLDOT || (g.a_group_stride != 0 && g.a_group_stride != g.rows_a * g.Kp) ||
+        (g.a_group_stride != 0 && g.nt_group != 1) || g.nt_group > T3_MAXT || g.rows_a < TM || g.rows_b < TN ||
+        g.rows_a % TM || g.rows_b % TN)
       return cudaErrorInvalidValue;
     CUtensorMap ta, tbh, tbl;
-    if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, g.Kp, g.rows_a, 32, TM,
+    const int64_t a_rows = g.a_group_stride ? (int64_t)groups * g.rows_a : g.rows_a;   // stacked groups
+    if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.A, g.Kp, a_rows, 32, TM,
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&tbh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_hi, g.Kp, g.rows_b, TK, TN,
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
