@@ -664,6 +664,7 @@ ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, in
   const int ncols = T * n_orb_act, nJ = (ncols + 127) / 128, rowsTp = nJ * 128;
   float *Cf, *ones = nullptr, *dsC = nullptr, *dsR = nullptr;
   uint8_t *qC = nullptr, *qR = nullptr;
+  __nv_bfloat16 *Rh = nullptr, *Rl = nullptr;   // R~_tgt^T pre-split for the TMA-fed kernel
   auto layout = [&](Arena &A) {
     Cf = A.take<float>((size_t)n_omega * MpN * KpN);
     if (fp8) {
@@ -673,6 +674,8 @@ ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, in
       dsR = A.take<float>((size_t)rowsTp);
     } else {
       ones = A.take<float>((size_t)n_omega * KpN);
+      Rh = A.take<__nv_bfloat16>((size_t)rowsTp * KpN);
+      Rl = A.take<__nv_bfloat16>((size_t)rowsTp * KpN);
     }
   };
   ctx->a5.begin_sizing();
@@ -689,7 +692,9 @@ ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, in
     g.A8 = qC; g.B8 = qR; g.ds_a = dsC; g.ds_b = dsR; g.Kp = Kq; g.rows_a = MpN; g.rows_b = rowsTp;
   } else {
     CHECK_LAUNCH(ctx, launch_scale_table(nullptr, N, KpN, n_omega, nullptr, nullptr, SCALE_NONE, ones, s), 1);
+    CHECK_LAUNCH(ctx, launch_split_bf16(BtT32, Rh, Rl, (int64_t)rowsTp * KpN, s), 1);
     g.A = Cf; g.a_group_stride = (int64_t)MpN * KpN; g.B = BtT32; g.scale = ones; g.Kp = KpN;
+    g.B_hi = Rh; g.B_lo = Rl; g.rows_a = MpN; g.rows_b = rowsTp;   // C_j stacked by frequency
   }
   g.n_t = n_omega; g.nt_group = 1;
   g.out_mode = TC_OUT_COLDOT;

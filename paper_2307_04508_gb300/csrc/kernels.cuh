@@ -123,8 +123,8 @@ struct TcGemmArgs {
   int *err = nullptr;
   // Pre-split B (BF16 hi and lo, row-major [rows_b][Kp]) selects the TMA-fed
   // kernel with A in tensor memory: operands arrive by tiled bulk copies
-  // (nt_group <= 2; not for TC_OUT_COLDOT; A groups only stacked,
-  // a_group_stride = rows_a Kp, with nt_group = 1).
+  // (nt_group <= 2; A groups only stacked, a_group_stride = rows_a Kp, with
+  // nt_group = 1).
   const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
   int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
   // FP8 E4M3 form (launch_tc_fp8_gemm): codes qa [n_t][rows_a][Kp], qb [rows_b][Kp] and

@@ -961,7 +961,7 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
   dim3 grid(n_tiles, groups, splits);
   if (g.B_hi && g.B_lo) {
-    if (g.out_mode == TC_OUT_COLDOT || (g.a_group_stride != 0 && g.a_group_stride != g.rows_a * g.Kp) ||
+    if ((g.a_group_stride != 0 && g.a_group_stride != g.rows_a * g.Kp) ||
         (g.a_group_stride != 0 && g.nt_group != 1) || g.nt_group > T3_MAXT || g.rows_a < TM || g.rows_b < TN ||
         g.rows_a % TM || g.rows_b % TN)
       return cudaErrorInvalidValue;
