@@ -95,7 +95,7 @@ cudaError_t launch_eig_vectors(EigWork &w, int n, int k, double *Ut, int *flags,
                                cudaStream_t s, int *launches);
 
 // ---- split-BF16 tensor-core contraction (tc_gemm.cu) ----
-// D_t = A diag(s_t) B^T for t < n_t; A [*][Kp], B [*][Kp], scale [n_t][Kp] FP32,
+// D_t = A diag(s_t) B^T for t < n_t; A [*][Kp] FP32, B pre-split, scale [n_t][Kp] FP32,
 // zero-padded (rows of A and B to 128, Kp to 64).  tiles: device list of
 // (tile row of A, tile row of B) pairs.  Output: FP64 partial tiles
 // partial[split][group][nt_group][tile][128][128], group = t / nt_group.
@@ -121,10 +121,10 @@ struct TcGemmArgs {
   int n_tile_rows = 0, cd_cols_p = 0;
   float *cd_out = nullptr;
   int *err = nullptr;
-  // Pre-split B (BF16 hi and lo, row-major [rows_b][Kp]) selects the TMA-fed
-  // kernel with A in tensor memory: operands arrive by tiled bulk copies
-  // (nt_group <= 2; A groups only stacked, a_group_stride = rows_a Kp, with
-  // nt_group = 1).
+  // B pre-split (BF16 hi and lo, row-major [rows_b][Kp]; required): the
+  // kernel keeps A in tensor memory and brings the operands in by tiled bulk
+  // copies (nt_group <= 2; A groups only stacked, a_group_stride = rows_a Kp,
+  // with nt_group = 1).
   const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
   int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
   // FP8 E4M3 form (launch_tc_fp8_gemm): codes qa [n_t][rows_a][Kp], qb [rows_b][Kp] and

@@ -1,35 +1,30 @@
-// Split-BF16 tensor-core contraction on sm_103a (tcgen05 + TMEM):
+// Tensor-core contractions on sm_103a (tcgen05 + TMEM, operands by TMA):
 //
-//   D_t[i][j] = sum_k A[i][k] s_t[k] B[j][k],   t = 0..n_t-1 (n_t <= 8)
+//   D_t[i][j] = sum_k A[i][k] s_t[k] B[j][k],   t = 0..n_t-1
 //
 // the scaled rank-k products of the LT-GW path (Pi(tau_k) moments, Eq. LT
 // and the M^m form; the NAF metric, Eq. nafeq; projections and the W_nm
 // contraction, Eqs. naftrafo and ScreenedCoulombOrbital) in the mixed
-// precision form: each operand value x is split into x_hi = bf16(x) and
-// x_lo = bf16(x - x_hi), and D accumulates hi*hi + hi*lo + lo*hi with FP32
-// accumulation in tensor memory, drained into FP64 every `drain_k` pairs.  The
-// drain length bounds the FP32 accumulation error: each MMA adds its products
-// into D with an FP32 rounding that loses about half an ulp on average, all in
-// the same direction for sums of one sign, so the relative bias grows with
-// the number of MMAs into one accumulator (about 1.7e-5 after 2048 pairs of
-// three products).  With at most two scales per CTA and more than one drain,
-// two accumulator sets alternate, so a drain overlaps the next window's MMAs.
+// precision forms.
 //
-// Operands are FP32, K-major, zero-padded to multiples of the tile (rows to
-// 128 / 64, K to 64) so the kernel needs no bounds checks.  The scale s_t is
-// applied to the A operand by the converter warps as they fill shared memory
-// (the per-pair scale is fused into the operand load); B is split once per
-// K-chunk and reused by all n_t products.
+// Split BF16 (tc_tma_ts_kernel): each operand value x is split into
+// x_hi = bf16(x) and x_lo = bf16(x - x_hi), and D accumulates hi*hi + hi*lo +
+// lo*hi with FP32 accumulation in tensor memory, drained into FP64 every
+// `drain_k` pairs.  The drain length bounds the FP32 accumulation error: each
+// MMA adds its products into D with an FP32 rounding that loses about half an
+// ulp on average, all in the same direction for sums of one sign, so the
+// relative bias grows with the number of MMAs into one accumulator (about
+// 1.7e-5 after 2048 pairs of three products).  B arrives pre-split; the scale
+// s_t is applied to A by converter warps that write the scaled split of A into
+// tensor memory (the per-pair scale is fused into the operand load).
 //
-// CTA = one 128 x 128 output tile for up to 4 scales (4 x 128 TMEM columns),
-// one K-split range.  Operand tiles of 128 x 128 keep the tensor core's
-// shared-memory operand traffic within bandwidth.  Warp roles (21 warps):
-//   warp 0       TMEM allocation; lane 0 issues tcgen05.mma
-//   warps 1-16   converters: FP32 global -> scaled BF16 hi/lo in the 128B-swizzled
-//                K-major layout the tensor core reads
-//   warps 17-20  epilogue: tcgen05.ld of the accumulators, FP64 partial sums
-// Every mbarrier wait is bounded (about two seconds of wall time); on expiry
-// the CTA records an error flag and unwinds.
+// FP8 E4M3 (tc_fp8_kernel): codes of both operands with per-row scales,
+// kind::f8f6f4, de-scaled in the epilogue.
+//
+// Operands are zero-padded to multiples of the tile (rows to 128, K to 64 or
+// 128) so the kernels need no bounds checks.  CTA = one 128 x 128 output tile
+// for its scales, one K-split range.  Every mbarrier wait is bounded (about two
+// seconds of wall time); on expiry the CTA records an error flag and unwinds.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stddef.h>
@@ -46,26 +41,10 @@ namespace ltgw {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;    // tile rows (A), cols (B), K chunk
-constexpr int MAXT = 4;                       // scales per CTA (TMEM: 4 x 128 columns)
-constexpr int SA = 4, SB = 2;                 // A / B stage ring depths
+constexpr int MAXT = 4;                       // scales per CTA at most (TMEM: 4 x 128 columns)
 constexpr int CONV_WARPS = 16, EPI_WARPS = 4;
-constexpr int NTHREADS = 32 * (1 + CONV_WARPS + EPI_WARPS);
-constexpr uint32_t A_BYTES = TM * TK * 2;      // one bf16 tile, 16 KB
-constexpr uint32_t B_BYTES = TN * TK * 2;      // 16 KB
-constexpr uint32_t A_STAGE = 2 * A_BYTES;      // hi + lo
-constexpr uint32_t B_STAGE = 2 * B_BYTES;
-constexpr uint32_t SMEM_BYTES = SA * A_STAGE + SB * B_STAGE + 1024;  // + alignment slack
-
-struct Bars {
-  alignas(16) float scale[2][MAXT][TK];   // scale ring (converters only), read as float4
-  uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[2], acc_empty[2], fin;
-  uint64_t s_full[2], s_empty[2];
-  uint32_t tmem_base;
-  int abort;
-};
-static_assert(offsetof(Bars, scale) % 16 == 0, "scale ring must be 16-byte aligned for float4 reads");
-static_assert((TK * sizeof(float)) % 16 == 0, "scale rows must keep 16-byte alignment");
-static_assert(offsetof(Bars, a_full) % 8 == 0, "mbarriers need 8-byte alignment");
+constexpr uint32_t B_BYTES = TN * TK * 2;      // one bf16 tile, 16 KB
+constexpr uint32_t B_STAGE = 2 * B_BYTES;      // hi + lo
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -137,12 +116,6 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
-}
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -150,83 +123,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
-// Byte offset of the 16-byte chunk c (k = 8c..8c+7) of row r in a K-major,
-// 128B-swizzled tile: 8-row atoms of 1024 B, chunk index XOR (row mod 8).
-__device__ __forceinline__ uint32_t swz(int r, int c) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-}
-
-// Split 8 floats into bf16 hi / lo and store both 16-byte chunks.
-__device__ __forceinline__ void split_store(const float v[8], uint8_t *hi, uint8_t *lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-    float2 hf = __bfloat1622float2(hb);
-    __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
-    h[q] = *reinterpret_cast<uint32_t *>(&hb);
-    l[q] = *reinterpret_cast<uint32_t *>(&lb);
-  }
-  *reinterpret_cast<uint4 *>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4 *>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-__device__ __forceinline__ void load8(const float *p, float v[8]) {
-  float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-  float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-
-// ---- roles shared by both kernels ----
-
-// MMA issue (one thread): per K-chunk, the B stage then nt A stages, three
-// products each (hi*hi, hi*lo, lo*hi); the TMEM accumulators are drained every
-// chunks_per_drain chunks, window dr into accumulator set dr % nbuf.
-template <int NSA, int NSB>
-__device__ __forceinline__ void mma_issue(uint32_t tmem, const uint8_t *sA, const uint8_t *sB, uint64_t *a_full, uint64_t *a_empty,
-                          uint64_t *b_full, uint64_t *b_empty, uint64_t *acc_full, uint64_t *acc_empty,
-                          uint64_t *fin, int nchunks, int chunks_per_drain, int ndrains, int nt, int nbuf,
-                          int *abort, int *err) {
-  int ia = 0, ib = 0;
-  uint32_t pa = 0, pb = 0;
-  bool ok = true;
-  for (int dr = 0; dr < ndrains && ok; ++dr) {
-    const int buf = dr % nbuf;
-    ok = mbar_wait(&acc_empty[buf], ((dr / nbuf) & 1) ^ 1, abort, err);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int c_end = min(nchunks, (dr + 1) * chunks_per_drain);
-    for (int c = dr * chunks_per_drain; c < c_end && ok; ++c) {
-      ok = mbar_wait(&b_full[ib], pb, abort, err);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t bhi = smem_u32(sB + ib * B_STAGE), blo = bhi + B_BYTES;
-      for (int t = 0; t < nt; ++t) {
-        ok = mbar_wait(&a_full[ia], pa, abort, err);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t ahi = smem_u32(sA + ia * A_STAGE), alo = ahi + A_BYTES;
-        const uint32_t d = tmem + (uint32_t)((buf * nt + t) * TN);
-#pragma unroll
-        for (int kk = 0; kk < TK / 16; ++kk) {
-          const uint32_t off = kk * 32;
-          const uint32_t first = (c == dr * chunks_per_drain && kk == 0) ? 0u : 1u;
-          mma_bf16(d, make_desc(ahi + off), make_desc(bhi + off), first);
-          mma_bf16(d, make_desc(ahi + off), make_desc(blo + off), 1u);
-          mma_bf16(d, make_desc(alo + off), make_desc(bhi + off), 1u);
-        }
-        mma_commit(&a_empty[ia]);
-        if (++ia == NSA) { ia = 0; pa ^= 1; }
-      }
-      mma_commit(&b_empty[ib]);
-      if (++ib == NSB) { ib = 0; pb ^= 1; }
-    }
-    if (ok) mma_commit(&acc_full[buf]);
-  }
-  // all issued MMAs complete before the CTA tears down
-  mma_commit(fin);
-  mbar_wait(fin, 0, abort, err, false);
-}
 
 // Epilogue (EPI_WARPS warps): tcgen05.ld of the accumulators after each drain
 // window (set dr % nbuf), into FP64 / FP32 partial tiles or the column-dot reduction.
@@ -325,151 +221,7 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
   }
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) tc_split_gemm_kernel(TcGemmArgs g) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *sA = smem;                       // SA stages of [hi | lo]
-  uint8_t *sB = smem + SA * A_STAGE;        // SB stages of [hi | lo]
-  __shared__ __align__(16) Bars bars;
-  __shared__ float cd_red[EPI_WARPS][TN];
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, grp = blockIdx.y, split = blockIdx.z;
-  const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
-  const int t0 = grp * g.nt_group;
-  const int nt = min(g.nt_group, g.n_t - t0);
-  const float *Ag = g.A + (int64_t)grp * g.a_group_stride;
-  const int64_t kb = (int64_t)split * g.k_per_split;
-  const int64_t ke = min(g.Kp, kb + g.k_per_split);
-  const int nchunks = (int)((ke - kb) / TK);
-  const int chunks_per_drain = (int)(g.drain_k / TK);
-  const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
-  const int nbuf = (ndrains > 1 && 2 * g.nt_group <= MAXT) ? 2 : 1;   // accumulator sets
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < SA; ++s) { mbar_init(&bars.a_full[s], CONV_WARPS); mbar_init(&bars.a_empty[s], 1); }
-    for (int s = 0; s < SB; ++s) { mbar_init(&bars.b_full[s], CONV_WARPS); mbar_init(&bars.b_empty[s], 1); }
-    for (int s = 0; s < 2; ++s) { mbar_init(&bars.s_full[s], 8); mbar_init(&bars.s_empty[s], CONV_WARPS); }
-    for (int s = 0; s < 2; ++s) { mbar_init(&bars.acc_full[s], 1); mbar_init(&bars.acc_empty[s], 32 * EPI_WARPS); }
-    mbar_init(&bars.fin, 1);
-    bars.abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-        smem_u32(&bars.tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = bars.tmem_base;
-
-  if (warp == 0) {
-    if (lane == 0)
-      mma_issue<SA, SB>(tmem, sA, sB, bars.a_full, bars.a_empty, bars.b_full, bars.b_empty, bars.acc_full,
-                        bars.acc_empty, &bars.fin, nchunks, chunks_per_drain, ndrains, nt, nbuf, &bars.abort, g.err);
-    __syncwarp();
-  } else if (warp <= CONV_WARPS) {
-    // ---------------------------------------------------------------- converters
-    // Each thread converts rows r and r + 64 of both tiles at one 16-byte chunk
-    // (8 k values); one mbarrier arrival per warp after __syncwarp keeps the
-    // barrier traffic at 16 arrivals per stage.
-    const int ct = threadIdx.x - 32;           // 0 .. CONV_THREADS-1
-    const int cc = ct & 7;                     // 16-byte chunk (8 k values) within TK
-    const int r0 = ct >> 3, r1 = r0 + 64;      // 128 rows x 8 chunks = 1024 units, 2 per thread
-    const float *Ar0 = Ag + (int64_t)(ti * TM + r0) * g.Kp + cc * 8;
-    const float *Ar1 = Ag + (int64_t)(ti * TM + r1) * g.Kp + cc * 8;
-    const float *Br0 = g.B + (int64_t)(tj * TN + r0) * g.Kp + cc * 8;
-    const float *Br1 = g.B + (int64_t)(tj * TN + r1) * g.Kp + cc * 8;
-    // scales: threads 0..255 each fetch one value of the next chunk's 4 x 64
-    // table and publish it through a two-slot shared ring
-    const int st_t = ct >> 6, st_k = ct & 63;
-    const bool st_writer = ct < MAXT * TK;
-    const float *Sg = g.scale + (int64_t)(t0 + st_t) * g.Kp + st_k;
-    const bool st_live = st_writer && st_t < nt;
-    const uint32_t o0 = swz(r0, cc), o1 = swz(r1, cc);
-    int ia = 0, ib = 0;
-    uint32_t pa = 0, pb = 0;
-    float a0[8], a1[8], b0[8], b1[8], n0[8], n1[8], m0[8], m1[8];
-    float snext = st_live ? __ldg(Sg + kb) : 0.0f;
-    load8(Ar0 + kb, n0);
-    load8(Ar1 + kb, n1);
-    load8(Br0 + kb, m0);
-    load8(Br1 + kb, m1);
-    bool ok = true;
-    // publish chunk 0's scales
-    if (st_writer) {
-      bars.scale[0][st_t][st_k] = snext;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars.s_full[0]);
-    }
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const int64_t k0 = kb + (int64_t)c * TK;
-      const int sb = c & 1;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) { a0[q] = n0[q]; a1[q] = n1[q]; b0[q] = m0[q]; b1[q] = m1[q]; }
-      if (c + 1 < nchunks) {  // prefetch the next chunk while this one converts
-        load8(Ar0 + k0 + TK, n0);
-        load8(Ar1 + k0 + TK, n1);
-        load8(Br0 + k0 + TK, m0);
-        load8(Br1 + k0 + TK, m1);
-        snext = st_live ? __ldg(Sg + k0 + TK) : 0.0f;
-      }
-      if (!mbar_wait(&bars.b_empty[ib], pb ^ 1, &bars.abort, g.err)) break;
-      {
-        uint8_t *hi = sB + ib * B_STAGE;
-        split_store(b0, hi + o0, hi + B_BYTES + o0);
-        split_store(b1, hi + o1, hi + B_BYTES + o1);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars.b_full[ib]);
-      if (++ib == SB) { ib = 0; pb ^= 1; }
-      if (!mbar_wait(&bars.s_full[sb], (c >> 1) & 1, &bars.abort, g.err)) break;
-      for (int t = 0; t < nt; ++t) {
-        float sc[8], v0[8], v1[8];
-        {
-          const float4 *sp = reinterpret_cast<const float4 *>(&bars.scale[sb][t][cc * 8]);
-          float4 x = sp[0], y = sp[1];
-          sc[0] = x.x; sc[1] = x.y; sc[2] = x.z; sc[3] = x.w;
-          sc[4] = y.x; sc[5] = y.y; sc[6] = y.z; sc[7] = y.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) { v0[q] = a0[q] * sc[q]; v1[q] = a1[q] * sc[q]; }
-        if (!mbar_wait(&bars.a_empty[ia], pa ^ 1, &bars.abort, g.err)) { ok = false; break; }
-        uint8_t *hi = sA + ia * A_STAGE;
-        split_store(v0, hi + o0, hi + A_BYTES + o0);
-        split_store(v1, hi + o1, hi + A_BYTES + o1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars.a_full[ia]);
-        if (++ia == SA) { ia = 0; pa ^= 1; }
-      }
-      if (!ok) break;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars.s_empty[sb]);   // this warp is done with chunk c's scales
-      if (c + 1 < nchunks && st_writer) {              // publish chunk c+1's scales
-        const int nbuf = (c + 1) & 1;
-        if (!mbar_wait(&bars.s_empty[nbuf], (((c + 1) >> 1) & 1) ^ 1, &bars.abort, g.err)) break;
-        bars.scale[nbuf][st_t][st_k] = snext;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars.s_full[nbuf]);
-      }
-    }
-  } else {
-    epilogue_drain(g, tmem, bars.acc_full, bars.acc_empty, &bars.abort, ndrains, nt, nbuf, tile, grp, split, ti, tj,
-                   cd_red);
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
-  }
-}
-
-// ---- the same contraction with A in tensor memory, operands brought in by TMA ----
+// ---- split BF16 with A in tensor memory, operands brought in by TMA ----
 // B arrives pre-split (BF16 hi and lo arrays, row-major [rows][Kp]) as two
 // tiled TMA copies per chunk with the 128-byte swizzle the tensor core reads,
 // so no thread touches it.  A arrives as an FP32 tile (two 128B-swizzled
@@ -923,7 +675,7 @@ bool encode_2d(CUtensorMap *m, CUtensorMapDataType dt, size_t esize, const void 
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return std::max<size_t>(SMEM_BYTES, std::max<size_t>(T3_SMEM, F8_SMEM)); }
+size_t tc_gemm_smem_bytes() { return std::max<size_t>(T3_SMEM, F8_SMEM); }
 
 cudaError_t launch_tc_fp8_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s) {
   if (n_tiles <= 0 || g.n_t <= 0) return cudaSuccess;
@@ -960,7 +712,8 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
   const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
   dim3 grid(n_tiles, groups, splits);
-  if (g.B_hi && g.B_lo) {
+  if (!g.B_hi || !g.B_lo) return cudaErrorInvalidValue;   // the kernel takes B pre-split
+  {
     if ((g.a_group_stride != 0 && g.a_group_stride != g.rows_a * g.Kp) ||
         (g.a_group_stride != 0 && g.nt_group != 1) || g.nt_group > T3_MAXT || g.rows_a < TM || g.rows_b < TN ||
         g.rows_a % TM || g.rows_b % TN)
@@ -984,15 +737,6 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
     tc_tma_ts_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(g, ta, tbh, tbl);
     return cudaGetLastError();
   }
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)SMEM_BYTES);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
-  tc_split_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(g);
-  return cudaGetLastError();
 }
 
 }  // namespace ltgw
