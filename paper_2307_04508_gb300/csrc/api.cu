@@ -332,16 +332,17 @@ TcPlan tc_plan(const ltgw_ctx *ctx, const TcGemmArgs &g, int n_tiles, int nt_gro
   p.nt_group = nt_group;
   p.groups = (g.n_t + nt_group - 1) / nt_group;
   const int64_t align = g.A8 ? 128 : 64;
+  const int64_t klen = (g.k_end ? g.k_end : g.Kp) - g.k_begin;   // pairs contracted
   if (g.out_mode == TC_OUT_COLDOT) {
     // the column dot needs the whole contraction (K = the NAF count) in one drain
-    p.kps = g.Kp; p.splits = 1; p.out_mode = TC_OUT_COLDOT;
+    p.kps = klen; p.splits = 1; p.out_mode = TC_OUT_COLDOT;
     return p;
   }
   if (want_splits > 0) {
-    p.kps = ((g.Kp + want_splits - 1) / want_splits + align - 1) / align * align;
-    p.splits = (g.Kp + p.kps - 1) / p.kps;
+    p.kps = ((klen + want_splits - 1) / want_splits + align - 1) / align * align;
+    p.splits = (klen + p.kps - 1) / p.kps;
   } else {
-    p.splits = tc_splits(ctx, (int64_t)n_tiles * p.groups, g.Kp, g.drain_k, align, &p.kps);
+    p.splits = tc_splits(ctx, (int64_t)n_tiles * p.groups, klen, g.drain_k, align, &p.kps);
   }
   p.out_mode = p.kps <= g.drain_k ? TC_OUT_F32 : TC_OUT_F64;
   return p;
@@ -357,11 +358,12 @@ TcPlan tc_plan(const ltgw_ctx *ctx, const TcGemmArgs &g, int n_tiles, int nt_gro
 ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int> &tiles, int coldot_rows,
                    TcRun *run, cudaStream_t s) {
   const int n_tiles = (int)(tiles.size() / 2);
-  if (g.out_mode == TC_OUT_COLDOT) g.drain_k = std::max<int64_t>(g.drain_k, g.Kp);
+  if (g.out_mode == TC_OUT_COLDOT) g.drain_k = std::max<int64_t>(g.drain_k, (g.k_end ? g.k_end : g.Kp) - g.k_begin);
   const int kind = g.A8 ? 2 : (g.B_hi ? 1 : 0);
   TcPlan plan = tc_plan(ctx, g, n_tiles, g.nt_group, 0);
   std::vector<TcPlan> cands{plan};
-  const ltgw_ctx::TcKey key{kind, n_tiles, g.n_t, g.out_mode, g.Kp, g.rows_a, g.rows_b};
+  const ltgw_ctx::TcKey key{kind, n_tiles, g.n_t, g.out_mode, (g.k_end ? g.k_end : g.Kp) - g.k_begin, g.rows_a,
+                            g.rows_b};
   bool tune = false;
   if (ctx->autotune && g.out_mode != TC_OUT_COLDOT) {
     auto it = ctx->tuned.find(key);
@@ -375,7 +377,7 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
       // scales per CTA vary only where the caller reduces with reduce_sym (column-major partials)
       if (g.out_colmajor && g.n_t > 1 && kind == 1) ntgs = {2, 1};
       if (g.out_colmajor && g.n_t > 1 && kind == 2) ntgs = {4, 2, 1};
-      const int64_t min_split = std::min<int64_t>(64, (g.Kp + g.drain_k - 1) / g.drain_k);
+      const int64_t min_split = std::min<int64_t>(64, ((g.k_end ? g.k_end : g.Kp) - g.k_begin + g.drain_k - 1) / g.drain_k);
       for (int ntg : ntgs) {
         const TcPlan base = tc_plan(ctx, g, n_tiles, ntg, 0);
         for (int64_t sp : {base.splits, base.splits / 2, base.splits * 2}) {
@@ -508,17 +510,23 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
     g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.nt_group = 2; g.B_hi = Bhi; g.B_lo = Blo;
   }
   g.n_t = n_t; g.rows_a = Mp; g.rows_b = Mp; g.out_colmajor = 1;
+  // Pairs go in blocks of at most 64 K-splits x drain_k (one FP32 drain per
+  // CTA, partials bounded); each block's partials are added to Pi or M^k.
   TcRun run;
+  const int64_t kblk = 64 * g.drain_k;
   ctx->mark(EV_PI0, s);
-  if (tc_run(ctx, ctx->a4, g, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
-  ctx->mark(EV_PI1, s);
+  for (int64_t k0 = 0; k0 < g.Kp; k0 += kblk) {
+    TcGemmArgs gb = g;
+    gb.k_begin = k0;
+    gb.k_end = std::min(g.Kp, k0 + kblk);
+    if (tc_run(ctx, ctx->a4, gb, tiles, 0, &run, s) != LTGW_OK) return ctx->status();
+    if (gb.k_end == g.Kp) ctx->mark(EV_PI1, s);
+    CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
+                                           nI, n_t, N, n_tau ? 1.0 : -2.0 * spin, n_tau ? M : Pi, s,
+                                           k0 ? 1.0 : 0.0, run.nt_group, 1), 1);
+  }
   ctx->pi_tc_flops = (fp8 ? 1.0 : 3.0) * 2.0 * (double)run.n_tiles * 128 * 128 * (double)g.Kp * n_t;
-  if (n_tau == 0) {
-    CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                           nI, n_t, N, -2.0 * spin, Pi, s, 0.0, run.nt_group, 1), 1);
-  } else {
-    CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles, d_tindex,
-                                           nI, n_t, N, 1.0, M, s, 0.0, run.nt_group, 1), 1);
+  if (n_tau) {
     CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
                  (n_omega + 63) / 64);
   }

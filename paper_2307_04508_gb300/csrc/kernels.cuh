@@ -107,6 +107,7 @@ struct TcGemmArgs {
   int nt_group = 4;              // scales per CTA (1..4); group = blockIdx.y
   int64_t a_group_stride = 0;    // A of group g starts at A + g * a_group_stride
   const int *tiles = nullptr;
+  int64_t k_begin = 0, k_end = 0;   // the pair range [k_begin, k_end) contracted (k_end 0: Kp)
   int64_t k_per_split = 0;
   int64_t drain_k = 2048;        // pairs per FP32 accumulation (bounds its rounding bias)
   int out_mode = TC_OUT_F64;     // F32 requires k_per_split <= drain_k
@@ -131,6 +132,7 @@ struct TcGemmArgs {
   // per-row de-scales ds_a [n_t][rows_a], ds_b [rows_b], applied in the epilogue.
   const uint8_t *A8 = nullptr, *B8 = nullptr;
   const float *ds_a = nullptr, *ds_b = nullptr;
+  int groups_fastest = 0;   // set by the launcher: grid order (groups, tiles, splits)
 };
 cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s);
 // hi = bf16(x), lo = bf16(x - hi) elementwise: the split the tensor-core kernels use.

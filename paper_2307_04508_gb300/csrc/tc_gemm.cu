@@ -128,13 +128,13 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 // window (set dr % nbuf), into FP64 / FP32 partial tiles or the column-dot reduction.
 __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tmem, uint64_t *acc_full, uint64_t *acc_empty,
                                int *abort, int ndrains, int nt, int nbuf, int tile, int grp, int split, int ti,
-                               int tj, float (*cd_red)[TN]) {
+                               int tj, float (*cd_red)[TN], int n_tiles, int n_groups) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ew = warp & 3;                   // TMEM lane quarter this warp may read
   const int row = ew * 32 + lane;
   const int64_t tile_elems = (int64_t)TM * TN;
-  const int64_t base = (((int64_t)split * gridDim.y + grp) * g.nt_group * gridDim.x + tile) * tile_elems;
-  const int64_t tstride = (int64_t)gridDim.x * tile_elems;   // between scales
+  const int64_t base = (((int64_t)split * n_groups + grp) * g.nt_group * n_tiles + tile) * tile_elems;
+  const int64_t tstride = (int64_t)n_tiles * tile_elems;   // between scales
   for (int dr = 0; dr < ndrains; ++dr) {
     const int buf = dr % nbuf;
     if (!mbar_wait(&acc_full[buf], (dr / nbuf) & 1, abort, g.err)) break;
@@ -213,7 +213,7 @@ __device__ __forceinline__ void epilogue_drain(const TcGemmArgs &g, uint32_t tme
       asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI_WARPS) : "memory");   // epilogue warps only
       if (row < TN) {
         const float v = cd_red[0][row] + cd_red[1][row] + cd_red[2][row] + cd_red[3][row];
-        g.cd_out[(((int64_t)split * gridDim.y + grp) * g.n_tile_rows + ti) * g.cd_cols_p + tj * TN + row] = v;
+        g.cd_out[(((int64_t)split * n_groups + grp) * g.n_tile_rows + ti) * g.cd_cols_p + tj * TN + row] = v;
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -330,14 +330,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   __shared__ float cd_red[EPI_WARPS][TN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, grp = blockIdx.y, split = blockIdx.z;
+  // grid (groups, tiles, splits) for many tiles: the groups of one tile, which
+  // read the same A and B panels, are adjacent in launch order and resident
+  // together; else (tiles, groups, splits)
+  const bool gfirst = g.groups_fastest != 0;
+  const int grp = gfirst ? blockIdx.x : blockIdx.y, tile = gfirst ? blockIdx.y : blockIdx.x, split = blockIdx.z;
+  const int n_groups = gfirst ? gridDim.x : gridDim.y, n_tiles = gfirst ? gridDim.y : gridDim.x;
   const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
   const int t0 = grp * g.nt_group;
   const int nt = min(g.nt_group, g.n_t - t0);
   const int nsa = (512 - TN * g.nt_group) / TK;       // A stages in TMEM after the accumulators
   const uint32_t acol0 = (uint32_t)(TN * g.nt_group); // first A column
-  const int64_t kb = (int64_t)split * g.k_per_split;
-  const int64_t ke = min(g.Kp, kb + g.k_per_split);
+  const int64_t kb = g.k_begin + (int64_t)split * g.k_per_split;
+  const int64_t ke = min(g.k_end ? g.k_end : g.Kp, kb + g.k_per_split);
   const int nchunks = (int)((ke - kb) / TK);
   const int chunks_per_drain = (int)(g.drain_k / TK);
   const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     }
   } else {
     epilogue_drain(g, tmem, bars.acc_full, bars.acc_empty, &bars.abort, ndrains, nt, 1, tile, grp, split, ti, tj,
-                   cd_red);
+                   cd_red, n_tiles, n_groups);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -555,8 +560,8 @@ __global__ void __launch_bounds__(F8_THREADS, 1)
   const int ti = g.tiles[2 * tile], tj = g.tiles[2 * tile + 1];
   const int t0 = grp * g.nt_group;
   const int nt = min(g.nt_group, g.n_t - t0);
-  const int64_t kb = (int64_t)split * g.k_per_split;
-  const int64_t ke = min(g.Kp, kb + g.k_per_split);
+  const int64_t kb = g.k_begin + (int64_t)split * g.k_per_split;
+  const int64_t ke = min(g.k_end ? g.k_end : g.Kp, kb + g.k_per_split);
   const int nchunks = (int)((ke - kb) / F8_K);
   const int chunks_per_drain = (int)(g.drain_k / F8_K);
   const int ndrains = (nchunks + chunks_per_drain - 1) / chunks_per_drain;
@@ -631,7 +636,7 @@ __global__ void __launch_bounds__(F8_THREADS, 1)
     __syncwarp();
   } else {
     epilogue_drain(g, tmem, bars.acc_full, bars.acc_empty, &bars.abort, ndrains, nt, 1, tile, grp, split, ti, tj,
-                   cd_red);
+                   cd_red, (int)gridDim.x, (int)gridDim.y);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -686,7 +691,9 @@ cudaError_t launch_tc_fp8_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t s)
       g.rows_a % TM || g.rows_b % TN || (int64_t)g.n_t * g.rows_a > INT32_MAX)
     return cudaErrorInvalidValue;
   const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
-  const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
+  const int64_t k_len = (g.k_end ? g.k_end : g.Kp) - g.k_begin;
+  if (g.k_begin < 0 || g.k_begin % F8_K || k_len <= 0 || g.k_begin + k_len > g.Kp) return cudaErrorInvalidValue;
+  const int splits = (int)((k_len + g.k_per_split - 1) / g.k_per_split);
   CUtensorMap ta, tb;
   if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g.A8, g.Kp, (int64_t)g.n_t * g.rows_a, F8_K, TM,
                  CU_TENSOR_MAP_SWIZZLE_128B) ||
@@ -710,8 +717,9 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   if (g.out_mode == TC_OUT_F32 && g.k_per_split > g.drain_k) return cudaErrorInvalidValue;
   if (g.out_mode == TC_OUT_COLDOT && (g.nt_group != 1 || g.k_per_split > g.drain_k)) return cudaErrorInvalidValue;
   const int groups = (g.n_t + g.nt_group - 1) / g.nt_group;
-  const int splits = (int)((g.Kp + g.k_per_split - 1) / g.k_per_split);
-  dim3 grid(n_tiles, groups, splits);
+  const int64_t k_len = (g.k_end ? g.k_end : g.Kp) - g.k_begin;
+  if (g.k_begin < 0 || g.k_begin % TK || k_len <= 0 || g.k_begin + k_len > g.Kp) return cudaErrorInvalidValue;
+  const int splits = (int)((k_len + g.k_per_split - 1) / g.k_per_split);
   if (!g.B_hi || !g.B_lo) return cudaErrorInvalidValue;   // the kernel takes B pre-split
   {
     if ((g.a_group_stride != 0 && g.a_group_stride != g.rows_a * g.Kp) ||
@@ -734,7 +742,13 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
                                        (int)T3_SMEM);
     });
     if (attr_err2 != cudaSuccess) return attr_err2;
-    tc_tma_ts_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(g, ta, tbh, tbl);
+    TcGemmArgs h = g;
+    // groups first when they share A (Pi's scales) and there are many tiles, or
+    // when the tiles are very many (W_nm's frequencies share only B); measured:
+    // large Pi and W_nm faster, the mid W_nm (188 tiles) slower that way
+    h.groups_fastest = n_tiles <= 65535 && (g.a_group_stride == 0 ? n_tiles >= 64 : n_tiles >= 4096);
+    const dim3 grid = h.groups_fastest ? dim3(groups, n_tiles, splits) : dim3(n_tiles, groups, splits);
+    tc_tma_ts_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(h, ta, tbh, tbl);
     return cudaGetLastError();
   }
 }
