@@ -287,7 +287,7 @@ def run_gpu(args):
     alu_peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
     # DRAM bytes per launch (read + write) from the ncu captures summarised in profiles/
     # (tc_tma_ts_pi_mid.md, hh_fused_double_mid.md); mid workload only
-    traffic_pi = 112.06e6 + 44.71e6 if args.workload == "mid" and args.precision == "bf16x3" else None
+    traffic_pi = 112.52e6 + 44.94e6 if args.workload == "mid" and args.precision == "bf16x3" else None
     traffic_tri = 26.0e6 + 0.01e6 if args.workload == "mid" else None
     roof_pi = pi_roofline(args.precision, pi_flops, pi_ms, pk, src, traffic_pi)
     # Householder reduction of the N_aux x N_aux metric: 4/3 N^3 algorithmic flops,
