@@ -185,9 +185,10 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     w.lu = A.take<double>((size_t)5 * n * n);
     w.count = A.take<int>(2);
     const int64_t nsplit = (n + 63) / 64, nblk = (n + 63) / 64;
-    // compact-WY scratch: split partials of G and W1, W1, every block's G, T and M_b
-    w.wy = A.take<double>((size_t)nsplit * 64 * (64 + (size_t)n) + 64 * (size_t)n + 2 * (size_t)nblk * 64 * 64 +
-                          (size_t)nblk * n * 64);
+    // compact-WY scratch: split partials of W1, W1, every block's G and T, and
+    // every block's M_b (before the T recurrences: the split partials of G)
+    w.wy = A.take<double>((size_t)nsplit * 64 * (size_t)n + 64 * (size_t)n + 2 * (size_t)nblk * 64 * 64 +
+                          (size_t)nblk * std::max((size_t)n * 64, (size_t)nsplit * 64 * 64));
     w.grid_ws = A.take<double>((size_t)4 * n + 2 * (size_t)ctx->n_sm + 8);
   };
   ar.begin_sizing();

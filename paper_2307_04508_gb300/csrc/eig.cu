@@ -1055,26 +1055,21 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
   if (nref > 0) {
     const int nblk = (nref + WY_NB - 1) / WY_NB;
     const int nsplit_max = (int)((n + WY_KSPLIT - 1) / WY_KSPLIT);
-    T *Gp = reinterpret_cast<T *>(w.wy);                         // [nsplit][nb][nb], reused per block
-    T *W1p = Gp + (int64_t)nsplit_max * WY_NB * WY_NB;           // [nsplit][nb][k]
+    T *W1p = reinterpret_cast<T *>(w.wy);                        // [nsplit][nb][k]
     T *W1 = W1p + (int64_t)nsplit_max * WY_NB * k;               // [nb][k]
     T *Gs = W1 + (int64_t)WY_NB * k;                             // [nblk][nb][nb]
     T *Tm = Gs + (int64_t)nblk * WY_NB * WY_NB;                  // [nblk][WY_NB][WY_NB]
     T *Mall = Tm + (int64_t)nblk * WY_NB * WY_NB;                // [nblk][n-1][WY_NB]
-    for (int bi = 0; bi < nblk; ++bi) {
-      const int j0 = bi * WY_NB, nb = std::min(WY_NB, nref - j0);
-      const int r0 = j0 + 1;              // first row where this block's V is non-zero
-      const int64_t len = n - r0;
-      const int nsplit = (int)((len + WY_KSPLIT - 1) / WY_KSPLIT);
-      GemmArgs<T> g;                      // G partials = V_b V_b^T over row chunks
-      g.M = nb; g.N = nb; g.K = len; g.ksplit = WY_KSPLIT;
-      g.A = V + (int64_t)j0 * n + r0; g.lda = n;
-      g.B = V + (int64_t)j0 * n + r0; g.ldb = n;
-      g.C = Gp; g.ldc = nb; g.strideC = (int64_t)nb * nb;
-      e = launch_gemm<T>(g, nsplit, true, true, s);
+    {
+      // every block's G = V_b V_b^T in one launch (column chunks of WY_KSPLIT;
+      // a block-at-a-time GEMM keeps only ~n/64 SMs busy), the chunk partials
+      // in the M_b region, which is written only after the T recurrences
+      T *Gp = Mall;                                              // [nchunk][nblk][nb][nb]
+      const int64_t nchunk = (n - 1 + WY_KSPLIT - 1) / WY_KSPLIT;
+      e = launch_gram_panels(V, n, nref, WY_NB, WY_KSPLIT, Gp, s);
       if (e != cudaSuccess) return e;
-      sum_partials_kernel<T><<<64, 256, 0, s>>>(Gp, nsplit, (int64_t)nb * nb, (int64_t)nb * nb,
-                                                Gs + (int64_t)bi * WY_NB * WY_NB);
+      sum_partials_kernel<T><<<152, 256, 0, s>>>(Gp, (int)nchunk, (int64_t)nblk * WY_NB * WY_NB,
+                                                 (int64_t)nblk * WY_NB * WY_NB, Gs);
       *launches += 2;
     }
     wy_build_t_kernel<T><<<nblk, 4 * WY_NB, 2 * WY_NB * (WY_NB + 1) * sizeof(T), s>>>(Gs, w.tau, nref, Tm);

@@ -194,7 +194,47 @@ __global__ void __launch_bounds__(NT) gemm_coldot_kernel(ColDotArgs g) {
   }
 }
 
+// Gram blocks of the reflector panels: panel q holds rows j0 = q*nb ..
+// j0+nbq-1 of V (row j is zero outside columns j+1..n-1), and chunk c covers
+// its columns r0 + c*ks .. r0 + (c+1)*ks - 1 with r0 = j0 + 1.  The chunk's
+// partial of G_q = V_q V_q^T goes to P + (c * npanel + q) * nb * nb with
+// leading dimension nbq; chunks past the panel's end write zeros, so one sum
+// over every chunk index gives every panel's G.  grid: x = chunk, y = panel.
+__global__ void __launch_bounds__(NT) gram_panels_kernel(const double *__restrict__ V, int n, int nref,
+                                                         int nb, int64_t ks, double *__restrict__ P) {
+  __shared__ TileSmem<double> sm;
+  const int c = blockIdx.x, q = blockIdx.y;
+  const int j0 = q * nb, nbq = min(nb, nref - j0);
+  const int64_t r0 = j0 + 1, len = n - r0, k0 = (int64_t)c * ks;
+  double acc[4][4] = {};
+  if (k0 < len) {
+    const double *A = V + (int64_t)j0 * n + r0 + k0;
+    tile_accumulate<double, true, true>(acc, sm, A, n, A, n, 0, 0, nbq, nbq, min(ks, len - k0), SCALE_NONE,
+                                        nullptr, 0.0, 0.0);
+  }
+  double *Pq = P + ((int64_t)c * gridDim.y + q) * nb * nb;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = tx + 16 * j;
+      if (gm < nbq && gn < nbq) Pq[gm * nbq + gn] = acc[i][j];
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gram_panels(const double *V, int n, int nref, int nb, int64_t ks, double *P, cudaStream_t s) {
+  if (nref <= 0 || n < 2) return cudaSuccess;
+  if (nb <= 0 || nb > BM || ks <= 0) return cudaErrorInvalidValue;
+  const int npanel = (nref + nb - 1) / nb;
+  const int64_t nchunk = (n - 1 + ks - 1) / ks;   // chunks of the longest panel (q = 0)
+  gram_panels_kernel<<<dim3((unsigned)nchunk, (unsigned)npanel), NT, 0, s>>>(V, n, nref, nb, ks, P);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_gemm(const GemmArgs<T> &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s) {

@@ -39,6 +39,12 @@ cudaError_t launch_gemm(const GemmArgs<T> &g, int batch, bool a_kmaj, bool b_kma
 inline cudaError_t launch_gemm_f64(const GemmF64Args &g, int batch, bool a_kmaj, bool b_kmaj, cudaStream_t s) {
   return launch_gemm<double>(g, batch, a_kmaj, b_kmaj, s);
 }
+// Every reflector panel's Gram block in one launch: panel q = rows q*nb ..
+// of V (n x n, row j zero outside columns j+1..n-1, nb <= 64), chunk c of its
+// columns from q*nb + 1 on (ks wide) into P + (c * npanel + q) * nb * nb
+// (ld = the panel's row count; zeros past the panel's end), npanel =
+// ceil(nref / nb), ceil((n - 1) / ks) chunks.
+cudaError_t launch_gram_panels(const double *V, int n, int nref, int nb, int64_t ks, double *P, cudaStream_t s);
 
 // W[b][t][m] = sum_P Bt[t][P][m] (C_b Bt[t])[P][m], C_b is N x N (K-major rows).
 struct ColDotArgs {

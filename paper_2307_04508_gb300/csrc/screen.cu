@@ -6,8 +6,8 @@
 // Two forms:
 //  * launch_screen: one launch per pivot k for all frequencies, ping-ponging
 //    between two buffers (first step forms A = 1 - Pi, last writes C = -X - 1);
-//  * launch_screen_blocked: pivot blocks of 64 - the block is inverted in
-//    shared memory, and the rank-64 update A -= A[:,P] A_PP^-1 A[P,:] runs on
+//  * launch_screen_blocked: pivot blocks of 64 - the block is inverted by a
+//    4-CTA cluster, and the rank-64 update A -= A[:,P] A_PP^-1 A[P,:] runs on
 //    the FP64 tiled GEMM (about N/64 x 5 launches instead of N).
 #include <math.h>
 
@@ -71,63 +71,94 @@ __global__ void form_a_kernel(const double *__restrict__ Pi, T *__restrict__ X, 
   }
 }
 
-// Z = X[P,P]^-1 for each frequency (one block of 256 threads each): sweep
-// with each thread's 16 elements of the bs x bs block held in registers;
-// only the pivot row and column go through shared memory.
+// Z = X[P,P]^-1 for each frequency, by the sweep on a cluster of SB_CL CTAs
+// (one CTA per frequency would leave most SMs idle through the bs pivots).
+// CTA c of the cluster holds rows SB_RPC*c .. SB_RPC*c + SB_RPC - 1 of the
+// block in registers: warp w rows 2w and 2w + 1 of them, lane l columns l and
+// l + 32.  At pivot k the warp holding row k forms the reciprocal of the pivot
+// and writes row k scaled by it, and the reciprocal, into every CTA's shared
+// memory; each CTA keeps its own rows' column k locally; then one cluster
+// barrier.  The buffers alternate with the pivot's parity, so the writes for
+// pivot k + 1 never meet the reads for pivot k.
+constexpr int SB_CL = 4;
+constexpr int SB_RPC = SB_B / SB_CL;         // rows per CTA
+constexpr int SB_THREADS = SB_RPC / 2 * 32;  // one warp per two rows
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_cluster_f64(uint32_t local_addr, unsigned rank, double v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(v) : "memory");
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) block_inverse_kernel(const T *__restrict__ X, int N, int p0, int bs,
-                                                            T *__restrict__ Z, int *flags) {
-  constexpr int PER = SB_B * SB_B / 256;
-  __shared__ T rowk[SB_B], colk[SB_B];
-  __shared__ T s_rp;
-  const int b = blockIdx.x;
+__global__ void __cluster_dims__(SB_CL, 1, 1) __launch_bounds__(SB_THREADS)
+    block_inverse_kernel(const T *__restrict__ X, int N, int p0, int bs, T *__restrict__ Z, int *flags) {
+  static_assert(sizeof(T) == sizeof(double), "the pivot row is exchanged as f64");
+  __shared__ T rowk[2][SB_B + 1];   // [SB_B]: the pivot's reciprocal
+  __shared__ T colk[2][SB_RPC];
+  unsigned crank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  const int b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lr0 = 2 * warp, i0 = (int)crank * SB_RPC + lr0;
   const T *Xb = X + (int64_t)b * N * N;
-  T v[PER];
+  T v[2][2];
 #pragma unroll
-  for (int c = 0; c < PER; ++c) {
-    const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
-    v[c] = (i < bs && j < bs) ? Xb[(int64_t)(p0 + i) * N + (p0 + j)] : (T)0;
-  }
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + r, j = lane + 32 * h;
+      v[r][h] = (i < bs && j < bs) ? Xb[(int64_t)(p0 + i) * N + (p0 + j)] : (T)0;
+    }
+  const uint32_t rowk_addr = (uint32_t)__cvta_generic_to_shared(&rowk[0][0]);
+  cluster_sync();   // every CTA of the cluster is running before the first remote write
   for (int k = 0; k < bs; ++k) {
-    // publish column k and row k scaled by the pivot's reciprocal (computed
-    // once, by the pivot's owner), so each update below is one FMA
-    bool own = false;
-    T piv = 0;
+    const int par = k & 1, hk = k >> 5;
+    if (lane == (k & 31)) {
+      colk[par][lr0] = hk ? v[0][1] : v[0][0];
+      colk[par][lr0 + 1] = hk ? v[1][1] : v[1][0];
+    }
+    if ((int)crank == k / SB_RPC && warp == (k % SB_RPC) >> 1) {   // this warp holds row k
+      const int rk = k & 1;
+      const T mine = rk ? (hk ? v[1][1] : v[1][0]) : (hk ? v[0][1] : v[0][0]);
+      const T piv = __shfl_sync(0xffffffffu, mine, k & 31);
+      if (lane == 0 && !(piv > (T)0 && isfinite(piv))) atomicExch(&flags[FLAG_NOT_SPD], 1);
+      const T rp = (T)1 / piv;
+      const T a0 = (rk ? v[1][0] : v[0][0]) * rp, a1 = (rk ? v[1][1] : v[0][1]) * rp;
+      const uint32_t row = rowk_addr + (uint32_t)(par * (SB_B + 1) * sizeof(T));
 #pragma unroll
-    for (int c = 0; c < PER; ++c) {   // constant indices keep v[] in registers
-      const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
-      if (j == k && i < bs) colk[i] = v[c];
-      if (i == k && j == k) { own = true; piv = v[c]; }
+      for (unsigned c = 0; c < SB_CL; ++c) {
+        st_cluster_f64(row + lane * sizeof(T), c, a0);
+        st_cluster_f64(row + (lane + 32) * sizeof(T), c, a1);
+        if (lane == 0) st_cluster_f64(row + SB_B * sizeof(T), c, rp);
+      }
     }
-    if (own) {
-      if (!(piv > (T)0 && isfinite(piv))) atomicExch(&flags[FLAG_NOT_SPD], 1);
-      s_rp = (T)1 / piv;
-    }
-    __syncthreads();
-    const T rp = s_rp;
+    cluster_sync();
+    const T rp = rowk[par][SB_B];
 #pragma unroll
-    for (int c = 0; c < PER; ++c) {
-      const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
-      if (i == k && j < bs) rowk[j] = v[c] * rp;
-    }
-    __syncthreads();
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-    for (int c = 0; c < PER; ++c) {
-      const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
-      if (i >= bs || j >= bs) continue;
-      if (i == k && j == k) v[c] = -rp;
-      else if (i == k) v[c] = rowk[j];
-      else if (j == k) v[c] = colk[i] * rp;
-      else v[c] = fma(-colk[i], rowk[j], v[c]);
-    }
-    __syncthreads();
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + r, j = lane + 32 * h;
+        if (i >= bs || j >= bs) continue;
+        if (i == k && j == k) v[r][h] = -rp;
+        else if (i == k) v[r][h] = rowk[par][j];
+        else if (j == k) v[r][h] = colk[par][lr0 + r] * rp;
+        else v[r][h] = fma(-colk[par][lr0 + r], rowk[par][j], v[r][h]);
+      }
   }
   T *Zb = Z + (int64_t)b * SB_B * SB_B;
 #pragma unroll
-  for (int c = 0; c < PER; ++c) {
-    const int q = threadIdx.x + 256 * c, i = q / SB_B, j = q % SB_B;
-    if (i < bs && j < bs) Zb[i * SB_B + j] = -v[c];
-  }
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + r, j = lane + 32 * h;
+      if (i < bs && j < bs) Zb[i * SB_B + j] = -v[r][h];
+    }
 }
 
 // rowsP[b][r][j] = X[b][p0 + r][j]
@@ -181,7 +212,7 @@ cudaError_t screen_blocked_impl(const double *Pi, int N, int n_omega, T *work, d
   ++*launches;
   for (int p0 = 0; p0 < N; p0 += SB_B) {
     const int bs = std::min(SB_B, N - p0);
-    block_inverse_kernel<T><<<n_omega, 256, 0, s>>>(X, N, p0, bs, Z, flags);
+    block_inverse_kernel<T><<<dim3(SB_CL, n_omega), SB_THREADS, 0, s>>>(X, N, p0, bs, Z, flags);
     dim3 cg((N + 255) / 256 < 8 ? (N + 255) / 256 : 8, bs, n_omega);
     copy_rows_kernel<T><<<cg, 256, 0, s>>>(X, N, p0, bs, rowsP);
     GemmArgs<T> g;   // R = X[:, P] Z
