@@ -185,9 +185,13 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     w.lu = A.take<double>((size_t)5 * n * n);
     w.count = A.take<int>(2);
     const int64_t nsplit = (n + 63) / 64, nblk = (n + 63) / 64;
-    // compact-WY scratch: split partials of W1, W1, every block's G and T, and
+    // compact-WY scratch: W1 and its partials (block-at-a-time form: split
+    // partials of 64 x n and W1 64 x n; cooperative form: one 64 x 64 partial
+    // per CTA and one W1 per 64-column slice), every block's G and T, and
     // every block's M_b (before the T recurrences: the split partials of G)
-    w.wy = A.take<double>((size_t)nsplit * 64 * (size_t)n + 64 * (size_t)n + 2 * (size_t)nblk * 64 * 64 +
+    w.wy_r0 = (int64_t)std::max((size_t)nsplit * 64 * (size_t)n + 64 * (size_t)n,
+                                ((size_t)ctx->n_sm + (size_t)nsplit) * 64 * 64);
+    w.wy = A.take<double>((size_t)w.wy_r0 + 2 * (size_t)nblk * 64 * 64 +
                           (size_t)nblk * std::max((size_t)n * 64, (size_t)nsplit * 64 * 64));
     w.grid_ws = A.take<double>((size_t)4 * n + 2 * (size_t)ctx->n_sm + 8);
   };

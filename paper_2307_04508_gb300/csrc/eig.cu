@@ -881,6 +881,123 @@ __global__ void wy_build_t_kernel(const T *__restrict__ Gall, const double *__re
   for (int q = threadIdx.x; q < WY_NB * WY_NB; q += blockDim.x) Tm[q] = sT[q / WY_NB][q % WY_NB];   // zero-padded
 }
 
+// ---- the compact-WY blocks applied by one cooperative kernel ----
+// Launched as G CTAs for each of the S column slices (columns 64 s .. 64 s +
+// 63 of Y).  CTA (s, c) owns the row chunks ch = c, c + G, c + 2G, ... of
+// WA_RC rows.  For each block b, last to first (rows r0 = 64 b + 1 .. n-1):
+//   1. the partial of W1 = V_b Y[r0:, slice] over the own chunks -> Wp[s][c];
+//   2. grid barrier; CTA c sums entries c*256 + t (+ G*256 ...) of the
+//      slice's partials                                            -> W1[s];
+//   3. grid barrier; Y[own rows, slice] -= M_b[own rows] W1[s].
+// A CTA reads and writes only its own rows of Y, so step 3 of one block and
+// step 1 of the next need no barrier between them.  Each step does
+// WA_RC x 64 x 64 FMAs per chunk (64 rows of V_b by the slice, or the chunk's
+// rows by 64 columns), so the FP64 work spreads over every SM in units a
+// quarter of a 64 x 64 x 64 tile.
+constexpr int WA_RC = 32;
+constexpr size_t WA_SMEM = (size_t)(64 * (WA_RC + 1) + 64 * 64) * sizeof(double);   // step 3 (the larger)
+
+struct WyApplyArgs {
+  const double *V;   // [n + 64][n] reflectors (rows)
+  const double *M;   // [nblk][n - 1][64]: M_b[r - 1][i] = (V_b^T T_b)[r][i]
+  double *Y;         // [n][k], updated in place
+  double *Wp;        // [S * G][64 * 64] partials of W1
+  double *W1;        // [S][64 * 64]
+  GridBar *gb;
+  int *flags;
+  int n, k, nref, nblk, G;
+};
+
+__global__ void __launch_bounds__(256) wy_apply_kernel(WyApplyArgs g) {
+  extern __shared__ __align__(16) double wa_sm[];
+  const int s = blockIdx.x / g.G, c = blockIdx.x % g.G;
+  const int n = g.n, k = g.k, col0 = 64 * s, ncol = min(64, k - col0);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double *W1s = g.W1 + (int64_t)s * 4096;
+  unsigned bar = 0;
+  for (int b = g.nblk - 1; b >= 0; --b) {
+    const int j0 = 64 * b, nb = min(64, g.nref - j0), r0 = j0 + 1;
+    // ---- 1: Vs[r][i] = V_b[i][a + r] (transposed), Ys[r][cc] = Y[a + r][col0 + cc]
+    double *Vs = wa_sm, *Ys = wa_sm + WA_RC * 65;
+    double acc[4][4] = {};
+    for (int ch = c; ch * WA_RC < n; ch += g.G) {
+      const int a = max(ch * WA_RC, r0), e = min(n, ch * WA_RC + WA_RC);
+      if (a >= e) continue;   // the same for the whole CTA
+      const int len = e - a;
+      for (int q = tid; q < 64 * WA_RC; q += 256) {
+        const int i = q / WA_RC, r = q % WA_RC;
+        Vs[r * 65 + i] = (i < nb && r < len) ? g.V[(int64_t)(j0 + i) * n + a + r] : 0.0;
+        const int r2 = q >> 6, cc = q & 63;
+        Ys[r2 * 64 + cc] = (r2 < len && cc < ncol) ? g.Y[(int64_t)(a + r2) * k + col0 + cc] : 0.0;
+      }
+      __syncthreads();
+      for (int r = 0; r < len; ++r) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) av[u] = Vs[r * 65 + ty + 16 * u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) bv[v] = Ys[r * 64 + tx + 16 * v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+      }
+      __syncthreads();
+    }
+    double *Wpc = g.Wp + (int64_t)blockIdx.x * 4096;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Wpc[(ty + 16 * u) * 64 + tx + 16 * v] = acc[u][v];
+    if (!grid_barrier(g.gb, bar++, g.flags)) return;
+    // ---- 2: the slice's partials summed, 256 entries per CTA at a time
+    const double *Wps = g.Wp + (int64_t)s * g.G * 4096;
+    for (int q = c * 256 + tid; q < 4096; q += g.G * 256) {
+      double t = 0.0;
+      for (int m = 0; m < g.G; ++m) t += __ldcg(Wps + (int64_t)m * 4096 + q);
+      W1s[q] = t;
+    }
+    if (!grid_barrier(g.gb, bar++, g.flags)) return;
+    // ---- 3: Ms[i][r] = M_b[a + r - 1][i] (transposed), Ws = W1[s]
+    double *Ms = wa_sm, *Ws = wa_sm + 64 * (WA_RC + 1);
+    for (int q = tid; q < 4096; q += 256) Ws[q] = __ldcg(W1s + q);
+    __syncthreads();
+    for (int ch = c; ch * WA_RC < n; ch += g.G) {
+      const int a = max(ch * WA_RC, r0), e = min(n, ch * WA_RC + WA_RC);
+      if (a >= e) continue;
+      const int len = e - a;
+      for (int q = tid; q < WA_RC * 64; q += 256) {
+        const int r = q >> 6, i = q & 63;
+        Ms[i * (WA_RC + 1) + r] = (r < len && i < nb) ? g.M[((int64_t)b * (n - 1) + (a + r - 1)) * 64 + i] : 0.0;
+      }
+      __syncthreads();
+      double upd[2][4] = {};
+      for (int i = 0; i < nb; ++i) {
+        double av[2], bv[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) av[u] = Ms[i * (WA_RC + 1) + ty + 16 * u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) bv[v] = Ws[i * 64 + tx + 16 * v];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) upd[u][v] = fma(av[u], bv[v], upd[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = ty + 16 * u;
+        if (r >= len) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int cc = tx + 16 * v;
+          if (cc < ncol) g.Y[(int64_t)(a + r) * k + col0 + cc] -= upd[u][v];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Ut[c][r] = X[r][c]
 template <typename T>
 __global__ void transpose_kernel(const T *__restrict__ X, int n, int k, double *__restrict__ Ut) {
@@ -913,7 +1030,7 @@ cudaError_t allow_max_dynamic_smem(const void *kernel, std::once_flag &flag) {
   });
   return result;
 }
-std::once_flag g_smem_hh[2], g_smem_bisect, g_smem_invit[2], g_smem_bounds, g_smem_wy;
+std::once_flag g_smem_hh[2], g_smem_bisect, g_smem_invit[2], g_smem_bounds, g_smem_wy, g_smem_wa;
 
 // Try the fused reduction in arithmetic T; false when it cannot be launched.
 template <typename T>
@@ -1055,9 +1172,11 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
   if (nref > 0) {
     const int nblk = (nref + WY_NB - 1) / WY_NB;
     const int nsplit_max = (int)((n + WY_KSPLIT - 1) / WY_KSPLIT);
+    // region 0 (w.wy_r0 doubles): W1's split partials and W1 for the
+    // block-at-a-time form, or the cooperative kernel's partials and W1
     T *W1p = reinterpret_cast<T *>(w.wy);                        // [nsplit][nb][k]
     T *W1 = W1p + (int64_t)nsplit_max * WY_NB * k;               // [nb][k]
-    T *Gs = W1 + (int64_t)WY_NB * k;                             // [nblk][nb][nb]
+    T *Gs = reinterpret_cast<T *>(w.wy) + w.wy_r0;               // [nblk][nb][nb]
     T *Tm = Gs + (int64_t)nblk * WY_NB * WY_NB;                  // [nblk][WY_NB][WY_NB]
     T *Mall = Tm + (int64_t)nblk * WY_NB * WY_NB;                // [nblk][n-1][WY_NB]
     {
@@ -1083,7 +1202,44 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
       if (e != cudaSuccess) return e;
     }
     *launches += 2;
-    for (int bi = nblk - 1; bi >= 0; --bi) {
+    // the blocks applied by one cooperative kernel when its CTAs fit at once
+    // and region 0 holds their partials; otherwise two GEMMs per block
+    bool applied = false;
+    if (sizeof(T) == sizeof(double)) {
+      int dev = 0, nsm = 0, coop = 0, per_sm = 0;
+      const int S = (k + 63) / 64;
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop && S <= nsm &&
+          allow_max_dynamic_smem((const void *)wy_apply_kernel, g_smem_wa) == cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)wy_apply_kernel, 256, WA_SMEM) ==
+              cudaSuccess && per_sm >= 1) {
+        int G = nsm / S;
+        while (G > 1 && (int64_t)(S * G + S) * 4096 > w.wy_r0) --G;
+        if ((int64_t)(S * G + S) * 4096 <= w.wy_r0) {
+          WyApplyArgs a;
+          a.V = reinterpret_cast<const double *>(V);
+          a.M = reinterpret_cast<const double *>(Mall);
+          a.Y = reinterpret_cast<double *>(X);
+          a.Wp = w.wy;
+          a.W1 = w.wy + (int64_t)S * G * 4096;
+          // the fused reduction's barrier word (that kernel has finished)
+          a.gb = reinterpret_cast<GridBar *>(w.grid_ws + 4 * (size_t)n + 2);
+          a.flags = flags;
+          a.n = n; a.k = k; a.nref = nref; a.nblk = nblk; a.G = G;
+          e = cudaMemsetAsync(a.gb, 0, sizeof(GridBar), s);
+          if (e != cudaSuccess) return e;
+          void *args[] = {&a};
+          e = cudaLaunchCooperativeKernel((const void *)wy_apply_kernel, dim3((unsigned)(S * G)), dim3(256), args,
+                                          WA_SMEM, s);
+          if (e != cudaSuccess) return e;
+          *launches += 1;
+          applied = true;
+        }
+      }
+      cudaGetLastError();
+    }
+    for (int bi = nblk - 1; bi >= 0 && !applied; --bi) {
       const int j0 = bi * WY_NB, nb = std::min(WY_NB, nref - j0);
       const int r0 = j0 + 1;
       const int64_t len = n - r0;

@@ -90,6 +90,7 @@ struct EigWork {
   double *lu = nullptr;                               // [5 n kcap] inverse-iteration scratch
   int *count = nullptr;                               // [2]
   double *wy = nullptr;                               // [WY scratch] see eig.cu
+  int64_t wy_r0 = 0;                                  // doubles of wy's first region (W1 scratch)
   double *grid_ws = nullptr;                          // [4 n + 2 n_sm + 8] fused-reduction scratch
   int *flags = nullptr;                               // device error flags
 };
