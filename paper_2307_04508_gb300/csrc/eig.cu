@@ -322,16 +322,31 @@ __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
     } else {
       const T *Pk = g.P + (size_t)((k - 1) & 1) * n;
       const T *pb = g.pub + (size_t)(k & 1) * n;
+      // p of step k-1 and the published row k into wv and x by every thread,
+      // its loads issued together: one L2 round trip, where the team's loop
+      // below (a global store between its loads) would wait once per element
+      for (int j0 = k + threadIdx.x; j0 < n; j0 += 4 * blockDim.x) {
+        T pv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * blockDim.x;
+          if (j < n) { pv[u] = __ldcg(Pk + j); xv[u] = __ldcg(pb + j); }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * blockDim.x;
+          if (j < n) { wv[j] = pv[u]; x[j] = xv[u]; }
+        }
+      }
+      __syncthreads();
+      const T pkk = wv[k];   // read before the team's second loop rewrites wv
       T dsum = 0;
       if (threadIdx.x < p1)
         for (int j = k + threadIdx.x; j < n; j += p1) {
           const T vj = (j == k) ? (T)1 : vprev[j] * sc_prev;   // normalise v_{k-1}
           vprev[j] = vj;
           if (b == 0) g.V[(int64_t)(k - 1) * n + j] = vj;
-          const T pj = __ldcg(Pk + j);
-          wv[j] = pj;
-          x[j] = __ldcg(pb + j);
-          dsum = fma(pj, vj, dsum);
+          dsum = fma(wv[j], vj, dsum);
         }
       if (warp < p1w) {
         dsum = warp_sum(dsum);
@@ -342,7 +357,7 @@ __global__ void __launch_bounds__(512, 1) hh_fused_kernel(HhFusedArgs<T> g) {
         T pv = 0;
         for (int q = 0; q < p1w; ++q) pv += wbuf[0][q];
         const T gam = (T)0.5 * tau_prev * pv;
-        const T wk = __ldcg(Pk + k) - gam;   // v_{k-1}[k] = 1
+        const T wk = pkk - gam;   // v_{k-1}[k] = 1
         for (int j = k + threadIdx.x; j < n; j += p1) {
           const T wj = wv[j] - gam * vprev[j];
           wv[j] = wj;
@@ -1092,14 +1107,17 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
     if (e != cudaSuccess) return e;
   }
   {
-    // one warp per block and at most 32 / BIS_L eigenvalues per warp, spread
-    // so that every SM gets work
+    // at most 32 / BIS_L eigenvalues per warp, spread so that every SM gets
+    // work; four warps per block, one per scheduler of the SM (the warps of
+    // one-warp blocks can share a scheduler, and each FP64 instruction holds
+    // it for the whole warp), with one copy of d and e^2 in shared memory
     int dev = 0, nsm = 148;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       nsm = 148;
     cudaGetLastError();
     const int epw = std::max(1, std::min(32 / BIS_L, (k + nsm - 1) / nsm));
-    bisect_kernel<<<(k + epw - 1) / epw, 32, smem, s>>>(w.d, w.p, w.scal, n, k, epw, w.lam);
+    const int nwarps = (k + epw - 1) / epw;
+    bisect_kernel<<<(nwarps + 3) / 4, 128, smem, s>>>(w.d, w.p, w.scal, n, k, epw, w.lam);
   }
   T *X = reinterpret_cast<T *>(w.X), *lu = reinterpret_cast<T *>(w.lu), *V = reinterpret_cast<T *>(w.V);
   {
