@@ -288,7 +288,7 @@ def run_gpu(args):
     # DRAM bytes per launch (read + write) from the ncu captures summarised in profiles/
     # (tc_tma_ts_pi_mid.md, hh_fused_double_mid.md); mid workload only
     traffic_pi = 112.52e6 + 44.94e6 if args.workload == "mid" and args.precision == "bf16x3" else None
-    traffic_tri = 26.0e6 + 0.01e6 if args.workload == "mid" else None
+    traffic_tri = 25.98e6 + 0.05e6 if args.workload == "mid" else None
     roof_pi = pi_roofline(args.precision, pi_flops, pi_ms, pk, src, traffic_pi)
     # Householder reduction of the N_aux x N_aux metric: 4/3 N^3 algorithmic flops,
     # N - 2 steps of one grid barrier each (latency-bound at mid size)
