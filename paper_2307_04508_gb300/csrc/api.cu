@@ -79,6 +79,10 @@ struct ltgw_ctx {
   int *flags = nullptr;
   bool timing = false;
   cudaEvent_t ev[EV_COUNT] = {};
+  // side stream for the copy of inputs first read late in the solve (B_tgt),
+  // forked from and joined back to the caller's stream by two events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   ltgw_stats stats{};
   int launches = 0;
   double pi_tc_flops = 0.0;
@@ -773,6 +777,13 @@ ltgw_status ltgw_create(ltgw_ctx **out, int device) {
     return LTGW_ERR_NOMEM;
   }
   for (auto &e : c->ev) cudaEventCreate(&e);
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ltgw_destroy(c);
+    return LTGW_ERR_DEVICE;
+  }
   *out = c;
   return LTGW_OK;
 }
@@ -787,6 +798,9 @@ void ltgw_destroy(ltgw_ctx *ctx) {
   ctx->a5.release();
   if (ctx->flags) cudaFree(ctx->flags);
   for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   delete ctx;
 }
 
@@ -965,8 +979,38 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   }
   copy_in(ctx, d_epsn, h_epsn.data(), T * sizeof(double), s);
   copy_in(ctx, d_shift, h_shift.data(), T * sizeof(double), s);
-  if (!bov_dev) copy_in(ctx, d_Bov, B_ov, (size_t)n_aux * n_ov_all * sizeof(double), s);
-  if (!btg_dev) copy_in(ctx, d_Btg, B_tgt, (size_t)T * n_aux * n_orb * sizeof(double), s);
+  // host B_ov: only the active pairs' columns cross the link (the frozen
+  // columns are never read)
+  if (!bov_dev && n_fc == 0) copy_in(ctx, d_Bov, B_ov, (size_t)n_aux * n_ov_all * sizeof(double), s);
+  if (!bov_dev && n_fc > 0)
+    LTGW_CUDA(ctx, cudaMemcpy2DAsync(d_Bov + (int64_t)n_fc * n_virt, (size_t)n_ov_all * sizeof(double),
+                                     B_ov + (int64_t)n_fc * n_virt, (size_t)n_ov_all * sizeof(double),
+                                     (size_t)n_ov * sizeof(double), (size_t)n_aux, cudaMemcpyDefault, s));
+  // host B_tgt is first read by the projections, after the NAF: its copy runs
+  // on the side stream meanwhile.  A solve that fails before the join waits
+  // for the copy, so the caller may release B_tgt when the call returns.
+  struct SideJoin {
+    ltgw_ctx *ctx = nullptr;
+    bool pending = false;
+    ltgw_status join(cudaStream_t s) {
+      if (!pending) return LTGW_OK;
+      pending = false;
+      LTGW_CUDA(ctx, cudaStreamWaitEvent(s, ctx->join_ev, 0));
+      return LTGW_OK;
+    }
+    ~SideJoin() {
+      if (pending) cudaStreamSynchronize(ctx->side);
+    }
+  } btg_join;
+  btg_join.ctx = ctx;
+  if (!btg_dev) {
+    LTGW_CUDA(ctx, cudaEventRecord(ctx->fork_ev, s));
+    LTGW_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
+    LTGW_CUDA(ctx, cudaMemcpyAsync(d_Btg, B_tgt, (size_t)T * n_aux * n_orb * sizeof(double), cudaMemcpyDefault,
+                                   ctx->side));
+    btg_join.pending = true;
+    LTGW_CUDA(ctx, cudaEventRecord(ctx->join_ev, ctx->side));
+  }
   if (ctx->status() != LTGW_OK) return ctx->status();
   CHECK_LAUNCH(ctx, launch_pair_gaps(d_eps, n_occ, n_virt, n_fc, d_delta, s), 1);
 
@@ -1010,6 +1054,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   }
   ctx->stats.n_naf = N;
   ctx->stats.naf_near_threshold = near;
+  if (btg_join.join(s) != LTGW_OK) return ctx->status();   // B_tgt is read from here on
 
   // ---- phase-2 workspace
   double *d_Bt = nullptr, *d_Btt = nullptr, *d_M = nullptr, *d_Pi, *d_X0, *d_X1, *d_C, *d_W, *d_sig, *d_eqp;
