@@ -1183,9 +1183,10 @@ cudaError_t eig_vectors_impl(EigWork &w, int n, int k, double *Ut, int *flags, c
   }
   // compact-WY back-transformation, blocks of WY_NB reflectors from the last:
   // Y <- Y - M_b (V_b^T Y) with M_b = V_b T_b.  Every block's G, T and M_b are
-  // formed first (the T recurrences in one launch, all M_b in one batched
-  // GEMM over rows 1..n-1; V carries WY_NB zero rows past its end for the
-  // last block), then the blocks are applied in order: two GEMMs each.
+  // formed first (every G in one launch, the T recurrences in one launch, all
+  // M_b in one batched GEMM over rows 1..n-1; V carries WY_NB zero rows past
+  // its end for the last block), then the blocks are applied in order: by one
+  // cooperative kernel, or two GEMMs each where that kernel cannot launch.
   const int nref = n - 2;  // reflectors 0 .. n-3
   if (nref > 0) {
     const int nblk = (nref + WY_NB - 1) / WY_NB;
