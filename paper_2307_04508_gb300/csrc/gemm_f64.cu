@@ -49,6 +49,9 @@ __device__ __forceinline__ void tile_accumulate(T acc[4][4], TileSmem<T> &sm, co
                                                 double p1) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
+  // micro-tile rows ty + 16 i (i < n_rows) lie inside M: the zero-padded rows
+  // of a tile at the edge do no FMAs (their accumulators are never stored)
+  const int n_rows = min(4, max(0, (M - m0 - ty + 15) / 16));
   for (int64_t k0 = 0; k0 < K; k0 += BK) {
     if (scale_mode != SCALE_NONE && tid < BK) {
       int64_t k = k0 + tid;
@@ -79,17 +82,34 @@ __device__ __forceinline__ void tile_accumulate(T acc[4][4], TileSmem<T> &sm, co
       sm.Bs[k][n] = v;
     }
     __syncthreads();
+    if (n_rows == 4) {
 #pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      T a[4], b[4];
+      for (int k = 0; k < BK; ++k) {
+        T a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sm.As[k][ty + 16 * i];
+        for (int i = 0; i < 4; ++i) a[i] = sm.As[k][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sm.Bs[k][tx + 16 * j];
+        for (int j = 0; j < 4; ++j) b[j] = sm.Bs[k][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    } else if (n_rows > 0) {   // the tile's last rows: only the valid ones
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        T b[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = sm.Bs[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (i < n_rows) {
+            const T a = sm.As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a, b[j], acc[i][j]);
+          }
+        }
+      }
     }
     __syncthreads();
   }
