@@ -32,22 +32,27 @@ __device__ __forceinline__ cplx operator/(cplx a, cplx b) {
 }
 
 // Sigma^c_n(i w_l) = -(1/pi) sum_m sum_j g_j z/(z^2 + w_j^2) W_nm(i w_j),
-// z = i w_l + e_F - e_m.  One block per (target, l); threads over m.
+// z = x + i w_l with x = e_F - e_m.  One block per (target, l); threads over
+// m.  With d = z^2 + w_j^2 = (x^2 - w_l^2 + w_j^2) + i 2 x w_l, the term is
+// z conj(d) / |d|^2: the parts that depend on m only are formed once per m,
+// leaving one real division per (m, j) (FP64 divisions and complex
+// arithmetic are what this kernel spends its time on).
 __global__ void sigma_kernel(SigmaArgs a) {
   const int t = blockIdx.y, l = blockIdx.x;
   const double wl = a.omega[l];
   double sre = 0.0, sim = 0.0;
   for (int m = threadIdx.x; m < a.n_orb; m += blockDim.x) {
-    const cplx z = mk(a.eps_F - a.eps_m[m], wl);
-    const cplx z2 = z * z;
+    const double x = a.eps_F - a.eps_m[m];
+    const double dre0 = x * x - wl * wl, dim = 2.0 * x * wl;
+    const double dim2 = dim * dim, wdim = wl * dim, xdim = x * dim;
     for (int j = 0; j < a.n_omega; ++j) {
       const double wj = a.omega[j];
       const double Wv = a.W[((int64_t)j * a.n_tgt + t) * a.n_orb + m];
-      cplx den = mk(z2.re + wj * wj, z2.im);
-      cplx q = z / den;
-      const double c = a.weight[j] * Wv;
-      sre = fma(c, q.re, sre);
-      sim = fma(c, q.im, sim);
+      const double dre = dre0 + wj * wj;
+      const double inv = 1.0 / fma(dre, dre, dim2);       // 1 / |d|^2
+      const double c = a.weight[j] * Wv * inv;
+      sre = fma(c, fma(x, dre, wdim), sre);              // Re z conj(d) = x dre + w_l dim
+      sim = fma(c, fma(wl, dre, -xdim), sim);            // Im z conj(d) = w_l dre - x dim
     }
   }
   __shared__ double sh_re[32], sh_im[32];
@@ -69,19 +74,28 @@ __global__ void sigma_kernel(SigmaArgs a) {
 
 constexpr int MAXP = 128;
 
+// 1 / t = conj(t) / |t|^2 (|t| stays far from the FP64 range limits here)
+__device__ __forceinline__ cplx crecip(cplx t) {
+  const double inv = 1.0 / fma(t.re, t.re, t.im * t.im);
+  return {t.re * inv, -t.im * inv};
+}
+
 // Continued fraction value and derivative at z, evaluated from the innermost
-// level outwards.
+// level outwards: t_p = 1 + a_p (z - z_{p-1}) / t_{p+1} and its derivative,
+// one complex reciprocal per level.
 __device__ void pade_eval(const cplx *a, const cplx *zn, int np, cplx z, cplx &val, cplx &dval) {
   cplx t = mk(1.0, 0.0), dt = mk(0.0, 0.0);
   for (int p = np - 1; p >= 1; --p) {
-    cplx num = a[p] * (z - zn[p - 1]);
-    cplx nt = mk(1.0, 0.0) + num / t;
-    cplx ndt = a[p] / t - num * dt / (t * t);
+    const cplx rt = crecip(t);
+    const cplx num = a[p] * (z - zn[p - 1]);
+    const cplx nt = mk(1.0, 0.0) + num * rt;
+    const cplx ndt = (a[p] - num * dt * rt) * rt;   // d/dz [num / t]
     t = nt;
     dt = ndt;
   }
-  val = a[0] / t;
-  dval = mk(0.0, 0.0) - a[0] * dt / (t * t);
+  const cplx rt = crecip(t);
+  val = a[0] * rt;
+  dval = mk(0.0, 0.0) - a[0] * dt * rt * rt;
 }
 
 // One thread per target: Pade coefficients through every pade_stride-th node,
