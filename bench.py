@@ -228,6 +228,19 @@ def pi_error_vs_fp64(ctx, prob, N, n_omega, prec, stream):
     return float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
 
 
+def replicas_value(total_ms, steps, world, dist=None, device="cpu"):
+    """Whole-job solves/s of `world` independent replicas, each timing `steps`
+    solves in total_ms: the slowest rank's time bounds the job (max over ranks
+    through `dist` when world > 1).  Returns (value, the max total_ms)."""
+    total_ms = float(total_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def run_gpu(args):
     import torch
     from paper_2307_04508_gb300 import ltgw
@@ -270,13 +283,7 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         step_ms, stats = _solve_loop(ctx, p, dev, out_dev, stream, flush, args.steps)
     e_main = out_dev[1].cpu().numpy().copy()
-    if dist:
-        t = torch.tensor([step_ms.sum()], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    else:
-        total_ms = float(step_ms.sum())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = replicas_value(step_ms.sum(), args.steps, world, dist, "cuda")
     st = stats[-1]
     launches = int(sum(x["kernel_launches"] for x in stats))
     N, n_ov = st["n_naf"], (prob.n_occ - prob.n_frozen) * prob.n_virt
