@@ -979,6 +979,17 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   }
   copy_in(ctx, d_epsn, h_epsn.data(), T * sizeof(double), s);
   copy_in(ctx, d_shift, h_shift.data(), T * sizeof(double), s);
+  // a solve that fails from here on waits for its stream before it returns,
+  // so that no copy from the caller's (possibly pinned) B_ov or B_tgt is
+  // still in flight when the call returns
+  struct SyncOnError {
+    ltgw_ctx *ctx;
+    cudaStream_t s;
+    bool active;
+    ~SyncOnError() {
+      if (active && ctx->status() != LTGW_OK) cudaStreamSynchronize(s);
+    }
+  } sync_on_error{ctx, s, !bov_dev || !btg_dev};
   // host B_ov: only the active pairs' columns cross the link (the frozen
   // columns are never read)
   if (!bov_dev && n_fc == 0) copy_in(ctx, d_Bov, B_ov, (size_t)n_aux * n_ov_all * sizeof(double), s);
