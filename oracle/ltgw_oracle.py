@@ -48,8 +48,10 @@ __all__ = [
     "gl_grid", "fermi_level", "active_ov", "naf_metric", "naf_basis", "naf_project",
     "pair_gaps", "polarizability_direct", "laplace_moments", "polarizability_lt",
     "screened_interaction", "w_nm", "sigma_iw", "pade_coefficients", "pade_eval",
-    "qp_newton", "solve", "sinc_laplace_grid", "pade_nodes",
-    "E4M3_MAX", "e4m3_round", "fp8_row_quantize", "pi_scale_table", "polarizability_fp8",
+    "qp_newton", "solve", "solve_projected", "occ_blocks", "naf_metric_blocked", "naf_project_blocked",
+    "solve_blocked", "sinc_laplace_grid", "pade_nodes",
+    "E4M3_MAX", "e4m3_round", "fp8_row_quantize", "fp8_row_split", "fp8_split_product", "pi_scale_table",
+    "polarizability_fp8",
     "cosine_grid", "tau_moments", "polarizability_tau", "evgw_energies", "evgw",
 ]
 
@@ -204,10 +206,12 @@ def polarizability_tau(M: np.ndarray, gamma: np.ndarray, spin: int = 2) -> np.nd
 # FP8 E4M3 form of the Pi contraction (per-auxiliary-row scales)
 # ----------------------------------------------------------------------------
 # Not a step of the paper: the low-precision variant of the Pi contraction.
-# Its plain definition: every operand value is rounded to the FP8 E4M3 grid
-# after a per-row scale that maps the row's largest magnitude to the largest
-# finite E4M3 value, and the products of the rounded values are summed
-# exactly.  The values fed to the rounding are formed in FP32 exactly as a
+# Its plain definition: every operand value, after a per-row scale that maps
+# the row's largest magnitude to the largest finite E4M3 value, is written as
+# a two-term E4M3 expansion x ~ h + l (h = e4m3(x), l = e4m3(x - h), both in
+# the row's scaled units), and the products h_a h_b + h_a l_b + l_a h_b of two
+# operands are summed exactly (l_a l_b, below the expansion's own error, is
+# left out).  The values fed to the rounding are formed in FP32 exactly as a
 # GPU forms them (FP32 copy of R~, FP32 per-pair scale, FP32 products), so
 # that both sides take every rounding decision on the same number.
 E4M3_MAX = 448.0
@@ -238,6 +242,31 @@ def fp8_row_quantize(X):
     return e4m3_round(X * inv[:, None]), inv
 
 
+def fp8_row_split(X):
+    """Per-row scaling onto the E4M3 grid as a two-term expansion: inv_r as in
+    fp8_row_quantize, xs = X_rj * inv_r (FP32), h = e4m3(xs), l = e4m3(xs - h)
+    (the difference is exact in FP32).  X ~ (h + l) / inv_r.  Returns (h, l as
+    float64, inv as float32)."""
+    X = np.asarray(X, dtype=np.float32)
+    m = np.abs(X).max(axis=1)
+    inv = np.zeros_like(m)
+    nz = m > 0
+    inv[nz] = np.float32(E4M3_MAX) / m[nz]
+    xs = (X * inv[:, None]).astype(np.float32).astype(np.float64)
+    h = e4m3_round(xs)
+    return h, e4m3_round(xs - h), inv
+
+
+def fp8_split_product(A, B):
+    """(h_A h_B^T + h_A l_B^T + l_A h_B^T) / (inv_A inv_B^T) for the two-term
+    expansions of the rows of A and B (fp8_row_split), summed exactly."""
+    ha, la, ia = fp8_row_split(A)
+    hb, lb, ib = fp8_row_split(B)
+    da = np.where(ia > 0, ia, 1.0).astype(np.float64)
+    db = np.where(ib > 0, ib, 1.0).astype(np.float64)
+    return (ha @ hb.T + ha @ lb.T + la @ hb.T) / da[:, None] / db[None, :]
+
+
 def pi_scale_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
     """Per-pair factors in FP32: Delta / (w_j^2 + Delta^2) per frequency (Eq. Pi),
     w_m Delta exp(-Delta^2 x_m) per Laplace point (the M^m form) or
@@ -255,19 +284,15 @@ def pi_scale_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
 def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None, tau=None, gamma=None) -> np.ndarray:
     """Pi in the FP8 E4M3 form: B32 = fp32(R~); for each frequency (Eq. Pi) or
     Laplace point (M^m form) with FP32 factors s_k, A_k = fp32(B32 * s_k);
-    A_k and B32 are quantised per auxiliary row (fp8_row_quantize) and
-    M_k = (qA_k / invA_k) (qB / invB)^T summed exactly, lower triangle
-    mirrored; then Pi as in polarizability_direct, polarizability_lt or (tau,
-    gamma) polarizability_tau."""
+    M_k = fp8_split_product(A_k, B32) (two-term E4M3 expansions per auxiliary
+    row, three products summed exactly), lower triangle mirrored; then Pi as
+    in polarizability_direct, polarizability_lt or (tau, gamma)
+    polarizability_tau."""
     B32 = np.asarray(Bt, dtype=np.float32)
     S = pi_scale_table(delta, omegas, x, w, tau)
-    qb, invb = fp8_row_quantize(B32)
-    Bd = qb / np.where(invb > 0, invb, 1.0).astype(np.float64)[:, None]
     M = np.empty((len(S), B32.shape[0], B32.shape[0]))
     for k in range(len(S)):
-        qa, inva = fp8_row_quantize(B32 * S[k][None, :])
-        Ad = qa / np.where(inva > 0, inva, 1.0).astype(np.float64)[:, None]
-        Mk = Ad @ Bd.T
+        Mk = fp8_split_product((B32 * S[k][None, :]).astype(np.float32), B32)
         # qA qB^T is not exactly symmetric (the two operands carry different
         # scales): the lower triangle (P >= Q) is formed and mirrored
         M[k] = np.tril(Mk) + np.tril(Mk, -1).T
@@ -400,11 +425,8 @@ def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=2
     targets = np.asarray(targets)
     if np.any(targets < n_frozen):
         raise ValueError("frozen-core orbitals cannot be targets")
-    omegas, weights = gl_grid(n_omega, omega0)
-    eF = fermi_level(eps, n_occ)
     B_act = active_ov(B_ov, n_occ, n_virt, n_frozen)
-    delta = pair_gaps(eps, n_occ, n_virt, n_frozen)
-    inter = {"omegas": omegas, "weights": weights, "eps_F": eF}
+    inter = {}
     if naf_thresh >= 0.0:
         K = naf_metric(B_act)
         U, lam_kept, lam_all = naf_basis(K, naf_thresh)
@@ -415,6 +437,26 @@ def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=2
         Bt = B_act
         Bt_tgt = np.ascontiguousarray(B_tgt[:, :, n_frozen:])
         inter.update(U=None, n_naf=Bt.shape[0])
+    out = solve_projected(eps, Bt, Bt_tgt, targets, shift, n_occ, n_virt, n_frozen, n_omega, omega0, spin,
+                          tau_x, tau_w, return_all, cos_tau, cos_gamma, eps_qp_ref)
+    if return_all:
+        out[3].update(inter)
+    return out
+
+
+def solve_projected(eps, Bt, Bt_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=24, omega0=0.5,
+                    spin=2, tau_x=None, tau_w=None, return_all=False, cos_tau=None, cos_gamma=None,
+                    eps_qp_ref=None):
+    """The solve after the NAF step: Pi, the screening, W_nm, Sigma(i w), the
+    Pade fraction and Newton, from the active-pair block Bt [N][n_act*n_virt]
+    (in the NAF basis, or the raw block without NAF) and the targets' blocks
+    Bt_tgt [T][N][m] over the active orbitals m.  Other arguments as `solve`."""
+    eps = np.asarray(eps, dtype=np.float64)
+    targets = np.asarray(targets)
+    omegas, weights = gl_grid(n_omega, omega0)
+    eF = fermi_level(eps, n_occ)
+    delta = pair_gaps(eps, n_occ, n_virt, n_frozen)
+    inter = {"omegas": omegas, "weights": weights, "eps_F": eF}
     if cos_tau is not None:
         M = tau_moments(Bt, delta, np.asarray(cos_tau))
         Pi = polarizability_tau(M, np.asarray(cos_gamma), spin)
@@ -443,6 +485,61 @@ def solve(eps, B_ov, B_tgt, targets, shift, n_occ, n_virt, n_frozen=0, n_omega=2
         inter.update(Bt=Bt, Bt_tgt=Bt_tgt, Pi=Pi, C=C, W=W, pade=np.array(coefs), delta=delta)
         return sig, e_qp, status, inter
     return sig, e_qp, status
+
+
+# ----------------------------------------------------------------------------
+# The same solve for an RI tensor supplied one block of occupied orbitals at a
+# time (Eqs. nafeq and naftrafo: K is a sum over the active pairs, so it is
+# summed block by block; the projection acts column by column)
+# ----------------------------------------------------------------------------
+def occ_blocks(n_occ: int, n_frozen: int, occ_block: int):
+    """The active occupied ranges [i0, i1) of occ_block orbitals (the last may be shorter)."""
+    return [(i0, min(n_occ, i0 + occ_block)) for i0 in range(n_frozen, n_occ, occ_block)]
+
+
+def naf_metric_blocked(ov_block, blocks) -> np.ndarray:
+    """K_PQ = sum over blocks of sum_{ia in block} R^P_ia R^Q_ia; ov_block(i0, i1)
+    returns R [P][(i - i0) n_virt + a] for i0 <= i < i1."""
+    K = None
+    for i0, i1 in blocks:
+        R = ov_block(i0, i1)
+        K = naf_metric(R) if K is None else K + naf_metric(R)
+    return K
+
+
+def naf_project_blocked(ov_block, blocks, U: np.ndarray, n_virt: int) -> np.ndarray:
+    """R~ = U^T R for the active pairs, assembled block by block: [N][n_act n_virt]."""
+    n_pairs = sum(i1 - i0 for i0, i1 in blocks) * n_virt
+    out = np.empty((U.shape[1], n_pairs))
+    c = 0
+    for i0, i1 in blocks:
+        R = ov_block(i0, i1)
+        out[:, c:c + R.shape[1]] = naf_project(R, U)
+        c += R.shape[1]
+    return out
+
+
+def solve_blocked(eps, ov_block, B_tgt, targets, shift, n_occ, n_virt, n_frozen, occ_block, n_omega=24,
+                  omega0=0.5, naf_thresh=0.0, spin=2, tau_x=None, tau_w=None, return_all=False):
+    """`solve` with B_ov supplied by ov_block(i0, i1) for the active occupied
+    blocks of occ_block orbitals (NAF required, naf_thresh >= 0): K summed over
+    the blocks, then the kept eigenvectors, the blockwise projection and
+    solve_projected.  Other arguments as `solve`."""
+    if naf_thresh < 0.0:
+        raise ValueError("solve_blocked needs NAF (naf_thresh >= 0)")
+    targets = np.asarray(targets)
+    if np.any(targets < n_frozen):
+        raise ValueError("frozen-core orbitals cannot be targets")
+    blocks = occ_blocks(n_occ, n_frozen, occ_block)
+    K = naf_metric_blocked(ov_block, blocks)
+    U, lam_kept, lam_all = naf_basis(K, naf_thresh)
+    Bt = naf_project_blocked(ov_block, blocks, U, n_virt)
+    Bt_tgt = np.stack([naf_project(B_tgt[t][:, n_frozen:], U) for t in range(len(targets))])
+    out = solve_projected(eps, Bt, Bt_tgt, targets, shift, n_occ, n_virt, n_frozen, n_omega, omega0, spin,
+                          tau_x, tau_w, return_all)
+    if return_all:
+        out[3].update(K=K, U=U, lam=lam_all, n_naf=U.shape[1])
+    return out
 
 
 # ----------------------------------------------------------------------------

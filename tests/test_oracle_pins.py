@@ -275,3 +275,30 @@ def test_pade_node_choice_is_well_conditioned(tiny):
             a = O.pade_coefficients(zn, sig[t][sel] * (1 + noise))
             E, s = O.qp_newton(tiny.eps[n], tiny.shift[t], it["eps_F"], zn, a)
             assert s == 0 and abs(E - e[t]) < 1e-10
+
+
+# ---------------------------------------------------------------- blocked (streamed) form
+@pytest.mark.parametrize("occ_block", [1, 3, 7])
+def test_blocked_solve_equals_whole_solve(occ_block):
+    """K summed over occupied blocks and R~ projected block by block (the form
+    the large workload needs) give the pinned whole-tensor solve, with a
+    ragged last block, frozen core and a truncating threshold."""
+    prob = S.make_problem(9, 40, 90, n_frozen=2, seed=77, n_targets=4)
+    nv = prob.n_virt
+
+    def ov_block(i0, i1):
+        return prob.B_ov[:, i0 * nv:i1 * nv]
+
+    kw = dict(n_omega=16, naf_thresh=1e-3)
+    x, w = O.sinc_laplace_grid(8, -8.0, 2.0)
+    for tau in (None, (x, w)):
+        tx, tw = (None, None) if tau is None else tau
+        sa, ea, sta, ia = O.solve(prob.eps, prob.B_ov, prob.B_tgt, prob.targets, prob.shift, 9, nv, 2,
+                                  tau_x=tx, tau_w=tw, return_all=True, **kw)
+        sb, eb, stb, ib = O.solve_blocked(prob.eps, ov_block, prob.B_tgt, prob.targets, prob.shift, 9, nv, 2,
+                                          occ_block, tau_x=tx, tau_w=tw, return_all=True, **kw)
+        assert ia["n_naf"] == ib["n_naf"] < 90
+        assert np.all(sta == 0) and np.all(stb == 0)
+        assert np.abs(ea - eb).max() < 1e-12
+        assert np.abs(sa - sb).max() < 1e-12 * np.abs(sa).max()
+    assert O.occ_blocks(9, 2, occ_block)[0][0] == 2 and O.occ_blocks(9, 2, occ_block)[-1][1] == 9
