@@ -17,17 +17,25 @@ namespace {
 // Two sweep buffers of LTGW_SCREEN_STATIC_MAX_ELEMS doubles each, then flags.
 constexpr size_t kMaxElems = LTGW_SCREEN_STATIC_MAX_ELEMS;
 constexpr size_t kFlagDoubles = 8;  // room for ltgw::FLAG_COUNT ints
+static_assert(ltgw::FLAG_COUNT * sizeof(int) <= kFlagDoubles * sizeof(double),
+              "the flag tail of the scratch array must hold every device flag");
 static __device__ __align__(256) double g_screen_scratch[2 * kMaxElems + kFlagDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double *g_scratch_addr[kMaxDevices] = {};  // device address of g_screen_scratch, per device
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the array's name in host code is only a stand-in).
-cudaError_t scratch_address(int dev, double **out) {
+// Device address of the scratch array on the current device.  The array's
+// name in host code is only a stand-in, so the address is looked up with
+// cudaGetSymbolAddress: on every call made outside stream capture (a device
+// reset or a re-created primary context reloads the module and moves the
+// array), and from the per-device cache while `s` is capturing, where the
+// lookup's implicit module load must not run.
+cudaError_t scratch_address(int dev, cudaStream_t s, double **out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cudaGetLastError();
+  if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_screen_scratch);
     if (e != cudaSuccess) return e;
@@ -48,12 +56,12 @@ extern "C" ltgw_status ltgw_screen_static(int N, int n_omega, const double *Pi, 
     cudaGetLastError();
     return LTGW_ERR_DEVICE;
   }
+  cudaStream_t s = (cudaStream_t)stream;
   double *base = nullptr;
-  if (scratch_address(dev, &base) != cudaSuccess) {
+  if (scratch_address(dev, s, &base) != cudaSuccess) {
     cudaGetLastError();
     return LTGW_ERR_DEVICE;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   double *X0 = base, *X1 = base + kMaxElems;
   int *flags = reinterpret_cast<int *>(base + 2 * kMaxElems);
   // the array keeps the previous call's contents: the flags must start at zero

@@ -7,7 +7,8 @@ latency-sensitive caller that cannot afford cudaMalloc/cudaFree, which may
 block and synchronise the device.  ltgw_screen_static serves them with scratch
 held in a fixed device array inside the library.  These tests call it through
 the C ABI twice in a row and compare each result with the ordinary entry
-point, ltgw_screen, at the tolerance the screening parity test uses.
+point, ltgw_screen, and with the oracle's Cholesky route, at the tolerance the
+screening parity test uses.
 
 This file is named so that pytest collects it last.
 """
@@ -49,6 +50,9 @@ def test_static_screening_matches_allocating_entry_point_twice():
             a, b = C_static.cpu().numpy(), C_ref.cpu().numpy()
             assert np.all(np.isfinite(a))
             assert np.abs(a - b).max() <= TOL * np.abs(b).max()
+            # and against the oracle's Cholesky route, the definition itself
+            c = O.screened_interaction(Pi.cpu().numpy())
+            assert np.abs(a - c).max() <= TOL * np.abs(c).max()
     finally:
         ctx.close()
 
