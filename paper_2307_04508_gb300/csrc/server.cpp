@@ -3,10 +3,13 @@
 //
 // Each slot owns an ltgw context and a non-blocking CUDA stream, and runs one
 // solve at a time on a host thread of its own, so the kernels of different
-// requests overlap on the device.  A request is admitted, in arrival order,
-// as soon as a slot is free and its estimated device footprint fits in what
-// the budget leaves after the requests already running; completions record
-// the queueing, service and total latency of every request.
+// requests overlap on the device.  A request is admitted as soon as a slot is
+// free and its estimated device footprint fits in what the budget leaves
+// after the requests already running.  Admission goes in arrival order, but a
+// request that does not fit may be passed by later ones that do, at most
+// kMaxBypass times: after that nothing is admitted ahead of it, so a large
+// request waits for memory to drain instead of starving behind small ones.
+// Completions record the queueing, service and total latency of every request.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,6 +17,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <list>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -30,7 +34,10 @@ struct Pending {
   ltgw_request req{};
   size_t footprint = 0;
   Clock::time_point t_submit;
+  int bypassed = 0;   // later requests admitted ahead of this one
 };
+
+constexpr int kMaxBypass = 8;
 
 struct Slot {
   std::thread th;
@@ -51,7 +58,7 @@ struct ltgw_server {
   size_t retained = 0;   // workspace kept by the slots between requests
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Pending> queue;
+  std::list<Pending> queue;   // erasing one request keeps pointers to the others valid
   std::vector<std::unique_ptr<Slot>> slots;
   std::deque<ltgw_completion> done;
   int running = 0;
@@ -61,21 +68,32 @@ struct ltgw_server {
   int init_pending = 0;
   Clock::time_point t_created = Clock::now();
 
-  // Admit queued requests in arrival order while a slot is free and the head
-  // fits in the remaining budget.  Caller holds mu.
+  // Admit queued requests while a slot is free: the oldest that fits in the
+  // remaining budget first; a request that does not fit is passed (and
+  // counted) until it has been passed kMaxBypass times, after which the scan
+  // stops at it.  With nothing running, the oldest request is admitted
+  // whatever its footprint.  Caller holds mu.
   void dispatch_locked() {
-    while (!queue.empty()) {
-      Pending &head = queue.front();
-      if (in_flight + retained + head.footprint > budget && running > 0) return;
+    std::vector<Pending *> passed;
+    auto it = queue.begin();
+    while (it != queue.end()) {
       Slot *free_slot = nullptr;
       for (auto &s : slots)
         if (!s->has_job && !busy_slot(s.get())) { free_slot = s.get(); break; }
       if (!free_slot) return;
-      free_slot->job = head;
+      const bool fits = in_flight + retained + it->footprint <= budget || running == 0;
+      if (!fits) {
+        if (it->bypassed >= kMaxBypass) return;
+        passed.push_back(&*it);
+        ++it;
+        continue;
+      }
+      for (Pending *q : passed) ++q->bypassed;
+      free_slot->job = *it;
       free_slot->has_job = true;
-      in_flight += head.footprint;
+      in_flight += it->footprint;
       ++running;
-      queue.pop_front();
+      it = queue.erase(it);
       cv_work.notify_all();
     }
   }

@@ -110,3 +110,30 @@ def test_trim_releases_the_workspace():
         assert np.array_equal(outs[0], outs[1])
     finally:
         c.close()
+
+
+def test_request_that_does_not_fit_is_passed_a_bounded_number_of_times():
+    """Two slots; a medium request runs, a large one arrives that does not fit
+    beside it (or beside any small one), then ten small ones that do: the
+    small ones pass the large one exactly eight times (the server's bound),
+    after which it is admitted as soon as nothing else runs, before the
+    remaining small ones."""
+    from paper_2307_04508_gb300 import ltgw, serving
+
+    def req(i, n_occ, n_virt, n_aux):
+        return dict(index=i, n_occ=n_occ, n_frozen=n_occ // 6, n_virt=n_virt, n_aux=n_aux, n_targets=4,
+                    seed=900 + i, t_arrival=0.0)
+    reqs = [req(0, 30, 240, 810), req(1, 40, 320, 1080)] + [req(2 + i, 6, 48, 162) for i in range(10)]
+    fp = [ltgw.request_footprint(serving.request_params(r, ltgw.LTGW_FP64), 4) for r in reqs]
+    budget = fp[1] + (8 << 20)
+    assert fp[0] + fp[2] <= budget < fp[0] + fp[1] and fp[1] + fp[2] > budget
+    inputs = [serving.ingest(r, device=False) for r in reqs]
+    srv = ltgw.Server(0, n_slots=2, hbm_budget_bytes=budget)
+    try:
+        recs, _, _ = serving.run_stream(srv, reqs, ltgw.LTGW_FP64, honor_arrivals=False, inputs=inputs)
+    finally:
+        srv.close()
+    assert all(recs[r["index"]]["status"] in (ltgw.LTGW_OK, ltgw.LTGW_ERR_NO_CONVERGE) for r in reqs)
+    big_start = recs[1]["start_ms"]
+    passed = sum(1 for r in reqs[2:] if recs[r["index"]]["start_ms"] < big_start)
+    assert passed == 8, passed
