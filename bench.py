@@ -4,15 +4,19 @@ One step = one whole G0W0 solve through the C ABI: frozen-core slice, NAF
 metric + eigensolver + projection, Laplace grid, Pi(tau_k) moments and their
 frequency recombination, screening, W_nm, Sigma(i w), Pade and Newton.
 
-Workload (default): the mid-size synthetic system, 60 occupied orbitals (10
-frozen), 540 virtual, 1800 auxiliary functions, NAF at 1e-2, 32
-Gauss-Legendre frequencies, 8 Laplace points, 10 quasi-particle states.
-Default form: mixed precision (split-BF16 tensor-core contractions, FP64
-eigensolver / screening / Pade / Newton); the plain FP64 form is timed on the
-same inputs beside it and the QP deviation between the two is reported.
+Workload (default, --workload large): the large synthetic system, 320
+occupied orbitals (60 frozen), 3500 virtual, 9000 auxiliary functions, NAF at
+1e-2, 32 Gauss-Legendre frequencies, 10 Laplace points, 20 quasi-particle
+states, the RI tensor streamed by blocks of occupied orbitals.  Default form:
+mixed precision (split-BF16 tensor-core contractions, FP64 eigensolver /
+screening / Pade / Newton); the plain FP64 form is timed on the same inputs
+beside it, and both forms' quasi-particle energies are compared with the
+oracle's stored results for this workload.  --workload mid / tiny: the smaller
+systems (whole tensor resident).
 
 Prints one JSON line.  --impl reference times the CPU oracle (direct AC-GW,
-FP64, numpy) on the same workload instead.
+FP64, numpy) on the same workload instead (large: a bounded sample per step,
+extrapolated to one solve).
 """
 from __future__ import annotations
 
@@ -38,18 +42,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="mid", choices=["tiny", "mid", "large", "serving", "sweep"])
+    ap.add_argument("--workload", default="large",
+                    choices=["tiny", "mid", "large", "serving", "sweep", "eig", "request"])
+    ap.add_argument("--req-occ", type=int, default=8,
+                    help="request: n_occ of one serving-law request (launch-overhead measurement)")
+    ap.add_argument("--eig-n", type=int, default=9000,
+                    help="eig: size of the NAF metric whose eigensolver is timed (profiling workload)")
     ap.add_argument("--sweep-size", default="mid", choices=["mid", "large"],
                     help="sweep: the workload whose GL x Laplace grids are swept")
     ap.add_argument("--occ-block", type=int, default=20, help="large: occupied orbitals per streamed block")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=None,
                     help="serving: Poisson arrival rate (requests/s); default 0.7 x the mixed form's measured "
-                         "capacity (back-to-back throughput of the stream's first --compare-prefix requests)")
+                         "capacity (the whole stream closed loop)")
     ap.add_argument("--slots", type=int, default=4, help="serving: server worker slots")
-    ap.add_argument("--compare-prefix", type=int, default=32,
-                    help="serving: requests of the stream solved back to back in both forms for the ratio")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="large: skip the end-to-end (host inputs) measurement")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="large: skip the plain FP64 form's solve (about three minutes) beside the timed form")
     ap.add_argument("--no-autotune", action="store_true",
                     help="mid / large: fixed contraction configurations instead of the library's autotuner")
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "fp8", "fp8pi"],
@@ -59,9 +69,15 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, req_occ=8):
+    """tiny / mid, or "request": one request of the serving law with n_occ = req_occ
+    (frozen n_occ // 6, n_virt = 10 n_occ, N_aux = 3 (n_occ + n_virt), 4 states)."""
     from paper_2307_04508_gb300 import synthetic as S
-    cfg = dict(S.MID if name == "mid" else S.TINY)
+    if name == "request":
+        cfg = dict(n_occ=req_occ, n_frozen=req_occ // 6, n_virt=10 * req_occ, n_aux=33 * req_occ,
+                   seed=20230720 + req_occ, n_targets=4, n_omega=32, n_tau=8, naf_thresh=1e-2)
+    else:
+        cfg = dict(S.MID if name == "mid" else S.TINY)
     prob = S.make_workload(cfg)
     desc = (f"{name}: n_occ={cfg['n_occ']} ({cfg['n_frozen']} frozen), n_virt={cfg['n_virt']}, "
             f"N_aux={cfg['n_aux']}, NAF eps={cfg['naf_thresh']}, N_omega={cfg['n_omega']}, "
@@ -135,8 +151,35 @@ def oracle_solve(prob, cfg):
 
 
 def run_reference(args):
+    """The oracle (direct AC-GW, numpy FP64) on this host's cores, rank 0 only.
+    mid / tiny: whole solves.  large: each step is the bounded sample of
+    cpu_oracle_sample (half an occupied orbital's pairs), extrapolated to one
+    solve; N_NAF is taken from the oracle's stored results for this workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    cores = os.cpu_count()
+    if args.workload == "large":
+        from paper_2307_04508_gb300 import synthetic as S
+        cfg = S.LARGE
+        gold = golden_large()
+        n_naf = gold["n_naf"] if gold else 2258
+        prep = None
+        for _ in range(args.warmup):
+            _, _, _, prep, _ = cpu_oracle_sample(cfg, n_naf, frac=0.5, prep=prep)
+        secs, desc = [], ""
+        for _ in range(args.steps):
+            sec, _, desc, prep, _ = cpu_oracle_sample(cfg, n_naf, frac=0.5, prep=prep)
+            secs.append(sec)
+        v = len(secs) / sum(secs)
+        line = {"impl": "reference", "metric": "G0W0 solves/s", "value": v, "unit": "solves/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * np.mean(secs),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": LARGE_DESC, "form": "CPU oracle, direct AC-GW (no LT)"},
+                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"each step: {desc}"},
+                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     cfg, prob, desc = workload(args.workload)
     for _ in range(args.warmup):
@@ -147,7 +190,6 @@ def run_reference(args):
         oracle_solve(prob, cfg)
         ts.append(time.perf_counter() - t0)
     v = len(ts) / sum(ts)
-    cores = os.cpu_count()
     line = {"impl": "reference", "metric": "G0W0 solves/s", "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -190,15 +232,16 @@ def pi_roofline(prec, pi_flops, pi_ms, pk, src, traffic=None):
                 "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
                 "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": traffic}
     if prec in ("fp8", "fp8pi"):
-        a = pi_flops / (pi_ms / 1e3) / 1e12
+        a = 3 * pi_flops / (pi_ms / 1e3) / 1e12
         peak = 2.0 * pk["bf16_tflops"]
         return {"bound": "tensor", "kernel": "tc_fp8_kernel (Pi(tau_k) moments, FP8 E4M3 tcgen05 kind::f8f6f4)",
                 "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                 "peak_source": f"2 x bf16_tflops (the nominal fp8 / bf16 dense ratio, 4.5 / 2.25 PFLOP/s) of {src} "
                                "MEASURED_PEAKS.json",
-                "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": traffic,
-                "note": "algorithmic flops (SYRK as N^2 K); the padded 128 x 128 tiles do more MMA work; the "
-                        "quantisation pass before the kernel is not in ms_per_launch"}
+                "flops_per_launch": 3 * pi_flops, "ms_per_launch": pi_ms, "traffic": traffic,
+                "note": "algorithmic flops (SYRK as N^2 K, three E4M3 products per useful one: the two-term "
+                        "expansions); the padded 128 x 128 tiles do more MMA work; the quantisation pass before "
+                        "the kernel is not in ms_per_launch"}
     tc = 3 * pi_flops / (pi_ms / 1e3) / 1e12
     return {"bound": "tensor", "kernel": "tc_tma_ts_kernel (Pi(tau_k) moments, split-BF16 tcgen05, A in TMEM)",
             "achieved": tc, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tc / pk["bf16_tflops"],
@@ -253,7 +296,7 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg, prob, desc = workload(args.workload)
+    cfg, prob, desc = workload(args.workload, args.req_occ)
     ctx = ltgw.Context(local)
     ctx.set_autotune(not args.no_autotune)   # the warm-up solves time and fix the configurations
     stream = torch.cuda.Stream()
@@ -308,7 +351,7 @@ def run_gpu(args):
                 "flops_per_launch": tri_flops, "ms_per_launch": tri_ms,
                 "us_per_step": 1e3 * tri_ms / max(1, prob.n_aux - 2),
                 "note": "full-storage fused form does 2 N^3 FP64 flops (the 4/3 N^3 counted here exploit "
-                        "symmetry); one grid barrier (1.2 us measured alone) and three block barriers per "
+                        "symmetry); one grid barrier (1.2 us measured alone) and five block barriers per "
                         "reflector on top",
                 "traffic": traffic_tri}
     roofline = roof_tri if tri_ms > pi_ms else roof_pi
@@ -392,159 +435,334 @@ def run_gpu(args):
 def run_serving(args):
     """The serving stream: requests of mixed sizes (n_occ log-uniform in [8, 200],
     N_aux = 3 (n_occ + n_virt)) arriving as a Poisson process, inputs generated on
-    the device at arrival, admitted onto the request server's slots."""
+    the device at arrival, admitted onto the request server's slots.  The same
+    stream (same requests, same arrival times) is served in the mixed form and
+    in the plain FP64 form; the arrival rate is 0.7 x the mixed form's capacity
+    (the whole stream closed loop)."""
     import torch
     from paper_2307_04508_gb300 import ltgw, serving
     from paper_2307_04508_gb300 import synthetic as S
 
     rank = int(os.environ.get("RANK", "0"))
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    reqs = S.serving_stream(args.requests, rate_hz=args.rate or 1.0)   # sizes do not depend on the rate
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     # the server's admission budget and the ingest thread's budget for generated
     # inputs share the device: 55 % + 15 % of it, leaving room for the contexts
     total = torch.cuda.get_device_properties(0).total_memory
     budget, ingest_budget = int(0.55 * total), int(0.15 * total)
-    # same prefix of the stream, back to back, in both forms: the throughput ratio
-    pre = reqs[:min(args.compare_prefix, len(reqs))]
-    inputs = [serving.ingest(r, device=True) for r in pre]
-    cmp = {}
-    for name, prec in (("bf16x3", ltgw.LTGW_BF16X3), ("fp64", ltgw.LTGW_FP64)):
+    mixed_prec = PREC[args.precision] if args.precision != "fp64" else ltgw.LTGW_BF16X3
+
+    def serve(reqs, prec, clk=None):
         srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
         try:
-            recs, wall, _ = serving.run_stream(srv, pre, prec, honor_arrivals=False, inputs=inputs)
+            recs, wall, ingest_s = serving.run_stream_pipelined(srv, reqs, prec, mem_budget_bytes=ingest_budget)
         finally:
             srv.close()
-        cmp[name] = {"solves_per_s": len(recs) / wall, "e": {k: v["e_qp"].copy() for k, v in recs.items()},
-                     "ok": all(v["status"] in (0, 4) for v in recs.values())}
-    dev = max(np.abs(cmp["bf16x3"]["e"][k] - cmp["fp64"]["e"][k]).max() for k in cmp["fp64"]["e"]) * HA2MEV
-    del inputs
-    torch.cuda.empty_cache()
-    # capacity: the whole stream closed loop (all arriving at once) with its inputs
-    # generated on the device as in the open-loop run, mixed form
-    srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
-    try:
-        burst = S.serving_stream(len(reqs), rate_hz=1e9)
-        recs_c, wall_c, _ = serving.run_stream_pipelined(srv, burst, ltgw.LTGW_BF16X3, mem_budget_bytes=ingest_budget)
-    finally:
-        srv.close()
+        return recs, wall, ingest_s
+
+    # capacity: the whole stream closed loop (all arriving at once), mixed form
+    burst = S.serving_stream(args.requests, rate_hz=1e9)
+    recs_c, wall_c, _ = serve(burst, mixed_prec)
     capacity = len(recs_c) / wall_c
     rate = args.rate if args.rate else 0.7 * capacity
     reqs = S.serving_stream(args.requests, rate_hz=rate)
-    # the whole stream, open loop at the arrival rate, mixed form
-    srv = ltgw.Server(0, n_slots=args.slots, hbm_budget_bytes=budget)
-    try:
-        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-            recs, wall, ingest_s = serving.run_stream_pipelined(srv, reqs, ltgw.LTGW_BF16X3,
-                                                                mem_budget_bytes=ingest_budget)
-    finally:
-        srv.close()
-    sm = serving.summarize(recs, wall, ingest_s)
-    failures = [{"index": k, "status": v.get("status"), "message": v.get("message", ""),
-                 "n_occ": reqs[k]["n_occ"], "n_virt": reqs[k]["n_virt"], "n_aux": reqs[k]["n_aux"]}
-                for k, v in recs.items() if v.get("status") not in (ltgw.LTGW_OK, ltgw.LTGW_ERR_NO_CONVERGE)]
+    out = {}
+    with ClockSampler(local) as clk:
+        for name, prec in (("mixed", mixed_prec), ("fp64", ltgw.LTGW_FP64)):
+            recs, wall, ingest_s = serve(reqs, prec)
+            sm = serving.summarize(recs, wall, ingest_s)
+            out[name] = {"recs": recs, "summary": sm}
+    failures = [{"form": name, "index": k, "status": v.get("status"), "message": v.get("message", "")}
+                for name in out for k, v in out[name]["recs"].items()
+                if v.get("status") not in (ltgw.LTGW_OK, ltgw.LTGW_ERR_NO_CONVERGE)]
+    dev = max(float(np.abs(out["mixed"]["recs"][k]["e_qp"] - out["fp64"]["recs"][k]["e_qp"]).max())
+              for k in out["fp64"]["recs"]) * HA2MEV
+    sm, s64 = out["mixed"]["summary"], out["fp64"]["summary"]
+
+    def lat(x):
+        return {"p50": x["p50_ms"], "p99": x["p99_ms"], "p50_from_arrival": x.get("p50_from_arrival_ms"),
+                "p99_from_arrival": x.get("p99_from_arrival_ms"), "service_p50": x["service_p50_ms"]}
     line = {"metric": "G0W0 solves/s (serving stream)", "value": sm["solves_per_s"], "unit": "solves/s",
-            "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / len(reqs),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
-            "data": "synthetic",
+            "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * sm["wall_s"] / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision]
+            if args.precision != "fp64" else "bf16x3", "data": "synthetic",
             "config": {"workload": f"serving: {len(reqs)} requests, Poisson {rate:.3f}/s "
-                                   + ("; " if args.rate else "= 0.7 x ") + f"the measured capacity "
-                                   f"{capacity:.3f} solves/s (the same stream closed loop, device ingest "
-                                   "included), n_occ log-uniform "
-                                   "[8,200], n_virt = u n_occ (u in [8,12]), N_aux = 3(n_occ+n_virt), NAF 1e-2, "
-                                   "N_omega 32, N_tau 8, 4 states; inputs generated on the device at arrival",
+                                   + ("" if args.rate else f"= 0.7 x the measured capacity {capacity:.3f} solves/s "
+                                   "(the same stream closed loop, device ingest included), ")
+                                   + "n_occ log-uniform [8,200], n_virt = u n_occ (u in [8,12]), "
+                                   "N_aux = 3(n_occ+n_virt), NAF 1e-2, N_omega 32, N_tau 8, 4 states; inputs "
+                                   "generated on the device at arrival; both forms on the same arrival times",
                        "slots": args.slots, "hbm_budget_bytes": budget},
-            "latency_ms": {"p50": sm["p50_ms"], "p99": sm["p99_ms"],
-                           "p50_from_arrival": sm.get("p50_from_arrival_ms"),
-                           "p99_from_arrival": sm.get("p99_from_arrival_ms")},
-            "completed": sm["completed"], "failures": failures, "ingest_s": ingest_s,
-            "capacity_solves_per_s": capacity,
-            "prefix_comparison": {"requests": len(pre), "bf16x3_solves_per_s": cmp["bf16x3"]["solves_per_s"],
-                                  "fp64_solves_per_s": cmp["fp64"]["solves_per_s"],
-                                  "speedup": cmp["bf16x3"]["solves_per_s"] / cmp["fp64"]["solves_per_s"],
-                                  "qp_max_mev_bf16x3_vs_fp64": dev},
+            "latency_ms": lat(sm), "completed": sm["completed"], "ingest_s": sm["ingest_s"],
+            "fp64_form": {"solves_per_s": s64["solves_per_s"], "latency_ms": lat(s64), "completed": s64["completed"],
+                          "wall_s": s64["wall_s"]},
+            "speedup_vs_fp64_form": sm["solves_per_s"] / s64["solves_per_s"],
+            "qp_max_mev_mixed_vs_fp64_form": dev, "capacity_solves_per_s": capacity, "failures": failures,
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
+LARGE_DESC = ("large (config 2 shapes; config 3 is its mixed form): n_occ=320 (60 frozen), n_virt=3500, "
+              "N_aux=9000, NAF 1e-2, N_omega=32, N_tau=10 (library minimax Laplace grid), 20 QP states, "
+              "LT+NAF+FC, seed 20230712; RI tensor from the synthetic Philox law in FP64 (QR and loading GEMM "
+              "in FP64 on the device), held by the caller in 13 blocks of 20 occupied orbitals and streamed "
+              "through ltgw_solve_streamed (the library holds two blocks, never the whole tensor)")
+
+
+def golden_large():
+    """The oracle's stored results for the large workload (tests/golden/large_g0w0.json), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "large_g0w0.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def large_inputs(cfg, occ_block, host=False):
+    """The large workload's inputs, generated on the device in FP64: eps, targets,
+    shift (host numpy), the active B_ov blocks (device tensors, or pinned host
+    copies with host=True) and B_tgt.  Returns (law, blocks, B_tgt, seconds)."""
+    import torch
+    from paper_2307_04508_gb300.synthetic.device import DeviceLaw
+    t0 = time.perf_counter()
+    law = DeviceLaw(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["seed"], cfg["n_targets"],
+                    gemm="fp64")
+    blocks = []
+    for i0 in range(cfg["n_frozen"], cfg["n_occ"], occ_block):
+        blocks.append(law.b_ov_block(i0, min(cfg["n_occ"], i0 + occ_block)))
+    B_tgt = law.b_tgt()
+    torch.cuda.synchronize()
+    return law, blocks, B_tgt, time.perf_counter() - t0
+
+
+def cpu_oracle_sample(cfg, n_naf, frac=1.0, prep=None):
+    """Time the oracle (direct AC, numpy FP64, this host's cores) on a bounded
+    sample of the large workload and extrapolate one whole solve.  The sample
+    runs each of the oracle's steps on a slice whose cost scales in a known
+    way: the NAF metric, the projection and Pi (Eq. Pi, all N_omega
+    frequencies) on the pairs of `frac` of one occupied orbital (x n_pairs /
+    sample pairs); the eigendecomposition on the leading n_s x n_s block of the
+    sampled metric (x (N_aux / n_s)^3); the screening on 2 of the N_omega
+    matrices (x N_omega / 2); W_nm for 1 target at 1 frequency (x T N_omega);
+    Sigma, Pade and Newton in full on stand-in W.  Returns (seconds per
+    extrapolated solve, sample seconds, description, prep)."""
+    from oracle import ltgw_oracle as O
+    from paper_2307_04508_gb300 import synthetic as S
+    no, nv, na, nf, seed = cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["seed"]
+    n_act, T, n_om = no - nf, cfg["n_targets"], cfg["n_omega"]
+    n_orb_act = no + nv - nf
+    if prep is None:   # inputs of the sample (untimed): the law on the host in FP64
+        eps = S.orbital_energies(seed, no, nv, nf)
+        L = S.aux_loading(seed, na, no, nv)
+        R = L @ S.pair_normals_ov(seed, na, no, nv, nf, nf + 1)
+        Rt = L @ S.pair_normals_row(seed, na, no + nv, no - 1)
+        prep = {"eps": eps, "L": L, "R": R, "Rt": Rt}
+    eps, L = prep["eps"], prep["L"]
+    m = max(64, int(round(frac * nv)))
+    R = np.ascontiguousarray(prep["R"][:, :m])
+    n_s = min(na, max(256, int(round(3000 * frac ** (1 / 3)))))
+    parts = {}
+    t0 = time.perf_counter()
+    t = time.perf_counter()
+    K = O.naf_metric(R)
+    parts["naf_metric"] = (time.perf_counter() - t) * n_act * nv / m
+    t = time.perf_counter()
+    O.naf_basis(np.ascontiguousarray(K[:n_s, :n_s]), cfg["naf_thresh"])
+    parts["naf_eig"] = (time.perf_counter() - t) * (na / n_s) ** 3
+    U = np.ascontiguousarray(L[:, :n_naf])           # timing stand-in of the kept basis (same shape)
+    t = time.perf_counter()
+    Bt = O.naf_project(R, U)
+    parts["naf_project"] = (time.perf_counter() - t) * n_act * nv / m
+    t = time.perf_counter()
+    Bt_tgt = O.naf_project(prep["Rt"][:, nf:], U)[None]
+    parts["naf_project"] += (time.perf_counter() - t) * T
+    om, wt = O.gl_grid(n_om, 0.5)
+    delta = (eps[no:no + nv][:m] - eps[nf]).astype(np.float64)
+    t = time.perf_counter()
+    Pi = O.polarizability_direct(Bt, delta, om, 2)
+    parts["pi"] = (time.perf_counter() - t) * n_act * nv / m
+    t = time.perf_counter()
+    C = O.screened_interaction(Pi[:2])
+    parts["screen"] = (time.perf_counter() - t) * n_om / 2
+    t = time.perf_counter()
+    O.w_nm(C[:1], Bt_tgt)
+    parts["w_nm"] = (time.perf_counter() - t) * T * n_om
+    W = -np.abs(np.random.default_rng(0).standard_normal((T, n_orb_act, n_om))) * 1e-3
+    t = time.perf_counter()
+    eF = O.fermi_level(eps, no)
+    sig = O.sigma_iw(W, eps[nf:], eF, om, wt)
+    sel = O.pade_nodes(n_om)
+    for k in range(T):
+        a = O.pade_coefficients(1j * om[sel], sig[k][sel])
+        O.qp_newton(eps[no - 1], 0.0, eF, 1j * om[sel], a)
+    parts["sigma_pade_qp"] = time.perf_counter() - t
+    sample_s = time.perf_counter() - t0
+    desc = (f"oracle steps on a slice, extrapolated to one solve: NAF metric, projection and direct Pi "
+            f"({n_om} frequencies) on {m} of the {n_act * nv} active pairs (x {n_act * nv / m:.0f}); eigh of the "
+            f"leading {n_s} x {n_s} metric block (x ({na}/{n_s})^3); screening of 2 of {n_om} matrices; W_nm for "
+            f"1 target x 1 frequency (x {T * n_om}); Sigma/Pade/Newton in full; N_NAF = {n_naf}")
+    return sum(parts.values()), sample_s, desc, prep, parts
+
+
 def run_large(args):
-    """The large system, streamed: the RI tensor is generated on the device one
-    block of occupied orbitals at a time inside the solve (never resident in
-    FP64).  The generation time (host-side callback time) is reported and
-    excluded from `value`."""
+    """The large system (config 2 shapes; config 3 in the mixed forms), streamed
+    by occupied blocks from inputs resident in HBM.  `value`: solves/s of the
+    chosen form; the plain FP64 form beside it (one solve); QP errors against
+    the oracle's stored results; e2e through the same C ABI call with the
+    blocks in pinned host memory."""
     import torch
     from paper_2307_04508_gb300 import ltgw
     from paper_2307_04508_gb300 import synthetic as S
-    from paper_2307_04508_gb300.synthetic.device import DeviceLaw
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     cfg = S.LARGE
-    law = DeviceLaw(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["seed"], cfg["n_targets"],
-                    gemm="fp32")
-    B_tgt = law.b_tgt()
+    ob = args.occ_block
+    law, blocks, B_tgt, gen_s = large_inputs(cfg, ob)
     eps = torch.from_numpy(law.eps).cuda()
     targets = torch.from_numpy(law.targets.astype(np.int32)).cuda()
     shift = torch.from_numpy(law.shift).cuda()
     T = len(law.targets)
-    mixed = args.precision != "fp64"
+    n_om = cfg["n_omega"]
+    src = ltgw.BlockSource(blocks, cfg["n_frozen"], ob, cfg["n_virt"])
 
     def params(prec):
-        return ltgw.make_params(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["n_omega"],
-                                cfg["n_tau"], 0.5, cfg["naf_thresh"], 2, True, PREC[prec])
+        return ltgw.make_params(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], n_om, cfg["n_tau"],
+                                0.5, cfg["naf_thresh"], 2, True, PREC[prec])
 
-    p = params(args.precision)
+    p, p64 = params(args.precision), params("fp64")
     ctx = ltgw.Context(0)
     ctx.set_timing(True)
-    ctx.set_autotune(not args.no_autotune)   # the warm-up solve times and fixes the configurations
+    ctx.set_autotune(not args.no_autotune)   # the warm-up solves time and fix the configurations
     stream = torch.cuda.Stream()
-    out = (torch.empty((T, cfg["n_omega"], 2), dtype=torch.float64, device="cuda"),
+    out = (torch.empty((T, n_om, 2), dtype=torch.float64, device="cuda"),
            torch.empty(T, dtype=torch.float64, device="cuda"), torch.empty(T, dtype=torch.int32, device="cuda"))
 
-    def fill(i0, i1, dst, strm):
-        return law.fill_block(i0, i1, dst)
+    def timed(pp, n):
+        ms, stats = [], []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.solve_streamed(pp, eps, src, ob, B_tgt, targets, shift, *out, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(ctx.stats())
+        return np.array(ms), stats
 
-    def one(pp=p):
-        t0 = time.perf_counter()
-        ctx.solve_streamed(pp, eps, fill, args.occ_block, B_tgt, targets, shift, *out, stream=stream)
-        return time.perf_counter() - t0, ctx.stats()
-
-    for _ in range(max(args.warmup, 3)):
-        one()
-    res = []
+    timed(p, max(args.warmup, 3))
+    if dist:
+        dist.barrier()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for _ in range(args.steps):
-            res.append(one())
-    wall = np.array([r[0] for r in res])
-    gen = np.array([r[1]["ms_generate"] for r in res]) / 1e3
-    st = res[-1][1]
-    solve_s = wall - gen
+        step_ms, stats = timed(p, args.steps)
+    e_main = out[1].cpu().numpy().copy()
+    st_main = out[2].cpu().numpy().copy()
+    value, total_ms = replicas_value(step_ms.sum(), args.steps, world, dist, "cuda")
+    st = stats[-1]
     N, n_ov = st["n_naf"], (cfg["n_occ"] - cfg["n_frozen"]) * cfg["n_virt"]
     pi_flops = cfg["n_tau"] * N * N * n_ov
-    pi_ms = float(np.mean([r[1]["ms_pi_kernel"] for r in res]))
-    pk, src = peaks()
-    e_main = out[1].cpu().numpy().copy()
-    line = {"metric": "G0W0 solves/s (large system, streamed)", "value": len(res) / solve_s.sum(),
-            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * float(solve_s.mean()), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": "large: n_occ=320 (60 frozen), n_virt=3500, N_aux=9000, NAF 1e-2, N_omega=32, "
-                                   f"N_tau=10, 20 QP states; RI tensor generated on the device in blocks of "
-                                   f"{args.occ_block} occupied orbitals inside the solve (FP32 loading GEMM), "
-                                   "generation time excluded from value",
-                       "precision": args.precision},
-            "solves_per_s_incl_generation": len(res) / wall.sum(), "generation_s_per_solve": float(gen.mean()),
-            "n_naf": N, "pi_build_tflops": pi_flops / (pi_ms / 1e3) / 1e12,
-            "stage_ms": {k: st[k] for k in ("ms_naf", "ms_tridiag", "ms_pi", "ms_screen", "ms_wnm", "ms_sigma_qp",
-                                            "ms_total")},
-            "roofline_pi_build": pi_roofline(args.precision, pi_flops, pi_ms, pk, src),
-            "e_qp_ha": e_main.tolist(), "qp_status": out[2].cpu().numpy().tolist(),
-            "clocks": clk.summary()}
-    if args.precision in ("fp8", "fp8pi"):
-        # the same solve in the split-BF16 form (within a few 0.01 meV of FP64 at the mid size)
-        one(params("bf16x3"))
-        line["qp_mev_vs_bf16x3_form_per_state"] = (np.abs(e_main - out[1].cpu().numpy()) * HA2MEV).tolist()
-    print(json.dumps(line), flush=True)
+    pi_ms = float(np.mean([x["ms_pi_kernel"] for x in stats]))
+    tri_ms = float(np.mean([x["ms_tridiag"] for x in stats]))
+    pk, src_pk = peaks()
+    alu_peak = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    roof_pi = pi_roofline(args.precision, pi_flops, pi_ms, pk, src_pk, LARGE_TRAFFIC.get(("pi", args.precision)))
+    tri_flops = 4.0 / 3.0 * cfg["n_aux"] ** 3
+    tri_ach = tri_flops / (tri_ms / 1e3) / 1e12
+    roof_tri = {"bound": "alu", "kernel": "hh_fused_kernel<double> (NAF Householder tridiagonalisation, FP64)",
+                "achieved": tri_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": tri_ach / alu_peak,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
+                "flops_per_launch": tri_flops, "ms_per_launch": tri_ms,
+                "note": "4/3 N^3 algorithmic flops of the reduction (symmetry exploited); N = N_aux = 9000",
+                "traffic": LARGE_TRAFFIC.get(("hh", "any"))}
+    roofline = roof_tri if tri_ms > pi_ms else roof_pi
+    gold = golden_large()
+    line = {"metric": "G0W0 solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": LARGE_DESC, "precision": args.precision,
+                       "l2": "inputs 65.5 GB (> L2) streamed each step; no flush needed",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "note": "per solve over the timed steps (one request at a time)"},
+            "pi_build_tflops": pi_flops / (pi_ms / 1e3) / 1e12, "n_naf": N,
+            "stage_ms": {k: float(np.mean([x[k] for x in stats])) for k in
+                         ("ms_naf", "ms_naf_metric", "ms_tridiag", "ms_eig_vectors", "ms_naf_project", "ms_pi",
+                          "ms_pi_kernel", "ms_screen", "ms_wnm", "ms_sigma_qp", "ms_total")},
+            "roofline": roofline, "roofline_pi_build": roof_pi,
+            "gpu_launches": int(sum(x["kernel_launches"] for x in stats)), "clocks": clk.summary(),
+            "peaks_source": src_pk, "input_generation_s": gen_s, "qp_status": st_main.tolist()}
+    if gold is not None:
+        ed = np.array(gold["direct"]["e_qp"])
+        line["qp_mev_vs_fp64_oracle_per_state"] = (np.abs(e_main - ed) * HA2MEV).tolist()
+        line["qp_max_mev_vs_fp64_oracle"] = float(np.abs(e_main - ed).max() * HA2MEV)
+        line["oracle_reference"] = ("tests/golden/large_g0w0.json: the oracle's direct AC-GW solve (Eq. Pi, no "
+                                    "Laplace transform) on the same law, written on the host in FP64")
+    if args.precision != "fp64" and not args.no_fp64_form:
+        ms64, _ = timed(p64, 1)
+        e64 = out[1].cpu().numpy().copy()
+        line["fp64_form"] = {"solves_per_s": 1e3 / float(ms64.mean()), "ms_per_solve": float(ms64.mean()),
+                             "solves_timed": 1}
+        line["speedup_vs_fp64_form"] = value / line["fp64_form"]["solves_per_s"]
+        line["qp_max_mev_vs_fp64_form"] = float(np.abs(e_main - e64).max() * HA2MEV)
+        if gold is not None:
+            line["fp64_form"]["qp_max_mev_vs_fp64_oracle"] = float(
+                np.abs(e64 - np.array(gold["direct"]["e_qp"])).max() * HA2MEV)
+    if args.no_e2e:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        ctx.close()
+        return
+    # end to end: the caller's blocks and B_tgt in pinned host memory, outputs to host
+    host_blocks = [b.cpu().pin_memory() for b in blocks]
+    del src, blocks
+    torch.cuda.empty_cache()
+    hsrc = ltgw.BlockSource(host_blocks, cfg["n_frozen"], ob, cfg["n_virt"])
+    h_in = {"eps": np.ascontiguousarray(law.eps), "B_tgt": B_tgt.cpu().pin_memory(),
+            "targets": np.ascontiguousarray(law.targets.astype(np.int32)), "shift": np.ascontiguousarray(law.shift)}
+    del B_tgt
+    h_out = (np.zeros((T, n_om, 2)), np.zeros(T), np.zeros(T, dtype=np.int32))
+    ctx.solve_streamed(p, h_in["eps"], hsrc, ob, h_in["B_tgt"], h_in["targets"], h_in["shift"], *h_out,
+                       stream=stream)
+    n_e2e = max(1, min(args.steps, 5))
+    hsrc.bytes_copied = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ctx.solve_streamed(p, h_in["eps"], hsrc, ob, h_in["B_tgt"], h_in["targets"], h_in["shift"], *h_out,
+                           stream=stream)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = hsrc.bytes_copied / n_e2e + sum(v.nbytes if isinstance(v, np.ndarray) else v.numel() * v.element_size()
+                                          for v in h_in.values())
+    line["e2e"] = {"value": world * n_e2e / dt, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(sum(a.nbytes for a in h_out)), "steps": n_e2e,
+                   "note": "ltgw_solve_streamed with host inputs: every active block crosses the link twice per "
+                           "solve (metric, projection) from pinned memory, overlapped with the previous block's "
+                           "work; B_tgt, eps, targets, shift from host; results to host"}
+    line["e2e_qp_max_mev_vs_device_inputs"] = float(np.abs(h_out[1] - e_main).max() * HA2MEV)
+    del host_blocks, hsrc
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, sample_s, desc, _, parts = cpu_oracle_sample(cfg, N)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{desc}; sample ran {sample_s:.1f} s",
+                                "extrapolated_s_per_solve": sec, "parts_s": parts}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# DRAM bytes (read + write) per launch at the large workload, from the ncu
+# captures summarised in profiles/ (None until captured for the current kernels)
+LARGE_TRAFFIC = {}
 
 
 def run_sweep(args):
@@ -619,6 +837,42 @@ def run_sweep(args):
     ctx.close()
 
 
+def run_eig(args):
+    """The NAF eigensolver alone (ltgw_naf_basis, FP64) on the metric of an
+    --eig-n x --eig-n block of the synthetic law's RI tensor without its
+    rotation (--eig-n pairs), a few GB on the device: the profiling workload
+    of the eigensolver's kernels at the large workload's N_aux."""
+    import torch
+    from paper_2307_04508_gb300 import ltgw
+    from paper_2307_04508_gb300.synthetic import device as D
+    torch.cuda.set_device(0)
+    n = args.eig_n
+    nv = 3500
+    occ = max(1, (n + nv - 1) // nv)
+    # sigma_r Z[r, pairs] / sqrt(n_occ n_virt): the law without its rotation U
+    # (the metric's eigenvalues do not depend on U; no QR needed here)
+    sig = 0.5 * torch.exp(-6.0 * torch.arange(n, dtype=torch.float64, device="cuda") / n) / np.sqrt(320 * nv)
+    B = (D.pair_normals_ov(20230712, n, 320, nv, 60, 60 + occ)[:, :n] * sig[:, None]).contiguous()
+    Ut = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx = ltgw.Context(0)
+    ctx.set_timing(True)
+    thresh = 1e-2 * occ / 260.0   # the large workload's threshold, scaled to this block's share of the pairs
+    rows = []
+    for it in range(args.warmup + args.steps):
+        k = ctx.naf_basis(B, n, n, thresh, Ut, lam)
+        st = ctx.stats()
+        if it >= args.warmup:
+            rows.append(st)
+    tri = float(np.mean([r["ms_tridiag"] for r in rows]))
+    line = {"metric": "NAF eigensolver (profiling workload)", "n": n, "n_naf": k, "steps": args.steps,
+            "ms_tridiag": tri, "ms_eig_vectors": float(np.mean([r["ms_eig_vectors"] for r in rows])),
+            "ms_naf_metric": float(np.mean([r["ms_naf_metric"] for r in rows])),
+            "tridiag_tflops": 4.0 / 3.0 * n ** 3 / (tri / 1e3) / 1e12, "launches": rows[-1]["kernel_launches"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -629,6 +883,8 @@ def main():
         run_large(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "eig":
+        run_eig(args)
     else:
         run_gpu(args)
 

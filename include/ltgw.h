@@ -82,8 +82,9 @@ typedef struct {
                       /* metric, projections, Pi, W_nm) on the tensor cores with  */
                       /* split-BF16 operands (see ltgw_polarizability_mixed);     */
                       /* LTGW_FP8: the same with the Pi build and the W_nm        */
-                      /* contraction in FP8 E4M3 with per-row scales (rows are    */
-                      /* auxiliary functions; ltgw_polarizability_fp8);           */
+                      /* contraction in FP8 E4M3 with per-row scales and two-term */
+                      /* expansions (rows are auxiliary functions;                */
+                      /* ltgw_polarizability_fp8);                                */
                       /* LTGW_FP8_PI: FP8 for the Pi build only.                  */
                       /* The eigensolver, screening, Pade and Newton stay FP64.   */
   int reserved;       /* must be 0                                                */
@@ -103,6 +104,10 @@ typedef struct {
   double ms_tridiag;         /* device time of the NAF Householder tridiagonalisation */
   double ms_generate;        /* host time spent in the block callback (streamed solve) */
   int tc_autotuned;          /* contraction shapes the autotuner has timed (this context) */
+  double ms_naf_metric;      /* NAF stage parts (device time, ltgw_set_timing on): the */
+  double ms_eig_vectors;     /* metric K (streamed: with the block arrivals), the      */
+  double ms_naf_project;     /* eigenpairs after the tridiagonalisation (bisection,    */
+                             /* inverse iteration, back-transformation), the projections */
 } ltgw_stats;
 
 typedef struct ltgw_ctx ltgw_ctx;
@@ -183,15 +188,20 @@ ltgw_status ltgw_solve_ev(ltgw_ctx *ctx, const ltgw_params *p, const double *eps
 /*
  * The same solve without the occupied-virtual block resident: the caller
  * supplies the RI tensor one block of occupied orbitals at a time.
- *   fill(user, i0, i1, dst, stream) writes R^P_ia for active occupied
+ *   fill(user, i0, i1, dst, fill_stream) writes R^P_ia for active occupied
  *   orbitals i0 <= i < i1 (n_frozen <= i0 < i1 <= n_occ) into the device
  *   buffer dst [n_aux][(i1-i0)*n_virt] (pair index (i-i0)*n_virt + a), with
- *   its work complete (or ordered before later work on `stream`) when it
+ *   its work complete, or issued on fill_stream (a library stream), when it
  *   returns 0; any other return value aborts the solve (LTGW_ERR_BAD_ARG).
- * Blocks hold occ_block orbitals (the last may hold fewer); each is requested
- * twice: for the NAF metric K = sum over blocks of B B^T (Eq. nafeq), then for
- * the projection R~ = U^T R (Eq. naftrafo).  Needs NAF (naf_thresh >= 0).
- * Other arguments and outputs as for ltgw_solve.  Synchronises `stream`.
+ *   dst is free when fill is called (the library has waited for the work
+ *   that read it), so fill may write it by any means.  The library keeps two
+ *   block buffers: work that fill issues on fill_stream overlaps the
+ *   library's work on the previous block, which runs on `stream`.
+ * Blocks hold occ_block orbitals (the last may hold fewer) and are requested
+ * in ascending order, each twice: for the NAF metric K = sum over blocks of
+ * B B^T (Eq. nafeq), then for the projection R~ = U^T R (Eq. naftrafo).
+ * Needs NAF (naf_thresh >= 0).  Other arguments and outputs as for
+ * ltgw_solve.  Synchronises `stream` (and fill_stream).
  */
 typedef int (*ltgw_block_fn)(void *user, int i0, int i1, double *dst, void *stream);
 ltgw_status ltgw_solve_streamed(ltgw_ctx *ctx, const ltgw_params *p, const double *eps,
@@ -288,12 +298,16 @@ ltgw_status ltgw_polarizability_tau(ltgw_ctx *ctx, int N, int64_t n_pairs, const
  * per-pair factors of Eq. Pi (or of the M^m form) are formed in FP64 and
  * rounded to FP32, and every row of R~ and of each R~ diag(factor) (FP32
  * products) is scaled so that its largest magnitude maps to 448, the largest
- * finite E4M3 value, then rounded to E4M3 (nearest even, saturating).  The
- * products of the codes are summed on the tensor cores (kind::f8f6f4) in FP32,
- * drained every 4096 pairs, de-scaled per row and summed over K-splits in
- * FP64; each Pi_j (or M^m) is formed on its lower triangle and mirrored.
- * Relative error against the exact Pi about 1e-3 (E4M3 keeps 3 mantissa
- * bits).  Same arguments and layout as ltgw_polarizability.  Synchronises. */
+ * finite E4M3 value; each scaled value xs is written as the two-term E4M3
+ * expansion h + l, h = e4m3(xs), l = e4m3(xs - h) (nearest even, saturating;
+ * both in the row's scaled units).  The products h_a h_b + l_a h_b + h_a l_b
+ * are summed on the tensor cores (kind::f8f6f4, over three segments of codes)
+ * in FP32, drained every 4096 codes, de-scaled per row and summed over
+ * K-splits in FP64; each Pi_j (or M^m) is formed on its lower triangle and
+ * mirrored.  Relative error against the exact Pi about 1e-4 (a single E4M3
+ * term keeps 3 mantissa bits and gives about 4e-3, and 1 meV errors in the
+ * quasi-particle energies).  Same arguments and layout as
+ * ltgw_polarizability.  Synchronises. */
 ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
                                     const double *delta, int n_omega, const double *omegas,
                                     int n_tau, const double *x, const double *w, int spin,
@@ -334,9 +348,11 @@ typedef struct ltgw_server ltgw_server;
 
 /* A server with n_slots workers on `device`, each with its own context and
  * non-blocking stream (requests in different slots overlap on the device).
- * Requests are admitted in arrival order when a slot is free and the sum of
- * the estimated footprints of the running requests stays within
- * hbm_budget_bytes.  Each slot keeps its workspace between requests. */
+ * A request is admitted when a slot is free and the sum of the estimated
+ * footprints of the running requests, with its own, stays within
+ * hbm_budget_bytes: the oldest that fits first.  A request that does not fit
+ * may be passed by later ones that do at most 8 times; after that nothing is
+ * admitted ahead of it.  Each slot keeps its workspace between requests. */
 ltgw_status ltgw_server_create(ltgw_server **out, int device, int n_slots, size_t hbm_budget_bytes);
 /* Queue a request (never blocks on the GPU); LTGW_ERR_NOMEM if its estimated
  * footprint alone exceeds the budget. */
@@ -369,10 +385,12 @@ size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt);
  *               larger sizes return LTGW_ERR_BAD_ARG before any GPU work
  *   Pi, C       device [n_omega][N][N] on the current device, distinct
  * Runs on `stream` and synchronises it; LTGW_ERR_NOT_SPD if a pivot was not
- * positive.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array per device, so calls that
- * overlap on the GPU (other streams, other host threads) race. */
+ * positive.  A call looks up the array's device address (cudaGetSymbolAddress)
+ * on the current device each time it runs outside stream capture, so a device
+ * reset between calls is harmless; a call on a capturing stream reuses the
+ * address found by an earlier call on that device, so make one call on each
+ * device before any stream capture.  All calls share the one array per device,
+ * so calls that overlap on the GPU (other streams, other host threads) race. */
 ltgw_status ltgw_screen_static(int N, int n_omega, const double *Pi, double *C, void *stream);
 
 #ifdef __cplusplus

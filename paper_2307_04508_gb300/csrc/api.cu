@@ -67,7 +67,8 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-enum Stage { EV_START = 0, EV_NAF, EV_PI0, EV_PI1, EV_PI, EV_SCREEN, EV_WNM, EV_SIGQP, EV_END, EV_TRI0, EV_TRI1, EV_COUNT };
+enum Stage { EV_START = 0, EV_NAF, EV_PI0, EV_PI1, EV_PI, EV_SCREEN, EV_WNM, EV_SIGQP, EV_END, EV_TRI0, EV_TRI1,
+             EV_K0, EV_VEC1, EV_COUNT };
 
 }  // namespace
 
@@ -83,6 +84,11 @@ struct ltgw_ctx {
   // forked from and joined back to the caller's stream by two events
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // streamed solve: the block callback fills one of two block buffers on its
+  // own stream while the caller's stream consumes the other; per buffer, an
+  // event when its block has arrived and one when its consumers are done
+  cudaStream_t fill_stream = nullptr;
+  cudaEvent_t blk_ready[2] = {}, blk_done[2] = {};
   ltgw_stats stats{};
   int launches = 0;
   double pi_tc_flops = 0.0;
@@ -207,6 +213,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   }
   layout(ar);
   w.flags = ctx->flags;
+  ctx->mark(EV_K0, s);
   if (build_K) {
     if ((*build_K)(w.A) != LTGW_OK) return ctx->status();
   } else if (mixed) {
@@ -235,6 +242,7 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
   if (k <= 0) { ctx->fail(LTGW_ERR_NO_NAF, "NAF threshold kept no auxiliary function"); return ctx->status(); }
   nl = 0;
   e = launch_eig_vectors(w, n, k, Ut, ctx->flags, s, &nl);
+  ctx->mark(EV_VEC1, s);
   ctx->launches += nl;
   if (e != cudaSuccess) { ctx->fail(LTGW_ERR_DEVICE, std::string("eig_vectors: ") + cudaGetErrorString(e)); return ctx->status(); }
   if (lam_out) LTGW_CUDA(ctx, cudaMemcpyAsync(lam_out, w.lam, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -481,15 +489,15 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
   std::vector<int> tiles = lower_tiles(nI, &tindex);
   float *Af = nullptr, *scale;
   __nv_bfloat16 *Bhi = nullptr, *Blo = nullptr;   // the unscaled operand, pre-split for the TMA-fed kernel
-  uint8_t *qa = nullptr, *qb = nullptr;           // FP8 codes: scaled operands [n_t][Mp][Kq], B [Mp][Kq]
+  uint8_t *qa = nullptr, *qb = nullptr;           // FP8 codes: scaled operands [n_t][Mp][3 Kq], B [Mp][3 Kq]
   float *ds_a = nullptr, *ds_b = nullptr;         // FP8 per-row de-scales
   int *d_tindex;
   auto layout = [&](Arena &A) {
     Af = Af_in ? nullptr : A.take<float>((size_t)Mp * Kp);
     scale = A.take<float>((size_t)n_t * Kp);
     if (fp8) {
-      qa = A.take<uint8_t>((size_t)n_t * Mp * Kq);
-      qb = A.take<uint8_t>((size_t)Mp * Kq);
+      qa = A.take<uint8_t>((size_t)n_t * Mp * 3 * Kq);
+      qb = A.take<uint8_t>((size_t)Mp * 3 * Kq);
       ds_a = A.take<float>((size_t)n_t * Mp);
       ds_b = A.take<float>((size_t)Mp);
     } else {
@@ -510,10 +518,11 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
                                        mode == SCALE_LAPLACE ? d_w : nullptr, mode, scale, s), 1);
   TcGemmArgs g;
   if (fp8) {
-    CHECK_LAUNCH(ctx, launch_fp8_quantize(A, Kp, Kq, scale, n_t, Mp, qa, qb, ds_a, ds_b, s), 1);
-    // FP32 sums of exact E4M3 products: a 4096-pair drain keeps the accumulation
-    // bias (about 4e-6) far below the E4M3 rounding error
-    g.A8 = qa; g.B8 = qb; g.ds_a = ds_a; g.ds_b = ds_b; g.Kp = Kq; g.nt_group = 2; g.drain_k = 4096;
+    // two-term E4M3 expansions of both operands (three products over 3 Kq codes)
+    CHECK_LAUNCH(ctx, launch_fp8_quantize(A, Kp, Kq, scale, n_t, Mp, qa, qb, ds_a, ds_b, s, 1), 1);
+    // FP32 sums of exact E4M3 products: a 4096-code drain keeps the accumulation
+    // bias (about 4e-6) below the expansion's rounding error
+    g.A8 = qa; g.B8 = qb; g.ds_a = ds_a; g.ds_b = ds_b; g.Kp = 3 * Kq; g.nt_group = 2; g.drain_k = 4096;
   } else {
     CHECK_LAUNCH(ctx, launch_split_bf16(A, Bhi, Blo, (int64_t)Mp * Kp, s), 1);
     g.A = A; g.B = A; g.scale = scale; g.Kp = Kp; g.nt_group = 2; g.B_hi = Bhi; g.B_lo = Blo;
@@ -534,9 +543,9 @@ ltgw_status polarizability_tc(ltgw_ctx *ctx, int N, int64_t n_pairs, const doubl
                                            nI, n_t, N, n_tau ? 1.0 : -2.0 * spin, n_tau ? M : Pi, s,
                                            k0 ? 1.0 : 0.0, run.nt_group, 1), 1);
   }
-  ctx->pi_tc_flops = (fp8 ? 1.0 : 3.0) * 2.0 * (double)run.n_tiles * 128 * 128 * (double)g.Kp * n_t;
+  ctx->pi_tc_flops = (fp8 ? 1.0 : 3.0) * 2.0 * (double)run.n_tiles * 128 * 128 * (double)g.Kp * n_t;   // FP8: Kp = 3 Kq
   if (n_tau) {
-    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
+    CHECK_LAUNCH(ctx, launch_recombine(M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s, true),
                  (n_omega + 63) / 64);
   }
   return LTGW_OK;
@@ -685,8 +694,8 @@ ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, in
   auto layout = [&](Arena &A) {
     Cf = A.take<float>((size_t)n_omega * MpN * KpN);
     if (fp8) {
-      qC = A.take<uint8_t>((size_t)n_omega * MpN * Kq);
-      qR = A.take<uint8_t>((size_t)rowsTp * Kq);
+      qC = A.take<uint8_t>((size_t)n_omega * MpN * 3 * Kq);
+      qR = A.take<uint8_t>((size_t)rowsTp * 3 * Kq);
       dsC = A.take<float>((size_t)n_omega * MpN);
       dsR = A.take<float>((size_t)rowsTp);
     } else {
@@ -704,9 +713,10 @@ ltgw_status wnm_tc(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, in
                                              (int64_t)MpN * KpN, s), 1);
   TcGemmArgs g;
   if (fp8) {
-    CHECK_LAUNCH(ctx, launch_fp8_quantize(Cf, KpN, Kq, nullptr, 0, n_omega * MpN, nullptr, qC, nullptr, dsC, s), 1);
-    CHECK_LAUNCH(ctx, launch_fp8_quantize(BtT32, KpN, Kq, nullptr, 0, rowsTp, nullptr, qR, nullptr, dsR, s), 1);
-    g.A8 = qC; g.B8 = qR; g.ds_a = dsC; g.ds_b = dsR; g.Kp = Kq; g.rows_a = MpN; g.rows_b = rowsTp;
+    // two-term E4M3 expansions: C_j's rows as A operands, R~_tgt^T's as B
+    CHECK_LAUNCH(ctx, launch_fp8_quantize_a(Cf, KpN, Kq, n_omega * MpN, qC, dsC, s, 1), 1);
+    CHECK_LAUNCH(ctx, launch_fp8_quantize(BtT32, KpN, Kq, nullptr, 0, rowsTp, nullptr, qR, nullptr, dsR, s, 1), 1);
+    g.A8 = qC; g.B8 = qR; g.ds_a = dsC; g.ds_b = dsR; g.Kp = 3 * Kq; g.rows_a = MpN; g.rows_b = rowsTp;
   } else {
     CHECK_LAUNCH(ctx, launch_scale_table(nullptr, N, KpN, n_omega, nullptr, nullptr, SCALE_NONE, ones, s), 1);
     CHECK_LAUNCH(ctx, launch_split_bf16(BtT32, Rh, Rl, (int64_t)rowsTp * KpN, s), 1);
@@ -779,7 +789,12 @@ ltgw_status ltgw_create(ltgw_ctx **out, int device) {
   for (auto &e : c->ev) cudaEventCreate(&e);
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->fill_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->blk_ready[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->blk_ready[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->blk_done[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->blk_done[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     ltgw_destroy(c);
     return LTGW_ERR_DEVICE;
@@ -801,6 +816,11 @@ void ltgw_destroy(ltgw_ctx *ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+  if (ctx->fill_stream) cudaStreamDestroy(ctx->fill_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->blk_ready[b]) cudaEventDestroy(ctx->blk_ready[b]);
+    if (ctx->blk_done[b]) cudaEventDestroy(ctx->blk_done[b]);
+  }
   delete ctx;
 }
 
@@ -943,8 +963,16 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   for (int t = 0; t < T; ++t) h_epsn[t] = h_eps[h_tg[t]];
 
   const bool bov_dev = streamed || is_device_ptr(B_ov), btg_dev = is_device_ptr(B_tgt);
+  // a streamed solve that fails leaves no callback work in flight behind it
+  struct FillDrain {
+    ltgw_ctx *ctx;
+    bool on;
+    ~FillDrain() {
+      if (on) cudaStreamSynchronize(ctx->fill_stream);
+    }
+  } fill_drain{ctx, streamed};
   const int blk = streamed ? std::min(occ_block, n_act) : 0;
-  double *d_blk = nullptr;
+  double *d_blk[2] = {nullptr, nullptr};
   ctx->gen_ms = 0.0;
   // ---- phase-1 workspace: inputs, grids, NAF
   double *d_eps, *d_delta, *d_om, *d_wt, *d_x, *d_w, *d_E, *d_epsn, *d_shift, *d_Bov, *d_Btg, *d_Ut, *d_lam;
@@ -959,7 +987,8 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     d_epsn = A.take<double>(T);
     d_shift = A.take<double>(T);
     d_Bov = bov_dev ? const_cast<double *>(B_ov) : A.take<double>((size_t)n_aux * n_ov_all);
-    d_blk = streamed ? A.take<double>((size_t)n_aux * blk * n_virt) : nullptr;
+    d_blk[0] = streamed ? A.take<double>((size_t)n_aux * blk * n_virt) : nullptr;
+    d_blk[1] = streamed ? A.take<double>((size_t)n_aux * blk * n_virt) : nullptr;
     d_Btg = btg_dev ? const_cast<double *>(B_tgt) : A.take<double>((size_t)T * n_aux * n_orb);
     d_Ut = naf ? A.take<double>((size_t)n_aux * n_aux) : nullptr;
     d_lam = naf ? A.take<double>(n_aux) : nullptr;
@@ -1028,13 +1057,32 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   // ---- frozen-core slice: the active pairs are the trailing columns
   const double *B_act = streamed ? nullptr : d_Bov + (int64_t)n_fc * n_virt;
   const int64_t ld_act = n_ov_all;
-  // streamed: ask the caller for occupied block [i0, i1) into d_blk
-  auto get_block = [&](int i0, int i1) -> ltgw_status {
-    LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  // streamed: ask the caller for occupied block [i0, i1) into the next of the
+  // two block buffers (*dst).  The buffer's previous consumers are waited for
+  // on the host first, so the callback may write it by any means; its work,
+  // issued on the fill stream, then overlaps the consumers of the other
+  // buffer on `s`, which waits for the block's arrival.  block_done() marks
+  // the block's consumers issued.
+  int blk_next = 0;
+  auto get_block = [&](int i0, int i1, double **dst) -> ltgw_status {
+    const int b = blk_next;
+    LTGW_CUDA(ctx, cudaEventSynchronize(ctx->blk_done[b]));
     const auto t0 = std::chrono::steady_clock::now();
-    const int rc = fill(user, i0, i1, d_blk, (void *)s);
+    const int rc = fill(user, i0, i1, d_blk[b], (void *)ctx->fill_stream);
     ctx->gen_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (rc != 0) { ctx->fail(LTGW_ERR_BAD_ARG, "the block callback reported an error"); return ctx->status(); }
+    if (rc != 0) {
+      cudaStreamSynchronize(ctx->fill_stream);
+      ctx->fail(LTGW_ERR_BAD_ARG, "the block callback reported an error");
+      return ctx->status();
+    }
+    LTGW_CUDA(ctx, cudaEventRecord(ctx->blk_ready[b], ctx->fill_stream));
+    LTGW_CUDA(ctx, cudaStreamWaitEvent(s, ctx->blk_ready[b], 0));
+    *dst = d_blk[b];
+    return LTGW_OK;
+  };
+  auto block_done = [&]() -> ltgw_status {
+    LTGW_CUDA(ctx, cudaEventRecord(ctx->blk_done[blk_next], s));
+    blk_next ^= 1;
     return LTGW_OK;
   };
   KBuilder build_K = [&](double *K) -> ltgw_status {
@@ -1042,16 +1090,18 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
       const int i1 = std::min(n_occ, i0 + blk);
       const int64_t cols = (int64_t)(i1 - i0) * n_virt;
-      if (get_block(i0, i1) != LTGW_OK) return ctx->status();
+      double *B_blk = nullptr;
+      if (get_block(i0, i1, &B_blk) != LTGW_OK) return ctx->status();
       if (mixed) {
-        if (naf_metric_tc(ctx, n_aux, cols, d_blk, cols, K, s, 1.0) != LTGW_OK) return ctx->status();
+        if (naf_metric_tc(ctx, n_aux, cols, B_blk, cols, K, s, 1.0) != LTGW_OK) return ctx->status();
       } else {
         GemmF64Args g;  // K += B_blk B_blk^T
         g.M = n_aux; g.N = n_aux; g.K = cols;
-        g.A = d_blk; g.lda = cols; g.B = d_blk; g.ldb = cols;
+        g.A = B_blk; g.lda = cols; g.B = B_blk; g.ldb = cols;
         g.C = K; g.ldc = n_aux; g.syrk = 1; g.beta = 1.0;
         CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
       }
+      if (block_done() != LTGW_OK) return ctx->status();
     }
     return LTGW_OK;
   };
@@ -1106,13 +1156,15 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
       const int i1 = std::min(n_occ, i0 + blk);
       const int64_t cols = (int64_t)(i1 - i0) * n_virt;
-      if (get_block(i0, i1) != LTGW_OK) return ctx->status();
+      double *B_blk = nullptr;
+      if (get_block(i0, i1, &B_blk) != LTGW_OK) return ctx->status();
       OvWindow win;
       win.col0 = (int64_t)(i0 - n_fc) * n_virt;
       win.ld_bf = Kp_ov;
-      if (naf_project_tc(ctx, N, n_aux, d_Ut, d_blk, cols, cols, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64,
+      if (naf_project_tc(ctx, N, n_aux, d_Ut, B_blk, cols, cols, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64,
                          d_BtT32, s, &win) != LTGW_OK)
         return ctx->status();
+      if (block_done() != LTGW_OK) return ctx->status();
     }
     if (naf_project_tc(ctx, N, n_aux, d_Ut, nullptr, 0, 0, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64, d_BtT32,
                        s) != LTGW_OK)
@@ -1126,13 +1178,15 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
       for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
         const int i1 = std::min(n_occ, i0 + blk);
         const int64_t cols = (int64_t)(i1 - i0) * n_virt;
-        if (get_block(i0, i1) != LTGW_OK) return ctx->status();
+        double *B_blk = nullptr;
+        if (get_block(i0, i1, &B_blk) != LTGW_OK) return ctx->status();
         GemmF64Args g;  // R~_ov[:, block] = U^T R_blk
         g.M = N; g.N = (int)cols; g.K = n_aux;
         g.A = d_Ut; g.lda = n_aux;
-        g.B = d_blk; g.ldb = cols;
+        g.B = B_blk; g.ldb = cols;
         g.C = d_Bt + (int64_t)(i0 - n_fc) * n_virt; g.ldc = n_ov;
         CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+        if (block_done() != LTGW_OK) return ctx->status();
       }
     } else {
       GemmF64Args g;  // R~_ov = U^T R_ov
@@ -1266,6 +1320,9 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   st.ms_sigma_qp = ctx->ms(EV_WNM, EV_SIGQP);
   st.ms_total = ctx->ms(EV_START, EV_END);
   st.ms_tridiag = naf ? ctx->ms(EV_TRI0, EV_TRI1) : 0.0;
+  st.ms_naf_metric = naf ? ctx->ms(EV_K0, EV_TRI0) : 0.0;
+  st.ms_eig_vectors = naf ? ctx->ms(EV_TRI1, EV_VEC1) : 0.0;
+  st.ms_naf_project = naf ? ctx->ms(EV_VEC1, EV_NAF) : 0.0;
 
   st.ms_generate = ctx->gen_ms;
   std::vector<int> hs(T);
@@ -1416,9 +1473,14 @@ static ltgw_status naf_basis_api(ltgw_ctx *ctx, int n_aux, int64_t n_pairs, cons
   if (naf_basis_dev(ctx, ctx->a3, n_aux, n_pairs, B, ld, thresh, Ut, lambda, &k, &near, s, mixed) != LTGW_OK)
     return ctx->status();
   *n_naf = k;
+  ctx->stats = ltgw_stats{};
   ctx->stats.n_naf = k;
   ctx->stats.naf_near_threshold = near;
   LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->stats.ms_naf_metric = ctx->ms(EV_K0, EV_TRI0);
+  ctx->stats.ms_tridiag = ctx->ms(EV_TRI0, EV_TRI1);
+  ctx->stats.ms_eig_vectors = ctx->ms(EV_TRI1, EV_VEC1);
+  ctx->stats.kernel_launches = ctx->launches;
   return check_flags(ctx, s);
 }
 

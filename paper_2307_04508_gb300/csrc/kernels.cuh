@@ -59,9 +59,10 @@ cudaError_t launch_gemm_coldot(const ColDotArgs &g, int n_batch, cudaStream_t s)
 // delta[i*n_virt + a] = eps[n_occ + a] - eps[n_frozen + i], i < n_occ - n_frozen
 cudaError_t launch_pair_gaps(const double *eps, int n_occ, int n_virt, int n_frozen,
                              double *delta, cudaStream_t s);
-// Pi_j = alpha * sum_k E[j][k] M_k over n elements per matrix (n_tau <= 32, any n_omega)
+// Pi_j = alpha * sum_k E[j][k] M_k over n elements per matrix (n_tau <= 32, any n_omega);
+// fp32: FP32 arithmetic (FP64 in and out), for moments of the tensor-core forms
 cudaError_t launch_recombine(const double *M, int n_tau, const double *E, int n_omega,
-                             int64_t n_elem, double alpha, double *Pi, cudaStream_t s);
+                             int64_t n_elem, double alpha, double *Pi, cudaStream_t s, bool fp32 = false);
 // dst[r][c] = src[r][c0 + c] for a strided 2-D copy of rows (batched)
 cudaError_t launch_copy_cols(const double *src, int64_t lds, int64_t c0, double *dst,
                              int64_t ldd, int rows, int64_t cols, int batch,
@@ -148,8 +149,14 @@ cudaError_t launch_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *
 // inv = 448 / max|X_r|, qb[r][k] = e4m3(X_rk inv); for each factor row S[t] ([n_t][Kp])
 // the FP32 products X_rk S_tk get their own row scale, codes qa[t][r][k].  De-scales
 // (1 / inv, 0 for zero rows) in ds_b[r], ds_a[t][r]; code columns Kp..Kq-1 are zero.
+// split: rows of 3 Kq codes, the two-term expansion h = e4m3(x inv), l = e4m3(x inv - h)
+// in segments h | l | h (A operands) and h | h | l (B operands), so that a contraction
+// over the 3 Kq codes sums h_a h_b + l_a h_b + h_a l_b.
 cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const float *S, int n_t, int rows,
-                                uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s);
+                                uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s, int split);
+// X itself quantised per row as an A operand (split: segments h | l | h).
+cudaError_t launch_fp8_quantize_a(const float *X, int64_t Kp, int64_t Kq, int rows, uint8_t *q, float *ds,
+                                  cudaStream_t s, int split);
 // Scaled contraction on FP8 E4M3 codes (tcgen05 kind::f8f6f4): D_t = diag(ds_a[t]) qa[t] qb^T diag(ds_b),
 // up to four scales per CTA (nt_group <= 4), Kp (of the codes) and k_per_split multiples of 128;
 // partial tiles as launch_tc_split_gemm (column-major).

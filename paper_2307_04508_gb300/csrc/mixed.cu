@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include <algorithm>
@@ -282,16 +283,42 @@ __device__ __forceinline__ uint32_t e4m3x4(float4 x, float inv) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
+// E4M3 values of four packed codes (exact in FP32)
+__device__ __forceinline__ float4 e4m3x4_value(uint32_t c) {
+  const __half2_raw a = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(c & 0xffffu), __NV_E4M3);
+  const __half2_raw b = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(c >> 16), __NV_E4M3);
+  const float2 fa = __half22float2(__half2(a)), fb = __half22float2(__half2(b));
+  return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// Codes of x * inv (one term), or (split) of its two-term expansion h + l
+// with h = e4m3(x inv) and l = e4m3(x inv - h) (exact in FP32), both in the
+// row's scaled units: the row's three segments of Kq codes are written as
+// pattern[0..2] of {h, l} (A operands h | l | h, B operands h | h | l, so that
+// one accumulator sums h_a h_b + l_a h_b + h_a l_b).
+__device__ __forceinline__ void write_codes(uint32_t *row, int64_t k, int64_t q4, float4 x, float inv, int split,
+                                            bool a_pattern) {
+  const uint32_t h = e4m3x4(x, inv);
+  row[k] = h;
+  if (!split) return;
+  const float4 hv = e4m3x4_value(h);
+  const float4 r = make_float4(x.x * inv - hv.x, x.y * inv - hv.y, x.z * inv - hv.z, x.w * inv - hv.w);
+  const uint32_t l = e4m3x4(r, 1.0f);
+  row[q4 + k] = a_pattern ? l : h;
+  row[2 * q4 + k] = a_pattern ? h : l;
+}
+
 // One block per row r of X [rows][Kp] (FP32; Kp a multiple of 4): the row's
 // scale inv = 448 / max_k |X_rk| and codes qb[r][k] = e4m3(X_rk inv); for each
 // of the n_t factor rows S[t] the products p = X_rk S_tk (FP32) get their own
 // scale and codes qa[t][r][k].  De-scales 1 / inv (0 for a zero row) go to
-// ds_b[r] and ds_a[t][r]; code columns Kp..Kq-1 are zero.
+// ds_b[r] and ds_a[t][r]; code columns Kp..Kq-1 are zero.  split: each code
+// row holds three segments of Kq (the two-term expansion, write_codes).
 template <int MAXT>
 __global__ void __launch_bounds__(Q8_THREADS)
     fp8_quantize_kernel(const float *__restrict__ X, int64_t Kp, int64_t Kq, const float *__restrict__ S, int n_t,
                         int rows, uint8_t *__restrict__ qa, uint8_t *__restrict__ qb, float *__restrict__ ds_a,
-                        float *__restrict__ ds_b) {
+                        float *__restrict__ ds_b, int split) {
   __shared__ float red[Q8_THREADS / 32];
   __shared__ float inv_s[MAXT + 1];
   const int r = blockIdx.x;
@@ -327,35 +354,73 @@ __global__ void __launch_bounds__(Q8_THREADS)
     ds_b[r] = invb > 0.0f ? 1.0f / invb : 0.0f;
     for (int t = 0; t < n_t; ++t) ds_a[(int64_t)t * rows + r] = inv_s[t] > 0.0f ? 1.0f / inv_s[t] : 0.0f;
   }
-  uint32_t *qbr = reinterpret_cast<uint32_t *>(qb + (int64_t)r * Kq);
+  const int64_t Ks = split ? 3 * Kq : Kq;   // codes per row
+  uint32_t *qbr = qb ? reinterpret_cast<uint32_t *>(qb + (int64_t)r * Ks) : nullptr;
   for (int64_t k = threadIdx.x; k < q4; k += Q8_THREADS) {
     if (k >= n4) {
-      qbr[k] = 0u;
-      for (int t = 0; t < n_t; ++t) reinterpret_cast<uint32_t *>(qa + ((int64_t)t * rows + r) * Kq)[k] = 0u;
+      for (int seg = 0; seg < (split ? 3 : 1); ++seg) {
+        if (qbr) qbr[seg * q4 + k] = 0u;
+        for (int t = 0; t < n_t; ++t) reinterpret_cast<uint32_t *>(qa + ((int64_t)t * rows + r) * Ks)[seg * q4 + k] = 0u;
+      }
       continue;
     }
     const float4 x = xr[k];
-    qbr[k] = e4m3x4(x, invb);
+    if (qbr) write_codes(qbr, k, q4, x, invb, split, false);
 #pragma unroll
     for (int t = 0; t < MAXT; ++t) {
       if (t < n_t) {
         const float4 sv = reinterpret_cast<const float4 *>(S + (int64_t)t * Kp)[k];
         const float4 p = make_float4(x.x * sv.x, x.y * sv.y, x.z * sv.z, x.w * sv.w);
-        reinterpret_cast<uint32_t *>(qa + ((int64_t)t * rows + r) * Kq)[k] = e4m3x4(p, inv_s[t]);
+        write_codes(reinterpret_cast<uint32_t *>(qa + ((int64_t)t * rows + r) * Ks), k, q4, p, inv_s[t], split, true);
       }
     }
+  }
+}
+// One block per row r of X [rows][Kp]: codes of X itself as an A operand
+// (split: segments h | l | h), de-scale to ds[r].
+__global__ void __launch_bounds__(Q8_THREADS)
+    fp8_quantize_a_kernel(const float *__restrict__ X, int64_t Kp, int64_t Kq, int rows, uint8_t *__restrict__ q,
+                          float *__restrict__ ds, int split) {
+  __shared__ float red[Q8_THREADS / 32];
+  const int r = blockIdx.x;
+  const float4 *xr = reinterpret_cast<const float4 *>(X + (int64_t)r * Kp);
+  const int64_t n4 = Kp / 4, q4 = Kq / 4;
+  float m = 0.0f;
+  for (int64_t k = threadIdx.x; k < n4; k += Q8_THREADS) {
+    const float4 x = xr[k];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+  }
+  m = block_max(m, red);
+  const float inv = m > 0.0f ? E4M3_MAX / m : 0.0f;
+  if (threadIdx.x == 0) ds[r] = inv > 0.0f ? 1.0f / inv : 0.0f;
+  const int64_t Ks = split ? 3 * Kq : Kq;
+  uint32_t *qr = reinterpret_cast<uint32_t *>(q + (int64_t)r * Ks);
+  for (int64_t k = threadIdx.x; k < q4; k += Q8_THREADS) {
+    if (k >= n4) {
+      for (int seg = 0; seg < (split ? 3 : 1); ++seg) qr[seg * q4 + k] = 0u;
+      continue;
+    }
+    write_codes(qr, k, q4, xr[k], inv, split, true);
   }
 }
 }  // namespace
 
 cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const float *S, int n_t, int rows,
-                                uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s) {
+                                uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s, int split) {
   if (rows <= 0) return cudaSuccess;
   if (Kp % 4 || Kq % 16 || Kq < Kp || n_t < 0 || n_t > 32) return cudaErrorInvalidValue;
   if (n_t <= 8)
-    fp8_quantize_kernel<8><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b);
+    fp8_quantize_kernel<8><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b, split);
   else
-    fp8_quantize_kernel<32><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b);
+    fp8_quantize_kernel<32><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp8_quantize_a(const float *X, int64_t Kp, int64_t Kq, int rows, uint8_t *q, float *ds,
+                                  cudaStream_t s, int split) {
+  if (rows <= 0) return cudaSuccess;
+  if (Kp % 4 || Kq % 16 || Kq < Kp) return cudaErrorInvalidValue;
+  fp8_quantize_a_kernel<<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, rows, q, ds, split);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,9 @@ class Stats(ctypes.Structure):
                 ("ms_wnm", ctypes.c_double), ("ms_sigma_qp", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_pi_kernel", ctypes.c_double), ("pi_kernel_launches", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int), ("ms_tridiag", ctypes.c_double),
-                ("ms_generate", ctypes.c_double), ("tc_autotuned", ctypes.c_int)]
+                ("ms_generate", ctypes.c_double), ("tc_autotuned", ctypes.c_int),
+                ("ms_naf_metric", ctypes.c_double), ("ms_eig_vectors", ctypes.c_double),
+                ("ms_naf_project", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -154,6 +156,41 @@ class _DeviceBuffer:
 def device_view(ptr: int, shape, dtype: str = "<f8"):
     import torch
     return torch.as_tensor(_DeviceBuffer(ptr, shape, dtype), device="cuda")
+
+
+class BlockSource:
+    """Block callback for Context.solve_streamed over blocks the caller already
+    holds: blocks[b] is B_ov's columns for active occupied orbitals
+    [n_frozen + b occ_block, n_frozen + (b + 1) occ_block) (the last block may
+    be shorter), a torch tensor [n_aux][(i1 - i0) n_virt] on the device or in
+    pinned host memory.  A requested block is copied into the library's buffer
+    asynchronously (from pinned memory too) on a stream of torch's pool, and
+    the stream the library passes waits for the copy, so the copy overlaps the
+    library's work on the previous block.  The copy is not issued on the
+    library's stream itself: torch would then tie the pinned block's release
+    to that stream, which the library destroys with its context."""
+
+    def __init__(self, blocks, n_frozen: int, occ_block: int, n_virt: int):
+        self.blocks, self.n_frozen, self.occ_block, self.n_virt = list(blocks), n_frozen, occ_block, n_virt
+        self.bytes_copied = 0
+        self._stream = None
+
+    def __call__(self, i0: int, i1: int, dst: int, strm: int) -> int:
+        import torch
+        b, r = divmod(i0 - self.n_frozen, self.occ_block)
+        src = self.blocks[b]
+        if r or src.shape[1] != (i1 - i0) * self.n_virt:
+            raise ValueError(f"block [{i0}, {i1}) does not match the held block {b} of shape {tuple(src.shape)}")
+        if self._stream is None:
+            self._stream = torch.cuda.Stream()
+        view = device_view(dst, tuple(src.shape))
+        with torch.cuda.stream(self._stream):
+            view.copy_(src, non_blocking=True)
+        done = torch.cuda.Event()
+        done.record(self._stream)
+        torch.cuda.ExternalStream(strm).wait_event(done)
+        self.bytes_copied += src.numel() * src.element_size()
+        return 0
 
 
 def status_string(st: int) -> str:

@@ -1,11 +1,10 @@
-"""FP8 E4M3 form of the Pi contraction (per-auxiliary-row scales, FP32
-accumulation on tcgen05 kind::f8f6f4) against the oracle's FP8 definition,
-which rounds the same FP32 values to E4M3 and sums the products exactly: the
-two differ only by the FP32 accumulation, so the bar is 2e-5 relative
-Frobenius.  The error of the FP8 form itself (against the exact Pi, and in
-the quasi-particle energies of a whole solve against the FP64 oracle) is
-printed and bounded at its measured level: Pi and W_nm in FP8 stay within
-2 meV, Pi alone in FP8 within the 1 meV target."""
+"""FP8 E4M3 form of the Pi contraction (per-auxiliary-row scales, two-term
+E4M3 expansion of every operand value, FP32 accumulation on tcgen05
+kind::f8f6f4) against the oracle's FP8 definition, which rounds the same FP32
+values to the same codes and sums the products exactly: the two differ only
+by the FP32 accumulation, so the bar is 2e-5 relative Frobenius.  Whole
+solves in both FP8 modes (Pi and W_nm in FP8, or Pi alone) stay within the
+1 meV target of the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -62,12 +61,12 @@ def test_fp8_polarizability_direct_and_laplace(ctx, N, P, n_om):
     assert errl <= PI_TOL_FP8_VS_ORACLE
 
 
-@pytest.mark.parametrize("mode,bound_mev", [("fp8", 2.0), ("fp8_pi", 1.0)])
+@pytest.mark.parametrize("mode,bound_mev", [("fp8", 1.0), ("fp8_pi", 1.0)])
 def test_fp8_solve_mid_workload(ctx, mode, bound_mev):
     """Mid workload (1800 auxiliary functions, NAF 1e-2): per-state QP error
     against the FP64 oracle fed the same Laplace grid, with Pi and W_nm in FP8
-    (LTGW_FP8; measured 1.07-1.64 meV) or Pi alone in FP8 (LTGW_FP8_PI,
-    W_nm split-BF16; measured 0.79-0.95 meV, inside the 1 meV target)."""
+    (LTGW_FP8) or Pi alone in FP8 (LTGW_FP8_PI, W_nm split-BF16), both within
+    the 1 meV target (the oracle's two-term expansion puts them near 0.01 meV)."""
     from paper_2307_04508_gb300 import ltgw
     prob = S.make_workload(S.MID)
     tau = O.sinc_laplace_grid(8, -12.0, 3.0)

@@ -27,8 +27,12 @@ def oracle_lt(mid):
     return tau, e, st
 
 
-@pytest.mark.parametrize("mixed,occ_block", [(False, 7), (True, 7), (True, 50)])
-def test_streamed_matches_oracle(mid, oracle_lt, mixed, occ_block):
+@pytest.mark.parametrize("mixed,occ_block,async_fill", [(False, 7, False), (True, 7, False), (True, 50, False),
+                                                       (False, 7, True), (True, 7, True)])
+def test_streamed_matches_oracle(mid, oracle_lt, mixed, occ_block, async_fill):
+    """async_fill: the callback only issues its copy on the fill stream the
+    library passes and returns (the library's two block buffers and events
+    order it); otherwise it finishes the copy before returning."""
     from paper_2307_04508_gb300 import ltgw
     tau, e_o, st_o = oracle_lt
     B_ov = torch.from_numpy(mid.B_ov).cuda()
@@ -37,6 +41,10 @@ def test_streamed_matches_oracle(mid, oracle_lt, mixed, occ_block):
     def fill(i0, i1, dst, strm):
         calls.append((i0, i1))
         view = ltgw.device_view(dst, (1800, (i1 - i0) * 540))
+        if async_fill:
+            with torch.cuda.stream(torch.cuda.ExternalStream(strm)):
+                view.copy_(B_ov[:, i0 * 540:i1 * 540])
+            return 0
         view.copy_(B_ov[:, i0 * 540:i1 * 540])
         torch.cuda.synchronize()
         return 0
@@ -70,3 +78,27 @@ def test_streamed_requires_naf(mid):
         assert e.value.status == ltgw.LTGW_ERR_BAD_ARG
     finally:
         ctx.close()
+
+
+def test_block_source_from_pinned_host(mid, oracle_lt):
+    """ltgw.BlockSource over caller-held blocks in pinned host memory (the
+    end-to-end form of the large workload): asynchronous copies from host."""
+    from paper_2307_04508_gb300 import ltgw
+    tau, e_o, st_o = oracle_lt
+    ob = 9
+    blocks = [torch.from_numpy(np.ascontiguousarray(mid.B_ov[:, i0 * 540:min(60, i0 + ob) * 540])).pin_memory()
+              for i0 in range(10, 60, ob)]
+    src = ltgw.BlockSource(blocks, 10, ob, 540)
+    ctx = ltgw.Context(0)
+    try:
+        p = ltgw.make_params(60, 540, 1800, 10, 32, 8, 0.5, 1e-2, 2, True, ltgw.LTGW_FP64)
+        T = len(mid.targets)
+        sig, e, st = np.zeros((T, 32, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
+        ctx.solve_streamed(p, mid.eps, src, ob, mid.B_tgt, mid.targets.astype(np.int32), mid.shift, sig, e, st,
+                           tau_x=np.ascontiguousarray(tau[0]), tau_w=np.ascontiguousarray(tau[1]))
+        assert src.bytes_copied == 2 * sum(b.numel() * 8 for b in blocks)
+        del blocks, src   # the pinned blocks go first, while every stream is alive
+    finally:
+        ctx.close()
+    assert np.all(st == 0)
+    assert np.abs(e - e_o).max() <= QP_TOL, np.abs(e - e_o).max()
