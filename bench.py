@@ -505,8 +505,8 @@ def run_serving(args):
 
 LARGE_DESC = ("large (config 2 shapes; config 3 is its mixed form): n_occ=320 (60 frozen), n_virt=3500, "
               "N_aux=9000, NAF 1e-2, N_omega=32, N_tau=10 (library minimax Laplace grid), 20 QP states, "
-              "LT+NAF+FC, seed 20230712; RI tensor from the synthetic Philox law in FP64 (QR and loading GEMM "
-              "in FP64 on the device), held by the caller in 13 blocks of 20 occupied orbitals and streamed "
+              "LT+NAF+FC, seed 20230712; RI tensor from the synthetic Philox law in FP64 (QR on the host, "
+              "normals and loading GEMM on the device), held by the caller in 13 blocks of 20 occupied orbitals and streamed "
               "through ltgw_solve_streamed (the library holds two blocks, never the whole tensor)")
 
 
@@ -527,7 +527,7 @@ def large_inputs(cfg, occ_block, host=False):
     from paper_2307_04508_gb300.synthetic.device import DeviceLaw
     t0 = time.perf_counter()
     law = DeviceLaw(cfg["n_occ"], cfg["n_virt"], cfg["n_aux"], cfg["n_frozen"], cfg["seed"], cfg["n_targets"],
-                    gemm="fp64")
+                    gemm="fp64", host_qr=True)
     blocks = []
     for i0 in range(cfg["n_frozen"], cfg["n_occ"], occ_block):
         blocks.append(law.b_ov_block(i0, min(cfg["n_occ"], i0 + occ_block)))
@@ -536,7 +536,7 @@ def large_inputs(cfg, occ_block, host=False):
     return law, blocks, B_tgt, time.perf_counter() - t0
 
 
-def cpu_oracle_sample(cfg, n_naf, frac=1.0, prep=None):
+def cpu_oracle_sample(cfg, n_naf, frac=1.0, prep=None, L=None):
     """Time the oracle (direct AC, numpy FP64, this host's cores) on a bounded
     sample of the large workload and extrapolate one whole solve.  The sample
     runs each of the oracle's steps on a slice whose cost scales in a known
@@ -554,7 +554,7 @@ def cpu_oracle_sample(cfg, n_naf, frac=1.0, prep=None):
     n_orb_act = no + nv - nf
     if prep is None:   # inputs of the sample (untimed): the law on the host in FP64
         eps = S.orbital_energies(seed, no, nv, nf)
-        L = S.aux_loading(seed, na, no, nv)
+        L = S.aux_loading(seed, na, no, nv) if L is None else L
         R = L @ S.pair_normals_ov(seed, na, no, nv, nf, nf + 1)
         Rt = L @ S.pair_normals_row(seed, na, no + nv, no - 1)
         prep = {"eps": eps, "L": L, "R": R, "Rt": Rt}
@@ -743,13 +743,14 @@ def run_large(args):
                                           for v in h_in.values())
     line["e2e"] = {"value": world * n_e2e / dt, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(sum(a.nbytes for a in h_out)), "steps": n_e2e,
-                   "note": "ltgw_solve_streamed with host inputs: every active block crosses the link twice per "
-                           "solve (metric, projection) from pinned memory, overlapped with the previous block's "
-                           "work; B_tgt, eps, targets, shift from host; results to host"}
+                   "note": "ltgw_solve_streamed with host inputs: every active block crosses the link once per "
+                           "solve from pinned memory (the split copy kept from the metric's pass feeds the "
+                           "projection), overlapped with the previous block's work; B_tgt, eps, targets, shift "
+                           "from host; results to host"}
     line["e2e_qp_max_mev_vs_device_inputs"] = float(np.abs(h_out[1] - e_main).max() * HA2MEV)
     del host_blocks, hsrc
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sec, sample_s, desc, _, parts = cpu_oracle_sample(cfg, N)
+        sec, sample_s, desc, _, parts = cpu_oracle_sample(cfg, N, L=law.L.cpu().numpy())
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{desc}; sample ran {sample_s:.1f} s",
                                 "extrapolated_s_per_solve": sec, "parts_s": parts}

@@ -198,8 +198,12 @@ ltgw_status ltgw_solve_ev(ltgw_ctx *ctx, const ltgw_params *p, const double *eps
  *   block buffers: work that fill issues on fill_stream overlaps the
  *   library's work on the previous block, which runs on `stream`.
  * Blocks hold occ_block orbitals (the last may hold fewer) and are requested
- * in ascending order, each twice: for the NAF metric K = sum over blocks of
- * B B^T (Eq. nafeq), then for the projection R~ = U^T R (Eq. naftrafo).
+ * in ascending order for the NAF metric K = sum over blocks of B B^T
+ * (Eq. nafeq).  The tensor-core forms keep each block, transposed and split
+ * into BF16 hi / lo (4 bytes per value, n_aux * n_act * n_virt values in
+ * all), as the operand of the projection R~ = U^T R (Eq. naftrafo), so they
+ * request every block once; the FP64 form requests every block a second time
+ * for the projection (the tensor is never resident in FP64).
  * Needs NAF (naf_thresh >= 0).  Other arguments and outputs as for
  * ltgw_solve.  Synchronises `stream` (and fill_stream).
  */

@@ -593,14 +593,16 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
 // With Ut == nullptr (no NAF) they are copies of the active blocks of B_ov, B_tgt.
 // With `window` set, only the ov part runs, for n_ov columns of B_act written
 // into columns [col0, col0 + n_ov) of Bf (row stride ld_bf); padding is left
-// to the caller.
+// to the caller.  With Bh_in / Bl_in set (and B_act NULL), the ov block comes
+// already transposed and split: BF16 hi / lo [roundup(n_ov,128)][roundup(n_aux,64)].
 struct OvWindow {
   int64_t col0 = 0, ld_bf = 0;
 };
 
 ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, const double *B_act, int64_t ld_act,
                            int64_t n_ov, const double *B_tgt, int n_orb, int n_fc, int T, int n_orb_act, float *Bf,
-                           double *BtT64, float *BtT32, cudaStream_t s, const OvWindow *window = nullptr) {
+                           double *BtT64, float *BtT32, cudaStream_t s, const OvWindow *window = nullptr,
+                           const __nv_bfloat16 *Bh_in = nullptr, const __nv_bfloat16 *Bl_in = nullptr) {
   const int64_t Kp_ov = (n_ov + 63) / 64 * 64;
   const int MpN = (N + 127) / 128 * 128, KpN = (N + 63) / 64 * 64;
   const int64_t rowsT = (int64_t)T * n_orb_act, rowsTp = (rowsT + 127) / 128 * 128;
@@ -619,13 +621,14 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   const int MpT = (n_orb_act + 127) / 128 * 128;
   float *UtF, *BactT, *BtgT, *ones;
   __nv_bfloat16 *Bh, *Bl, *Uh = nullptr, *Ul = nullptr;   // B operands pre-split for the TMA-fed kernel
+  const bool pre = Bh_in != nullptr;
   auto layout = [&](Arena &A) {
     UtF = A.take<float>((size_t)MpN * Kpa);
-    BactT = A.take<float>((size_t)nI_ov * 128 * Kpa);
+    BactT = (B_act && !pre) ? A.take<float>((size_t)nI_ov * 128 * Kpa) : nullptr;
     BtgT = window ? nullptr : A.take<float>((size_t)T * MpT * Kpa);
     ones = A.take<float>((size_t)std::max(T, 1) * Kpa);
-    Bh = A.take<__nv_bfloat16>((size_t)nI_ov * 128 * Kpa);
-    Bl = A.take<__nv_bfloat16>((size_t)nI_ov * 128 * Kpa);
+    Bh = (B_act && !pre) ? A.take<__nv_bfloat16>((size_t)nI_ov * 128 * Kpa) : nullptr;
+    Bl = (B_act && !pre) ? A.take<__nv_bfloat16>((size_t)nI_ov * 128 * Kpa) : nullptr;
     if (!window) {
       Uh = A.take<__nv_bfloat16>((size_t)MpN * Kpa);
       Ul = A.take<__nv_bfloat16>((size_t)MpN * Kpa);
@@ -636,7 +639,7 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
   if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "tensor-core operand allocation failed"); return ctx->status(); }
   layout(ctx->a5);
   CHECK_LAUNCH(ctx, launch_to_f32_padded(Ut, n_aux, N, n_aux, UtF, MpN, Kpa, s), 1);
-  if (B_act)
+  if (B_act && !pre)
     CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_act, ld_act, 0, n_aux, (int)n_ov, BactT, Kpa, nI_ov * 128, 1, 0, 0, s),
                  1);
   if (!window)
@@ -644,11 +647,11 @@ ltgw_status naf_project_tc(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, co
                                                (int64_t)n_aux * n_orb, (int64_t)MpT * Kpa, s), 1);
   CHECK_LAUNCH(ctx, launch_scale_table(nullptr, n_aux, Kpa, std::max(T, 1), nullptr, nullptr, SCALE_NONE, ones, s), 1);
   // R~_ov = U^T R_ov: rows N (A = U^T), columns n_ov (B rows = R_ov^T)
-  if (B_act) {
-    CHECK_LAUNCH(ctx, launch_split_bf16(BactT, Bh, Bl, (int64_t)nI_ov * 128 * Kpa, s), 1);
+  if (B_act || pre) {
+    if (!pre) CHECK_LAUNCH(ctx, launch_split_bf16(BactT, Bh, Bl, (int64_t)nI_ov * 128 * Kpa, s), 1);
     TcGemmArgs g;
     g.A = UtF; g.B = BactT; g.scale = ones; g.Kp = Kpa; g.n_t = 1; g.nt_group = 1;
-    g.B_hi = Bh; g.B_lo = Bl; g.rows_a = MpN; g.rows_b = (int64_t)nI_ov * 128;
+    g.B_hi = pre ? Bh_in : Bh; g.B_lo = pre ? Bl_in : Bl; g.rows_a = MpN; g.rows_b = (int64_t)nI_ov * 128;
     TcRun run;
     const int nI = (N + 127) / 128;
     if (tc_run(ctx, ctx->a4, g, full_tiles(nI, nI_ov), 0, &run, s) != LTGW_OK) return ctx->status();
@@ -973,6 +976,13 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   } fill_drain{ctx, streamed};
   const int blk = streamed ? std::min(occ_block, n_act) : 0;
   double *d_blk[2] = {nullptr, nullptr};
+  // streamed tensor-core forms: every block, transposed and split into BF16
+  // hi / lo as the projection's operand, is kept from the metric's pass, so
+  // that the callback is asked for each block once
+  const bool keep_split = streamed && mixed;
+  const int64_t n_ov_p = (n_ov + 127) / 128 * 128, Kpa_aux = (n_aux + 63) / 64 * 64;
+  __nv_bfloat16 *d_Rh = nullptr, *d_Rl = nullptr;
+  float *d_Rt = nullptr;   // one block, transposed, FP32
   ctx->gen_ms = 0.0;
   // ---- phase-1 workspace: inputs, grids, NAF
   double *d_eps, *d_delta, *d_om, *d_wt, *d_x, *d_w, *d_E, *d_epsn, *d_shift, *d_Bov, *d_Btg, *d_Ut, *d_lam;
@@ -989,6 +999,9 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     d_Bov = bov_dev ? const_cast<double *>(B_ov) : A.take<double>((size_t)n_aux * n_ov_all);
     d_blk[0] = streamed ? A.take<double>((size_t)n_aux * blk * n_virt) : nullptr;
     d_blk[1] = streamed ? A.take<double>((size_t)n_aux * blk * n_virt) : nullptr;
+    d_Rh = keep_split ? A.take<__nv_bfloat16>((size_t)n_ov_p * Kpa_aux) : nullptr;
+    d_Rl = keep_split ? A.take<__nv_bfloat16>((size_t)n_ov_p * Kpa_aux) : nullptr;
+    d_Rt = keep_split ? A.take<float>((size_t)blk * n_virt * Kpa_aux) : nullptr;
     d_Btg = btg_dev ? const_cast<double *>(B_tgt) : A.take<double>((size_t)T * n_aux * n_orb);
     d_Ut = naf ? A.take<double>((size_t)n_aux * n_aux) : nullptr;
     d_lam = naf ? A.take<double>(n_aux) : nullptr;
@@ -1094,6 +1107,11 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
       if (get_block(i0, i1, &B_blk) != LTGW_OK) return ctx->status();
       if (mixed) {
         if (naf_metric_tc(ctx, n_aux, cols, B_blk, cols, K, s, 1.0) != LTGW_OK) return ctx->status();
+        // the projection's operand rows (i0 - n_fc) n_virt .. + cols, transposed and split
+        const int64_t off = (int64_t)(i0 - n_fc) * n_virt * Kpa_aux;
+        CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_blk, cols, 0, n_aux, (int)cols, d_Rt, (int)Kpa_aux, (int)cols,
+                                                   1, 0, 0, s), 1);
+        CHECK_LAUNCH(ctx, launch_split_bf16(d_Rt, d_Rh + off, d_Rl + off, cols * Kpa_aux, s), 1);
       } else {
         GemmF64Args g;  // K += B_blk B_blk^T
         g.M = n_aux; g.N = n_aux; g.K = cols;
@@ -1102,6 +1120,10 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
         CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, true, s), 1);
       }
       if (block_done() != LTGW_OK) return ctx->status();
+    }
+    if (keep_split && n_ov_p > n_ov) {
+      LTGW_CUDA(ctx, cudaMemsetAsync(d_Rh + n_ov * Kpa_aux, 0, (size_t)(n_ov_p - n_ov) * Kpa_aux * 2, s));
+      LTGW_CUDA(ctx, cudaMemsetAsync(d_Rl + n_ov * Kpa_aux, 0, (size_t)(n_ov_p - n_ov) * Kpa_aux * 2, s));
     }
     return LTGW_OK;
   };
@@ -1151,23 +1173,9 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   const double *Btt = d_Btg + n_fc;
   int64_t ld_btt = n_orb, stride_btt = (int64_t)n_aux * n_orb;
   if (mixed && streamed) {
-    const int64_t MpN = (N + 127) / 128 * 128;
-    LTGW_CUDA(ctx, cudaMemsetAsync(d_Bf, 0, (size_t)MpN * Kp_ov * sizeof(float), s));
-    for (int i0 = n_fc; i0 < n_occ; i0 += blk) {
-      const int i1 = std::min(n_occ, i0 + blk);
-      const int64_t cols = (int64_t)(i1 - i0) * n_virt;
-      double *B_blk = nullptr;
-      if (get_block(i0, i1, &B_blk) != LTGW_OK) return ctx->status();
-      OvWindow win;
-      win.col0 = (int64_t)(i0 - n_fc) * n_virt;
-      win.ld_bf = Kp_ov;
-      if (naf_project_tc(ctx, N, n_aux, d_Ut, B_blk, cols, cols, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64,
-                         d_BtT32, s, &win) != LTGW_OK)
-        return ctx->status();
-      if (block_done() != LTGW_OK) return ctx->status();
-    }
-    if (naf_project_tc(ctx, N, n_aux, d_Ut, nullptr, 0, 0, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64, d_BtT32,
-                       s) != LTGW_OK)
+    // one projection over every block's kept operand: no second pass of the callback
+    if (naf_project_tc(ctx, N, n_aux, d_Ut, nullptr, 0, n_ov, d_Btg, n_orb, n_fc, T, n_orb_act, d_Bf, d_BtT64,
+                       d_BtT32, s, nullptr, d_Rh, d_Rl) != LTGW_OK)
       return ctx->status();
   } else if (mixed) {
     if (naf_project_tc(ctx, N, n_aux, naf ? d_Ut : nullptr, B_act, ld_act, n_ov, d_Btg, n_orb, n_fc, T, n_orb_act,

@@ -82,10 +82,15 @@ def pair_normals_row(seed: int, rows: int, n_orb: int, p: int):
     return out
 
 
-def aux_loading(seed: int, n_aux: int, n_occ: int, n_virt: int, qr_dtype=None):
+def aux_loading(seed: int, n_aux: int, n_occ: int, n_virt: int, qr_dtype=None, host_qr: bool = False):
     """L[Q, r] = U[Q, r] sigma_r / sqrt(n_occ n_virt) on the device (FP64 result;
-    the QR factorisation runs in qr_dtype, FP64 by default)."""
+    the QR factorisation runs in qr_dtype, FP64 by default).  host_qr: the
+    host generator's L (numpy QR in FP64) copied to the device, for processes
+    where the device QR's library cannot be loaded (under a profiler)."""
     import torch
+    if host_qr:
+        from . import aux_loading as host_aux_loading
+        return torch.from_numpy(host_aux_loading(seed, n_aux, n_occ, n_virt)).cuda()
     g = normal_matrix(seed, STREAM_U, n_aux, n_aux)
     if qr_dtype is not None and qr_dtype != torch.float64:
         q, r = torch.linalg.qr(g.to(qr_dtype))
@@ -101,9 +106,10 @@ def aux_loading(seed: int, n_aux: int, n_occ: int, n_virt: int, qr_dtype=None):
 class DeviceLaw:
     """One request's synthetic RI tensor, generated on the device on demand."""
 
-    def __init__(self, n_occ, n_virt, n_aux, n_frozen=0, seed=20230710, n_targets=2, gemm="fp64"):
+    def __init__(self, n_occ, n_virt, n_aux, n_frozen=0, seed=20230710, n_targets=2, gemm="fp64", host_qr=False):
         """gemm: "fp64" (the exact law), "fp32" (QR and loading GEMM in FP32) or
-        "tf32" (QR in FP32, loading GEMM on the TF32 tensor cores)."""
+        "tf32" (QR in FP32, loading GEMM on the TF32 tensor cores); host_qr
+        (with "fp64"): the rotation from the host generator's QR."""
         import torch
         self.n_occ, self.n_virt, self.n_aux, self.n_frozen, self.seed = n_occ, n_virt, n_aux, n_frozen, seed
         self.gemm = gemm
@@ -111,7 +117,7 @@ class DeviceLaw:
         self.eps = orbital_energies(seed, n_occ, n_virt, n_frozen)
         self.targets = gap_targets(n_occ, n_targets)
         self.shift = uniform(seed, STREAM_SHIFT, len(self.targets), -0.05, 0.05)
-        self.L = aux_loading(seed, n_aux, n_occ, n_virt, qr_dtype=self.dtype)
+        self.L = aux_loading(seed, n_aux, n_occ, n_virt, qr_dtype=self.dtype, host_qr=host_qr and gemm == "fp64")
         self._Lc = self.L.to(self.dtype)
 
     def _gemm(self, z):

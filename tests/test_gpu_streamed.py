@@ -60,7 +60,9 @@ def test_streamed_matches_oracle(mid, oracle_lt, mixed, occ_block, async_fill):
     finally:
         ctx.close()
     nblk = -(-50 // occ_block)
-    assert len(calls) == 2 * nblk and calls[0][0] == 10 and calls[nblk - 1][1] == 60
+    # FP64: each block twice (metric, projection); split BF16 keeps the projection's
+    # operand from the metric's pass and asks once
+    assert len(calls) == (1 if mixed else 2) * nblk and calls[0][0] == 10 and calls[nblk - 1][1] == 60
     assert np.all(st == 0)
     tol = QP_TOL_MIXED if mixed else QP_TOL
     assert np.abs(e - e_o).max() <= tol, np.abs(e - e_o).max()
