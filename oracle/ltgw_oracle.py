@@ -51,7 +51,8 @@ __all__ = [
     "qp_newton", "solve", "solve_projected", "occ_blocks", "naf_metric_blocked", "naf_project_blocked",
     "solve_blocked", "sinc_laplace_grid", "pade_nodes",
     "E4M3_MAX", "e4m3_round", "fp8_row_quantize", "fp8_row_split", "fp8_split_product", "pi_scale_table",
-    "polarizability_fp8",
+    "polarizability_fp8", "SLICE_BITS", "slice_rows", "slice_product",
+    "pi_factor_table", "polarizability_emulated",
     "cosine_grid", "tau_moments", "polarizability_tau", "evgw_energies", "evgw",
 ]
 
@@ -267,10 +268,10 @@ def fp8_split_product(A, B):
     return (ha @ hb.T + ha @ lb.T + la @ hb.T) / da[:, None] / db[None, :]
 
 
-def pi_scale_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
-    """Per-pair factors in FP32: Delta / (w_j^2 + Delta^2) per frequency (Eq. Pi),
+def pi_factor_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
+    """Per-pair factors in FP64: Delta / (w_j^2 + Delta^2) per frequency (Eq. Pi),
     w_m Delta exp(-Delta^2 x_m) per Laplace point (the M^m form) or
-    exp(-Delta tau_k) per imaginary-time node, each formed in FP64 and rounded once."""
+    exp(-Delta tau_k) per imaginary-time node."""
     delta = np.asarray(delta, dtype=np.float64)
     if tau is not None:
         rows = [np.exp(-delta * t) for t in tau]
@@ -278,7 +279,12 @@ def pi_scale_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
         rows = [delta / (om * om + delta * delta) for om in omegas]
     else:
         rows = [w[m] * delta * np.exp(-delta * delta * x[m]) for m in range(len(x))]
-    return np.array(rows).astype(np.float32)
+    return np.array(rows)
+
+
+def pi_scale_table(delta, omegas=None, x=None, w=None, tau=None) -> np.ndarray:
+    """The factors of pi_factor_table, each formed in FP64 and rounded once to FP32."""
+    return pi_factor_table(delta, omegas, x, w, tau).astype(np.float32)
 
 
 def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None, tau=None, gamma=None) -> np.ndarray:
@@ -298,6 +304,71 @@ def polarizability_fp8(Bt, delta, omegas, spin: int = 2, x=None, w=None, tau=Non
         M[k] = np.tril(Mk) + np.tril(Mk, -1).T
     if tau is not None:
         return polarizability_tau(M, gamma, spin)
+    if x is None:
+        return -2.0 * spin * M
+    return polarizability_lt(M, omegas, x, spin)
+
+
+# ----------------------------------------------------------------------------
+# FP64-accurate product from integer slices (not a step of the paper: an
+# emulation of FP64 contractions on tensor cores that multiply small integers
+# exactly)
+# ----------------------------------------------------------------------------
+# Its plain definition: each row r of an operand X is written in fixed point
+# relative to e_r, the exponent of the row's largest magnitude (max|X_r| <
+# 2^e_r), Q = rint(X_r 2^(7 s - e_r)) (nearest, ties to even), and Q in s
+# balanced base-128 digits a_1 (most significant) .. a_s, so that
+# X_r ~ 2^e_r sum_i a_i 2^(-7 i) with |a_i| <= 64 (|a_1| <= 128).  Products of
+# two such operands keep the digit pairs with i + j <= s + 1 and sum them
+# exactly: D = sum_{i+j<=s+1} 2^(-7(i+j)) (a_i b_j^T) 2^(e_A + e_B).
+SLICE_BITS = 7
+
+
+def slice_rows(X, n_slices: int):
+    """(digits [n_slices][rows][cols] as float64 integers, e [rows]) of the
+    fixed-point rows of X (see above)."""
+    X = np.asarray(X, dtype=np.float64)
+    m = np.abs(X).max(axis=1)
+    _, e = np.frexp(m)                          # m = f 2^e, f in [0.5, 1): m < 2^e
+    e = np.where(m > 0, e, 0).astype(np.int64)
+    Q = np.rint(np.ldexp(X, (SLICE_BITS * n_slices - e)[:, None]))   # exact scaling, exact rounding
+    digits = np.empty((n_slices,) + X.shape)
+    for i in range(n_slices - 1, -1, -1):       # least significant first, balanced
+        t = np.floor((Q + 64.0) / 128.0)
+        digits[i] = Q - 128.0 * t
+        Q = t
+    digits[0] += 128.0 * Q                      # what is left belongs to the leading digit
+    return digits, e
+
+
+def slice_product(A, B, n_slices: int = 6) -> np.ndarray:
+    """A B^T from the integer slices of A's and B's rows, digit pairs with
+    i + j <= n_slices + 1, each pair's integer product summed exactly."""
+    a, ea = slice_rows(A, n_slices)
+    b, eb = slice_rows(B, n_slices)
+    D = np.zeros((A.shape[0], B.shape[0]))
+    for L in range(2, n_slices + 2):
+        acc = np.zeros((A.shape[0], B.shape[0]), dtype=np.int64)
+        for i in range(1, L):
+            j = L - i
+            if i <= n_slices and j <= n_slices:
+                acc += a[i - 1].astype(np.int64) @ b[j - 1].astype(np.int64).T
+        D += np.ldexp(acc.astype(np.float64), -SLICE_BITS * L)
+    return np.ldexp(np.ldexp(D, ea[:, None]), eb[None, :])
+
+
+def polarizability_emulated(Bt, delta, omegas, spin: int = 2, x=None, w=None, n_slices: int = 6) -> np.ndarray:
+    """Pi with every contraction from integer slices: for each frequency (Eq.
+    Pi) or Laplace point (M^m form) with FP64 factors f_t (pi_factor_table),
+    A_t = R~ diag(f_t) in FP64 (one rounding per entry), M_t =
+    slice_product(A_t, R~, n_slices), lower triangle (P >= Q) mirrored; then
+    Pi as in polarizability_direct or polarizability_lt."""
+    Bt = np.asarray(Bt, dtype=np.float64)
+    S = pi_factor_table(delta, omegas, x, w)
+    M = np.empty((len(S), Bt.shape[0], Bt.shape[0]))
+    for t in range(len(S)):
+        Mt = slice_product(Bt * S[t][None, :], Bt, n_slices)
+        M[t] = np.tril(Mt) + np.tril(Mt, -1).T
     if x is None:
         return -2.0 * spin * M
     return polarizability_lt(M, omegas, x, spin)
