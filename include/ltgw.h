@@ -317,11 +317,50 @@ ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const
                                     int n_tau, const double *x, const double *w, int spin,
                                     double *Pi, void *stream);
 
+/* The polarisability of ltgw_polarizability (Eq. Pi, or with n_tau > 0 the
+ * M^m form of Eq. LT) with every contraction FP64-accurate on the tensor
+ * cores (not a step of the paper: the FP64 form at tensor-core speed).  Per
+ * frequency or Laplace point t the FP64 factors f_t (Delta / (w_t^2 +
+ * Delta^2), or w_t Delta exp(-Delta^2 x_t); each operation rounded once)
+ * scale R~'s columns (one FP64 product per entry), and M_t = (R~ diag(f_t))
+ * R~^T is formed as in ltgw_gemm_emulated with n_slices slices (lower tiles,
+ * mirrored); the direct form writes Pi_j = -2 s M_j, the Laplace form
+ * recombines -2 s sum_m exp(-w_j^2 x_m) M^m in FP64.  Relative error about
+ * 2^(-7 n_slices) of the largest row products (n_slices = 6: about 1e-12 in
+ * Frobenius norm, the FP64 form's results to 1e-8 Ha in the quasi-particle
+ * energies).  n_slices in [2, 8]; other arguments, layout and errors as
+ * ltgw_polarizability.  Synchronises. */
+ltgw_status ltgw_polarizability_emulated(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                         const double *delta, int n_omega, const double *omegas,
+                                         int n_tau, const double *x, const double *w, int spin,
+                                         int n_slices, double *Pi, void *stream);
+
 /* Screening (Eq. ScreenedCoulombOrbital): C_j = [1 - Pi_j]^-1 - 1 for each of
  * n_omega matrices (device [n_omega][N][N] in and out, may not alias).
  * Synchronises; LTGW_ERR_NOT_SPD if a pivot was not positive. */
 ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C,
                         void *stream);
+
+/* FP64-accurate product C = A B^T on the tensor cores (not a step of the
+ * paper: an emulation of FP64 contractions with exact small-integer products).
+ * Each row r of A (and of B) is written in fixed point relative to e_r, the
+ * exponent of the row's largest magnitude (max|X_r| < 2^e_r):
+ * Q = rint(X_r 2^(7 s - e_r)) (ties to even), in s balanced base-128 digits
+ * a_1 .. a_s (|a_1| <= 128, |a_i| <= 64 after it); then
+ * C = sum over digit pairs with i + j <= s + 1 of 2^(-7(i+j)) a_i b_j^T,
+ * times 2^(e_A + e_B).  Every pair's integer products are exact in BF16 and
+ * summed exactly (FP32 drains of at most 1024 pairs, FP64 after), so the only
+ * errors are the dropped digits: about 2^(-7s) of the rows' largest
+ * magnitudes (s = 6: about 1e-12 relative Frobenius on products of Gaussian
+ * rows).  A [m][lda], B [n][ldb] (k columns used), C [m][ldc]: device, row
+ * major; sym: B = A, only the lower tiles are computed and C (ldc = n) is
+ * written whole, symmetric.  n_slices in [2, 8].  A and B must be finite
+ * (NaN or Inf give undefined values in C, no error).  A, B are read only and
+ * stay the caller's; the slices and partial tiles live in the context's
+ * scratch (LTGW_ERR_NOMEM if they do not fit).  Synchronises. */
+ltgw_status ltgw_gemm_emulated(ltgw_ctx *ctx, int m, int n, int64_t k, const double *A, int64_t lda,
+                               const double *B, int64_t ldb, double *C, int64_t ldc, int sym, int n_slices,
+                               void *stream);
 
 /* ---- request server (continuous admission of solves) -------------------- */
 
@@ -356,7 +395,10 @@ typedef struct ltgw_server ltgw_server;
  * footprints of the running requests, with its own, stays within
  * hbm_budget_bytes: the oldest that fits first.  A request that does not fit
  * may be passed by later ones that do at most 8 times; after that nothing is
- * admitted ahead of it.  Each slot keeps its workspace between requests. */
+ * admitted ahead of it.  A request whose solve runs out of device memory
+ * while others run goes back to the head of the queue with its estimate
+ * doubled (at most 4 times; at the full budget it runs alone).  Each slot
+ * keeps its workspace between requests. */
 ltgw_status ltgw_server_create(ltgw_server **out, int device, int n_slots, size_t hbm_budget_bytes);
 /* Queue a request (never blocks on the GPU); LTGW_ERR_NOMEM if its estimated
  * footprint alone exceeds the budget. */
@@ -367,7 +409,8 @@ int ltgw_server_poll(ltgw_server *srv, ltgw_completion *out, int max_out);
 ltgw_status ltgw_server_wait_all(ltgw_server *srv, double timeout_s);
 /* Finish the running requests, drop the queued ones, release everything. */
 void ltgw_server_destroy(ltgw_server *srv);
-/* Estimated device bytes of one solve (inputs staged + workspace). */
+/* Estimated device bytes of one solve (inputs staged + workspace, tensor-core
+ * partial tiles included; with NAF the post-NAF size is taken as n_aux / 2). */
 size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt);
 
 /* ---- allocation-free screening ------------------------------------------ */

@@ -586,6 +586,105 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
   return LTGW_OK;
 }
 
+// FP64-accurate products from integer slices on the tensor cores.  Each
+// operand row is cut into s balanced base-128 digits of its fixed-point form
+// (launch_slice_rows); the product sums 2^(-7(i+j)) a_i b_j^T over the digit
+// pairs with i + j <= s + 1, every pair on the split-BF16 kernel (A digits in
+// FP32 give hi = digit, lo = 0; B digits in the hi operand, zeros in the lo
+// one), so its integer products are exact and its FP32 sums too (drains of
+// at most 1024 pairs: |sum| <= 1024 * 128 * 128 = 2^24); the pair results
+// are added in FP64 in the reduction, then scaled by 2^(e_A + e_B).  Two of
+// the kernel's three products per step multiply zeros here: the price of
+// reusing the split-BF16 kernel unchanged.
+struct EmuPlan {
+  int m = 0, n = 0, s = 0, nIa = 0, nIb = 0, Mpa = 0, Mpb = 0;
+  int64_t K = 0, Kp = 0, stra = 0, strb = 0;
+  bool lower = false;   // lower tiles of a square product, mirrored
+  std::vector<int> tiles, tindex;
+  float *dA = nullptr, *ones = nullptr;
+  __nv_bfloat16 *dB = nullptr, *zeros = nullptr;
+  int *ea = nullptr, *eb = nullptr, *d_tindex = nullptr;
+  double *factors = nullptr;   // n_factors x K FP64 column factors of A (optional)
+};
+
+ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lower, int n_factors, EmuPlan *p,
+                        cudaStream_t st) {
+  p->m = m; p->n = n; p->s = s; p->K = K; p->lower = lower;
+  p->Kp = (K + 63) / 64 * 64;
+  p->nIa = (m + 127) / 128; p->nIb = (n + 127) / 128;
+  p->Mpa = p->nIa * 128; p->Mpb = p->nIb * 128;
+  p->stra = (int64_t)p->Mpa * p->Kp; p->strb = (int64_t)p->Mpb * p->Kp;
+  p->tiles = lower ? lower_tiles(p->nIa, &p->tindex) : full_tiles(p->nIa, p->nIb);
+  auto layout = [&](Arena &Ar) {
+    p->dA = Ar.take<float>((size_t)s * p->stra);
+    p->dB = Ar.take<__nv_bfloat16>((size_t)s * p->strb);
+    p->zeros = Ar.take<__nv_bfloat16>((size_t)p->strb);
+    p->ones = Ar.take<float>((size_t)p->Kp);
+    p->ea = Ar.take<int>(p->Mpa);
+    p->eb = Ar.take<int>(p->Mpb);
+    p->d_tindex = lower ? Ar.take<int>(p->tindex.size()) : nullptr;
+    p->factors = n_factors ? Ar.take<double>((size_t)n_factors * K) : nullptr;
+  };
+  ctx->a5.begin_sizing();
+  layout(ctx->a5);
+  if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "slice operand allocation failed"); return ctx->status(); }
+  layout(ctx->a5);
+  if (lower) copy_in(ctx, p->d_tindex, p->tindex.data(), p->tindex.size() * sizeof(int), st);
+  // padding rows stay zero: the slicing writes rows < m (n) only
+  LTGW_CUDA(ctx, cudaMemsetAsync(p->dA, 0, (size_t)s * p->stra * sizeof(float), st));
+  LTGW_CUDA(ctx, cudaMemsetAsync(p->dB, 0, (size_t)s * p->strb * sizeof(__nv_bfloat16), st));
+  LTGW_CUDA(ctx, cudaMemsetAsync(p->zeros, 0, (size_t)p->strb * sizeof(__nv_bfloat16), st));
+  LTGW_CUDA(ctx, cudaMemsetAsync(p->ea, 0, p->Mpa * sizeof(int), st));
+  LTGW_CUDA(ctx, cudaMemsetAsync(p->eb, 0, p->Mpb * sizeof(int), st));
+  CHECK_LAUNCH(ctx, launch_scale_table(nullptr, p->Kp, p->Kp, 1, nullptr, nullptr, SCALE_NONE, p->ones, st), 1);
+  return ctx->status();
+}
+
+// C = post * A diag(colscale) B^T from the slices in p (A's sliced here, B's
+// already in p->dB / p->eb).  C [m][ldc]; in the lower form C (ldc = n) is
+// written whole and symmetric.  post must be a power of two (or +-1, +-2, +-4):
+// it is folded into the exact 2^(-7L) factors.
+ltgw_status emu_product(ltgw_ctx *ctx, EmuPlan &p, const double *A, int64_t lda, const double *colscale,
+                        double post, double *C, int64_t ldc, cudaStream_t st) {
+  CHECK_LAUNCH(ctx, launch_slice_rows(A, lda, p.m, p.K, p.Kp, p.s, p.stra, p.dA, nullptr, p.ea, st, colscale), 1);
+  bool first = true;
+  for (int L = 2; L <= p.s + 1; ++L) {
+    for (int i = 1; i < L; ++i) {
+      const int j = L - i;
+      if (i > p.s || j > p.s) continue;
+      TcGemmArgs g;
+      g.A = p.dA + (int64_t)(i - 1) * p.stra; g.B = nullptr; g.scale = p.ones; g.Kp = p.Kp; g.n_t = 1;
+      g.nt_group = 1;
+      g.B_hi = p.dB + (int64_t)(j - 1) * p.strb; g.B_lo = p.zeros; g.rows_a = p.Mpa; g.rows_b = p.Mpb;
+      g.drain_k = 1024;   // |partial sums| <= 1024 * 2^14 = 2^24: exact in FP32
+      g.out_colmajor = p.lower ? 1 : 0;
+      TcRun run;
+      if (tc_run(ctx, ctx->a4, g, p.tiles, 0, &run, st) != LTGW_OK) return ctx->status();
+      const double alpha = post * ldexp(1.0, -7 * L);
+      if (p.lower) {
+        CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles,
+                                               p.d_tindex, p.nIa, 1, p.m, alpha, C, st, first ? 0.0 : 1.0,
+                                               run.nt_group, 1),
+                     1);
+      } else {
+        CHECK_LAUNCH(ctx, launch_tc_reduce_full_acc(run.partial, run.partial32, run.splits, run.groups, run.n_tiles,
+                                                    p.nIb, p.m, p.n, alpha, C, ldc, first ? 0.0 : 1.0, st), 1);
+      }
+      first = false;
+    }
+  }
+  CHECK_LAUNCH(ctx, launch_scale_exp2(C, p.lower ? p.m : ldc, p.m, p.n, p.ea, p.eb, st), 1);
+  return ctx->status();
+}
+
+ltgw_status emu_gemm(ltgw_ctx *ctx, int m, int n, int64_t K, const double *A, int64_t lda, const double *B,
+                     int64_t ldb, double *C, int64_t ldc, bool sym, int s, cudaStream_t st) {
+  EmuPlan p;
+  if (emu_prepare(ctx, m, n, K, s, sym, 0, &p, st) != LTGW_OK) return ctx->status();
+  CHECK_LAUNCH(ctx, launch_slice_rows(B, ldb, n, K, p.Kp, s, p.strb, nullptr, p.dB, p.eb, st), 1);
+  return emu_product(ctx, p, A, lda, nullptr, 1.0, C, ldc, st);
+}
+
 // Operands of the mixed form after the NAF step (Eq. naftrafo in split BF16):
 //   Bf       FP32 [roundup(N,128)][roundup(n_ov,64)]   R~_ov, the Pi operand
 //   BtT64    FP64 [T][n_orb_act][N]                      R~_tgt transposed (column dot)
@@ -1537,6 +1636,93 @@ ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const
                                     const double *delta, int n_omega, const double *omegas, int n_tau,
                                     const double *x, const double *w, int spin, double *Pi, void *stream) {
   return polarizability_tc_api(ctx, N, n_pairs, Bt, delta, n_omega, omegas, n_tau, x, w, spin, Pi, stream, true);
+}
+
+ltgw_status ltgw_gemm_emulated(ltgw_ctx *ctx, int m, int n, int64_t k, const double *A, int64_t lda,
+                               const double *B, int64_t ldb, double *C, int64_t ldc, int sym, int n_slices,
+                               void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, m >= 1 && n >= 1 && k >= 1 && lda >= k && ldb >= k && ldc >= n, "bad sizes");
+  REQUIRE(ctx, n_slices >= 2 && n_slices <= 8, "n_slices must be in [2, 8]");
+  REQUIRE(ctx, A && C && (sym || B), "a required pointer is NULL");
+  REQUIRE(ctx, !sym || (m == n && ldc == n), "sym needs m == n and ldc == n");
+  REQUIRE(ctx, is_device_ptr(A) && is_device_ptr(C) && (sym || is_device_ptr(B)), "A, B, C must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  ctx->stats = ltgw_stats{};
+  ctx->mark(EV_START, s);
+  if (emu_gemm(ctx, m, n, k, A, lda, sym ? A : B, sym ? lda : ldb, C, ldc, sym != 0, n_slices, s) != LTGW_OK)
+    return ctx->status();
+  ctx->mark(EV_END, s);
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->stats.ms_total = ctx->ms(EV_START, EV_END);
+  ctx->stats.kernel_launches = ctx->launches;
+  return check_flags(ctx, s);
+}
+
+ltgw_status ltgw_polarizability_emulated(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt,
+                                         const double *delta, int n_omega, const double *omegas, int n_tau,
+                                         const double *x, const double *w, int spin, int n_slices, double *Pi,
+                                         void *stream) {
+  if (!ctx) return LTGW_ERR_BAD_ARG;
+  ctx->reset();
+  REQUIRE(ctx, N >= 1 && n_pairs >= 1 && n_omega >= 1 && n_omega <= 256, "bad sizes");
+  REQUIRE(ctx, n_tau >= 0 && n_tau <= 32, "n_tau must be in [0, 32]");
+  REQUIRE(ctx, spin == 1 || spin == 2, "spin must be 1 or 2");
+  REQUIRE(ctx, n_slices >= 2 && n_slices <= 8, "n_slices must be in [2, 8]");
+  REQUIRE(ctx, Bt && delta && omegas && Pi && (n_tau == 0 || (x && w)), "a required pointer is NULL");
+  REQUIRE(ctx, is_device_ptr(Bt) && is_device_ptr(delta) && is_device_ptr(Pi), "Bt, delta, Pi must be device pointers");
+  LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  LTGW_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+  ctx->stats = ltgw_stats{};
+  ctx->mark(EV_START, s);
+  std::vector<double> h_om(omegas, omegas + n_omega), h_E((size_t)n_omega * std::max(n_tau, 1));
+  for (int j = 0; j < n_omega; ++j)
+    for (int k = 0; k < n_tau; ++k) h_E[(size_t)j * n_tau + k] = exp(-h_om[j] * h_om[j] * x[k]);
+  double *d_om, *d_x, *d_w, *d_E, *d_M;
+  auto layout = [&](Arena &A) {
+    d_om = A.take<double>(n_omega);
+    d_x = A.take<double>(std::max(n_tau, 1));
+    d_w = A.take<double>(std::max(n_tau, 1));
+    d_E = A.take<double>(h_E.size());
+    d_M = n_tau ? A.take<double>((size_t)n_tau * N * N) : nullptr;
+  };
+  ctx->a2.begin_sizing();
+  layout(ctx->a2);
+  if (ctx->a2.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "workspace allocation failed"); return ctx->status(); }
+  layout(ctx->a2);
+  copy_in(ctx, d_om, h_om.data(), n_omega * sizeof(double), s);
+  if (n_tau) {
+    copy_in(ctx, d_x, x, n_tau * sizeof(double), s);
+    copy_in(ctx, d_w, w, n_tau * sizeof(double), s);
+    copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
+  }
+  if (ctx->status() != LTGW_OK) return ctx->status();
+  const int n_t = n_tau ? n_tau : n_omega;
+  EmuPlan p;
+  if (emu_prepare(ctx, N, N, n_pairs, n_slices, true, n_t, &p, s) != LTGW_OK) return ctx->status();
+  ctx->mark(EV_PI0, s);
+  CHECK_LAUNCH(ctx, launch_pi_factor64(delta, n_pairs, n_t, n_tau ? d_x : d_om, n_tau ? d_w : nullptr,
+                                       n_tau ? SCALE_LAPLACE : SCALE_DIRECT, p.factors, s), 1);
+  CHECK_LAUNCH(ctx, launch_slice_rows(Bt, n_pairs, N, n_pairs, p.Kp, n_slices, p.strb, nullptr, p.dB, p.eb, s), 1);
+  // M^m (Laplace points) or Pi_j itself (direct: the factor -2 s is exact)
+  for (int t = 0; t < n_t; ++t)
+    if (emu_product(ctx, p, Bt, n_pairs, p.factors + (int64_t)t * n_pairs, n_tau ? 1.0 : -2.0 * spin,
+                    (n_tau ? d_M : Pi) + (int64_t)t * N * N, N, s) != LTGW_OK)
+      return ctx->status();
+  ctx->mark(EV_PI1, s);
+  if (n_tau)
+    CHECK_LAUNCH(ctx, launch_recombine(d_M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
+                 (n_omega + 63) / 64);
+  ctx->mark(EV_END, s);
+  LTGW_CUDA(ctx, cudaStreamSynchronize(s));   // the staged grid lives in the workspace
+  ctx->stats.ms_total = ctx->ms(EV_START, EV_END);
+  ctx->stats.ms_pi_kernel = ctx->ms(EV_PI0, EV_PI1);
+  ctx->stats.kernel_launches = ctx->launches;
+  return check_flags(ctx, s);
 }
 
 ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, double *C, void *stream) {

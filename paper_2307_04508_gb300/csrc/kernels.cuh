@@ -154,6 +154,22 @@ cudaError_t launch_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *
 // over the 3 Kq codes sums h_a h_b + l_a h_b + h_a l_b.
 cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const float *S, int n_t, int rows,
                                 uint8_t *qa, uint8_t *qb, float *ds_a, float *ds_b, cudaStream_t s, int split);
+// Rows of X (FP64 [rows][ld], `cols` used; with colscale, X_rk colscale_k as one
+// FP64 product) as s balanced base-128 digits of their fixed-point form
+// rint(X_r 2^(7 s - e_r)), e_r the exponent of the row's largest magnitude
+// (m < 2^e_r): digit i to dA / dB [i][r][Kp] (FP32 / BF16, either may be null; zero
+// past cols), e_r to exps[r].  The FP64-accurate product of two sliced operands sums
+// 2^(-7(i+j)) (a_i b_j^T) 2^(e_A + e_B) over i + j <= s + 1.
+cudaError_t launch_slice_rows(const double *X, int64_t ld, int rows, int64_t cols, int64_t Kp, int s,
+                              int64_t slice_stride, float *dA, __nv_bfloat16 *dB, int *exps, cudaStream_t st,
+                              const double *colscale = nullptr);
+// FP64 factors f[t][k] (k < K) of the Pi contraction per frequency (SCALE_DIRECT,
+// p0 = omega) or Laplace point (SCALE_LAPLACE, p0 = x, p1 = w), no fused operations.
+cudaError_t launch_pi_factor64(const double *delta, int64_t K, int n_t, const double *p0, const double *p1,
+                               int mode, double *f, cudaStream_t st);
+// C[r][c] *= 2^(ea[r] + eb[c]).
+cudaError_t launch_scale_exp2(double *C, int64_t ldc, int rows, int cols, const int *ea, const int *eb,
+                              cudaStream_t st);
 // X itself quantised per row as an A operand (split: segments h | l | h).
 cudaError_t launch_fp8_quantize_a(const float *X, int64_t Kp, int64_t Kq, int rows, uint8_t *q, float *ds,
                                   cudaStream_t s, int split);
@@ -177,7 +193,12 @@ cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0,
 cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32, int splits, int groups,
                                   int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
                                   int64_t ld64, int64_t stride64, float *out32, int64_t ld32,
-                                  int rows_p32, int64_t stride32, cudaStream_t s, int64_t cols32 = -1);
+                                  int rows_p32, int64_t stride32, cudaStream_t s, int64_t cols32 = -1,
+                                  double beta = 0.0);
+// out64[r][c] = alpha * (sum of the partials) + beta * out64[r][c], one group.
+cudaError_t launch_tc_reduce_full_acc(const double *partial, const float *partial32, int splits, int groups,
+                                      int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
+                                      int64_t ld64, double beta, cudaStream_t s);
 // W[g][c] = sum over splits and tile rows of cd_out[split][g][I][c], c < cols.
 cudaError_t launch_tc_reduce_coldot(const float *cd_out, int splits, int groups, int n_tile_rows,
                                     int cols_p, int cols, double *W, int64_t ldw, cudaStream_t s);

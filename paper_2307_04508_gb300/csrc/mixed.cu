@@ -48,6 +48,18 @@ __global__ void scale_table_kernel(const double *__restrict__ delta, int64_t K, 
 
 // One thread per lower-triangle element (i >= j) of one matrix t.  Partial
 // tiles are 128 x 128, four scales per group.
+// Sum of FP32 partials as an unevaluated pair hi + lo of FP32 numbers
+// (Knuth's TwoSum per term; about 48 significant bits): the FP32 partials
+// carry errors of 2^-24 of their own, so the pair's sum equals their FP64 sum
+// far below that, and FP32 additions run many times faster than FP64 ones on
+// this part (where the FP64 sum made the reductions FP64-bound).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
 __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const float *__restrict__ partial32,
                                      int splits, int groups, int n_tiles, const int *__restrict__ tile_index,
                                      int nJ, int N, int nt_group, int colmajor, double alpha, double beta,
@@ -58,8 +70,9 @@ __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const f
   const int64_t ntri = (int64_t)N * (N + 1) / 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ntri;
        e += (int64_t)gridDim.x * blockDim.x) {
-    // e -> (i, j), i >= j, row-major lower triangle
-    int a = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    // e -> (i, j), i >= j, row-major lower triangle (an FP32 estimate of the
+    // row, corrected by integer tests)
+    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
     while ((int64_t)(a + 1) * (a + 2) / 2 <= e) ++a;
     while ((int64_t)a * (a + 1) / 2 > e) --a;
     const int b = (int)(e - (int64_t)a * (a + 1) / 2);
@@ -69,9 +82,15 @@ __global__ void tc_reduce_sym_kernel(const double *__restrict__ partial, const f
     const int tile = tile_index[(i / 128) * nJ + (j / 128)];
     const int64_t in_tile = colmajor ? (int64_t)(j % 128) * 128 + (i % 128) : (int64_t)(i % 128) * 128 + (j % 128);
     double acc = 0.0;
-    for (int s = 0; s < splits; ++s) {
-      const int64_t off = ((((int64_t)s * groups + grp) * nt_group + slot) * n_tiles + tile) * (128 * 128) + in_tile;
-      acc += partial32 ? (double)partial32[off] : partial[off];
+    if (partial32) {
+      float hi = 0.0f, lo = 0.0f;
+      for (int s = 0; s < splits; ++s)
+        two_sum_acc(hi, lo, partial32[((((int64_t)s * groups + grp) * nt_group + slot) * n_tiles + tile) * (128 * 128) +
+                                      in_tile]);
+      acc = (double)hi + (double)lo;
+    } else {
+      for (int s = 0; s < splits; ++s)
+        acc += partial[((((int64_t)s * groups + grp) * nt_group + slot) * n_tiles + tile) * (128 * 128) + in_tile];
     }
     acc *= alpha;
     if (beta != 0.0) acc += beta * M[t * NN + (int64_t)i * N + j];
@@ -124,7 +143,7 @@ __global__ void tc_reduce_full_kernel(const double *__restrict__ partial, const 
                                       int splits, int groups, int n_tiles, int nJ, int rows, int cols,
                                       double alpha, double *__restrict__ out64, int64_t ld64, int64_t stride64,
                                       float *__restrict__ out32, int64_t ld32, int64_t cols32, int rows_p32,
-                                      int64_t stride32) {
+                                      int64_t stride32, double beta) {
   const int g = blockIdx.z;
   const int r = blockIdx.y;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (out32 ? cols32 : cols);
@@ -133,12 +152,20 @@ __global__ void tc_reduce_full_kernel(const double *__restrict__ partial, const 
     if (r < rows && c < cols) {
       const int tile = (r / 128) * nJ + (int)(c / 128);
       const int64_t off = (int64_t)(r % 128) * 128 + (c % 128);
-      for (int s = 0; s < splits; ++s) {
-        const int64_t base = (((int64_t)s * groups + g) * n_tiles + tile) * (128 * 128);
-        acc += partial32 ? (double)partial32[base + off] : partial[base + off];
+      if (partial32) {
+        float hi = 0.0f, lo = 0.0f;
+        for (int s = 0; s < splits; ++s)
+          two_sum_acc(hi, lo, partial32[(((int64_t)s * groups + g) * n_tiles + tile) * (128 * 128) + off]);
+        acc = (double)hi + (double)lo;
+      } else {
+        for (int s = 0; s < splits; ++s) acc += partial[(((int64_t)s * groups + g) * n_tiles + tile) * (128 * 128) + off];
       }
       acc *= alpha;
-      if (out64) out64[g * stride64 + (int64_t)r * ld64 + c] = acc;
+      if (out64) {
+        double *o = out64 + g * stride64 + (int64_t)r * ld64 + c;
+        if (beta != 0.0) acc += beta * *o;
+        *o = acc;
+      }
     }
     if (out32 && r < rows_p32) out32[g * stride32 + (int64_t)r * ld32 + c] = (float)acc;
   }
@@ -148,11 +175,10 @@ __global__ void tc_reduce_coldot_kernel(const float *__restrict__ cd, int splits
                                         int cols_p, int cols, double *__restrict__ W, int64_t ldw) {
   const int g = blockIdx.y;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     for (int s = 0; s < splits; ++s)
-      for (int I = 0; I < n_tile_rows; ++I)
-        acc += (double)cd[(((int64_t)s * groups + g) * n_tile_rows + I) * cols_p + c];
-    W[(int64_t)g * ldw + c] = acc;
+      for (int I = 0; I < n_tile_rows; ++I) two_sum_acc(hi, lo, cd[(((int64_t)s * groups + g) * n_tile_rows + I) * cols_p + c]);
+    W[(int64_t)g * ldw + c] = (double)hi + (double)lo;
   }
 }
 
@@ -208,7 +234,7 @@ cudaError_t launch_to_f32_transposed(const double *src, int64_t lds, int64_t c0,
 cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32, int splits, int groups,
                                   int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
                                   int64_t ld64, int64_t stride64, float *out32, int64_t ld32,
-                                  int rows_p32, int64_t stride32, cudaStream_t s, int64_t cols32) {
+                                  int rows_p32, int64_t stride32, cudaStream_t s, int64_t cols32, double beta) {
   if (cols32 < 0) cols32 = ld32;
   const int nrows = out32 ? std::max(rows, rows_p32) : rows;
   const int64_t ncols = out32 ? cols32 : cols;
@@ -217,8 +243,15 @@ cudaError_t launch_tc_reduce_full(const double *partial, const float *partial32,
   if (bx > 64) bx = 64;
   dim3 grid(bx, nrows, groups);
   tc_reduce_full_kernel<<<grid, 256, 0, s>>>(partial, partial32, splits, groups, n_tiles, nJ, rows, cols, alpha,
-                                             out64, ld64, stride64, out32, ld32, cols32, rows_p32, stride32);
+                                             out64, ld64, stride64, out32, ld32, cols32, rows_p32, stride32, beta);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tc_reduce_full_acc(const double *partial, const float *partial32, int splits, int groups,
+                                      int n_tiles, int nJ, int rows, int cols, double alpha, double *out64,
+                                      int64_t ld64, double beta, cudaStream_t s) {
+  return launch_tc_reduce_full(partial, partial32, splits, groups, n_tiles, nJ, rows, cols, alpha, out64, ld64, 0,
+                               nullptr, 0, 0, 0, s, -1, beta);
 }
 
 cudaError_t launch_transpose_f64(const double *src, int64_t lds, int64_t c0, int rows, int cols, double *dst,
@@ -403,6 +436,78 @@ __global__ void __launch_bounds__(Q8_THREADS)
     write_codes(qr, k, q4, xr[k], inv, split, true);
   }
 }
+// One block per row r of X (FP64, row stride ld, `cols` columns; with
+// colscale, X_rk colscale_k, one FP64 product): e_r = the exponent of the
+// row's largest magnitude m (m = f 2^e_r, f in [0.5, 1); 0 for a zero row),
+// the fixed-point row Q = rint(X_r 2^(7 s - e_r)) (exact scaling, ties to
+// even), and Q in s balanced base-128 digits, the least significant in
+// [-64, 63], the leading one in [-128, 128]: digit i (1 = leading) goes to
+// dA[i-1][r][k] (FP32) and/or dB[i-1][r][k] (BF16), exact either way; columns
+// cols..Kp-1 are zero.  exps[r] = e_r.
+__device__ __forceinline__ double scaled_entry(const double *xr, const double *colscale, int64_t k) {
+  return colscale ? __dmul_rn(xr[k], colscale[k]) : xr[k];
+}
+
+__global__ void __launch_bounds__(256)
+    slice_rows_kernel(const double *__restrict__ X, int64_t ld, int64_t cols, int64_t Kp, int s,
+                      int64_t slice_stride, float *__restrict__ dA, __nv_bfloat16 *__restrict__ dB,
+                      int *__restrict__ exps, const double *__restrict__ colscale) {
+  __shared__ unsigned long long red[8];
+  const int r = blockIdx.x;
+  const double *xr = X + (int64_t)r * ld;
+  unsigned long long mb = 0ull;   // |x| bit patterns order like the values
+  for (int64_t k = threadIdx.x; k < cols; k += blockDim.x)
+    mb = max(mb, (unsigned long long)__double_as_longlong(scaled_entry(xr, colscale, k)) & 0x7fffffffffffffffull);
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_down_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  mb = 0ull;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mb = max(mb, red[w]);
+  int e = 0;
+  if (mb != 0ull) frexp(__longlong_as_double((long long)mb), &e);   // m = f 2^e, f in [0.5, 1)
+  if (threadIdx.x == 0 && exps) exps[r] = e;
+  for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
+    // ldexp scales exactly without forming 2^(7 s - e), which overflows for tiny rows
+    long long Q = (k < cols && mb != 0ull) ? __double2ll_rn(ldexp(scaled_entry(xr, colscale, k), 7 * s - e)) : 0ll;
+    for (int i = s - 1; i >= 1; --i) {   // balanced digits, least significant first
+      const long long t = (Q + 64) >> 7;
+      const float d = (float)(Q - (t << 7));
+      if (dA) dA[i * slice_stride + (int64_t)r * Kp + k] = d;
+      if (dB) dB[i * slice_stride + (int64_t)r * Kp + k] = __float2bfloat16_rn(d);
+      Q = t;
+    }
+    if (dA) dA[(int64_t)r * Kp + k] = (float)Q;
+    if (dB) dB[(int64_t)r * Kp + k] = __float2bfloat16_rn((float)Q);
+  }
+}
+
+// FP64 per-pair factors f[t][k] of the Pi contraction, each operation rounded
+// once (no fused multiply-add): Delta / (w_t^2 + Delta^2) (direct, p0 = w),
+// (w_t Delta) exp(-Delta Delta x_t) (Laplace, p0 = x, p1 = w).
+__global__ void pi_factor64_kernel(const double *__restrict__ delta, int64_t K, const double *__restrict__ p0,
+                                   const double *__restrict__ p1, int mode, double *__restrict__ f) {
+  const int t = blockIdx.y;
+  const double a = p0[t], b = p1 ? p1[t] : 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+    const double d = delta[k];
+    double v;
+    if (mode == SCALE_DIRECT)
+      v = __ddiv_rn(d, __dadd_rn(__dmul_rn(a, a), __dmul_rn(d, d)));
+    else
+      v = __dmul_rn(__dmul_rn(b, d), exp(__dmul_rn(__dmul_rn(-d, d), a)));
+    f[(int64_t)t * K + k] = v;
+  }
+}
+
+// C[r][c] *= 2^(ea[r] + eb[c]) for r < rows, c < cols (exact: powers of two).
+__global__ void scale_exp2_kernel(double *__restrict__ C, int64_t ldc, int rows, int cols, const int *__restrict__ ea,
+                                  const int *__restrict__ eb) {
+  const int r = blockIdx.y;
+  if (r >= rows) return;
+  const int er = ea[r];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
+    C[(int64_t)r * ldc + c] = ldexp(C[(int64_t)r * ldc + c], er + eb[c]);
+}
 }  // namespace
 
 cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const float *S, int n_t, int rows,
@@ -413,6 +518,33 @@ cudaError_t launch_fp8_quantize(const float *X, int64_t Kp, int64_t Kq, const fl
     fp8_quantize_kernel<8><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b, split);
   else
     fp8_quantize_kernel<32><<<rows, Q8_THREADS, 0, s>>>(X, Kp, Kq, S, n_t, rows, qa, qb, ds_a, ds_b, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_rows(const double *X, int64_t ld, int rows, int64_t cols, int64_t Kp, int s,
+                              int64_t slice_stride, float *dA, __nv_bfloat16 *dB, int *exps, cudaStream_t st,
+                              const double *colscale) {
+  if (rows <= 0) return cudaSuccess;
+  if (s < 1 || s > 8 || Kp < cols) return cudaErrorInvalidValue;
+  slice_rows_kernel<<<rows, 256, 0, st>>>(X, ld, cols, Kp, s, slice_stride, dA, dB, exps, colscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pi_factor64(const double *delta, int64_t K, int n_t, const double *p0, const double *p1,
+                               int mode, double *f, cudaStream_t st) {
+  if (n_t <= 0 || K <= 0) return cudaSuccess;
+  int bx = (int)((K + 255) / 256);
+  if (bx > 152) bx = 152;
+  pi_factor64_kernel<<<dim3(bx, n_t), 256, 0, st>>>(delta, K, p0, p1, mode, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_exp2(double *C, int64_t ldc, int rows, int cols, const int *ea, const int *eb,
+                              cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  int bx = (cols + 255) / 256;
+  if (bx > 16) bx = 16;
+  scale_exp2_kernel<<<dim3(bx, rows), 256, 0, st>>>(C, ldc, rows, cols, ea, eb);
   return cudaGetLastError();
 }
 

@@ -35,9 +35,11 @@ struct Pending {
   size_t footprint = 0;
   Clock::time_point t_submit;
   int bypassed = 0;   // later requests admitted ahead of this one
+  int retries = 0;    // solves that ran out of device memory beside other requests
 };
 
 constexpr int kMaxBypass = 8;
+constexpr int kMaxRetries = 4;
 
 struct Slot {
   std::thread th;
@@ -135,7 +137,7 @@ struct ltgw_server {
       // what it keeps counts against admission (see dispatch_locked)
       size_t keep = 0;
       if (ctx) {
-        if (ltgw_workspace_bytes(ctx) > budget / (4 * slots.size())) ltgw_trim(ctx);
+        if (rs == LTGW_ERR_NOMEM || ltgw_workspace_bytes(ctx) > budget / (4 * slots.size())) ltgw_trim(ctx);
         keep = ltgw_workspace_bytes(ctx);
       }
       lock.lock();
@@ -144,6 +146,18 @@ struct ltgw_server {
       retained += keep - slot->retained;
       slot->retained = keep;
       --running;
+      // out of device memory beside other requests: the estimate was short.  The
+      // request goes back to the head of the queue with its footprint doubled (at
+      // most the budget: then it runs alone), up to kMaxRetries times.
+      if (rs == LTGW_ERR_NOMEM && job.retries < kMaxRetries && (running > 0 || job.footprint < budget)) {
+        job.retries++;
+        job.footprint = std::min(budget, 2 * job.footprint);
+        job.bypassed = kMaxBypass;   // nothing passes it again
+        queue.push_front(job);
+        dispatch_locked();
+        cv_done.notify_all();
+        continue;
+      }
       ltgw_completion c{};
       c.ticket = job.ticket;
       c.status = rs;
@@ -174,7 +188,11 @@ size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt) {
   if (!p || n_tgt < 1) return 0;
   const size_t n_aux = (size_t)p->n_aux, n_occ = (size_t)p->n_occ, n_virt = (size_t)p->n_virt;
   const size_t n_orb = n_occ + n_virt, n_act = n_occ - (size_t)p->n_frozen;
-  const size_t n_ov = n_act * n_virt, N = n_aux, T = (size_t)n_tgt, n_om = (size_t)p->n_omega;
+  // N: auxiliary functions after the NAF step, not known before the solve;
+  // estimated as half of n_aux with NAF on (a request whose solve then runs
+  // out of memory beside others is retried by the server with more room)
+  const size_t n_ov = n_act * n_virt, T = (size_t)n_tgt, n_om = (size_t)p->n_omega;
+  const size_t N = p->naf_thresh >= 0.0 ? (n_aux + 1) / 2 : n_aux;
   const size_t n_tau = p->use_laplace ? (size_t)p->n_tau : 0;
   size_t d = 0;  // doubles
   d += n_aux * n_occ * n_virt + T * n_aux * n_orb;            // inputs staged on the device
@@ -185,7 +203,18 @@ size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt) {
   if (p->precision != LTGW_FP64) {
     d += (2 * n_aux * n_ov + N * n_ov) / 2 + n_om * N * N / 2;  // FP32 copies, BF16 hi / lo of the ov block
     if (p->precision == LTGW_FP8 || p->precision == LTGW_FP8_PI)
-      d += ((n_tau ? n_tau : n_om) + 1) * N * n_ov / 8;         // FP8 codes of the scaled operands and R~
+      d += 3 * ((n_tau ? n_tau : n_om) + 1) * N * n_ov / 8;     // FP8 codes (two-term: 3 per value)
+    // the tensor-core partial tiles (FP32, one 128 x 128 tile per split), the
+    // largest of the contractions: the metric (lower tiles, up to 64 splits of
+    // the pairs), the projection (every tile, n_aux / 2048 splits) and the
+    // Pi build (lower tiles x scales, 64 splits per block of pairs)
+    auto cdiv = [](size_t a, size_t b) { return (a + b - 1) / b; };
+    const size_t nI = cdiv(n_aux, 128), nN = cdiv(N, 128), t = n_tau ? n_tau : n_om;
+    const size_t tile = 128 * 128 / 2;   // doubles per FP32 tile
+    const size_t k_part = nI * (nI + 1) / 2 * std::min<size_t>(64, cdiv(n_ov, 2048)) * tile;
+    const size_t p_part = nN * cdiv(n_ov, 128) * cdiv(n_aux, 2048) * tile;
+    const size_t pi_part = nN * (nN + 1) / 2 * t * std::min<size_t>(64, cdiv(n_ov, 2048)) * tile;
+    d += std::max(k_part, std::max(p_part, pi_part));
   } else {
     d += N * n_ov;                                              // projected ov block
   }

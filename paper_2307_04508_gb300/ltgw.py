@@ -92,8 +92,10 @@ SIGNATURES = {
     "ltgw_polarizability": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_polarizability_mixed": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
     "ltgw_polarizability_fp8": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "ltgw_polarizability_emulated": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _I, _P, _P]),
     "ltgw_polarizability_tau": (_I, [_P, _I, _I64, _P, _P, _I, _P, _I, _P, _P, _I, _I, _P, _P]),
     "ltgw_screen": (_I, [_P, _I, _I, _P, _P, _P]),
+    "ltgw_gemm_emulated": (_I, [_P, _I, _I, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _I, _P]),
     "ltgw_screen_static": (_I, [_I, _I, _P, _P, _P]),
     "ltgw_server_create": (_I, [ctypes.POINTER(ctypes.c_void_p), _I, _I, ctypes.c_size_t]),
     "ltgw_server_submit": (_I, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -359,6 +361,33 @@ class Context:
 
     def polarizability_fp8(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None, stream=None):
         self.polarizability_mixed(Bt, delta, omegas, Pi, spin, x, w, stream, fp8=True)
+
+    def polarizability_emulated(self, Bt, delta, omegas: np.ndarray, Pi, spin: int = 2, x=None, w=None,
+                                n_slices: int = 6, stream=None):
+        """FP64-accurate form from integer slices on the tensor cores (ltgw_polarizability_emulated)."""
+        N, n_pairs = int(Bt.shape[0]), int(Bt.shape[1])
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        n_tau = 0 if x is None else len(x)
+        xx = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        st = self._lib.ltgw_polarizability_emulated(self.handle, N, n_pairs, _ptr(Bt), _ptr(delta), len(om),
+                                                    _ptr(om), n_tau, _ptr(xx), _ptr(ww), spin, n_slices, _ptr(Pi),
+                                                    _stream_ptr(stream))
+        self._check(st)
+
+    def gemm_emulated(self, A, B, C, n_slices: int = 6, sym: bool = False, stream=None):
+        """ltgw_gemm_emulated: C = A B^T (torch CUDA FP64, rows with unit column
+        stride, any row stride) from integer slices; sym: B is A (pass None) and
+        C is symmetric."""
+        m, k = int(A.shape[0]), int(A.shape[1])
+        n = m if sym else int(B.shape[0])
+        for t in (A, C) if sym else (A, B, C):
+            if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
+                raise ValueError("gemm_emulated needs 2-D tensors with unit column stride")
+        st = self._lib.ltgw_gemm_emulated(self.handle, m, n, k, A.data_ptr(), A.stride(0),
+                                          None if sym else B.data_ptr(), k if sym else B.stride(0), C.data_ptr(),
+                                          C.stride(0), int(bool(sym)), n_slices, _stream_ptr(stream))
+        self._check(st)
 
     def screen(self, Pi, C, stream=None):
         n_omega, N = int(Pi.shape[0]), int(Pi.shape[1])
