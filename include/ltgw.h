@@ -63,7 +63,7 @@ typedef enum {
   LTGW_ERR_TIMEOUT = 8      /* a wait for completions ran out of time              */
 } ltgw_status;
 
-enum { LTGW_FP64 = 0, LTGW_BF16X3 = 1, LTGW_FP8 = 2, LTGW_FP8_PI = 3 };
+enum { LTGW_FP64 = 0, LTGW_BF16X3 = 1, LTGW_FP8 = 2, LTGW_FP8_PI = 3, LTGW_FP64_EMU = 4 };
 
 typedef struct {
   int n_occ;          /* occupied orbitals, frozen core included                  */
@@ -86,6 +86,10 @@ typedef struct {
                       /* expansions (rows are auxiliary functions;                */
                       /* ltgw_polarizability_fp8);                                */
                       /* LTGW_FP8_PI: FP8 for the Pi build only.                  */
+                      /* LTGW_FP64_EMU: the FP64 form with the NAF metric, the    */
+                      /* projections, Pi and W_nm FP64-accurate on the tensor     */
+                      /* cores from 6 integer slices per operand row (see          */
+                      /* ltgw_gemm_emulated); results as LTGW_FP64 to ~1e-12.      */
                       /* The eigensolver, screening, Pade and Newton stay FP64.   */
   int reserved;       /* must be 0                                                */
 } ltgw_params;
@@ -324,7 +328,8 @@ ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const
  * Delta^2), or w_t Delta exp(-Delta^2 x_t); each operation rounded once)
  * scale R~'s columns (one FP64 product per entry), and M_t = (R~ diag(f_t))
  * R~^T is formed as in ltgw_gemm_emulated with n_slices slices (lower tiles,
- * mirrored); the direct form writes Pi_j = -2 s M_j, the Laplace form
+ * mirrored; pairs in chunks of 131072, each sliced on its own, their products
+ * added); the direct form writes Pi_j = -2 s M_j, the Laplace form
  * recombines -2 s sum_m exp(-w_j^2 x_m) M^m in FP64.  Relative error about
  * 2^(-7 n_slices) of the largest row products (n_slices = 6: about 1e-12 in
  * Frobenius norm, the FP64 form's results to 1e-8 Ha in the quasi-particle
@@ -354,7 +359,7 @@ ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, dou
  * magnitudes (s = 6: about 1e-12 relative Frobenius on products of Gaussian
  * rows).  A [m][lda], B [n][ldb] (k columns used), C [m][ldc]: device, row
  * major; sym: B = A, only the lower tiles are computed and C (ldc = n) is
- * written whole, symmetric.  n_slices in [2, 8].  A and B must be finite
+ * written whole, symmetric.  m <= 65535; n_slices in [2, 8].  A and B must be finite
  * (NaN or Inf give undefined values in C, no error).  A, B are read only and
  * stay the caller's; the slices and partial tiles live in the context's
  * scratch (LTGW_ERR_NOMEM if they do not fit).  Synchronises. */
@@ -397,8 +402,11 @@ typedef struct ltgw_server ltgw_server;
  * may be passed by later ones that do at most 8 times; after that nothing is
  * admitted ahead of it.  A request whose solve runs out of device memory
  * while others run goes back to the head of the queue with its estimate
- * doubled (at most 4 times; at the full budget it runs alone).  Each slot
- * keeps its workspace between requests. */
+ * doubled (at the full budget it runs alone); one that runs out of memory
+ * alone is re-run alone once after the idle slots released their workspace,
+ * and fails (LTGW_ERR_NOMEM) if it runs out again.  Each slot keeps up to a
+ * quarter of the budget, shared among the slots, of workspace between
+ * requests; that retained workspace counts against admission. */
 ltgw_status ltgw_server_create(ltgw_server **out, int device, int n_slots, size_t hbm_budget_bytes);
 /* Queue a request (never blocks on the GPU); LTGW_ERR_NOMEM if its estimated
  * footprint alone exceeds the budget. */

@@ -174,12 +174,17 @@ ltgw_status check_flags(ltgw_ctx *ctx, cudaStream_t s) {
 ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B, int64_t ld, double *K,
                           cudaStream_t s, double beta = 0.0);
 
+// FP64-accurate C = A B^T from integer slices (defined below).
+ltgw_status emu_gemm(ltgw_ctx *ctx, int m, int n, int64_t K, const double *A, int64_t lda, const double *B,
+                     int64_t ldb, double *C, int64_t ldc, bool sym, int s, cudaStream_t st);
+
 // K builder for the streamed solve: fills w.A (n x n) itself.
 using KBuilder = std::function<ltgw_status(double *K)>;
 
 ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, const double *B,
                           int64_t ld, double thresh, double *Ut, double *lam_out, int *k_out,
-                          int *near_out, cudaStream_t s, bool mixed = false, const KBuilder *build_K = nullptr) {
+                          int *near_out, cudaStream_t s, bool mixed = false, const KBuilder *build_K = nullptr,
+                          int emu_slices = 0) {
   EigWork w;
   auto layout = [&](Arena &A) {
     w.A = A.take<double>((size_t)n * n);
@@ -218,6 +223,8 @@ ltgw_status naf_basis_dev(ltgw_ctx *ctx, Arena &ar, int n, int64_t n_pairs, cons
     if ((*build_K)(w.A) != LTGW_OK) return ctx->status();
   } else if (mixed) {
     if (naf_metric_tc(ctx, n, n_pairs, B, ld, w.A, s) != LTGW_OK) return ctx->status();
+  } else if (emu_slices) {
+    if (emu_gemm(ctx, n, n, n_pairs, B, ld, B, ld, w.A, n, true, emu_slices, s) != LTGW_OK) return ctx->status();
   } else {
     GemmF64Args g;
     g.M = n; g.N = n; g.K = n_pairs;
@@ -596,6 +603,8 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
 // are added in FP64 in the reduction, then scaled by 2^(e_A + e_B).  Two of
 // the kernel's three products per step multiply zeros here: the price of
 // reusing the split-BF16 kernel unchanged.
+constexpr int kEmuSlices = 6;   // slices per operand row in the LTGW_FP64_EMU solve
+
 struct EmuPlan {
   int m = 0, n = 0, s = 0, nIa = 0, nIb = 0, Mpa = 0, Mpb = 0;
   int64_t K = 0, Kp = 0, stra = 0, strb = 0;
@@ -605,10 +614,11 @@ struct EmuPlan {
   __nv_bfloat16 *dB = nullptr, *zeros = nullptr;
   int *ea = nullptr, *eb = nullptr, *d_tindex = nullptr;
   double *factors = nullptr;   // n_factors x K FP64 column factors of A (optional)
+  double *tmp = nullptr;       // m x n FP64 (optional): the unscaled sum when C accumulates
 };
 
 ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lower, int n_factors, EmuPlan *p,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool need_tmp = false) {
   p->m = m; p->n = n; p->s = s; p->K = K; p->lower = lower;
   p->Kp = (K + 63) / 64 * 64;
   p->nIa = (m + 127) / 128; p->nIb = (n + 127) / 128;
@@ -624,13 +634,14 @@ ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lowe
     p->eb = Ar.take<int>(p->Mpb);
     p->d_tindex = lower ? Ar.take<int>(p->tindex.size()) : nullptr;
     p->factors = n_factors ? Ar.take<double>((size_t)n_factors * K) : nullptr;
+    p->tmp = need_tmp ? Ar.take<double>((size_t)m * n) : nullptr;
   };
   ctx->a5.begin_sizing();
   layout(ctx->a5);
   if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "slice operand allocation failed"); return ctx->status(); }
   layout(ctx->a5);
   if (lower) copy_in(ctx, p->d_tindex, p->tindex.data(), p->tindex.size() * sizeof(int), st);
-  // padding rows stay zero: the slicing writes rows < m (n) only
+  // padding rows and columns stay zero: the slicing writes rows < m (n), k < K only
   LTGW_CUDA(ctx, cudaMemsetAsync(p->dA, 0, (size_t)s * p->stra * sizeof(float), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->dB, 0, (size_t)s * p->strb * sizeof(__nv_bfloat16), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->zeros, 0, (size_t)p->strb * sizeof(__nv_bfloat16), st));
@@ -640,13 +651,15 @@ ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lowe
   return ctx->status();
 }
 
-// C = post * A diag(colscale) B^T from the slices in p (A's sliced here, B's
-// already in p->dB / p->eb).  C [m][ldc]; in the lower form C (ldc = n) is
-// written whole and symmetric.  post must be a power of two (or +-1, +-2, +-4):
-// it is folded into the exact 2^(-7L) factors.
-ltgw_status emu_product(ltgw_ctx *ctx, EmuPlan &p, const double *A, int64_t lda, const double *colscale,
-                        double post, double *C, int64_t ldc, cudaStream_t st) {
-  CHECK_LAUNCH(ctx, launch_slice_rows(A, lda, p.m, p.K, p.Kp, p.s, p.stra, p.dA, nullptr, p.ea, st, colscale), 1);
+// C = beta C + post * (sliced A) (sliced B)^T from the digits in p->dA / p->dB
+// and the exponents p->ea / p->eb.  C [m][ldc]; in the lower form C (ldc = n)
+// is written whole and symmetric.  post must be a power of two (or +-1, +-2,
+// +-4): it is folded into the exact 2^(-7L) factors.  beta != 0 needs p->tmp.
+ltgw_status emu_pairs(ltgw_ctx *ctx, EmuPlan &p, double post, double *C, int64_t ldc, double beta,
+                      cudaStream_t st) {
+  if (beta != 0.0 && !p.tmp) { ctx->fail(LTGW_ERR_BAD_ARG, "emulated accumulation without scratch"); return ctx->status(); }
+  double *D = beta != 0.0 ? p.tmp : C;
+  const int64_t ldd = beta != 0.0 ? p.n : (p.lower ? p.m : ldc);
   bool first = true;
   for (int L = 2; L <= p.s + 1; ++L) {
     for (int i = 1; i < L; ++i) {
@@ -663,26 +676,108 @@ ltgw_status emu_product(ltgw_ctx *ctx, EmuPlan &p, const double *A, int64_t lda,
       const double alpha = post * ldexp(1.0, -7 * L);
       if (p.lower) {
         CHECK_LAUNCH(ctx, launch_tc_reduce_sym(run.partial, run.partial32, run.splits, run.groups, run.n_tiles,
-                                               p.d_tindex, p.nIa, 1, p.m, alpha, C, st, first ? 0.0 : 1.0,
+                                               p.d_tindex, p.nIa, 1, p.m, alpha, D, st, first ? 0.0 : 1.0,
                                                run.nt_group, 1),
                      1);
       } else {
         CHECK_LAUNCH(ctx, launch_tc_reduce_full_acc(run.partial, run.partial32, run.splits, run.groups, run.n_tiles,
-                                                    p.nIb, p.m, p.n, alpha, C, ldc, first ? 0.0 : 1.0, st), 1);
+                                                    p.nIb, p.m, p.n, alpha, D, ldd, first ? 0.0 : 1.0, st), 1);
       }
       first = false;
     }
   }
-  CHECK_LAUNCH(ctx, launch_scale_exp2(C, p.lower ? p.m : ldc, p.m, p.n, p.ea, p.eb, st), 1);
+  CHECK_LAUNCH(ctx, launch_scale_exp2_to(D, ldd, C, p.lower ? p.m : ldc, p.m, p.n, p.ea, p.eb, beta, st,
+                                         p.lower ? 1 : 0), 1);
   return ctx->status();
+}
+
+// A (with optional column factors) sliced into p->dA, then emu_pairs.
+ltgw_status emu_product(ltgw_ctx *ctx, EmuPlan &p, const double *A, int64_t lda, const double *colscale,
+                        double post, double *C, int64_t ldc, cudaStream_t st, double beta = 0.0) {
+  CHECK_LAUNCH(ctx, launch_slice_rows(A, lda, p.m, p.K, p.Kp, p.s, p.stra, p.dA, nullptr, p.ea, st, colscale), 1);
+  return emu_pairs(ctx, p, 1.0 * post, C, ldc, beta, st);
+}
+
+// C = beta C + A A^T (lower form): A sliced once into both operands.
+ltgw_status emu_syrk(ltgw_ctx *ctx, EmuPlan &p, const double *A, int64_t lda, double *C, double beta,
+                     cudaStream_t st) {
+  CHECK_LAUNCH(ctx, launch_slice_rows(A, lda, p.m, p.K, p.Kp, p.s, p.stra, p.dA, p.dB, p.ea, st), 1);
+  LTGW_CUDA(ctx, cudaMemcpyAsync(p.eb, p.ea, p.Mpa * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  return emu_pairs(ctx, p, 1.0, C, p.m, beta, st);
 }
 
 ltgw_status emu_gemm(ltgw_ctx *ctx, int m, int n, int64_t K, const double *A, int64_t lda, const double *B,
                      int64_t ldb, double *C, int64_t ldc, bool sym, int s, cudaStream_t st) {
   EmuPlan p;
   if (emu_prepare(ctx, m, n, K, s, sym, 0, &p, st) != LTGW_OK) return ctx->status();
+  if (sym) return emu_syrk(ctx, p, A, lda, C, 0.0, st);
   CHECK_LAUNCH(ctx, launch_slice_rows(B, ldb, n, K, p.Kp, s, p.strb, nullptr, p.dB, p.eb, st), 1);
   return emu_product(ctx, p, A, lda, nullptr, 1.0, C, ldc, st);
+}
+
+// Pi from slices (the emulated FP64 form): per frequency (n_tau == 0, Pi_j =
+// -2 s M_j written directly) or moment t (lt_form 1: Laplace factors; 2:
+// e^{-Delta tau_t}) M_t = (Bt diag(f_t)) Bt^T, then the recombination with
+// d_E [n_omega][n_tau].
+ltgw_status polarizability_emu(ltgw_ctx *ctx, int N, int64_t n_pairs, const double *Bt, int64_t ldb,
+                               const double *delta, int n_omega, const double *d_om, int n_tau, const double *d_x,
+                               const double *d_w, const double *d_E, double *d_M, int spin, double *Pi,
+                               cudaStream_t s, int lt_form, int n_slices) {
+  const int n_t = n_tau ? n_tau : n_omega;
+  // pairs in chunks, so that the slices of one chunk are held at a time
+  // (6 slices of FP32 A and BF16 B digits: 36 bytes per value); chunks after
+  // the first are added (each chunk's product is exact to its own slices)
+  const int64_t chunk = std::min<int64_t>(n_pairs, (int64_t)1 << 17);
+  EmuPlan p;
+  if (emu_prepare(ctx, N, N, chunk, n_slices, true, n_t, &p, s, n_pairs > chunk) != LTGW_OK) return ctx->status();
+  ctx->mark(EV_PI0, s);
+  const int mode = n_tau ? (lt_form == 2 ? SCALE_EXPTAU : SCALE_LAPLACE) : SCALE_DIRECT;
+  for (int64_t k0 = 0; k0 < n_pairs; k0 += chunk) {
+    const int64_t kc = std::min(chunk, n_pairs - k0);
+    p.K = kc;   // the row slicing writes every column < Kp: zeros past kc
+    CHECK_LAUNCH(ctx, launch_pi_factor64(delta + k0, kc, n_t, n_tau ? d_x : d_om,
+                                         mode == SCALE_LAPLACE ? d_w : nullptr, mode, p.factors, s), 1);
+    CHECK_LAUNCH(ctx, launch_slice_rows(Bt + k0, ldb, N, kc, p.Kp, n_slices, p.strb, nullptr, p.dB, p.eb, s), 1);
+    for (int t = 0; t < n_t; ++t)
+      if (emu_product(ctx, p, Bt + k0, ldb, p.factors + (int64_t)t * kc, n_tau ? 1.0 : -2.0 * spin,
+                      (n_tau ? d_M : Pi) + (int64_t)t * N * N, N, s, k0 > 0 ? 1.0 : 0.0) != LTGW_OK)
+        return ctx->status();
+  }
+  ctx->mark(EV_PI1, s);
+  if (n_tau)
+    CHECK_LAUNCH(ctx, launch_recombine(d_M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
+                 (n_omega + 63) / 64);
+  return LTGW_OK;
+}
+
+// Rows of R~ = U^T R from slices: Ut [N][n_aux] (rows = kept eigenvectors),
+// R [n_aux][ld_r] with `cols` columns (pairs or orbitals); out [N][ld_out].
+ltgw_status project_emu(ltgw_ctx *ctx, int N, int n_aux, const double *Ut, const double *R, int64_t ld_r,
+                        int cols, double *out, int64_t ld_out, int n_slices, cudaStream_t s) {
+  EmuPlan p;
+  if (emu_prepare(ctx, N, cols, n_aux, n_slices, false, 0, &p, s) != LTGW_OK) return ctx->status();
+  CHECK_LAUNCH(ctx, launch_slice_cols(R, ld_r, n_aux, cols, p.Kp, n_slices, p.strb, p.dB, p.eb, s), 1);
+  return emu_product(ctx, p, Ut, n_aux, nullptr, 1.0, out, ld_out, s);
+}
+
+// W_j[t][c] = sum_PQ Btt[t][P][c] C_j[P][Q] Btt[t][Q][c] (Eq. ScreenedCoulombOrbital):
+// Y = C_j Btt (all targets side by side) from slices, then the FP64 column dot.
+ltgw_status wnm_emu(ltgw_ctx *ctx, int N, int n_omega, const double *C, int T, int n_orb_act, const double *Btt,
+                    int64_t ld_btt, int64_t stride_btt, double *W, int n_slices, cudaStream_t s) {
+  const int cols = T * n_orb_act;
+  EmuPlan p;
+  if (emu_prepare(ctx, N, cols, N, n_slices, false, 0, &p, s, true) != LTGW_OK) return ctx->status();
+  for (int t = 0; t < T; ++t)
+    CHECK_LAUNCH(ctx, launch_slice_cols(Btt + (int64_t)t * stride_btt, ld_btt, N, n_orb_act, p.Kp, n_slices,
+                                        p.strb, p.dB + (int64_t)t * n_orb_act * p.Kp, p.eb + t * n_orb_act, s),
+                 1);
+  for (int j = 0; j < n_omega; ++j) {
+    if (emu_product(ctx, p, C + (int64_t)j * N * N, N, nullptr, 1.0, p.tmp, cols, s) != LTGW_OK)
+      return ctx->status();
+    CHECK_LAUNCH(ctx, launch_coldot64(p.tmp, cols, Btt, ld_btt, stride_btt, N, n_orb_act, T,
+                                      W + (int64_t)j * T * n_orb_act, n_orb_act, s), 1);
+  }
+  return LTGW_OK;
 }
 
 // Operands of the mixed form after the NAF step (Eq. naftrafo in split BF16):
@@ -843,8 +938,8 @@ ltgw_status validate(ltgw_ctx *ctx, const ltgw_params *p) {
   REQUIRE(ctx, p->spin == 1 || p->spin == 2, "spin must be 1 or 2");
   REQUIRE(ctx, p->use_laplace >= 0 && p->use_laplace <= 2, "use_laplace must be 0, 1 or 2");
   REQUIRE(ctx, !p->use_laplace || (p->n_tau >= 1 && p->n_tau <= 32), "n_tau must be in [1, 32]");
-  REQUIRE(ctx, p->precision >= LTGW_FP64 && p->precision <= LTGW_FP8_PI,
-          "precision must be LTGW_FP64, LTGW_BF16X3, LTGW_FP8 or LTGW_FP8_PI");
+  REQUIRE(ctx, p->precision >= LTGW_FP64 && p->precision <= LTGW_FP64_EMU,
+          "precision must be LTGW_FP64, LTGW_BF16X3, LTGW_FP8, LTGW_FP8_PI or LTGW_FP64_EMU");
   REQUIRE(ctx, p->reserved == 0, "reserved must be 0");
   REQUIRE(ctx, isfinite(p->naf_thresh), "naf_thresh must be finite");
   return LTGW_OK;
@@ -997,7 +1092,11 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   const int n_omega = p->n_omega, T = n_tgt;
   const int n_tau = p->use_laplace ? p->n_tau : 0;
   const bool naf = p->naf_thresh >= 0.0;
-  const bool mixed = p->precision != LTGW_FP64;   // contractions on the tensor cores
+  // emulated FP64 form: the FP64 form's data flow with K, the projections, Pi
+  // and W_nm FP64-accurate from integer slices on the tensor cores
+  const bool emu = p->precision == LTGW_FP64_EMU;
+  const int n_sl = kEmuSlices;
+  const bool mixed = p->precision != LTGW_FP64 && !emu;   // split-BF16 / FP8 contractions
   const bool fp8 = p->precision == LTGW_FP8 || p->precision == LTGW_FP8_PI;   // Pi build in FP8 E4M3
   const bool fp8_w = p->precision == LTGW_FP8;                                // W_nm in FP8 E4M3
   ctx->stats = ltgw_stats{};
@@ -1211,6 +1310,10 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
         CHECK_LAUNCH(ctx, launch_to_f32_transposed(B_blk, cols, 0, n_aux, (int)cols, d_Rt, (int)Kpa_aux, (int)cols,
                                                    1, 0, 0, s), 1);
         CHECK_LAUNCH(ctx, launch_split_bf16(d_Rt, d_Rh + off, d_Rl + off, cols * Kpa_aux, s), 1);
+      } else if (emu) {
+        EmuPlan ep;   // K += B_blk B_blk^T from slices
+        if (emu_prepare(ctx, n_aux, n_aux, cols, n_sl, true, 0, &ep, s, true) != LTGW_OK) return ctx->status();
+        if (emu_syrk(ctx, ep, B_blk, cols, K, 1.0, s) != LTGW_OK) return ctx->status();
       } else {
         GemmF64Args g;  // K += B_blk B_blk^T
         g.M = n_aux; g.N = n_aux; g.K = cols;
@@ -1231,7 +1334,7 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
   int N = n_aux, near = 0;
   if (naf) {
     if (naf_basis_dev(ctx, ctx->a3, n_aux, n_ov, B_act, ld_act, p->naf_thresh, d_Ut, d_lam, &N, &near, s,
-                      mixed, streamed ? &build_K : nullptr) != LTGW_OK)
+                      mixed, streamed ? &build_K : nullptr, emu ? n_sl : 0) != LTGW_OK)
       return ctx->status();
   }
   ctx->stats.n_naf = N;
@@ -1287,14 +1390,24 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
         const int64_t cols = (int64_t)(i1 - i0) * n_virt;
         double *B_blk = nullptr;
         if (get_block(i0, i1, &B_blk) != LTGW_OK) return ctx->status();
-        GemmF64Args g;  // R~_ov[:, block] = U^T R_blk
-        g.M = N; g.N = (int)cols; g.K = n_aux;
-        g.A = d_Ut; g.lda = n_aux;
-        g.B = B_blk; g.ldb = cols;
-        g.C = d_Bt + (int64_t)(i0 - n_fc) * n_virt; g.ldc = n_ov;
-        CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+        if (emu) {
+          if (project_emu(ctx, N, n_aux, d_Ut, B_blk, cols, (int)cols, d_Bt + (int64_t)(i0 - n_fc) * n_virt, n_ov,
+                          n_sl, s) != LTGW_OK)
+            return ctx->status();
+        } else {
+          GemmF64Args g;  // R~_ov[:, block] = U^T R_blk
+          g.M = N; g.N = (int)cols; g.K = n_aux;
+          g.A = d_Ut; g.lda = n_aux;
+          g.B = B_blk; g.ldb = cols;
+          g.C = d_Bt + (int64_t)(i0 - n_fc) * n_virt; g.ldc = n_ov;
+          CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
+        }
         if (block_done() != LTGW_OK) return ctx->status();
       }
+    } else if (emu) {
+      REQUIRE(ctx, n_ov <= INT32_MAX, "too many pairs for one emulated projection");
+      if (project_emu(ctx, N, n_aux, d_Ut, B_act, ld_act, (int)n_ov, d_Bt, n_ov, n_sl, s) != LTGW_OK)
+        return ctx->status();
     } else {
       GemmF64Args g;  // R~_ov = U^T R_ov
       g.M = N; g.N = (int)std::min<int64_t>(n_ov, INT32_MAX); g.K = n_aux;
@@ -1303,12 +1416,19 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
       g.C = d_Bt; g.ldc = n_ov;
       CHECK_LAUNCH(ctx, launch_gemm_f64(g, 1, true, false, s), 1);
     }
-    GemmF64Args h;  // R~_tgt[t] = U^T R_tgt[t][:, active]
-    h.M = N; h.N = n_orb_act; h.K = n_aux;
-    h.A = d_Ut; h.lda = n_aux; h.strideA = 0;
-    h.B = d_Btg + n_fc; h.ldb = n_orb; h.strideB = (int64_t)n_aux * n_orb;
-    h.C = d_Btt; h.ldc = n_orb_act; h.strideC = (int64_t)N * n_orb_act;
-    CHECK_LAUNCH(ctx, launch_gemm_f64(h, T, true, false, s), 1);
+    if (emu) {
+      for (int t = 0; t < T; ++t)   // R~_tgt[t] = U^T R_tgt[t][:, active]
+        if (project_emu(ctx, N, n_aux, d_Ut, d_Btg + (int64_t)t * n_aux * n_orb + n_fc, n_orb, n_orb_act,
+                        d_Btt + (int64_t)t * N * n_orb_act, n_orb_act, n_sl, s) != LTGW_OK)
+          return ctx->status();
+    } else {
+      GemmF64Args h;  // R~_tgt[t] = U^T R_tgt[t][:, active]
+      h.M = N; h.N = n_orb_act; h.K = n_aux;
+      h.A = d_Ut; h.lda = n_aux; h.strideA = 0;
+      h.B = d_Btg + n_fc; h.ldb = n_orb; h.strideB = (int64_t)n_aux * n_orb;
+      h.C = d_Btt; h.ldc = n_orb_act; h.strideC = (int64_t)N * n_orb_act;
+      CHECK_LAUNCH(ctx, launch_gemm_f64(h, T, true, false, s), 1);
+    }
     Bt = d_Bt; ld_bt = n_ov;
     Btt = d_Btt; ld_btt = n_orb_act; stride_btt = (int64_t)N * n_orb_act;
   }
@@ -1342,6 +1462,10 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
       if (polarizability_tc(ctx, N, n_ov, nullptr, 0, d_Bf, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E,
                             d_M, p->spin, d_Pi, s, fp8, p->use_laplace) != LTGW_OK)
         return ctx->status();
+    } else if (emu) {
+      if (polarizability_emu(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M, p->spin,
+                             d_Pi, s, p->use_laplace, n_sl) != LTGW_OK)
+        return ctx->status();
     } else if (polarizability_dev(ctx, N, n_ov, Bt, ld_bt, d_delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M,
                                   p->spin, d_Pi, s, p->use_laplace) != LTGW_OK) {
       return ctx->status();
@@ -1358,6 +1482,9 @@ ltgw_status solve_impl(ltgw_ctx *ctx, const ltgw_params *p, const double *eps, c
     // ---- W_nm(i w_j)
     if (mixed) {
       if (wnm_tc(ctx, N, n_omega, d_C, T, n_orb_act, d_BtT64, d_BtT32, d_W, s, fp8_w) != LTGW_OK) return ctx->status();
+    } else if (emu) {
+      if (wnm_emu(ctx, N, n_omega, d_C, T, n_orb_act, Btt, ld_btt, stride_btt, d_W, n_sl, s) != LTGW_OK)
+        return ctx->status();
     } else {
       ColDotArgs cd;
       cd.N = N; cd.ncols = n_orb_act; cd.n_tgt = T;
@@ -1647,6 +1774,7 @@ ltgw_status ltgw_gemm_emulated(ltgw_ctx *ctx, int m, int n, int64_t k, const dou
   REQUIRE(ctx, n_slices >= 2 && n_slices <= 8, "n_slices must be in [2, 8]");
   REQUIRE(ctx, A && C && (sym || B), "a required pointer is NULL");
   REQUIRE(ctx, !sym || (m == n && ldc == n), "sym needs m == n and ldc == n");
+  REQUIRE(ctx, m <= 65535, "m must be <= 65535");
   REQUIRE(ctx, is_device_ptr(A) && is_device_ptr(C) && (sym || is_device_ptr(B)), "A, B, C must be device pointers");
   LTGW_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
@@ -1701,22 +1829,9 @@ ltgw_status ltgw_polarizability_emulated(ltgw_ctx *ctx, int N, int64_t n_pairs, 
     copy_in(ctx, d_E, h_E.data(), h_E.size() * sizeof(double), s);
   }
   if (ctx->status() != LTGW_OK) return ctx->status();
-  const int n_t = n_tau ? n_tau : n_omega;
-  EmuPlan p;
-  if (emu_prepare(ctx, N, N, n_pairs, n_slices, true, n_t, &p, s) != LTGW_OK) return ctx->status();
-  ctx->mark(EV_PI0, s);
-  CHECK_LAUNCH(ctx, launch_pi_factor64(delta, n_pairs, n_t, n_tau ? d_x : d_om, n_tau ? d_w : nullptr,
-                                       n_tau ? SCALE_LAPLACE : SCALE_DIRECT, p.factors, s), 1);
-  CHECK_LAUNCH(ctx, launch_slice_rows(Bt, n_pairs, N, n_pairs, p.Kp, n_slices, p.strb, nullptr, p.dB, p.eb, s), 1);
-  // M^m (Laplace points) or Pi_j itself (direct: the factor -2 s is exact)
-  for (int t = 0; t < n_t; ++t)
-    if (emu_product(ctx, p, Bt, n_pairs, p.factors + (int64_t)t * n_pairs, n_tau ? 1.0 : -2.0 * spin,
-                    (n_tau ? d_M : Pi) + (int64_t)t * N * N, N, s) != LTGW_OK)
-      return ctx->status();
-  ctx->mark(EV_PI1, s);
-  if (n_tau)
-    CHECK_LAUNCH(ctx, launch_recombine(d_M, n_tau, d_E, n_omega, (int64_t)N * N, -2.0 * spin, Pi, s),
-                 (n_omega + 63) / 64);
+  if (polarizability_emu(ctx, N, n_pairs, Bt, n_pairs, delta, n_omega, d_om, n_tau, d_x, d_w, d_E, d_M, spin, Pi, s,
+                         1, n_slices) != LTGW_OK)
+    return ctx->status();
   ctx->mark(EV_END, s);
   LTGW_CUDA(ctx, cudaStreamSynchronize(s));   // the staged grid lives in the workspace
   ctx->stats.ms_total = ctx->ms(EV_START, EV_END);

@@ -164,12 +164,25 @@ cudaError_t launch_slice_rows(const double *X, int64_t ld, int rows, int64_t col
                               int64_t slice_stride, float *dA, __nv_bfloat16 *dB, int *exps, cudaStream_t st,
                               const double *colscale = nullptr);
 // FP64 factors f[t][k] (k < K) of the Pi contraction per frequency (SCALE_DIRECT,
-// p0 = omega) or Laplace point (SCALE_LAPLACE, p0 = x, p1 = w), no fused operations.
+// p0 = omega), Laplace point (SCALE_LAPLACE, p0 = x, p1 = w) or imaginary-time
+// node (SCALE_EXPTAU, p0 = tau), no fused operations.
 cudaError_t launch_pi_factor64(const double *delta, int64_t K, int n_t, const double *p0, const double *p1,
                                int mode, double *f, cudaStream_t st);
 // C[r][c] *= 2^(ea[r] + eb[c]).
 cudaError_t launch_scale_exp2(double *C, int64_t ldc, int rows, int cols, const int *ea, const int *eb,
                               cudaStream_t st);
+// D[r][c] = beta D[r][c] + S[r][c] 2^(ea[r] + eb[c]) (rows <= 65535); lower (rows ==
+// cols, S symmetric): the entries c <= r scaled, each written to (r, c) and (c, r).
+cudaError_t launch_scale_exp2_to(const double *S, int64_t lds, double *D, int64_t ldd, int rows, int cols,
+                                 const int *ea, const int *eb, double beta, cudaStream_t st, int lower = 0);
+// The slices of X's columns 0..cols-1 as operand rows (X FP64 [rows][ld], the
+// contraction index is X's row): digit i of column c to dB[i][c][k] (BF16), its
+// exponent to exps[c]; as launch_slice_rows applied to X^T.
+cudaError_t launch_slice_cols(const double *X, int64_t ld, int rows, int cols, int64_t Kp, int s,
+                              int64_t slice_stride, __nv_bfloat16 *dB, int *exps, cudaStream_t st);
+// W[t][c] = sum_r Y[r][t ncols + c] Bt[t][r][c] in FP64 (Bt [n_tgt] x [N][ldb]).
+cudaError_t launch_coldot64(const double *Y, int64_t ldy, const double *Bt, int64_t ldb, int64_t strideB, int N,
+                            int ncols, int n_tgt, double *W, int64_t ldw, cudaStream_t st);
 // X itself quantised per row as an A operand (split: segments h | l | h).
 cudaError_t launch_fp8_quantize_a(const float *X, int64_t Kp, int64_t Kq, int rows, uint8_t *q, float *ds,
                                   cudaStream_t s, int split);

@@ -8,6 +8,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <climits>
 #include <cuda_fp8.h>
 
 #include <algorithm>
@@ -483,7 +484,8 @@ __global__ void __launch_bounds__(256)
 
 // FP64 per-pair factors f[t][k] of the Pi contraction, each operation rounded
 // once (no fused multiply-add): Delta / (w_t^2 + Delta^2) (direct, p0 = w),
-// (w_t Delta) exp(-Delta Delta x_t) (Laplace, p0 = x, p1 = w).
+// (w_t Delta) exp(-Delta Delta x_t) (Laplace, p0 = x, p1 = w), exp(-Delta tau_t)
+// (imaginary time, p0 = tau).
 __global__ void pi_factor64_kernel(const double *__restrict__ delta, int64_t K, const double *__restrict__ p0,
                                    const double *__restrict__ p1, int mode, double *__restrict__ f) {
   const int t = blockIdx.y;
@@ -493,20 +495,99 @@ __global__ void pi_factor64_kernel(const double *__restrict__ delta, int64_t K, 
     double v;
     if (mode == SCALE_DIRECT)
       v = __ddiv_rn(d, __dadd_rn(__dmul_rn(a, a), __dmul_rn(d, d)));
-    else
+    else if (mode == SCALE_LAPLACE)
       v = __dmul_rn(__dmul_rn(b, d), exp(__dmul_rn(__dmul_rn(-d, d), a)));
+    else
+      v = exp(__dmul_rn(-d, a));   // SCALE_EXPTAU: e^{-Delta tau_t}
     f[(int64_t)t * K + k] = v;
   }
 }
 
-// C[r][c] *= 2^(ea[r] + eb[c]) for r < rows, c < cols (exact: powers of two).
-__global__ void scale_exp2_kernel(double *__restrict__ C, int64_t ldc, int rows, int cols, const int *__restrict__ ea,
-                                  const int *__restrict__ eb) {
+// D[r][c] = beta D[r][c] + S[r][c] 2^(ea[r] + eb[c]) for r < rows, c < cols
+// (the scaling is exact; S may be D with beta = 0).  lower: the product of a
+// lower-tile form (S symmetric, rows == cols) whose mirrored upper entries
+// must take the lower entry's scale 2^(ea[r] + eb[c]), r >= c: only c <= r
+// is read, and each value is written to (r, c) and (c, r).
+__global__ void scale_exp2_kernel(const double *S, int64_t lds, double *D, int64_t ldd, int rows, int cols,
+                                  const int *__restrict__ ea, const int *__restrict__ eb, double beta, int lower) {
   const int r = blockIdx.y;
   if (r >= rows) return;
   const int er = ea[r];
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
-    C[(int64_t)r * ldc + c] = ldexp(C[(int64_t)r * ldc + c], er + eb[c]);
+  const int cend = lower ? min(r + 1, cols) : cols;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cend; c += gridDim.x * blockDim.x) {
+    const double v = ldexp(S[(int64_t)r * lds + c], er + eb[c]);
+    double *d = D + (int64_t)r * ldd + c;
+    const double o = beta != 0.0 ? beta * *d + v : v;
+    *d = o;
+    if (lower && c != r) D[(int64_t)c * ldd + r] = o;
+  }
+}
+
+// The slices of X^T's rows, i.e. of X's columns: X FP64 [rows][ld], columns
+// 0..cols-1 (each an operand row, contraction index = X's row).  Block: 32
+// columns x 8 row lanes.  Pass 1: e_c, the exponent of column c's largest
+// magnitude (as in slice_rows_kernel); pass 2: 32 x 32 tiles through shared
+// memory, the digits of column c written to dB[i][c][k] (k = X's row, BF16) so
+// that a warp's stores run along k.  exps[c] = e_c.
+__global__ void __launch_bounds__(256)
+    slice_cols_kernel(const double *__restrict__ X, int64_t ld, int rows, int cols, int64_t Kp, int s,
+                      int64_t slice_stride, __nv_bfloat16 *__restrict__ dB, int *__restrict__ exps) {
+  __shared__ unsigned long long red[8][33];
+  __shared__ double tile[32][33];
+  __shared__ int e_s[32];
+  const int c0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+  const int c = c0 + tx;
+  unsigned long long mb = 0ull;
+  if (c < cols)
+    for (int r = ty; r < rows; r += 8)
+      mb = max(mb, (unsigned long long)__double_as_longlong(X[(int64_t)r * ld + c]) & 0x7fffffffffffffffull);
+  red[ty][tx] = mb;
+  __syncthreads();
+  if (ty == 0) {
+    for (int q = 1; q < 8; ++q) mb = max(mb, red[q][tx]);
+    int e = 0;
+    if (mb != 0ull) frexp(__longlong_as_double((long long)mb), &e);
+    e_s[tx] = mb != 0ull ? e : INT_MIN;   // INT_MIN: a zero column
+    if (c < cols && exps) exps[c] = e;
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < rows; r0 += 32) {
+    for (int q = ty; q < 32; q += 8) {
+      const int r = r0 + q;
+      tile[q][tx] = (r < rows && c < cols) ? X[(int64_t)r * ld + c] : 0.0;
+    }
+    __syncthreads();
+    // thread (tx, ty): row k = r0 + tx of columns c0 + ty, ty + 8, ...
+    const int k = r0 + tx;
+    for (int q = ty; q < 32; q += 8) {
+      const int cc = c0 + q;
+      if (cc >= cols || k >= rows) continue;
+      const int e = e_s[q];
+      long long Q = e != INT_MIN ? __double2ll_rn(ldexp(tile[tx][q], 7 * s - e)) : 0ll;
+      for (int i = s - 1; i >= 1; --i) {
+        const long long t = (Q + 64) >> 7;
+        dB[i * slice_stride + (int64_t)cc * Kp + k] = __float2bfloat16_rn((float)(Q - (t << 7)));
+        Q = t;
+      }
+      dB[(int64_t)cc * Kp + k] = __float2bfloat16_rn((float)Q);
+    }
+    __syncthreads();
+  }
+}
+
+// W[t][c] = sum_r Y[r][t ncols + c] Bt[t][r][c] (FP64), t < n_tgt, c < ncols:
+// the column dot of W_nm (Eq. ScreenedCoulombOrbital) on a product Y = C_j Bt.
+__global__ void coldot64_kernel(const double *__restrict__ Y, int64_t ldy, const double *__restrict__ Bt,
+                                int64_t ldb, int64_t strideB, int N, int ncols, int n_tgt, double *__restrict__ W,
+                                int64_t ldw) {
+  const int t = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    const double *y = Y + (int64_t)t * ncols + c;
+    const double *b = Bt + (int64_t)t * strideB + c;
+    for (int r = 0; r < N; ++r) acc = fma(y[(int64_t)r * ldy], b[(int64_t)r * ldb], acc);
+    W[(int64_t)t * ldw + c] = acc;
+  }
 }
 }  // namespace
 
@@ -541,10 +622,33 @@ cudaError_t launch_pi_factor64(const double *delta, int64_t K, int n_t, const do
 
 cudaError_t launch_scale_exp2(double *C, int64_t ldc, int rows, int cols, const int *ea, const int *eb,
                               cudaStream_t st) {
+  return launch_scale_exp2_to(C, ldc, C, ldc, rows, cols, ea, eb, 0.0, st);
+}
+
+cudaError_t launch_scale_exp2_to(const double *S, int64_t lds, double *D, int64_t ldd, int rows, int cols,
+                                 const int *ea, const int *eb, double beta, cudaStream_t st, int lower) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if (rows > 65535 || (lower && rows != cols)) return cudaErrorInvalidValue;
   int bx = (cols + 255) / 256;
   if (bx > 16) bx = 16;
-  scale_exp2_kernel<<<dim3(bx, rows), 256, 0, st>>>(C, ldc, rows, cols, ea, eb);
+  scale_exp2_kernel<<<dim3(bx, rows), 256, 0, st>>>(S, lds, D, ldd, rows, cols, ea, eb, beta, lower);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_cols(const double *X, int64_t ld, int rows, int cols, int64_t Kp, int s,
+                              int64_t slice_stride, __nv_bfloat16 *dB, int *exps, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if (s < 1 || s > 8 || Kp < rows) return cudaErrorInvalidValue;
+  slice_cols_kernel<<<(cols + 31) / 32, dim3(32, 8), 0, st>>>(X, ld, rows, cols, Kp, s, slice_stride, dB, exps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coldot64(const double *Y, int64_t ldy, const double *Bt, int64_t ldb, int64_t strideB, int N,
+                            int ncols, int n_tgt, double *W, int64_t ldw, cudaStream_t st) {
+  if (N <= 0 || ncols <= 0 || n_tgt <= 0) return cudaSuccess;
+  int bx = (ncols + 127) / 128;
+  if (bx > 64) bx = 64;
+  coldot64_kernel<<<dim3(bx, n_tgt), 128, 0, st>>>(Y, ldy, Bt, ldb, strideB, N, ncols, n_tgt, W, ldw);
   return cudaGetLastError();
 }
 

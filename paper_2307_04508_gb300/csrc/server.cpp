@@ -35,17 +35,25 @@ struct Pending {
   size_t footprint = 0;
   Clock::time_point t_submit;
   int bypassed = 0;   // later requests admitted ahead of this one
-  int retries = 0;    // solves that ran out of device memory beside other requests
+  int retries = 0;    // solves that ran out of device memory
+  bool alone = false;        // admitted with nothing else running
+  bool after_trim = false;   // re-run alone after the idle slots released their workspace
 };
 
 constexpr int kMaxBypass = 8;
-constexpr int kMaxRetries = 4;
+// A request that runs out of device memory beside others goes back with its
+// footprint doubled until it runs alone; one that fails alone is re-run once
+// after the idle slots released their workspace.  Doubling from the smallest
+// footprint (64 MiB) reaches any budget within 40 retries.
+constexpr int kMaxRetries = 40;
 
 struct Slot {
   std::thread th;
   bool has_job = false;
   Pending job;
-  size_t retained = 0;   // workspace its context keeps between requests
+  size_t retained = 0;       // workspace its context keeps between requests
+  ltgw_ctx *ctx = nullptr;   // used by its own thread only, except that an idle slot's
+                             // workspace may be released under the server's lock
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -92,6 +100,7 @@ struct ltgw_server {
       }
       for (Pending *q : passed) ++q->bypassed;
       free_slot->job = *it;
+      free_slot->job.alone = running == 0;
       free_slot->has_job = true;
       in_flight += it->footprint;
       ++running;
@@ -113,6 +122,7 @@ struct ltgw_server {
     }
     {
       std::lock_guard<std::mutex> lock(mu);
+      slot->ctx = ctx;
       if (st != LTGW_OK && init_status == LTGW_OK) init_status = st;
       --init_pending;
       cv_done.notify_all();
@@ -146,12 +156,26 @@ struct ltgw_server {
       retained += keep - slot->retained;
       slot->retained = keep;
       --running;
-      // out of device memory beside other requests: the estimate was short.  The
+      // Out of device memory.  Beside other requests the estimate was short: the
       // request goes back to the head of the queue with its footprint doubled (at
-      // most the budget: then it runs alone), up to kMaxRetries times.
-      if (rs == LTGW_ERR_NOMEM && job.retries < kMaxRetries && (running > 0 || job.footprint < budget)) {
+      // most the budget: then it runs alone).  Alone, the idle slots' retained
+      // workspace may be what was missing: they release it (their threads are
+      // waiting for work, their contexts unused), and the request runs alone
+      // once more.  Failing after that, it fails.
+      if (rs == LTGW_ERR_NOMEM && job.retries < kMaxRetries && !(job.alone && job.after_trim)) {
         job.retries++;
-        job.footprint = std::min(budget, 2 * job.footprint);
+        if (job.alone) {
+          for (auto &o : slots)
+            if (o.get() != slot && !o->has_job && !busy_slot(o.get()) && o->ctx && o->retained) {
+              ltgw_trim(o->ctx);
+              retained -= o->retained;
+              o->retained = 0;
+            }
+          job.after_trim = true;
+          job.footprint = budget;
+        } else {
+          job.footprint = std::min(budget, 2 * job.footprint);
+        }
         job.bypassed = kMaxBypass;   // nothing passes it again
         queue.push_front(job);
         dispatch_locked();
@@ -176,6 +200,7 @@ struct ltgw_server {
       dispatch_locked();
       cv_done.notify_all();
     }
+    slot->ctx = nullptr;   // no other thread reaches the context from here on
     lock.unlock();
     if (stream) cudaStreamDestroy(stream);
     if (ctx) ltgw_destroy(ctx);
@@ -200,21 +225,26 @@ size_t ltgw_request_footprint(const ltgw_params *p, int n_tgt) {
   d += n_tau * N * N + 2 * n_om * N * N;                       // Laplace moments, Pi, C
   d += n_om * (N * N + 128 * N + 4096);                        // screening sweep scratch
   d += T * N * n_orb + n_om * T * n_orb;                       // projected targets, W
-  if (p->precision != LTGW_FP64) {
+  // the tensor-core partial tiles (FP32, one 128 x 128 tile per split), the
+  // largest of the contractions: the metric (lower tiles, up to 64 splits of
+  // the pairs), the projection (every tile, n_aux / 2048 splits) and the Pi
+  // build (lower tiles x scales, 64 splits per block of pairs)
+  auto cdiv = [](size_t a, size_t b) { return (a + b - 1) / b; };
+  const size_t nI = cdiv(n_aux, 128), nN = cdiv(N, 128), t = n_tau ? n_tau : n_om;
+  const size_t tile = 128 * 128 / 2;   // doubles per FP32 tile
+  const size_t k_part = nI * (nI + 1) / 2 * std::min<size_t>(64, cdiv(n_ov, 2048)) * tile;
+  const size_t p_part = nN * cdiv(n_ov, 128) * cdiv(n_aux, 2048) * tile;
+  const size_t pi_part = nN * (nN + 1) / 2 * t * std::min<size_t>(64, cdiv(n_ov, 2048)) * tile;
+  const size_t partials = std::max(k_part, std::max(p_part, pi_part));
+  if (p->precision == LTGW_FP64_EMU) {
+    // projected ov block; the largest slice set (6 slices: 4 bytes per A digit,
+    // 2 per B digit, of the metric's n_aux x n_ov operands) and the partials
+    d += N * n_ov + 9 * n_aux * n_ov / 2 + partials;
+  } else if (p->precision != LTGW_FP64) {
     d += (2 * n_aux * n_ov + N * n_ov) / 2 + n_om * N * N / 2;  // FP32 copies, BF16 hi / lo of the ov block
     if (p->precision == LTGW_FP8 || p->precision == LTGW_FP8_PI)
       d += 3 * ((n_tau ? n_tau : n_om) + 1) * N * n_ov / 8;     // FP8 codes (two-term: 3 per value)
-    // the tensor-core partial tiles (FP32, one 128 x 128 tile per split), the
-    // largest of the contractions: the metric (lower tiles, up to 64 splits of
-    // the pairs), the projection (every tile, n_aux / 2048 splits) and the
-    // Pi build (lower tiles x scales, 64 splits per block of pairs)
-    auto cdiv = [](size_t a, size_t b) { return (a + b - 1) / b; };
-    const size_t nI = cdiv(n_aux, 128), nN = cdiv(N, 128), t = n_tau ? n_tau : n_om;
-    const size_t tile = 128 * 128 / 2;   // doubles per FP32 tile
-    const size_t k_part = nI * (nI + 1) / 2 * std::min<size_t>(64, cdiv(n_ov, 2048)) * tile;
-    const size_t p_part = nN * cdiv(n_ov, 128) * cdiv(n_aux, 2048) * tile;
-    const size_t pi_part = nN * (nN + 1) / 2 * t * std::min<size_t>(64, cdiv(n_ov, 2048)) * tile;
-    d += std::max(k_part, std::max(p_part, pi_part));
+    d += partials;
   } else {
     d += N * n_ov;                                              // projected ov block
   }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libltgw.so")
 LTGW_OK, LTGW_ERR_BAD_ARG, LTGW_ERR_NOMEM, LTGW_ERR_NOT_SPD = 0, 1, 2, 3
 LTGW_ERR_NO_CONVERGE, LTGW_ERR_DEVICE, LTGW_ERR_EIG, LTGW_ERR_NO_NAF = 4, 5, 6, 7
 LTGW_ERR_TIMEOUT = 8
-LTGW_FP64, LTGW_BF16X3, LTGW_FP8, LTGW_FP8_PI = 0, 1, 2, 3
+LTGW_FP64, LTGW_BF16X3, LTGW_FP8, LTGW_FP8_PI, LTGW_FP64_EMU = 0, 1, 2, 3, 4
 
 
 class Params(ctypes.Structure):
@@ -466,12 +466,12 @@ def make_params(n_occ, n_virt, n_aux, n_frozen=0, n_omega=32, n_tau=8, omega0=0.
 
 
 def solve_problem(ctx: Context, prob, n_omega=32, n_tau=8, naf_thresh=-1.0, use_laplace=False, spin=2,
-                  omega0=0.5, tau=None, device_arrays=None, stream=None):
+                  omega0=0.5, tau=None, device_arrays=None, stream=None, precision=LTGW_FP64):
     """Solve a synthetic ``Problem`` (host numpy arrays) and return
     (sigma [T][n_omega] complex, e_qp [T], status [T]).  ``device_arrays``,
     if given, is a dict of torch CUDA tensors used instead of the host inputs."""
     p = make_params(prob.n_occ, prob.n_virt, prob.n_aux, prob.n_frozen, n_omega, n_tau, omega0, naf_thresh,
-                    spin, use_laplace)
+                    spin, use_laplace, precision)
     T = len(prob.targets)
     sig = np.zeros((T, n_omega, 2))
     e = np.zeros(T)

@@ -145,3 +145,69 @@ def test_emulated_polarizability(ctx, N, P, n_om, laplace):
     print(f"emulated Pi N={N} P={P} laplace={laplace}: vs oracle slices {e_or:.2e}, vs FP64 Pi {e_ex:.2e}")
     assert e_or <= (1e-12 if laplace else 1e-13)
     assert e_ex <= 1e-11
+
+
+# ---------------------------------------------------------------- whole solve
+# LTGW_FP64_EMU: the FP64 form with the NAF metric, the projections, Pi and
+# W_nm from 6 slices; against the plain FP64 oracle with the FP64 form's bars
+# (quasi-particle energies within 1e-8 Ha, the same N_NAF) and Sigma(i w)
+# within 1e-10 of its largest magnitude (the slices' 2^-42 relative errors
+# in Pi, K and the projections, against the FP64 form's rounding)
+EMU_SIG_TOL = 1e-10
+
+
+def _emu_cases():
+    tau6 = O.sinc_laplace_grid(6, -9.0, 2.0)
+    tau9 = O.sinc_laplace_grid(9, -11.0, 2.5)
+    tau8 = O.sinc_laplace_grid(8, -12.0, 3.0)
+    return {
+        "tiny_direct": (lambda: S.make_workload(S.TINY), 24, -1.0, None, 2),
+        "tiny_laplace": (lambda: S.make_workload(S.TINY), 24, -1.0, tau6, 2),
+        "ragged_frozen_naf_spin1": (lambda: S.make_problem(7, 45, 131, n_frozen=2, seed=4242, n_targets=4), 21,
+                                    1e-3, None, 1),
+        "ragged_laplace_naf": (lambda: S.make_problem(9, 70, 150, n_frozen=1, seed=99, n_targets=3), 17, 5e-3,
+                               tau9, 2),
+        "single_active_occupied": (lambda: S.make_problem(3, 30, 20, n_frozen=2, seed=7, n_targets=2), 16, -1.0,
+                                   None, 2),
+        "mid_laplace": (lambda: S.make_workload(S.MID), 32, 1e-2, tau8, 2),
+    }
+
+
+@pytest.mark.parametrize("case", list(_emu_cases()))
+def test_emulated_solve_matches_oracle(ctx, case):
+    from paper_2307_04508_gb300 import ltgw
+    make, n_om, thr, tau, spin = _emu_cases()[case]
+    prob = make()
+    tx, tw = (None, None) if tau is None else tau
+    sig_o, e_o, st_o, it = O.solve(prob.eps, prob.B_ov, prob.B_tgt, prob.targets, prob.shift, prob.n_occ,
+                                   prob.n_virt, prob.n_frozen, n_omega=n_om, naf_thresh=thr, spin=spin, tau_x=tx,
+                                   tau_w=tw, return_all=True)
+    sig, e, st = ltgw.solve_problem(ctx, prob, n_omega=n_om, n_tau=0 if tau is None else len(tau[0]),
+                                    naf_thresh=thr, use_laplace=tau is not None, spin=spin, tau=tau,
+                                    precision=ltgw.LTGW_FP64_EMU)
+    stats = ctx.stats()
+    print(f"emulated solve {case}: QP {np.abs(e - e_o).max():.2e} Ha, "
+          f"Sigma {np.abs(sig - sig_o).max() / np.abs(sig_o).max():.2e}, {stats['ms_total']:.1f} ms")
+    assert np.all(st == 0) and np.all(st_o == 0)
+    assert stats["n_naf"] == it["n_naf"]
+    assert np.abs(e - e_o).max() <= 1e-8
+    assert np.abs(sig - sig_o).max() <= EMU_SIG_TOL * np.abs(sig_o).max()
+
+
+def test_emulated_solve_imaginary_time(ctx):
+    """The imaginary-time form (factors e^{-Delta tau_k}, fitted gamma) in the
+    emulated form against the oracle's."""
+    from paper_2307_04508_gb300 import ltgw
+    prob = S.make_problem(9, 70, 150, n_frozen=1, seed=99, n_targets=3)
+    eps, n_occ, nf = prob.eps, prob.n_occ, prob.n_frozen
+    om, _ = O.gl_grid(17, 0.5)
+    tau, gamma, _ = O.cosine_grid(12, eps[n_occ] - eps[n_occ - 1], eps[-1] - eps[nf], om)
+    _, e_o, st_o = O.solve(prob.eps, prob.B_ov, prob.B_tgt, prob.targets, prob.shift, n_occ, prob.n_virt, nf,
+                           n_omega=17, naf_thresh=5e-3, cos_tau=tau, cos_gamma=gamma)
+    p = ltgw.make_params(n_occ, prob.n_virt, prob.n_aux, nf, 17, 12, 0.5, 5e-3, 2, 2, ltgw.LTGW_FP64_EMU)
+    T = len(prob.targets)
+    sig, e, st = np.zeros((T, 17, 2)), np.zeros(T), np.zeros(T, dtype=np.int32)
+    ctx.solve(p, prob.eps, prob.B_ov, prob.B_tgt, prob.targets.astype(np.int32), prob.shift, sig, e, st,
+              tau_x=np.ascontiguousarray(tau), tau_w=np.ascontiguousarray(gamma))
+    assert np.all(st == 0) and np.all(st_o == 0)
+    assert np.abs(e - e_o).max() <= 1e-8

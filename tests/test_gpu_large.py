@@ -12,7 +12,8 @@ checked on one sampled block, far below every tolerance below.
 Tolerances: the FP64 form against the oracle mode for mode (Laplace form with
 the stored grid on both sides, Sec. 2 Eq. LT): quasi-particle energies within
 1e-8 Ha, Sigma(i w) within 1e-11 of its largest magnitude, the same number of
-natural auxiliary functions.  The mixed forms (library Laplace grid, split
+natural auxiliary functions; the emulated FP64 form (contractions from 6
+integer slices) the same with Sigma within 1e-10.  The mixed forms (library Laplace grid, split
 BF16 or FP8 contractions) against the oracle's direct AC-GW form (Eq. Pi, no
 Laplace transform): within 1 meV per state.
 """
@@ -91,16 +92,21 @@ def test_device_law_matches_host_law(large, gold):
     assert np.abs(dev - host).max() <= 1e-12 * np.abs(host).max()
 
 
-def test_fp64_form_matches_oracle(large, gold):
+# LTGW_FP64 and LTGW_FP64_EMU (the contractions from integer slices, Sigma to
+# the slices' 2^-42 relative errors)
+@pytest.mark.parametrize("precision,sig_tol", [(0, SIG_TOL), (4, 1e-10)])
+def test_fp64_form_matches_oracle(large, gold, precision, sig_tol):
     """Laplace form with the stored grid on both sides (reading c-1)."""
     lt = gold["laplace"]
-    sig, e, st, stats = _solve(large, 0, tau=(np.array(lt["tau_x"]), np.array(lt["tau_w"])))
-    assert stats["n_naf"] == gold["n_naf"]
-    assert np.all(st == 0) and lt["status"] == [0] * len(st)
+    sig, e, st, stats = _solve(large, precision, tau=(np.array(lt["tau_x"]), np.array(lt["tau_w"])))
     e_o = np.array(lt["e_qp"])
     sig_o = np.array(lt["sigma_re"]) + 1j * np.array(lt["sigma_im"])
+    print(f"large precision {precision}: QP {np.abs(e - e_o).max():.2e} Ha, "
+          f"Sigma {np.abs(sig - sig_o).max() / np.abs(sig_o).max():.2e}, {stats['ms_total'] / 1e3:.1f} s")
+    assert stats["n_naf"] == gold["n_naf"]
+    assert np.all(st == 0) and lt["status"] == [0] * len(st)
     assert np.abs(e - e_o).max() <= QP_TOL, np.abs(e - e_o).max()
-    assert np.abs(sig - sig_o).max() <= SIG_TOL * np.abs(sig_o).max()
+    assert np.abs(sig - sig_o).max() <= sig_tol * np.abs(sig_o).max()
 
 
 @pytest.mark.parametrize("precision", [1, 2, 3])   # LTGW_BF16X3, LTGW_FP8, LTGW_FP8_PI
