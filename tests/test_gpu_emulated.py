@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import ltgw_oracle as O
+from paper_2307_04508_gb300 import synthetic as S
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
