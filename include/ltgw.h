@@ -328,7 +328,7 @@ ltgw_status ltgw_polarizability_fp8(ltgw_ctx *ctx, int N, int64_t n_pairs, const
  * Delta^2), or w_t Delta exp(-Delta^2 x_t); each operation rounded once)
  * scale R~'s columns (one FP64 product per entry), and M_t = (R~ diag(f_t))
  * R~^T is formed as in ltgw_gemm_emulated with n_slices slices (lower tiles,
- * mirrored; pairs in chunks of 131072, each sliced on its own, their products
+ * mirrored; pairs in equal chunks of at most 131072, each sliced on its own, their products
  * added); the direct form writes Pi_j = -2 s M_j, the Laplace form
  * recombines -2 s sum_m exp(-w_j^2 x_m) M^m in FP64.  Relative error about
  * 2^(-7 n_slices) of the largest row products (n_slices = 6: about 1e-12 in
@@ -354,7 +354,7 @@ ltgw_status ltgw_screen(ltgw_ctx *ctx, int N, int n_omega, const double *Pi, dou
  * a_1 .. a_s (|a_1| <= 128, |a_i| <= 64 after it); then
  * C = sum over digit pairs with i + j <= s + 1 of 2^(-7(i+j)) a_i b_j^T,
  * times 2^(e_A + e_B).  Every pair's integer products are exact in BF16 and
- * summed exactly (FP32 drains of at most 1024 pairs, FP64 after), so the only
+ * summed exactly (FP32 sums below 2^24 per drain, FP64 after), so the only
  * errors are the dropped digits: about 2^(-7s) of the rows' largest
  * magnitudes (s = 6: about 1e-12 relative Frobenius on products of Gaussian
  * rows).  A [m][lda], B [n][ldb] (k columns used), C [m][ldc]: device, row

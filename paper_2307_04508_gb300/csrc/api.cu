@@ -598,8 +598,9 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
 // (launch_slice_rows); the product sums 2^(-7(i+j)) a_i b_j^T over the digit
 // pairs with i + j <= s + 1, every pair on the split-BF16 kernel (A digits in
 // FP32 give hi = digit, lo = 0; B digits in the hi operand, zeros in the lo
-// one), so its integer products are exact and its FP32 sums too (drains of
-// at most 1024 pairs: |sum| <= 1024 * 128 * 128 = 2^24); the pair results
+// one), so its integer products are exact and its FP32 sums too (|sum| <=
+// 2^24: drains of 1024 pairs for the leading digits, |a_1 b_1| <= 2^14, and
+// 2048 for the others, |a_i b_j| <= 2^13); the pair results
 // are added in FP64 in the reduction, then scaled by 2^(e_A + e_B).  Two of
 // the kernel's three products per step multiply zeros here: the price of
 // reusing the split-BF16 kernel unchanged.
@@ -669,7 +670,10 @@ ltgw_status emu_pairs(ltgw_ctx *ctx, EmuPlan &p, double post, double *C, int64_t
       g.A = p.dA + (int64_t)(i - 1) * p.stra; g.B = nullptr; g.scale = p.ones; g.Kp = p.Kp; g.n_t = 1;
       g.nt_group = 1;
       g.B_hi = p.dB + (int64_t)(j - 1) * p.strb; g.B_lo = p.zeros; g.rows_a = p.Mpa; g.rows_b = p.Mpb;
-      g.drain_k = 1024;   // |partial sums| <= 1024 * 2^14 = 2^24: exact in FP32
+      // FP32 sums of integers stay exact below 2^24: |a_1 b_1| <= 2^14 (1024
+      // pairs per drain), every other pair has a digit of at most 64 in
+      // magnitude, |a_i b_j| <= 2^13 (2048 pairs)
+      g.drain_k = (i == 1 && j == 1) ? 1024 : 2048;
       g.out_colmajor = p.lower ? 1 : 0;
       TcRun run;
       if (tc_run(ctx, ctx->a4, g, p.tiles, 0, &run, st) != LTGW_OK) return ctx->status();
@@ -727,7 +731,9 @@ ltgw_status polarizability_emu(ltgw_ctx *ctx, int N, int64_t n_pairs, const doub
   // pairs in chunks, so that the slices of one chunk are held at a time
   // (6 slices of FP32 A and BF16 B digits: 36 bytes per value); chunks after
   // the first are added (each chunk's product is exact to its own slices)
-  const int64_t chunk = std::min<int64_t>(n_pairs, (int64_t)1 << 17);
+  const int64_t max_chunk = (int64_t)1 << 17;
+  const int64_t n_chunks = (n_pairs + max_chunk - 1) / max_chunk;
+  const int64_t chunk = std::min(n_pairs, ((n_pairs + n_chunks - 1) / n_chunks + 63) / 64 * 64);   // balanced
   EmuPlan p;
   if (emu_prepare(ctx, N, N, chunk, n_slices, true, n_t, &p, s, n_pairs > chunk) != LTGW_OK) return ctx->status();
   ctx->mark(EV_PI0, s);
