@@ -796,8 +796,10 @@ def run_large(args):
 
 
 # DRAM bytes (read + write) per launch at the large workload, from the ncu
-# captures summarised in profiles/ (None until captured for the current kernels)
-LARGE_TRAFFIC = {}
+# captures summarised in profiles/ (None until captured for the current kernels):
+# the Householder reduction at N_aux = 9000, profiles/hh_fused_double_large.md
+# (dram__bytes_read.sum 1.835 TB + dram__bytes_write.sum 1.881 TB)
+LARGE_TRAFFIC = {("hh", "any"): 1.835e12 + 1.881e12}
 
 
 def run_sweep(args):
