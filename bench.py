@@ -237,14 +237,13 @@ def pi_roofline(prec, pi_flops, pi_ms, pk, src, traffic=None):
                 "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x max SM clock (recipe unit counts)",
                 "flops_per_launch": pi_flops, "ms_per_launch": pi_ms, "traffic": traffic}
     if prec == "fp64emu":
-        a = 63 * pi_flops / (pi_ms / 1e3) / 1e12
+        a = 21 * pi_flops / (pi_ms / 1e3) / 1e12
         return {"bound": "tensor", "kernel": "tc_tma_ts_kernel (Pi(tau_k) moments from integer slices: 21 digit "
-                                             "pairs x 3 BF16 products per useful product)",
+                                             "pairs, one BF16 product each)",
                 "achieved": a, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": a / pk["bf16_tflops"],
                 "peak_source": f"bf16_tflops (burst) of {src} MEASURED_PEAKS.json",
-                "flops_per_launch": 63 * pi_flops, "ms_per_launch": pi_ms, "traffic": traffic,
-                "note": "issued tensor flops (two of the three products per digit pair multiply zeros); the "
-                        "stage time includes the slicing and the FP64 pair sums"}
+                "flops_per_launch": 21 * pi_flops, "ms_per_launch": pi_ms, "traffic": traffic,
+                "note": "issued tensor flops; the stage time includes the slicing and the FP64 pair sums"}
     if prec in ("fp8", "fp8pi"):
         a = 3 * pi_flops / (pi_ms / 1e3) / 1e12
         peak = 2.0 * pk["bf16_tflops"]
@@ -521,7 +520,7 @@ def run_serving(args):
         print(json.dumps(line), flush=True)
 
 
-LARGE_DESC = ("large (config 2 shapes; config 3 is its mixed form): n_occ=320 (60 frozen), n_virt=3500, "
+LARGE_DESC = ("large: n_occ=320 (60 frozen), n_virt=3500, "
               "N_aux=9000, NAF 1e-2, N_omega=32, N_tau=10 (library minimax Laplace grid), 20 QP states, "
               "LT+NAF+FC, seed 20230712; RI tensor from the synthetic Philox law in FP64 (QR on the host, "
               "normals and loading GEMM on the device), held by the caller in 13 blocks of 20 occupied orbitals and streamed "
@@ -624,7 +623,7 @@ def cpu_oracle_sample(cfg, n_naf, frac=1.0, prep=None, L=None):
 
 
 def run_large(args):
-    """The large system (config 2 shapes; config 3 in the mixed forms), streamed
+    """The large system (FP64 form, or its mixed forms), streamed
     by occupied blocks from inputs resident in HBM.  `value`: solves/s of the
     chosen form; the plain FP64 form beside it (one solve); QP errors against
     the oracle's stored results; e2e through the same C ABI call with the
@@ -966,7 +965,7 @@ def run_emu(args):
     pairs = sum(1 for i in range(1, s + 1) for j in range(1, s + 1) if i + j <= s + 1)
     useful = float(N) * N * P * n_tau * 2.0 / 2.0   # N^2 P per moment (SYRK: half of 2 N^2 P)
     nI = (N + 127) // 128
-    issued = 2.0 * 3 * pairs * n_tau * (nI * (nI + 1) // 2) * 128 * 128 * ((P + 63) // 64 * 64)
+    issued = 2.0 * pairs * n_tau * (nI * (nI + 1) // 2) * 128 * 128 * ((P + 63) // 64 * 64)
     pk, _src = peaks()
     bf16 = pk["bf16_tflops"]
     line = {"metric": "Pi contraction, FP64-accurate forms (ms per call)", "n": N, "pairs": P, "n_tau": n_tau,
@@ -978,7 +977,7 @@ def run_emu(args):
             "emulated_issued_bf16_tflops": issued / (st["ms_pi_kernel"] / 1e3) / 1e12,
             "bf16_peak_tflops": bf16, "launches": st["kernel_launches"],
             "note": "useful = N^2 P per Laplace moment (the symmetric product); issued = the BF16 tensor work the "
-                    "slice form launches: 3 products per digit pair (two multiply zeros), padded lower tiles"}
+                    "slice form launches: one product per digit pair, padded lower tiles"}
     print(json.dumps(line), flush=True)
     ctx.close()
 

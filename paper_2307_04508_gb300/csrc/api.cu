@@ -383,7 +383,7 @@ ltgw_status tc_run(ltgw_ctx *ctx, Arena &ar, TcGemmArgs g, const std::vector<int
                    TcRun *run, cudaStream_t s) {
   const int n_tiles = (int)(tiles.size() / 2);
   if (g.out_mode == TC_OUT_COLDOT) g.drain_k = std::max<int64_t>(g.drain_k, (g.k_end ? g.k_end : g.Kp) - g.k_begin);
-  const int kind = g.A8 ? 2 : (g.B_hi ? 1 : 0);
+  const int kind = g.A8 ? 2 : (g.B_hi ? (g.single ? 3 : 1) : 0);
   TcPlan plan = tc_plan(ctx, g, n_tiles, g.nt_group, 0);
   std::vector<TcPlan> cands{plan};
   const ltgw_ctx::TcKey key{kind, n_tiles, g.n_t, g.out_mode, (g.k_end ? g.k_end : g.Kp) - g.k_begin, g.rows_a,
@@ -596,14 +596,12 @@ ltgw_status naf_metric_tc(ltgw_ctx *ctx, int n, int64_t n_pairs, const double *B
 // FP64-accurate products from integer slices on the tensor cores.  Each
 // operand row is cut into s balanced base-128 digits of its fixed-point form
 // (launch_slice_rows); the product sums 2^(-7(i+j)) a_i b_j^T over the digit
-// pairs with i + j <= s + 1, every pair on the split-BF16 kernel (A digits in
-// FP32 give hi = digit, lo = 0; B digits in the hi operand, zeros in the lo
-// one), so its integer products are exact and its FP32 sums too (|sum| <=
+// pairs with i + j <= s + 1, every pair on the split-BF16 kernel in its
+// one-product mode (A digits in FP32 convert to hi = digit exactly; B digits
+// are the hi operand), so its integer products are exact and its FP32 sums too (|sum| <=
 // 2^24: drains of 1024 pairs for the leading digits, |a_1 b_1| <= 2^14, and
 // 2048 for the others, |a_i b_j| <= 2^13); the pair results
-// are added in FP64 in the reduction, then scaled by 2^(e_A + e_B).  Two of
-// the kernel's three products per step multiply zeros here: the price of
-// reusing the split-BF16 kernel unchanged.
+// are added in FP64 in the reduction, then scaled by 2^(e_A + e_B).
 constexpr int kEmuSlices = 6;   // slices per operand row in the LTGW_FP64_EMU solve
 
 struct EmuPlan {
@@ -612,7 +610,7 @@ struct EmuPlan {
   bool lower = false;   // lower tiles of a square product, mirrored
   std::vector<int> tiles, tindex;
   float *dA = nullptr, *ones = nullptr;
-  __nv_bfloat16 *dB = nullptr, *zeros = nullptr;
+  __nv_bfloat16 *dB = nullptr;
   int *ea = nullptr, *eb = nullptr, *d_tindex = nullptr;
   double *factors = nullptr;   // n_factors x K FP64 column factors of A (optional)
   double *tmp = nullptr;       // m x n FP64 (optional): the unscaled sum when C accumulates
@@ -629,7 +627,6 @@ ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lowe
   auto layout = [&](Arena &Ar) {
     p->dA = Ar.take<float>((size_t)s * p->stra);
     p->dB = Ar.take<__nv_bfloat16>((size_t)s * p->strb);
-    p->zeros = Ar.take<__nv_bfloat16>((size_t)p->strb);
     p->ones = Ar.take<float>((size_t)p->Kp);
     p->ea = Ar.take<int>(p->Mpa);
     p->eb = Ar.take<int>(p->Mpb);
@@ -645,7 +642,6 @@ ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lowe
   // padding rows and columns stay zero: the slicing writes rows < m (n), k < K only
   LTGW_CUDA(ctx, cudaMemsetAsync(p->dA, 0, (size_t)s * p->stra * sizeof(float), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->dB, 0, (size_t)s * p->strb * sizeof(__nv_bfloat16), st));
-  LTGW_CUDA(ctx, cudaMemsetAsync(p->zeros, 0, (size_t)p->strb * sizeof(__nv_bfloat16), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->ea, 0, p->Mpa * sizeof(int), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->eb, 0, p->Mpb * sizeof(int), st));
   CHECK_LAUNCH(ctx, launch_scale_table(nullptr, p->Kp, p->Kp, 1, nullptr, nullptr, SCALE_NONE, p->ones, st), 1);
@@ -669,7 +665,8 @@ ltgw_status emu_pairs(ltgw_ctx *ctx, EmuPlan &p, double post, double *C, int64_t
       TcGemmArgs g;
       g.A = p.dA + (int64_t)(i - 1) * p.stra; g.B = nullptr; g.scale = p.ones; g.Kp = p.Kp; g.n_t = 1;
       g.nt_group = 1;
-      g.B_hi = p.dB + (int64_t)(j - 1) * p.strb; g.B_lo = p.zeros; g.rows_a = p.Mpa; g.rows_b = p.Mpb;
+      g.B_hi = p.dB + (int64_t)(j - 1) * p.strb; g.B_lo = nullptr; g.rows_a = p.Mpa; g.rows_b = p.Mpb;
+      g.single = 1;   // digits are exact in BF16: one product per step
       // FP32 sums of integers stay exact below 2^24: |a_1 b_1| <= 2^14 (1024
       // pairs per drain), every other pair has a digit of at most 64 in
       // magnitude, |a_i b_j| <= 2^13 (2048 pairs)

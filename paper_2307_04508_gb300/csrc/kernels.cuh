@@ -136,6 +136,9 @@ struct TcGemmArgs {
   // with nt_group = 1).
   const __nv_bfloat16 *B_hi = nullptr, *B_lo = nullptr;
   int64_t rows_a = 0, rows_b = 0;   // padded row counts of A and B (tensor-map extents)
+  // single: B is exact in BF16 (B_lo not given) and so is every A value (its
+  // lo part is zero): one product per step, A_hi B_hi (integer digit operands)
+  int single = 0;
   // FP8 E4M3 form (launch_tc_fp8_gemm): codes qa [n_t][rows_a][Kp], qb [rows_b][Kp] and
   // per-row de-scales ds_a [n_t][rows_a], ds_b [rows_b], applied in the epilogue.
   const uint8_t *A8 = nullptr, *B8 = nullptr;

@@ -313,6 +313,22 @@ __device__ __forceinline__ void mma_stage_ts(uint32_t d, uint32_t a, uint64_t bh
       : "memory");
 }
 
+// The same stage with one product per step, D += A_hi B_hi (operands exact in BF16).
+__device__ __forceinline__ void mma_stage_single(uint32_t d, uint32_t a, uint64_t bh, uint32_t acc0) {
+  asm volatile(
+      "{\n.reg .pred p;\n.reg .b32 a1, a2, a3;\n.reg .b64 h1, h2, h3;\n"
+      "setp.ne.b32 p, %3, 0;\n"
+      "add.u32 a1, %1, 8;\nadd.u32 a2, %1, 16;\nadd.u32 a3, %1, 24;\n"
+      "add.u64 h1, %2, 2;\nadd.u64 h2, %2, 4;\nadd.u64 h3, %2, 6;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %4, p;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], h1, %4, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], h2, %4, 1;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], h3, %4, 1;\n"
+      "}\n" ::"r"(d),
+      "r"(a), "l"(bh), "r"(acc0), "r"(IDESC)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
                "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
@@ -389,8 +405,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint64_t bh = db0 + (uint64_t)((ib * B_STAGE) >> 4);
-          mma_stage_ts(d, tmem + acol0 + (uint32_t)(ia * TK), bh, bh + (B_BYTES >> 4),
-                       c == dr * chunks_per_drain ? 0u : 1u);
+          if (g.single)
+            mma_stage_single(d, tmem + acol0 + (uint32_t)(ia * TK), bh, c == dr * chunks_per_drain ? 0u : 1u);
+          else
+            mma_stage_ts(d, tmem + acol0 + (uint32_t)(ia * TK), bh, bh + (B_BYTES >> 4),
+                         c == dr * chunks_per_drain ? 0u : 1u);
           mma_commit(&bars.a_empty[ia]);
           mma_commit(&bars.b_empty[ib]);
           for (ia += nt; ia >= nsa;) { ia -= nsa; pa ^= 1; }
@@ -422,9 +441,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         if (++jf == T3_SF) { jf = 0; pf ^= 1; }
         if (!mbar_wait(&bars.b_empty[jb], pb ^ 1, &bars.abort, g.err)) break;
         uint8_t *bs = sB + jb * B_STAGE;
-        mbar_expect_tx(&bars.b_full[jb], B_STAGE);
+        mbar_expect_tx(&bars.b_full[jb], g.single ? B_BYTES : B_STAGE);
         tma_load_2d(bs, &tmBhi, k0, tj * TN, &bars.b_full[jb]);
-        tma_load_2d(bs + B_BYTES, &tmBlo, k0, tj * TN, &bars.b_full[jb]);
+        if (!g.single) tma_load_2d(bs + B_BYTES, &tmBlo, k0, tj * TN, &bars.b_full[jb]);
         if (++jb == T3_SB) { jb = 0; pb ^= 1; }
       }
     }
@@ -472,7 +491,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t ta = tmem + lane_addr + acol0 + (uint32_t)(ia * TK + sub * 8);
         tmem_st8(ta, hi);
-        tmem_st8(ta + TK / 2, lo);
+        if (!g.single) tmem_st8(ta + TK / 2, lo);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
@@ -720,7 +739,7 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
   const int64_t k_len = (g.k_end ? g.k_end : g.Kp) - g.k_begin;
   if (g.k_begin < 0 || g.k_begin % TK || k_len <= 0 || g.k_begin + k_len > g.Kp) return cudaErrorInvalidValue;
   const int splits = (int)((k_len + g.k_per_split - 1) / g.k_per_split);
-  if (!g.B_hi || !g.B_lo) return cudaErrorInvalidValue;   // the kernel takes B pre-split
+  if (!g.B_hi || (!g.B_lo && !g.single)) return cudaErrorInvalidValue;   // the kernel takes B pre-split
   {
     if ((g.a_group_stride != 0 && g.a_group_stride != g.rows_a * g.Kp) ||
         (g.a_group_stride != 0 && g.nt_group != 1) || g.nt_group > T3_MAXT || g.rows_a < TM || g.rows_b < TN ||
@@ -732,7 +751,7 @@ cudaError_t launch_tc_split_gemm(const TcGemmArgs &g, int n_tiles, cudaStream_t 
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&tbh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_hi, g.Kp, g.rows_b, TK, TN,
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_2d(&tbl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.B_lo, g.Kp, g.rows_b, TK, TN,
+        !encode_2d(&tbl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.single ? g.B_hi : g.B_lo, g.Kp, g.rows_b, TK, TN,
                    CU_TENSOR_MAP_SWIZZLE_128B))
       return cudaErrorNotSupported;
     static std::once_flag once2;
