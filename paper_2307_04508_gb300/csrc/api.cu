@@ -639,7 +639,8 @@ ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lowe
   if (ctx->a5.commit() != cudaSuccess) { ctx->fail(LTGW_ERR_NOMEM, "slice operand allocation failed"); return ctx->status(); }
   layout(ctx->a5);
   if (lower) copy_in(ctx, p->d_tindex, p->tindex.data(), p->tindex.size() * sizeof(int), st);
-  // padding rows and columns stay zero: the slicing writes rows < m (n), k < K only
+  // padding rows (and, for column slicing, padding k) stay zero: the slicing
+  // writes rows < m (n) only; row slicing writes every k < Kp, column slicing k < K
   LTGW_CUDA(ctx, cudaMemsetAsync(p->dA, 0, (size_t)s * p->stra * sizeof(float), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->dB, 0, (size_t)s * p->strb * sizeof(__nv_bfloat16), st));
   LTGW_CUDA(ctx, cudaMemsetAsync(p->ea, 0, p->Mpa * sizeof(int), st));
@@ -650,8 +651,8 @@ ltgw_status emu_prepare(ltgw_ctx *ctx, int m, int n, int64_t K, int s, bool lowe
 
 // C = beta C + post * (sliced A) (sliced B)^T from the digits in p->dA / p->dB
 // and the exponents p->ea / p->eb.  C [m][ldc]; in the lower form C (ldc = n)
-// is written whole and symmetric.  post must be a power of two (or +-1, +-2,
-// +-4): it is folded into the exact 2^(-7L) factors.  beta != 0 needs p->tmp.
+// is written whole and symmetric.  post must be plus or minus a power of two:
+// it is folded into the exact 2^(-7L) factors.  beta != 0 needs p->tmp.
 ltgw_status emu_pairs(ltgw_ctx *ctx, EmuPlan &p, double post, double *C, int64_t ldc, double beta,
                       cudaStream_t st) {
   if (beta != 0.0 && !p.tmp) { ctx->fail(LTGW_ERR_BAD_ARG, "emulated accumulation without scratch"); return ctx->status(); }
@@ -696,7 +697,7 @@ ltgw_status emu_pairs(ltgw_ctx *ctx, EmuPlan &p, double post, double *C, int64_t
 ltgw_status emu_product(ltgw_ctx *ctx, EmuPlan &p, const double *A, int64_t lda, const double *colscale,
                         double post, double *C, int64_t ldc, cudaStream_t st, double beta = 0.0) {
   CHECK_LAUNCH(ctx, launch_slice_rows(A, lda, p.m, p.K, p.Kp, p.s, p.stra, p.dA, nullptr, p.ea, st, colscale), 1);
-  return emu_pairs(ctx, p, 1.0 * post, C, ldc, beta, st);
+  return emu_pairs(ctx, p, post, C, ldc, beta, st);
 }
 
 // C = beta C + A A^T (lower form): A sliced once into both operands.

@@ -63,3 +63,24 @@ def test_create_without_device_fails_cleanly(lib):
     with pytest.raises(ltgw.LtgwError) as e:
         ltgw.Context(0)
     assert e.value.status == ltgw.LTGW_ERR_DEVICE
+
+
+def test_request_footprint_host_estimate(lib):
+    """ltgw_request_footprint is host arithmetic: it covers the staged inputs,
+    grows with every size, and counts the extra operands of the tensor-core
+    forms (FP8 codes on top of the split-BF16 copies) and the emulated form's
+    slices on top of the FP64 form's arrays."""
+    from paper_2307_04508_gb300 import ltgw
+
+    def fp(n_occ=40, n_virt=400, n_aux=1320, prec=ltgw.LTGW_FP64, n_tgt=4, naf=1e-2):
+        p = ltgw.make_params(n_occ, n_virt, n_aux, n_occ // 6, 32, 8, 0.5, naf, 2, True, prec)
+        return ltgw.request_footprint(p, n_tgt)
+
+    base = fp()
+    assert base >= 1320 * 40 * 400 * 8
+    assert fp(n_occ=60) > base and fp(n_virt=500) > base and fp(n_aux=1500) > base and fp(n_tgt=8) > base
+    assert fp(naf=-1.0) > base   # without NAF every auxiliary function stays
+    assert fp(prec=ltgw.LTGW_FP8) > fp(prec=ltgw.LTGW_BF16X3)
+    assert fp(prec=ltgw.LTGW_FP64_EMU) > base
+    p = ltgw.make_params(40, 400, 1320, 6, 32, 8, 0.5, 1e-2, 2, True, 0)
+    assert ltgw.request_footprint(p, 0) == 0
