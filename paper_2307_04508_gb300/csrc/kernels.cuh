@@ -171,9 +171,6 @@ cudaError_t launch_slice_rows(const double *X, int64_t ld, int rows, int64_t col
 // node (SCALE_EXPTAU, p0 = tau), no fused operations.
 cudaError_t launch_pi_factor64(const double *delta, int64_t K, int n_t, const double *p0, const double *p1,
                                int mode, double *f, cudaStream_t st);
-// C[r][c] *= 2^(ea[r] + eb[c]).
-cudaError_t launch_scale_exp2(double *C, int64_t ldc, int rows, int cols, const int *ea, const int *eb,
-                              cudaStream_t st);
 // D[r][c] = beta D[r][c] + S[r][c] 2^(ea[r] + eb[c]) (rows <= 65535); lower (rows ==
 // cols, S symmetric): the entries c <= r scaled, each written to (r, c) and (c, r).
 cudaError_t launch_scale_exp2_to(const double *S, int64_t lds, double *D, int64_t ldd, int rows, int cols,

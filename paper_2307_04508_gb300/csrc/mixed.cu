@@ -620,11 +620,6 @@ cudaError_t launch_pi_factor64(const double *delta, int64_t K, int n_t, const do
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_exp2(double *C, int64_t ldc, int rows, int cols, const int *ea, const int *eb,
-                              cudaStream_t st) {
-  return launch_scale_exp2_to(C, ldc, C, ldc, rows, cols, ea, eb, 0.0, st);
-}
-
 cudaError_t launch_scale_exp2_to(const double *S, int64_t lds, double *D, int64_t ldd, int rows, int cols,
                                  const int *ea, const int *eb, double beta, cudaStream_t st, int lower) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
